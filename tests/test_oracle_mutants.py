@@ -1,0 +1,48 @@
+"""Plausible mistakes planted in copies of the oracle must each fail a pin.
+
+The mistakes are planted in edited copies of the oracle source compiled into
+a temporary directory, on the CPU; the real oracle is untouched.
+"""
+import pytest
+
+import oracle
+from tests import pins
+
+MUTANTS = {
+    # vertex rule threshold off by one (index < k-2 instead of < k-1)
+    "vertex_threshold": ("vertex_index(&g, elive, &s, v) < k - 1", "vertex_index(&g, elive, &s, v) < k - 2"),
+    # edge rule threshold off by one
+    "edge_threshold": ("edges[2 * e + 1]) < k - 2)", "edges[2 * e + 1]) < k - 3)"),
+    # common neighbour test dropped: counts every neighbour of v
+    "no_common_check": ("        if (s->nbr_mark[w] != s->stamp) continue;\n", ""),
+    # (Not listed: keeping the edges of a deleted vertex live.  That edit is
+    # equivalent: a vertex that misses a colour c makes each of its live
+    # edges miss c as a common-neighbour colour in the same sweep, so those
+    # edges fail the edge rule anyway; pin_incident_edges_fail checks this.)
+    # a dead edge still counts as a witness in the edge index
+    "dead_witness_edge": ("    for (int64_t i = g->off[v]; i < g->off[v + 1]; i++) {\n        if (!elive[g->eid[i]]) continue;\n        int32_t w = g->nbr[i];",
+                          "    for (int64_t i = g->off[v]; i < g->off[v + 1]; i++) {\n        int32_t w = g->nbr[i];"),
+    # the sweep index recorded one too late
+    "sweep_off_by_one": ("if (v_sweep) v_sweep[v] = (int32_t)sweeps;", "if (v_sweep) v_sweep[v] = (int32_t)sweeps + 1;"),
+    # Gauss-Seidel instead of Jacobi: vertices leave before the edge rule runs
+    "not_jacobi": ("            if (vlive[v] && vertex_index(&g, elive, &s, v) < k - 1) {\n                fail_v[v] = 1;",
+                   "            if (vlive[v] && vertex_index(&g, elive, &s, v) < k - 1) {\n                fail_v[v] = 1;\n                for (int64_t i = g.off[v]; i < g.off[v + 1]; i++) elive[g.eid[i]] = 0;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = oracle.source_text()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    path = oracle.compile_variant(src.replace(old, new), str(tmp_path / f"libmut_{name}.so"))
+    orc = oracle.Oracle(path)
+    failures = []
+    for pin in pins.ALL_PINS:
+        try:
+            msg = pin(orc)
+        except Exception as exc:  # a crash in the mutant also counts as caught
+            msg = f"raised {exc!r}"
+        if msg:
+            failures.append(f"{pin.__name__}: {msg}")
+    assert failures, f"mutant {name} passed every pin"
