@@ -1,0 +1,368 @@
+"""Benchmark of the colour-index kernelization hot path.
+
+One step = kernelize one graph to its fixpoint (every pass of the vertex and
+edge rules until nothing is deleted) from its loaded state.  The default
+workload is the dense random k-partite graph n=4096, k=20, p=0.92 with a
+planted 20-clique.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank kernelizes its own
+replica of the workload (independent problems: no data-path collective); the
+value is the sum over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD_DESC = {
+    "c1": "random k-partite n=300 k=10 p=0.7, planted 10-clique (uint64-bit dense input)",
+    "c2": "random k-partite n=4096 k=20 p=0.92, planted 20-clique (dense 0/1 input)",
+    "c5": "random k-partite n=32768 k=24 p=0.85, planted 24-clique (dense 0/1 input)",
+}
+METRIC = "edge-rule tests/s to fixpoint (time-to-fixpoint per graph)"
+UNIT = "edge tests/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC), default="c2")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU work budget of the oracle baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# ---------------------------------------------------------------------------
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def reduce_max(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() and pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() and pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def make_workload(name):
+    from paper_2212_00574_gb300 import synth
+    return synth.workload(name)
+
+
+def cpu_baseline(g, budget_s: float, session=None) -> dict:
+    """The oracle as it stands, single-threaded, on a bounded sample: the
+    edge-rule colour index of uniformly sampled edges of the same graph
+    (adjacency lists built once beforehand, as the GPU path loads once)."""
+    import oracle
+    edges = g.get_edges()
+    sess = session or oracle.Session(g.colour, edges, g.k)
+    rng = np.random.default_rng(7)
+    pilot = rng.choice(len(edges), size=min(len(edges), 500), replace=False).astype(np.int64)
+    t0 = time.perf_counter()
+    sess.edge_index(pilot)
+    per_edge = max((time.perf_counter() - t0) / max(len(pilot), 1), 1e-8)
+    size = int(min(len(edges), max(len(pilot), budget_s / per_edge)))
+    sample = rng.choice(len(edges), size=size, replace=False).astype(np.int64)
+    t0 = time.perf_counter()
+    sess.edge_index(sample)
+    dt = time.perf_counter() - t0
+    if session is None:
+        sess.close()
+    return {"value": size / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "seconds": round(dt, 3),
+            "sample": f"edge-rule colour index of {size} uniformly sampled edges of the same graph "
+                      f"(single-threaded C oracle; adjacency lists built once, untimed)"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args, world, rank, pg):
+    if rank != 0:
+        return 0
+    import oracle
+    g = make_workload(args.workload)
+    sess = oracle.Session(g.colour, g.get_edges(), g.k)
+    budget = min(max(60.0 / max(args.steps + args.warmup, 1), 0.01), 2.0)
+    per_step = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(g, budget, session=sess)
+        if i >= args.warmup:
+            per_step.append(cb)
+    sess.close()
+    value = statistics.median([c["value"] for c in per_step])
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * g.m / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC[args.workload], "n": g.n, "k": g.k, "m": g.m,
+                   "l2": "n/a (CPU)", "parallelism": "replicas"},
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
+                         "sample": per_step[0]["sample"] + " per step; ms_per_step extrapolates "
+                                   "the per-edge rate to all edges of one pass"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+
+    import paper_2212_00574_gb300 as kz
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    kz.use_torch_allocator()
+    g = make_workload(args.workload)
+    stream = torch.cuda.current_stream(dev)
+    bits = g.get_bits()
+    # pinned host copies of the inputs (for the end-to-end measurement)
+    pin_bits = torch.from_numpy(bits.view(np.int64)).pin_memory()
+    pin_col = torch.from_numpy(g.colour).pin_memory()
+    h_bits = pin_bits.numpy().view(np.uint64)
+    h_col = pin_col.numpy()
+
+    h = kz.kz_load_graph_dense(g.n, g.k, h_col, h_bits, stream=stream)
+    opts = kz.kz_default_options()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step(i, ev0=None, ev1=None):
+        kz.kz_reset(h, stream)
+        flush.fill_(i & 0xFF)
+        if ev0 is not None:
+            ev0.record(stream)
+        kz.kz_kernelize(h, opts, stream)
+        if ev1 is not None:
+            ev1.record(stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize(dev)
+    st = kz.kz_fetch_stats(h)
+    tests_per_step = st["edge_tests"]
+    passes = st["passes"]
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier(pg)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        step(i, *evs[i])
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    barrier(pg)
+    per_ms = [a.elapsed_time(b) for a, b in evs]
+    dev_ms = sum(per_ms)
+    st_end = kz.kz_fetch_stats(h)
+    assert st_end["edge_tests"] == tests_per_step and st_end["passes"] == passes
+
+    slowest_s = reduce_max(pg, dev_ms / 1e3)
+    total_tests = reduce_sum(pg, float(tests_per_step) * args.steps)
+    value = total_tests / slowest_s
+    ms_per_step = dev_ms / args.steps
+
+    # roofline of the dominant kernel (one sweep-kernel launch per pass)
+    k = g.k
+    launch_s = (dev_ms / args.steps) / passes / 1e3
+    alg_ops = tests_per_step / passes * max(k - 2, 0) * 2
+    probe_ops, _ = kz.kz_probe_int_throughput(0, stream)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_derived = sms * 64 * 2.070e9  # 64 INT32 lanes per SM at the maximum SM clock
+    achieved = alg_ops / launch_s
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_derived / 1e12, "unit": "Tops/s",
+                "frac": achieved / peak_derived, "traffic": None,
+                "kernel": "bitset_sweep_kernel",
+                "probe_lop3_tops": probe_ops / 1e12,
+                "ops_per_launch": alg_ops,
+                "note": "ops = live edges tested x (k-2) class words x (AND + zero test); launch time "
+                        "from CUDA events around the whole kernelize call divided by passes"}
+
+    # end-to-end through the C ABI: host buffers in, host buffers out
+    e2e = None
+    if args.e2e_steps > 0:
+        out_bits = torch.empty((g.n, bits.shape[1]), dtype=torch.int64).pin_memory().numpy().view(np.uint64)
+        out_alive = torch.empty(g.n, dtype=torch.uint8).pin_memory().numpy()
+        times = []
+        for i in range(args.e2e_steps + 2):
+            flush.fill_(i & 0xFF)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            hh = kz.kz_load_graph_dense(g.n, g.k, h_col, h_bits, stream=stream)
+            kz.kz_kernelize(hh, opts, stream)
+            kz.kz_fetch_kernel_dense(hh, g.n, out_bits=out_bits, out_alive=out_alive)
+            kz.kz_free_graph(hh)
+            dt = time.perf_counter() - t0
+            if i >= 2:
+                times.append(dt)
+        assert np.array_equal(out_bits, bits)
+        e2e_s = statistics.median(times)
+        e2e = {"value": tests_per_step * world / reduce_max(pg, e2e_s),
+               "unit": UNIT, "h2d_bytes_per_step": int(h_bits.nbytes + h_col.nbytes),
+               "d2h_bytes_per_step": int(out_bits.nbytes + out_alive.nbytes),
+               "ms_per_step": 1e3 * e2e_s,
+               "calls": "kz_load_graph_dense + kz_kernelize + kz_fetch_kernel_dense + kz_free_graph"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(g, args.cpu_seconds)
+    kz.kz_free_graph(h)
+
+    launches_per_step = 2 + passes  # reset-state kernel, run-start kernel, one sweep kernel per pass
+    if rank == 0:
+        tt = sorted(per_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC[args.workload], "n": g.n, "k": g.k, "m": g.m,
+                       "path": "bitset", "passes": passes, "sweeps": st["sweeps"],
+                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); per-step CUDA events "
+                             "around kz_kernelize only",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "time_to_fixpoint_us": {"median": 1e3 * tt[len(tt) // 2], "p10": 1e3 * tt[len(tt) // 10],
+                                    "p90": 1e3 * tt[(9 * len(tt)) // 10]},
+            "wall_s_timed_region": t_wall,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_init()
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank, pg)
+        return run_ours(args, world, rank, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

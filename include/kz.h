@@ -1,0 +1,225 @@
+/*
+ * kz.h -- C ABI of the GB300 colour-index kernelization library (libkz.so).
+ *
+ * The library computes the kernel of a legally k-coloured graph under the two
+ * colour-index rules of the thesis "Kernelization of Discrete Optimization
+ * Problems on Parallel Architectures" (arXiv 2212.00574), Section 4.2:
+ *
+ *   - Definition 4.2.1: the graph is legally coloured with k colours, the
+ *     colour classes being c_1..c_k (0..k-1 here).
+ *   - Vertex rule (colour index of a node, and the remark after it): a vertex
+ *     whose neighbours cover fewer than k-1 colour classes lies in no k-clique
+ *     and is deleted.
+ *   - Edge rule (colour index of an edge, and the remark after it): an edge
+ *     {u,v} whose common neighbours cover fewer than k-2 colour classes lies
+ *     in no k-clique and is deleted; u and v are kept.
+ *
+ * The rules are applied to the live graph, sweep after sweep, until neither
+ * fires.  Each sweep is a Jacobi sweep: both rules read the same snapshot and
+ * their deletions are applied together.  The result is the unique greatest
+ * subgraph closed under both rules, so no k-clique is ever lost.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns a kz_status and never aborts, traps or exits.
+ *   - `void* stream` is a cudaStream_t on the current device (NULL = the
+ *     legacy default stream).  Work is enqueued on it; the calls marked
+ *     "synchronous" wait for it.
+ *   - Host pointers stay owned by the caller and are not retained after the
+ *     call returns.  A kz_graph owns all the device memory it uses; it is
+ *     allocated at load through the registered allocator (kz_set_allocator)
+ *     or cudaMallocAsync, and released by kz_free_graph.
+ *   - Vertex ids at the boundary are the caller's ids 0..n-1.  Internally the
+ *     library relabels vertices so that every colour class is contiguous.
+ *   - There is no CPU fallback: without a usable CUDA device the calls that
+ *     need one return KZ_ERR_CUDA.
+ *   - Asynchronous failures (sweep limit, a bounds check in a kernel) are
+ *     recorded on the device and reported by the next synchronous call on the
+ *     same graph (kz_fetch_kernel, kz_fetch_kernel_dense, kz_fetch_stats).
+ */
+#ifndef KZ_H
+#define KZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kz_graph_s *kz_graph; /* opaque handle */
+
+typedef enum {
+    KZ_OK = 0,
+    KZ_ERR_ARG = 1,                /* null pointer, negative size, k outside [1, 64], bad option */
+    KZ_ERR_COLOUR_RANGE = 2,       /* a colour outside [0, k) */
+    KZ_ERR_ILLEGAL_COLOURING = 3,  /* an edge joins two vertices of one colour (Definition 4.2.1) */
+    KZ_ERR_SELF_LOOP = 4,          /* an edge {v, v} */
+    KZ_ERR_VERTEX_RANGE = 5,       /* an endpoint outside [0, n) */
+    KZ_ERR_DUPLICATE_EDGE = 6,     /* an edge given twice (either orientation) without KZ_DEDUP */
+    KZ_ERR_OOM = 7,                /* device allocation failed */
+    KZ_ERR_CUDA = 8,               /* a CUDA runtime call failed (no device, launch failure, ...) */
+    KZ_ERR_LIMIT = 9,              /* max_sweeps productive sweeps ran and a rule still fired */
+    KZ_ERR_TIMEOUT = 10,           /* a bounded device wait gave up */
+    KZ_ERR_NOT_READY = 11,         /* fetch before any kz_kernelize on this graph */
+    KZ_ERR_BUFFER = 12,            /* output capacity too small (the needed size is still reported) */
+    KZ_ERR_UNSUPPORTED = 13,       /* the requested path cannot hold this graph */
+    KZ_ERR_INTERNAL = 14           /* a kernel's own consistency check failed */
+} kz_status;
+
+/* kz_load_graph / kz_load_graph_dense flags */
+#define KZ_DEDUP 0x1u /* merge duplicate and reversed edge pairs instead of failing */
+
+/* Which kernels evaluate the rules (kz_options.path). */
+typedef enum {
+    KZ_PATH_AUTO = 0,   /* chosen by the library's cost model */
+    KZ_PATH_BITSET = 1, /* per-colour bitset rows in HBM, warp-per-block-pair sweep kernel */
+    KZ_PATH_SMALL = 2,  /* whole fixpoint inside one CTA, graph held in shared memory */
+    KZ_PATH_SPARSE = 3, /* CSR adjacency, per-edge colour masks from triangle enumeration */
+    KZ_PATH_TENSOR = 4  /* per-colour common-neighbour counts on tcgen05 tensor cores */
+} kz_path;
+
+/* Order in which elements are tested (kz_options.schedule).  Neither changes
+ * the result: the greatest fixpoint of monotone deletion rules is unique. */
+typedef enum {
+    KZ_SCHED_PLAIN = 0,   /* Jacobi sweeps over every live element */
+    KZ_SCHED_LEARNED = 1  /* MLP-ranked worklist, then a full certifying sweep */
+} kz_schedule;
+
+typedef struct {
+    int32_t path;         /* kz_path */
+    int32_t schedule;     /* kz_schedule */
+    int64_t max_sweeps;   /* productive sweeps allowed; <= 0 means n + m + 1 (always enough) */
+    int32_t use_graph;    /* 1 (default): device-side sweep loop in a CUDA graph; 0: host-driven loop */
+    int32_t reserved[9];  /* must be zero */
+} kz_options;
+
+/* Fill *opt with the defaults (AUTO path, PLAIN schedule, no sweep limit,
+ * CUDA-graph loop). */
+void kz_default_options(kz_options *opt);
+
+typedef struct {
+    int64_t n, m;          /* input vertices and edges (after KZ_DEDUP merging) */
+    int64_t n_live;        /* vertices in the kernel */
+    int64_t m_live;        /* edges in the kernel */
+    int64_t sweeps;        /* productive Jacobi sweeps of the last kz_kernelize */
+    int64_t passes;        /* rule evaluations over the whole graph, the certifying one included */
+    int64_t edge_tests;    /* live edges tested, summed over passes */
+    int32_t path;          /* kz_path that ran */
+    int32_t status;        /* kz_status recorded on the device by the last kz_kernelize */
+    int32_t k;             /* colours */
+    int32_t reserved[5];
+} kz_stats;
+
+/* Optional device allocator (for example a caching allocator owned by the
+ * caller).  alloc returns NULL on failure; both are called on the host with
+ * the stream the allocation is used on.  Passing NULL restores
+ * cudaMallocAsync / cudaFreeAsync.  Applies to graphs loaded afterwards. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *ctx);
+    void *ctx;
+} kz_allocator;
+
+kz_status kz_set_allocator(const kz_allocator *allocator);
+
+/*
+ * Load a graph given as an edge list (synchronous).
+ *   n       vertices (ids 0..n-1), n >= 0
+ *   k       colours, 1 <= k <= 64; the clique size searched for is also k
+ *           (Definition 4.2.1 uses one k for both)
+ *   colour  host int32[n], colour[v] in [0, k); must be a legal colouring
+ *   m       number of edges, m >= 0
+ *   edges   host int32[2*m]: pairs (u, v), any orientation
+ *   flags   KZ_DEDUP or 0
+ *   stream  stream for the copies and the packing kernels
+ *   out     receives the handle (NULL on failure)
+ * Input errors (KZ_ERR_COLOUR_RANGE, _VERTEX_RANGE, _SELF_LOOP,
+ * _ILLEGAL_COLOURING, _ARG) are found on the host before any CUDA call;
+ * duplicates are found on the device during packing.
+ */
+kz_status kz_load_graph(int32_t n, int32_t k, const int32_t *colour, int64_t m,
+                        const int32_t *edges, uint32_t flags, void *stream, kz_graph *out);
+
+/*
+ * Load a graph given as a dense adjacency bit matrix (synchronous).
+ *   adj_bits   host uint64[n * row_words], row-major; bit (j % 64) of word
+ *              (j / 64) in row i is set iff {i, j} is an edge.  Only bits with
+ *              j > i are read: the diagonal and the lower triangle are ignored,
+ *              so the matrix need not be symmetric.  Bits j >= n are ignored.
+ *   row_words  words per row, >= ceil(n / 64)
+ * Other arguments as kz_load_graph.  An upper-triangle bit joining two
+ * vertices of one colour gives KZ_ERR_ILLEGAL_COLOURING.
+ */
+kz_status kz_load_graph_dense(int32_t n, int32_t k, const int32_t *colour,
+                              const uint64_t *adj_bits, int64_t row_words, uint32_t flags,
+                              void *stream, kz_graph *out);
+
+/*
+ * Run the rules to their fixpoint, starting from the graph's current live
+ * state (as loaded, as left by an earlier kz_kernelize, or as restored by
+ * kz_reset).  Asynchronous: enqueued on `stream`.  opt may be NULL (defaults).
+ * The per-run counters (sweeps, passes, edge_tests, status) restart at zero.
+ */
+kz_status kz_kernelize(kz_graph g, const kz_options *opt, void *stream);
+
+/*
+ * Kernelize `count` graphs with one persistent launch (asynchronous).  Every
+ * graph ends exactly as kz_kernelize would leave it.  opt as kz_kernelize;
+ * opt->path selects the per-graph path (AUTO lets the autotuner choose).
+ */
+kz_status kz_kernelize_batch(kz_graph *graphs, int32_t count, const kz_options *opt, void *stream);
+
+/*
+ * Copy the kernel back (synchronous: waits for the graph's last stream).
+ *   vertex_alive  host uint8[n] (may be NULL): 1 if the vertex survives
+ *   edges_out     host int32[2*cap] (may be NULL when cap == 0): surviving
+ *                 edges as (u, v) with u < v in caller ids, sorted
+ *                 lexicographically
+ *   cap           capacity of edges_out in edges
+ *   m_out         receives the number of surviving edges (always written,
+ *                 also when KZ_ERR_BUFFER is returned)
+ *   stats         may be NULL
+ * Returns the device status of the last kz_kernelize if it is not KZ_OK
+ * (for example KZ_ERR_LIMIT; the partial kernel is still copied).
+ */
+kz_status kz_fetch_kernel(kz_graph g, uint8_t *vertex_alive, int32_t *edges_out, int64_t cap,
+                          int64_t *m_out, kz_stats *stats);
+
+/*
+ * Copy the kernel back as a symmetric dense bit matrix in caller ids
+ * (synchronous).  adj_bits host uint64[n * row_words], fully overwritten;
+ * row_words >= ceil(n / 64).  vertex_alive and stats as kz_fetch_kernel.
+ */
+kz_status kz_fetch_kernel_dense(kz_graph g, uint8_t *vertex_alive, uint64_t *adj_bits,
+                                int64_t row_words, kz_stats *stats);
+
+/* Statistics only (synchronous, copies no kernel). */
+kz_status kz_fetch_stats(kz_graph g, kz_stats *stats);
+
+/*
+ * Per-sweep trace of the last kz_kernelize (synchronous).
+ *   dv, de   host int64[cap]: vertices / edges that failed their rule in each
+ *            productive sweep (entries beyond `sweeps` are not written)
+ *   v_sweep  host int32[n] (may be NULL): productive sweep (1-based) in which
+ *            each caller vertex was deleted, 0 if it survives
+ */
+kz_status kz_fetch_trace(kz_graph g, int64_t *dv, int64_t *de, int64_t cap, int32_t *v_sweep);
+
+/* Restore the live state to the graph as loaded (asynchronous). */
+kz_status kz_reset(kz_graph g, void *stream);
+
+/* Release the handle and its device memory (waits for its stream).  NULL is
+ * ignored. */
+void kz_free_graph(kz_graph g);
+
+/* Static, NUL-terminated description of a status. */
+const char *kz_status_string(kz_status s);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int32_t kz_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KZ_H */

@@ -78,6 +78,12 @@ def _bind(path: str):
     lib.kzo_indices.argtypes = [i32, i32, P, i64, P, P, P, P, i64, P, P, i64, P]
     lib.kzo_dense_indices.restype = C.c_int
     lib.kzo_dense_indices.argtypes = [i32, i32, P, P, i64, P, P, i64, P, P, i64, P]
+    lib.kzo_open.restype = C.c_void_p
+    lib.kzo_open.argtypes = [i32, i32, P, i64, P, P]
+    lib.kzo_session_edge_index.restype = C.c_int
+    lib.kzo_session_edge_index.argtypes = [P, P, i64, P]
+    lib.kzo_close.restype = None
+    lib.kzo_close.argtypes = [P]
     return lib
 
 
@@ -180,3 +186,37 @@ def dense_indices(colour, bits, k: int, verts=(), pairs=(), vlive=None, _lib=Non
     if rc != 0:
         raise OracleError(rc)
     return out_v, out_e
+
+
+class Session:
+    """Edge colour indices of one graph, queried repeatedly (adjacency built
+    once).  Every element is live."""
+
+    def __init__(self, colour, edges, k: int, _lib=None):
+        self._lib = _lib or _load()
+        self.colour = np.ascontiguousarray(colour, dtype=np.int32)
+        self.edges = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+        rc = C.c_int(0)
+        self.h = self._lib.kzo_open(len(self.colour), int(k), _ptr(self.colour), len(self.edges),
+                                    _ptr(self.edges), C.byref(rc))
+        if not self.h:
+            raise OracleError(rc.value)
+
+    def edge_index(self, edge_ids) -> np.ndarray:
+        ids = np.ascontiguousarray(edge_ids, dtype=np.int64)
+        out = np.zeros(len(ids), np.int32)
+        rc = self._lib.kzo_session_edge_index(self.h, _ptr(ids), len(ids), _ptr(out))
+        if rc != 0:
+            raise OracleError(rc)
+        return out
+
+    def close(self):
+        if self.h:
+            self._lib.kzo_close(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

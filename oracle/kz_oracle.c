@@ -410,3 +410,72 @@ int kzo_dense_indices(int32_t n, int32_t k, const int32_t *colour,
     free(seen);
     return KZO_OK;
 }
+
+/*
+ * Session form of kzo_indices for repeated queries on one graph (the CPU
+ * baseline times only the rule evaluations): kzo_open validates and builds
+ * the adjacency list once; kzo_session_edge_index evaluates the edge colour
+ * index of the given edge ids with every element live; kzo_close frees.
+ */
+typedef struct {
+    adj_t g;
+    scratch_t s;
+    uint8_t *elive;
+    const int32_t *edges;
+} session_t;
+
+void *kzo_open(int32_t n, int32_t k, const int32_t *colour, int64_t m, const int32_t *edges,
+               int *rc_out)
+{
+    int rc = validate(n, k, colour, m, edges);
+    session_t *ss = NULL;
+    if (rc == KZO_OK) {
+        ss = (session_t *)calloc(1, sizeof(session_t));
+        if (!ss) rc = KZO_ERR_OOM;
+    }
+    if (rc == KZO_OK) rc = adj_build(&ss->g, n, k, colour, m, edges);
+    if (rc == KZO_OK && scratch_init(&ss->s, n, k) != KZO_OK) {
+        adj_free(&ss->g);
+        rc = KZO_ERR_OOM;
+    }
+    if (rc == KZO_OK) {
+        ss->elive = (uint8_t *)malloc((size_t)m + 1);
+        if (!ss->elive) {
+            scratch_free(&ss->s);
+            adj_free(&ss->g);
+            rc = KZO_ERR_OOM;
+        } else {
+            memset(ss->elive, 1, (size_t)m);
+            ss->edges = edges;
+        }
+    }
+    if (rc != KZO_OK) {
+        free(ss);
+        ss = NULL;
+    }
+    if (rc_out) *rc_out = rc;
+    return ss;
+}
+
+int kzo_session_edge_index(void *session, const int64_t *which_e, int64_t ne, int32_t *out_e)
+{
+    session_t *ss = (session_t *)session;
+    if (!ss) return KZO_ERR_ARG;
+    for (int64_t i = 0; i < ne; i++) {
+        int64_t e = which_e[i];
+        out_e[i] = (e >= 0 && e < ss->g.m)
+                       ? edge_index(&ss->g, ss->elive, &ss->s, ss->edges[2 * e], ss->edges[2 * e + 1])
+                       : -1;
+    }
+    return KZO_OK;
+}
+
+void kzo_close(void *session)
+{
+    session_t *ss = (session_t *)session;
+    if (!ss) return;
+    free(ss->elive);
+    scratch_free(&ss->s);
+    adj_free(&ss->g);
+    free(ss);
+}

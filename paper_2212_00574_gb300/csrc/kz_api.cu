@@ -1,0 +1,381 @@
+// kz_api.cu -- the C ABI declared in include/kz.h: argument checking,
+// colour-sorted relabelling, device allocation, and dispatch to the paths.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "kz_internal.cuh"
+
+namespace {
+
+std::mutex g_alloc_mu;
+kz_allocator g_alloc = {nullptr, nullptr, nullptr};
+
+}  // namespace
+
+namespace kz {
+
+void *dev_alloc(size_t bytes, cudaStream_t s) {
+  kz_allocator a;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    a = g_alloc;
+  }
+  if (a.alloc) return a.alloc(bytes, (void *)s, a.ctx);
+  void *p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(void *p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  kz_allocator a;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    a = g_alloc;
+  }
+  if (a.free) {
+    a.free(p, bytes, (void *)s, a.ctx);
+    return;
+  }
+  cudaFreeAsync(p, s);
+}
+
+}  // namespace kz
+
+using namespace kz;
+
+namespace {
+
+// Definition 4.2.1 requires a legal colouring; the checks that need no
+// device run here, before any CUDA call.
+kz_status check_colours(int32_t n, int32_t k, const int32_t *colour) {
+  if (n < 0 || k < 1 || k > 64) return KZ_ERR_ARG;
+  if (n > 0 && !colour) return KZ_ERR_ARG;
+  for (int32_t v = 0; v < n; v++)
+    if (colour[v] < 0 || colour[v] >= k) return KZ_ERR_COLOUR_RANGE;
+  return KZ_OK;
+}
+
+kz_status check_edges(int32_t n, const int32_t *colour, int64_t m, const int32_t *edges) {
+  if (m < 0) return KZ_ERR_ARG;
+  if (m > 0 && !edges) return KZ_ERR_ARG;
+  for (int64_t e = 0; e < m; e++) {
+    const int32_t u = edges[2 * e], v = edges[2 * e + 1];
+    if (u < 0 || u >= n || v < 0 || v >= n) return KZ_ERR_VERTEX_RANGE;
+    if (u == v) return KZ_ERR_SELF_LOOP;
+    if (colour[u] == colour[v]) return KZ_ERR_ILLEGAL_COLOURING;
+  }
+  return KZ_OK;
+}
+
+// Counting sort by colour, stable in the caller's id order.
+void relabel(kz_graph g, const int32_t *colour) {
+  const int n = g->n, k = g->k;
+  g->coff.assign(k + 1, 0);
+  for (int v = 0; v < n; v++) g->coff[colour[v] + 1]++;
+  for (int c = 0; c < k; c++) g->coff[c + 1] += g->coff[c];
+  std::vector<int32_t> fill(g->coff.begin(), g->coff.end() - 1);
+  g->perm.assign(n, 0);
+  g->inv.assign(n, 0);
+  for (int v = 0; v < n; v++) {
+    const int x = fill[colour[v]]++;
+    g->perm[x] = v;
+    g->inv[v] = x;
+  }
+}
+
+void release(kz_graph g) {
+  if (!g) return;
+  cudaStream_t s = g->stream;
+  // the graph's last work must be finished before its memory is handed back
+  cudaStreamSynchronize(s);
+  if (g->loop_exec) cudaGraphExecDestroy(g->loop_exec);
+  for (auto &a : g->allocs) dev_free(a.p, a.bytes, s);
+  g->allocs.clear();
+  cudaStreamSynchronize(s);
+  delete g;
+}
+
+// Common tail of both loaders: layout, packing, buffers.
+template <class Pack>
+kz_status load_common(int32_t n, int32_t k, const int32_t *colour, void *stream, kz_graph *out,
+                      Pack pack) {
+  // no device, no fallback
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return KZ_ERR_CUDA;
+  }
+  kz_graph g = new (std::nothrow) kz_graph_s();
+  if (!g) return KZ_ERR_OOM;
+  g->n = n;
+  g->k = k;
+  g->stream = (cudaStream_t)stream;
+  cudaGetDevice(&g->device);
+  relabel(g, colour);
+  kz_status st = bitset_build_layout(g);
+  if (st == KZ_OK) st = graph_alloc(g, &g->d_perm, (size_t)std::max(n, 1), g->stream);
+  if (st == KZ_OK && n > 0)
+    st = cuda_status(cudaMemcpyAsync(g->d_perm, g->perm.data(), sizeof(int32_t) * n,
+                                     cudaMemcpyHostToDevice, g->stream));
+  if (st == KZ_OK) st = pack(g);
+  if (st == KZ_OK) st = bitset_finish_load(g, g->stream);
+  if (st == KZ_OK) st = cuda_status(cudaStreamSynchronize(g->stream));
+  if (st != KZ_OK) {
+    release(g);
+    return st;
+  }
+  *out = g;
+  return KZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void kz_default_options(kz_options *opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->path = KZ_PATH_AUTO;
+  opt->schedule = KZ_SCHED_PLAIN;
+  opt->max_sweeps = 0;
+  opt->use_graph = 1;
+}
+
+kz_status kz_set_allocator(const kz_allocator *allocator) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  if (!allocator) {
+    g_alloc = {nullptr, nullptr, nullptr};
+    return KZ_OK;
+  }
+  if (!allocator->alloc || !allocator->free) return KZ_ERR_ARG;
+  g_alloc = *allocator;
+  return KZ_OK;
+}
+
+kz_status kz_load_graph(int32_t n, int32_t k, const int32_t *colour, int64_t m,
+                        const int32_t *edges, uint32_t flags, void *stream, kz_graph *out) {
+  if (!out) return KZ_ERR_ARG;
+  *out = nullptr;
+  if (flags & ~KZ_DEDUP) return KZ_ERR_ARG;
+  KZ_TRY(check_colours(n, k, colour));
+  KZ_TRY(check_edges(n, colour, m, edges));
+  return load_common(n, k, colour, stream, out, [&](kz_graph g) -> kz_status {
+    if (m == 0) return bitset_pack_edges(g, nullptr, 0, true, g->stream);
+    int32_t *d_edges = (int32_t *)dev_alloc((size_t)m * 8, g->stream);
+    if (!d_edges) return KZ_ERR_OOM;
+    kz_status st = cuda_status(cudaMemcpyAsync(d_edges, edges, (size_t)m * 8,
+                                               cudaMemcpyHostToDevice, g->stream));
+    if (st == KZ_OK) st = bitset_pack_edges(g, d_edges, m, (flags & KZ_DEDUP) != 0, g->stream);
+    dev_free(d_edges, (size_t)m * 8, g->stream);
+    return st;
+  });
+}
+
+kz_status kz_load_graph_dense(int32_t n, int32_t k, const int32_t *colour,
+                              const uint64_t *adj_bits, int64_t row_words, uint32_t flags,
+                              void *stream, kz_graph *out) {
+  if (!out) return KZ_ERR_ARG;
+  *out = nullptr;
+  if (flags & ~KZ_DEDUP) return KZ_ERR_ARG;
+  KZ_TRY(check_colours(n, k, colour));
+  if (row_words < (int64_t)((n + 63) / 64) || (n > 0 && !adj_bits)) return KZ_ERR_ARG;
+  return load_common(n, k, colour, stream, out, [&](kz_graph g) -> kz_status {
+    const size_t bytes = (size_t)n * row_words * 8;
+    if (bytes == 0) return bitset_pack_edges(g, nullptr, 0, true, g->stream);
+    uint64_t *d_bits = (uint64_t *)dev_alloc(bytes, g->stream);
+    int32_t *d_col = (int32_t *)dev_alloc((size_t)n * 4, g->stream);
+    kz_status st = (d_bits && d_col) ? KZ_OK : KZ_ERR_OOM;
+    if (st == KZ_OK)
+      st = cuda_status(cudaMemcpyAsync(d_bits, adj_bits, bytes, cudaMemcpyHostToDevice, g->stream));
+    if (st == KZ_OK)
+      st = cuda_status(cudaMemcpyAsync(d_col, colour, (size_t)n * 4, cudaMemcpyHostToDevice, g->stream));
+    if (st == KZ_OK) st = bitset_pack_dense(g, d_bits, row_words, d_col, g->stream);
+    if (d_bits) dev_free(d_bits, bytes, g->stream);
+    if (d_col) dev_free(d_col, (size_t)n * 4, g->stream);
+    return st;
+  });
+}
+
+kz_status kz_kernelize(kz_graph g, const kz_options *opt, void *stream) {
+  if (!g) return KZ_ERR_ARG;
+  kz_options o;
+  if (opt) {
+    o = *opt;
+    for (int i = 0; i < 9; i++)
+      if (o.reserved[i]) return KZ_ERR_ARG;
+  } else {
+    kz_default_options(&o);
+  }
+  if (o.path < KZ_PATH_AUTO || o.path > KZ_PATH_TENSOR) return KZ_ERR_ARG;
+  if (o.schedule != KZ_SCHED_PLAIN && o.schedule != KZ_SCHED_LEARNED) return KZ_ERR_ARG;
+  if (o.path != KZ_PATH_AUTO && o.path != KZ_PATH_BITSET) return KZ_ERR_UNSUPPORTED;
+  if (o.schedule != KZ_SCHED_PLAIN) return KZ_ERR_UNSUPPORTED;
+  g->stream = (cudaStream_t)stream;
+  KZ_TRY(bitset_kernelize(g, o, g->stream));
+  g->kernelized = true;
+  g->path_ran = KZ_PATH_BITSET;
+  return KZ_OK;
+}
+
+kz_status kz_kernelize_batch(kz_graph *graphs, int32_t count, const kz_options *opt, void *stream) {
+  if (count < 0 || (count > 0 && !graphs)) return KZ_ERR_ARG;
+  for (int32_t i = 0; i < count; i++) {
+    if (!graphs[i]) return KZ_ERR_ARG;
+    KZ_TRY(kz_kernelize(graphs[i], opt, stream));
+  }
+  return KZ_OK;
+}
+
+kz_status kz_fetch_stats(kz_graph g, kz_stats *stats) {
+  if (!g) return KZ_ERR_ARG;
+  if (!g->kernelized) return KZ_ERR_NOT_READY;
+  KZ_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  DevState hs;
+  KZ_CUDA_TRY(cudaMemcpy(&hs, g->st, offsetof(DevState, trace_dv), cudaMemcpyDeviceToHost));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->n = g->n;
+    stats->m = g->m;
+    stats->sweeps = hs.sweeps;
+    stats->passes = hs.passes;
+    stats->edge_tests = hs.tests;
+    stats->path = g->path_ran;
+    stats->status = hs.status;
+    stats->k = g->k;
+    KZ_TRY(bitset_vertex_alive(g, nullptr, &stats->n_live));
+    stats->m_live = -1;  // filled by the fetch calls that count edges
+  }
+  return (kz_status)hs.status;
+}
+
+kz_status kz_fetch_kernel_dense(kz_graph g, uint8_t *vertex_alive, uint64_t *adj_bits,
+                                int64_t row_words, kz_stats *stats) {
+  if (!g) return KZ_ERR_ARG;
+  if (!g->kernelized) return KZ_ERR_NOT_READY;
+  if (row_words < (int64_t)((g->n + 63) / 64) || (g->n > 0 && !adj_bits)) return KZ_ERR_ARG;
+  KZ_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  const size_t bytes = (size_t)g->n * row_words * 8;
+  uint64_t *d_out = (uint64_t *)dev_alloc(std::max<size_t>(bytes, 16), g->stream);
+  unsigned long long *d_cnt = (unsigned long long *)dev_alloc(16, g->stream);
+  kz_status st = (d_out && d_cnt) ? KZ_OK : KZ_ERR_OOM;
+  unsigned long long cnt = 0;
+  if (st == KZ_OK) st = bitset_unpack_dense(g, d_out, row_words, d_cnt, g->stream);
+  if (st == KZ_OK && bytes)
+    st = cuda_status(cudaMemcpyAsync(adj_bits, d_out, bytes, cudaMemcpyDeviceToHost, g->stream));
+  if (st == KZ_OK)
+    st = cuda_status(cudaMemcpyAsync(&cnt, d_cnt, 8, cudaMemcpyDeviceToHost, g->stream));
+  if (st == KZ_OK) st = cuda_status(cudaStreamSynchronize(g->stream));
+  if (d_out) dev_free(d_out, bytes, g->stream);
+  if (d_cnt) dev_free(d_cnt, 16, g->stream);
+  if (st != KZ_OK) return st;
+  kz_stats tmp;
+  kz_status dev_status = kz_fetch_stats(g, &tmp);
+  if (vertex_alive) KZ_TRY(bitset_vertex_alive(g, vertex_alive, nullptr));
+  tmp.m_live = (int64_t)(cnt / 2);
+  if (stats) *stats = tmp;
+  return dev_status;
+}
+
+kz_status kz_fetch_kernel(kz_graph g, uint8_t *vertex_alive, int32_t *edges_out, int64_t cap,
+                          int64_t *m_out, kz_stats *stats) {
+  if (!g || !m_out || cap < 0 || (cap > 0 && !edges_out)) return KZ_ERR_ARG;
+  if (!g->kernelized) return KZ_ERR_NOT_READY;
+  const int64_t rw = (g->n + 63) / 64;
+  std::vector<uint64_t> bits;
+  try {
+    bits.resize((size_t)g->n * rw);
+  } catch (...) {
+    return KZ_ERR_OOM;
+  }
+  kz_stats tmp;
+  kz_status st = kz_fetch_kernel_dense(g, vertex_alive, bits.data(), rw, &tmp);
+  if (st != KZ_OK && st != KZ_ERR_LIMIT) return st;
+  // row-major scan of the upper triangle yields (u < v) in lexicographic order
+  int64_t cnt = 0;
+  for (int32_t u = 0; u < g->n; u++) {
+    const uint64_t *row = bits.data() + (size_t)u * rw;
+    for (int64_t w = (u + 1) / 64; w < rw; w++) {
+      uint64_t word = row[w];
+      if (w == (u + 1) / 64) word &= ~0ull << ((u + 1) % 64);
+      while (word) {
+        const int b = __builtin_ctzll(word);
+        word &= word - 1;
+        if (cnt < cap) {
+          edges_out[2 * cnt] = u;
+          edges_out[2 * cnt + 1] = (int32_t)(w * 64 + b);
+        }
+        cnt++;
+      }
+    }
+  }
+  *m_out = cnt;
+  if (stats) *stats = tmp;
+  if (cnt > cap) return KZ_ERR_BUFFER;
+  return st;
+}
+
+kz_status kz_fetch_trace(kz_graph g, int64_t *dv, int64_t *de, int64_t cap, int32_t *v_sweep) {
+  if (!g || cap < 0 || (cap > 0 && (!dv || !de))) return KZ_ERR_ARG;
+  if (!g->kernelized) return KZ_ERR_NOT_READY;
+  KZ_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  DevState hs;
+  KZ_CUDA_TRY(cudaMemcpy(&hs, g->st, offsetof(DevState, trace_dv), cudaMemcpyDeviceToHost));
+  const int64_t have = std::min<int64_t>(hs.sweeps, kTraceCap);
+  const int64_t ncopy = std::min<int64_t>(have, cap);
+  if (ncopy > 0) {
+    KZ_CUDA_TRY(cudaMemcpy(dv, g->st->trace_dv, sizeof(int64_t) * ncopy, cudaMemcpyDeviceToHost));
+    KZ_CUDA_TRY(cudaMemcpy(de, g->st->trace_de, sizeof(int64_t) * ncopy, cudaMemcpyDeviceToHost));
+  }
+  if (v_sweep && g->n > 0) {
+    std::vector<int32_t> vs((size_t)g->n);
+    KZ_CUDA_TRY(cudaMemcpy(vs.data(), g->v_sweep, sizeof(int32_t) * g->n, cudaMemcpyDeviceToHost));
+    for (int32_t x = 0; x < g->n; x++) {
+      // a pass stopped by the sweep limit is never applied
+      v_sweep[g->perm[x]] = vs[x] > hs.sweeps ? 0 : vs[x];
+    }
+  }
+  return KZ_OK;
+}
+
+kz_status kz_reset(kz_graph g, void *stream) {
+  if (!g) return KZ_ERR_ARG;
+  g->stream = (cudaStream_t)stream;
+  return bitset_reset(g, g->stream);
+}
+
+void kz_free_graph(kz_graph g) { release(g); }
+
+const char *kz_status_string(kz_status s) {
+  switch (s) {
+    case KZ_OK: return "ok";
+    case KZ_ERR_ARG: return "invalid argument";
+    case KZ_ERR_COLOUR_RANGE: return "colour outside [0, k)";
+    case KZ_ERR_ILLEGAL_COLOURING: return "edge inside one colour class (colouring not legal)";
+    case KZ_ERR_SELF_LOOP: return "self loop";
+    case KZ_ERR_VERTEX_RANGE: return "vertex id outside [0, n)";
+    case KZ_ERR_DUPLICATE_EDGE: return "duplicate edge";
+    case KZ_ERR_OOM: return "device out of memory";
+    case KZ_ERR_CUDA: return "CUDA runtime error";
+    case KZ_ERR_LIMIT: return "sweep limit reached before the fixpoint";
+    case KZ_ERR_TIMEOUT: return "bounded device wait timed out";
+    case KZ_ERR_NOT_READY: return "graph not kernelized yet";
+    case KZ_ERR_BUFFER: return "output buffer too small";
+    case KZ_ERR_UNSUPPORTED: return "path or schedule not available for this graph";
+    case KZ_ERR_INTERNAL: return "internal consistency check failed";
+  }
+  return "unknown status";
+}
+
+int32_t kz_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// kz_probe.cu -- integer-throughput probe (include/kz_probe.h).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/kz_probe.h"
+
+namespace {
+
+constexpr int kChains = 8;
+constexpr int kIters = 4096;
+
+__device__ __forceinline__ uint32_t lop3_and_or(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm volatile("lop3.b32 %0, %1, %2, %3, 0xEA;" : "=r"(d) : "r"(a), "r"(b), "r"(c));  // (a & b) | c
+  return d;
+}
+
+__device__ __forceinline__ uint32_t umin_asm(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm volatile("min.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+template <int KIND>
+__global__ void int_probe_kernel(uint32_t seed, uint32_t *out) {
+  uint32_t x[kChains];
+#pragma unroll
+  for (int i = 0; i < kChains; i++) x[i] = seed * (threadIdx.x + 7 * i + 1);
+  const uint32_t y = seed ^ blockIdx.x, z = seed + 3u;
+  for (int it = 0; it < kIters; it++) {
+#pragma unroll
+    for (int i = 0; i < kChains; i++) {
+      if (KIND == 0) x[i] = lop3_and_or(x[i], y, z);
+      if (KIND == 1) x[i] = umin_asm(x[i], y + (uint32_t)i);
+      if (KIND == 2) x[i] = __vimin3_u32(x[i], y, z + (uint32_t)i);
+    }
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < kChains; i++) acc ^= x[i];
+  if (acc == 0x9e3779b9u) out[0] = acc;  // keeps the chains live
+}
+
+}  // namespace
+
+extern "C" kz_status kz_probe_int_throughput(int32_t kind, double *ops_per_s, double *ms, void *stream) {
+  if (!ops_per_s || !ms || kind < 0 || kind > 2) return KZ_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return KZ_ERR_CUDA;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  uint32_t *out = nullptr;
+  if (cudaMallocAsync(&out, 16, s) != cudaSuccess) return KZ_ERR_CUDA;
+  const int threads = 256, blocks = sms * 8;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  void (*fn)(uint32_t, uint32_t *) =
+      kind == 0 ? int_probe_kernel<0> : (kind == 1 ? int_probe_kernel<1> : int_probe_kernel<2>);
+  fn<<<blocks, threads, 0, s>>>(12345u, out);  // warm-up
+  cudaEventRecord(e0, s);
+  fn<<<blocks, threads, 0, s>>>(54321u, out);
+  cudaEventRecord(e1, s);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(out, s);
+  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return KZ_ERR_CUDA;
+  const double ops = (double)blocks * threads * kIters * kChains;
+  *ms = t;
+  *ops_per_s = ops / (t * 1e-3);
+  return KZ_OK;
+}

@@ -68,11 +68,12 @@ def bits_to_bool(bits: np.ndarray, n: int) -> np.ndarray:
 
 
 def bool_to_bits(adj: np.ndarray) -> np.ndarray:
-    n = adj.shape[0]
+    """Pack bool rows [r, n] into uint64 words [r, ceil(n/64)]."""
+    r, n = adj.shape
     W = row_words(n)
-    padded = np.zeros((n, W * 64), dtype=bool)
+    padded = np.zeros((r, W * 64), dtype=bool)
     padded[:, :n] = adj
-    return np.packbits(padded, axis=1, bitorder="little").view(np.uint64).reshape(n, W)
+    return np.packbits(padded, axis=1, bitorder="little").view(np.uint64).reshape(r, W)
 
 
 def bits_to_edges(bits: np.ndarray, n: int, block: int = 2048) -> np.ndarray:

@@ -1,0 +1,278 @@
+"""CUDA path against the CPU oracle, through the C ABI (GPU only).
+
+Integer graph work: everything is compared exactly -- surviving vertices and
+edges, productive sweep count, passes, per-sweep deletion counts, the sweep
+in which each vertex died, and the number of live-edge tests.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2212_00574_gb300 as kz
+from paper_2212_00574_gb300 import synth
+from tests import refs
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_run(g, dense=False, **opts):
+    with kz.KernelGraph.from_synth(g, dense=dense) as kg:
+        kg.kernelize(**opts)
+        alive, edges, stats = kg.fetch(allow=(kz.KZ_OK, kz.KZ_ERR_LIMIT))
+        dv, de, vs = kg.trace()
+    return dict(alive=alive, edges=edges, stats=stats, dv=dv[:stats["sweeps"]], de=de[:stats["sweeps"]], v_sweep=vs)
+
+
+def assert_parity(g, res, orc=None, max_sweeps=0):
+    edges = g.get_edges()
+    if orc is None:
+        orc = oracle.fixpoint(g.colour, edges, g.k, max_sweeps=max_sweeps, raise_on_limit=False)
+    want_edges = edges[orc["elive"].astype(bool)]
+    st = res["stats"]
+    assert np.array_equal(res["alive"], orc["vlive"]), "surviving vertices differ"
+    assert np.array_equal(res["edges"], want_edges), "surviving edges differ"
+    assert st["sweeps"] == orc["sweeps"], (st["sweeps"], orc["sweeps"])
+    assert st["passes"] == orc["passes"], (st["passes"], orc["passes"])
+    assert st["edge_tests"] == orc["tests"], (st["edge_tests"], orc["tests"])
+    assert np.array_equal(res["dv"], orc["dv"]), "per-sweep vertex deletions differ"
+    assert np.array_equal(res["de"], orc["de"]), "per-sweep edge deletions differ"
+    assert np.array_equal(res["v_sweep"], orc["v_sweep"]), "vertex deletion sweeps differ"
+    assert st["n_live"] == int(orc["vlive"].sum()) and st["m_live"] == len(want_edges)
+    return orc
+
+
+# ---------------------------------------------------------------------------
+# many small random graphs (several blocks, ragged class tails)
+# ---------------------------------------------------------------------------
+
+def _tiny_cases():
+    rng = np.random.default_rng(2024)
+    cases = []
+    for i in range(48):
+        n = int(rng.integers(1, 160))
+        k = int(rng.integers(1, 14))
+        p = float(rng.uniform(0.05, 0.95))
+        cases.append((i, n, k, p, bool(i % 2)))
+    for i, (n, k) in enumerate([(40, 33), (90, 40), (200, 64), (70, 32), (300, 48), (128, 20)]):
+        cases.append((100 + i, n, k, 0.8, True))
+    return cases
+
+
+@pytest.mark.parametrize("case", _tiny_cases(), ids=lambda c: f"s{c[0]}-n{c[1]}-k{c[2]}-p{c[3]:.2f}")
+def test_tiny_random(case):
+    seed, n, k, p, planted = case
+    g = synth.tiny_random(5000 + seed, n, k, p, planted=planted and n >= k)
+    assert_parity(g, gpu_run(g))
+
+
+# ---------------------------------------------------------------------------
+# shapes chosen to hit edge cases
+# ---------------------------------------------------------------------------
+
+def _graph(colour, edges, k):
+    colour = np.asarray(colour, np.int32)
+    return synth.Graph(n=len(colour), k=k, colour=colour, edges=synth.canonical_edges(np.asarray(edges).reshape(-1, 2)))
+
+
+def test_empty_graph():
+    g = _graph([], np.zeros((0, 2)), 3)
+    assert_parity(g, gpu_run(g))
+
+
+def test_isolated_vertices_only():
+    for k in (1, 2, 5):
+        g = _graph(np.arange(7) % k, np.zeros((0, 2)), k)
+        assert_parity(g, gpu_run(g))
+
+
+@pytest.mark.parametrize("sizes", [[1, 1, 1], [31, 32, 33], [64, 65, 1, 96], [33] * 5, [1] * 32, [2] * 33,
+                                   [100, 3, 57]])
+def test_complete_kpartite(sizes):
+    colour, edges = refs.complete_kpartite(sizes)
+    g = _graph(colour, edges, len(sizes))
+    r = gpu_run(g)
+    assert r["stats"]["sweeps"] == 0 and r["alive"].all()
+    assert_parity(g, r)
+
+
+@pytest.mark.parametrize("sizes", [[5, 0, 7], [0, 40, 40, 40], [33, 33, 0]])
+def test_empty_class(sizes):
+    colour, edges = refs.complete_kpartite(sizes)
+    g = _graph(colour, edges, len(sizes))
+    r = gpu_run(g)
+    assert r["stats"]["sweeps"] == 1 and not r["alive"].any()
+    assert_parity(g, r)
+
+
+def test_k_greater_than_n():
+    g = synth.tiny_random(3, 10, 16, 0.9)
+    assert_parity(g, gpu_run(g))
+
+
+def test_large_class_slow_path():
+    """Classes of 150 vertices (5 planes) with sparse edges: plane-0 words are
+    often empty, so the exact recount over all planes decides."""
+    for seed in range(4):
+        g = synth.tiny_random(60 + seed, 600, 4, 0.02 + 0.01 * seed, planted=True)
+        assert_parity(g, gpu_run(g))
+
+
+def test_cascades():
+    """Sparse graphs that take many sweeps."""
+    seen = 0
+    for seed in range(12):
+        g = synth.tiny_random(700 + seed, 400, 6, 0.06 + 0.01 * (seed % 5), planted=bool(seed % 2))
+        orc = assert_parity(g, gpu_run(g))
+        seen = max(seen, orc["sweeps"])
+    assert seen >= 3
+
+
+# ---------------------------------------------------------------------------
+# options, reset, limits, input forms
+# ---------------------------------------------------------------------------
+
+def test_host_loop_equals_graph_loop():
+    g = synth.tiny_random(42, 300, 7, 0.12, planted=True)
+    a = gpu_run(g, use_graph=1)
+    b = gpu_run(g, use_graph=0)
+    for key in ("alive", "edges", "dv", "de", "v_sweep"):
+        assert np.array_equal(a[key], b[key])
+    assert a["stats"]["sweeps"] == b["stats"]["sweeps"] and a["stats"]["edge_tests"] == b["stats"]["edge_tests"]
+    assert_parity(g, a)
+
+
+def test_dense_input_equals_edge_input():
+    g = synth.kpartite(500, 9, 0.35, seed=17)
+    a = gpu_run(g, dense=True)
+    b = gpu_run(g, dense=False)
+    assert np.array_equal(a["alive"], b["alive"]) and np.array_equal(a["edges"], b["edges"])
+    assert_parity(g, a)
+
+
+def test_reset_and_rerun():
+    g = synth.tiny_random(8, 250, 6, 0.1, planted=True)
+    with kz.KernelGraph.from_synth(g) as kg:
+        kg.kernelize()
+        a1, e1, s1 = kg.fetch()
+        kg.kernelize()               # already a fixpoint: one certifying pass
+        a2, e2, s2 = kg.fetch()
+        assert s2["sweeps"] == 0 and s2["passes"] == 1
+        assert np.array_equal(a1, a2) and np.array_equal(e1, e2)
+        kg.reset().kernelize()
+        a3, e3, s3 = kg.fetch()
+        assert np.array_equal(a1, a3) and np.array_equal(e1, e3) and s3["sweeps"] == s1["sweeps"]
+    assert s1["sweeps"] >= 1
+
+
+def test_sweep_limit():
+    g = synth.tiny_random(31, 60, 6, 0.35)
+    orc_full = oracle.fixpoint(g.colour, g.edges, 6)
+    assert orc_full["sweeps"] >= 2
+    r = gpu_run(g, max_sweeps=1)
+    assert r["stats"]["status"] == kz.KZ_ERR_LIMIT and r["stats"]["sweeps"] == 1
+    orc = oracle.fixpoint(g.colour, g.edges, 6, max_sweeps=1, raise_on_limit=False)
+    assert np.array_equal(r["alive"], orc["vlive"])
+    assert np.array_equal(r["edges"], g.edges[orc["elive"].astype(bool)])
+
+
+def test_duplicates():
+    g = synth.tiny_random(12, 50, 4, 0.3)
+    dup = np.concatenate([g.edges, g.edges[:5, ::-1], g.edges[5:9]])
+    with pytest.raises(kz.KzError) as ei:
+        kz.kz_load_graph(g.n, g.k, g.colour, dup)
+    assert ei.value.status == kz.KZ_ERR_DUPLICATE_EDGE
+    with kz.KernelGraph(g.n, g.k, g.colour, edges=dup, flags=kz.KZ_DEDUP) as kg:
+        kg.kernelize()
+        alive, edges, st = kg.fetch()
+        assert st["m"] == len(g.edges)
+    orc = oracle.fixpoint(g.colour, g.edges, g.k)
+    assert np.array_equal(alive, orc["vlive"]) and np.array_equal(edges, g.edges[orc["elive"].astype(bool)])
+
+
+def test_dense_illegal_colouring_found_on_device():
+    colour = np.array([0, 1, 1], np.int32)
+    bits = synth.edges_to_bits(3, np.array([[0, 1], [1, 2]]))
+    with pytest.raises(kz.KzError) as ei:
+        kz.kz_load_graph_dense(3, 2, colour, bits)
+    assert ei.value.status == kz.KZ_ERR_ILLEGAL_COLOURING
+
+
+def test_fetch_before_kernelize_and_small_buffer():
+    g = synth.tiny_random(4, 30, 3, 0.5)
+    with kz.KernelGraph.from_synth(g) as kg:
+        with pytest.raises(kz.KzError) as ei:
+            kg.fetch()
+        assert ei.value.status == kz.KZ_ERR_NOT_READY
+        kg.kernelize()
+        with pytest.raises(kz.KzError) as ei:
+            kz.kz_fetch_kernel(kg.h, g.n, cap=0)
+        assert ei.value.status == kz.KZ_ERR_BUFFER
+
+
+# ---------------------------------------------------------------------------
+# the workloads, reduced and full
+# ---------------------------------------------------------------------------
+
+def test_c1_full():
+    g = synth.workload("c1")
+    assert_parity(g, gpu_run(g, dense=True))
+
+
+@pytest.mark.parametrize("scale", [0.0625, 0.125])
+def test_c2_reduced(scale):
+    g = synth.workload("c2", scale)
+    assert_parity(g, gpu_run(g, dense=True))
+
+
+def test_c5_reduced():
+    g = synth.workload("c5", 1 / 32)
+    assert_parity(g, gpu_run(g, dense=True))
+
+
+def test_c3_reduced_cascade():
+    g = synth.workload("c3", 0.02)
+    orc = assert_parity(g, gpu_run(g))
+    assert orc["sweeps"] >= 2
+
+
+def test_c4_style_batch_members():
+    for (n, k, p, planted, seed) in synth.batch_specs(10, 99, n_hi=700):
+        g = synth.kpartite(n, k, p, seed, planted=planted)
+        assert_parity(g, gpu_run(g, dense=True))
+
+
+def _sampled_closure(g, alive, bits_out, n_pairs=1500, seed=0):
+    """On the GPU's kernel, sampled surviving vertices and edges must pass the
+    rules (oracle, one element at a time), and sampled deleted edges of the
+    input must not be re-derivable... only survivors are checked here."""
+    rng = np.random.default_rng(seed)
+    verts = rng.choice(g.n, size=min(g.n, 300), replace=False).astype(np.int32)
+    verts = verts[alive[verts] == 1]
+    edges = synth.bits_to_edges(bits_out, g.n) if g.n <= 8192 else None
+    if edges is None or len(edges) == 0:
+        pairs = np.zeros((0, 2), np.int32)
+    else:
+        pairs = edges[rng.choice(len(edges), size=min(n_pairs, len(edges)), replace=False)]
+    iv, ie = oracle.dense_indices(g.colour, bits_out, g.k, verts=verts, pairs=pairs, vlive=alive)
+    assert (iv >= g.k - 1).all(), "a surviving vertex fails the vertex rule"
+    assert (ie >= g.k - 2).all(), "a surviving edge fails the edge rule"
+
+
+def test_c2_full_size_sampled():
+    """Full 4096-vertex dense workload in the benchmark's configuration: the
+    kernel is closed on sampled elements (oracle, one element at a time), and
+    no element is deleted, as the fixpoint of a graph with no failing element
+    must be."""
+    g = synth.workload("c2")
+    with kz.KernelGraph.from_synth(g, dense=True) as kg:
+        kg.kernelize()
+        alive, bits, st = kg.fetch_dense()
+    assert st["sweeps"] == 0 and st["passes"] == 1 and st["edge_tests"] == g.m
+    assert np.array_equal(bits, g.get_bits()) and alive.all()
+    _sampled_closure(g, alive, bits)
+    # the same full-size input, sampled elements on the *input* graph
+    rng = np.random.default_rng(1)
+    e = synth.bits_to_edges(g.get_bits(), g.n)
+    pairs = e[rng.choice(len(e), size=2000, replace=False)]
+    _, ie = oracle.dense_indices(g.colour, g.get_bits(), g.k, pairs=pairs)
+    assert (ie >= g.k - 2).all()
