@@ -30,6 +30,10 @@ WORKLOAD_DESC = {
     "c1": "random k-partite n=300 k=10 p=0.7, planted 10-clique (uint64-bit dense input)",
     "c2": "random k-partite n=4096 k=20 p=0.92, planted 20-clique (dense 0/1 input)",
     "c5": "random k-partite n=32768 k=24 p=0.85, planted 24-clique (dense 0/1 input)",
+    "c3": "Chung-Lu n=200000 k=12, Zipf(1.2) class sizes, power-law degrees (exponent 2.3, mean 60), "
+          "~6M edges, 5 planted 12-cliques (edge-list input)",
+    "c4": "batch of 1024 random k-partite graphs, n log-uniform [64,4096], k U{6..32}, p U[0.3,0.95], "
+          "planted k-clique on even indices, one persistent launch",
 }
 METRIC = "edge-rule tests/s to fixpoint (time-to-fixpoint per graph)"
 UNIT = "edge tests/s"
@@ -46,6 +50,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU work budget of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--path", choices=["auto", "bitset", "small", "sparse"], default="auto")
+    ap.add_argument("--loop", choices=["graph", "host"], default="graph",
+                    help="host: one direct launch per pass (for profilers that cannot see graph kernels)")
     return ap.parse_args()
 
 
@@ -232,15 +239,20 @@ def run_ours(args, world, rank, local, pg):
     kz.use_torch_allocator()
     g = make_workload(args.workload)
     stream = torch.cuda.current_stream(dev)
-    bits = g.get_bits()
-    # pinned host copies of the inputs (for the end-to-end measurement)
-    pin_bits = torch.from_numpy(bits.view(np.int64)).pin_memory()
+    dense = args.workload != "c3"
     pin_col = torch.from_numpy(g.colour).pin_memory()
-    h_bits = pin_bits.numpy().view(np.uint64)
     h_col = pin_col.numpy()
-
-    h = kz.kz_load_graph_dense(g.n, g.k, h_col, h_bits, stream=stream)
-    opts = kz.kz_default_options()
+    if dense:
+        bits = g.get_bits()
+        # pinned host copies of the inputs (for the end-to-end measurement)
+        pin_bits = torch.from_numpy(bits.view(np.int64)).pin_memory()
+        h_bits = pin_bits.numpy().view(np.uint64)
+        h = kz.kz_load_graph_dense(g.n, g.k, h_col, h_bits, stream=stream)
+    else:
+        pin_edges = torch.from_numpy(g.get_edges()).pin_memory()
+        h_edges = pin_edges.numpy()
+        h = kz.kz_load_graph(g.n, g.k, h_col, h_edges, stream=stream)
+    opts = kz.kz_default_options(path=args.path, use_graph=1 if args.loop == "graph" else 0)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def step(i, ev0=None, ev1=None):
@@ -281,25 +293,48 @@ def run_ours(args, world, rank, local, pg):
     value = total_tests / slowest_s
     ms_per_step = dev_ms / args.steps
 
-    # roofline of the dominant kernel (one sweep-kernel launch per pass)
+    # roofline of the dominant kernel (one sweep-kernel launch per pass).  The
+    # binding operation is the word AND of one class word of u's row with v's
+    # (a LOP3 on the 64-lane integer logic pipe); the zero test runs on the
+    # separate min pipe.  Algorithmic ANDs per launch = live edges tested x
+    # (k-2) needed classes (one plane-0 word each on a dense graph).
     k = g.k
     launch_s = (dev_ms / args.steps) / passes / 1e3
-    alg_ops = tests_per_step / passes * max(k - 2, 0) * 2
+    alg_ops = tests_per_step / passes * max(k - 2, 0)
     probe_ops, _ = kz.kz_probe_int_throughput(0, stream)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_derived = sms * 64 * 2.070e9  # 64 INT32 lanes per SM at the maximum SM clock
+    peak_derived = sms * 64 * 2.070e9  # 64 32-bit logic lanes per SM (probe-confirmed) x max SM clock
     achieved = alg_ops / launch_s
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_derived / 1e12, "unit": "Tops/s",
                 "frac": achieved / peak_derived, "traffic": None,
-                "kernel": "bitset_sweep_kernel",
+                "kernel": "bitset_sweep_kernel" if args.path != "small" else "cta_fixpoint_kernel",
                 "probe_lop3_tops": probe_ops / 1e12,
                 "ops_per_launch": alg_ops,
-                "note": "ops = live edges tested x (k-2) class words x (AND + zero test); launch time "
-                        "from CUDA events around the whole kernelize call divided by passes"}
+                "note": "ops = live edges tested x (k-2) class-word ANDs; peak = SMs x 64 logic lanes x "
+                        "2070 MHz (derived; the LOP3 probe measures it); launch time = CUDA events around "
+                        "kz_kernelize / passes (includes graph-launch overhead)"}
 
     # end-to-end through the C ABI: host buffers in, host buffers out
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and not dense:
+        times = []
+        for i in range(args.e2e_steps + 1):
+            flush.fill_(i & 0xFF)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            hh = kz.kz_load_graph(g.n, g.k, h_col, h_edges, stream=stream)
+            kz.kz_kernelize(hh, opts, stream)
+            alive_o, kept, _ = kz.kz_fetch_kernel(hh, g.n)
+            kz.kz_free_graph(hh)
+            dt = time.perf_counter() - t0
+            if i >= 1:
+                times.append(dt)
+        e2e_s = statistics.median(times)
+        e2e = {"value": tests_per_step * world / reduce_max(pg, e2e_s), "unit": UNIT,
+               "h2d_bytes_per_step": int(h_edges.nbytes + h_col.nbytes),
+               "d2h_bytes_per_step": int(alive_o.nbytes + kept.nbytes), "ms_per_step": 1e3 * e2e_s,
+               "calls": "kz_load_graph + kz_kernelize + kz_fetch_kernel + kz_free_graph"}
+    if args.e2e_steps > 0 and dense:
         out_bits = torch.empty((g.n, bits.shape[1]), dtype=torch.int64).pin_memory().numpy().view(np.uint64)
         out_alive = torch.empty(g.n, dtype=torch.uint8).pin_memory().numpy()
         times = []
@@ -335,7 +370,7 @@ def run_ours(args, world, rank, local, pg):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC[args.workload], "n": g.n, "k": g.k, "m": g.m,
-                       "path": "bitset", "passes": passes, "sweeps": st["sweeps"],
+                       "path": args.path, "passes": passes, "sweeps": st["sweeps"],
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); per-step CUDA events "
                              "around kz_kernelize only",
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -352,12 +387,87 @@ def run_ours(args, world, rank, local, pg):
     return 0
 
 
+def run_batch(args, world, rank, local, pg):
+    """Batched workload: one step = kz_kernelize_batch over every graph."""
+    import torch
+
+    import paper_2212_00574_gb300 as kz
+    from paper_2212_00574_gb300 import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    kz.use_torch_allocator()
+    stream = torch.cuda.current_stream(dev)
+    specs = synth.batch_specs(1024, synth.SEED_BASE + 4)
+    graphs = [synth.kpartite(n, k, p, seed, planted=pl) for (n, k, p, pl, seed) in specs]
+    handles = [kz.kz_load_graph_dense(g.n, g.k, g.colour, g.get_bits(), stream=stream) for g in graphs]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    results = {}
+    for label, path in (("batched", "auto"), ("in_cta_persistent", "small"), ("plain_per_graph", "bitset")):
+        opts = kz.kz_default_options(path=path)
+
+        def step(i, ev0=None, ev1=None):
+            for h in handles:
+                kz.kz_reset(h, stream)
+            flush.fill_(i & 0xFF)
+            if ev0 is not None:
+                ev0.record(stream)
+            kz.kz_kernelize_batch(handles, opts, stream)
+            if ev1 is not None:
+                ev1.record(stream)
+
+        for i in range(args.warmup):
+            step(i)
+        torch.cuda.synchronize(dev)
+        tests = sum(kz.kz_fetch_stats(h)["edge_tests"] for h in handles)
+        sweeps = [kz.kz_fetch_stats(h)["sweeps"] for h in handles]
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        barrier(pg)
+        torch.cuda.synchronize(dev)
+        clocks.start()
+        for i in range(args.steps):
+            step(i, *evs[i])
+        torch.cuda.synchronize(dev)
+        clk = clocks.stop()
+        barrier(pg)
+        per_ms = [a.elapsed_time(b) for a, b in evs]
+        results[label] = dict(ms=sum(per_ms) / args.steps, tests=tests, clocks=clk,
+                              sweeps_max=max(sweeps), sweeps_total=sum(sweeps))
+    for h in handles:
+        kz.kz_free_graph(h)
+    b = results["batched"]
+    slowest = reduce_max(pg, b["ms"] * args.steps / 1e3)
+    value = reduce_sum(pg, float(b["tests"]) * args.steps) / slowest
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": b["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC["c4"], "graphs": len(graphs),
+                       "m_total": int(sum(g.m for g in graphs)),
+                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "time_to_fixpoint_us_per_graph": 1e3 * b["ms"] / len(graphs),
+            "plain_per_graph_loop": {"ms_per_step": results["plain_per_graph"]["ms"],
+                                     "speedup_of_batched": results["plain_per_graph"]["ms"] / b["ms"]},
+            "in_cta_persistent": {"ms_per_step": results["in_cta_persistent"]["ms"]},
+            "sweeps": {"max": b["sweeps_max"], "total": b["sweeps_total"]},
+            "clocks": b["clocks"],
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local, pg = dist_init()
     try:
         if args.impl == "reference":
             return run_reference(args, world, rank, pg)
+        if args.workload == "c4":
+            return run_batch(args, world, rank, local, pg)
         return run_ours(args, world, rank, local, pg)
     finally:
         if pg is not None:

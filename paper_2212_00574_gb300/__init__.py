@@ -23,7 +23,8 @@ import numpy as np
 from . import build as _build
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "kz.h")
-HEADERS = [HEADER, os.path.join(os.path.dirname(HEADER), "kz_probe.h")]
+HEADERS = [HEADER, os.path.join(os.path.dirname(HEADER), "kz_probe.h"),
+           os.path.join(os.path.dirname(HEADER), "kz_learned.h")]
 
 KZ_OK = 0
 STATUS_NAMES = {
@@ -101,6 +102,14 @@ def _lib():
                 "kz_status_string": (C.c_char_p, [C.c_int]),
                 "kz_version": (i32, []),
                 "kz_probe_int_throughput": (C.c_int, [i32, P, P, P]),
+                "kz_model_create": (C.c_int, [P, P]),
+                "kz_model_get": (C.c_int, [P, P]),
+                "kz_model_free": (None, [P]),
+                "kz_mlp_forward": (C.c_int, [P, P, i64, P, P]),
+                "kz_mlp_grad": (C.c_int, [P, P, P, i64, P, P, P]),
+                "kz_mlp_adam": (C.c_int, [P, P, C.c_float, P]),
+                "kz_collect_trace": (C.c_int, [P, i64, C.c_uint64, P, P, i64, P]),
+                "kz_attach_model": (C.c_int, [P, P, C.c_float]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -376,3 +385,57 @@ class KernelGraph:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ---------------------------------------------------------------------------
+# learned schedule (include/kz_learned.h)
+# ---------------------------------------------------------------------------
+
+KZ_MLP_PARAMS = 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def kz_model_create(weights=None) -> int:
+    h = C.c_void_p()
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
+    if w is not None and w.size != KZ_MLP_PARAMS:
+        raise ValueError("weights must have KZ_MLP_PARAMS entries")
+    _check(_lib().kz_model_create(_ptr(w), C.byref(h)), "kz_model_create")
+    return h.value
+
+
+def kz_model_get(m: int) -> np.ndarray:
+    w = np.zeros(KZ_MLP_PARAMS, np.float32)
+    _check(_lib().kz_model_get(C.c_void_p(m), _ptr(w)), "kz_model_get")
+    return w
+
+
+def kz_model_free(m: int):
+    _lib().kz_model_free(C.c_void_p(m))
+
+
+def kz_mlp_forward(m: int, X_ptr: int, B: int, logits_ptr: int, stream=None):
+    _check(_lib().kz_mlp_forward(C.c_void_p(m), C.c_void_p(X_ptr), int(B), C.c_void_p(logits_ptr),
+                                 _stream(stream)), "kz_mlp_forward")
+
+
+def kz_mlp_grad(m: int, X_ptr: int, y_ptr: int, B: int, grad_ptr: int, loss_ptr: int, stream=None):
+    _check(_lib().kz_mlp_grad(C.c_void_p(m), C.c_void_p(X_ptr), C.c_void_p(y_ptr), int(B), C.c_void_p(grad_ptr),
+                              C.c_void_p(loss_ptr), _stream(stream)), "kz_mlp_grad")
+
+
+def kz_mlp_adam(m: int, grad_ptr: int, lr: float, stream=None):
+    _check(_lib().kz_mlp_adam(C.c_void_p(m), C.c_void_p(grad_ptr), C.c_float(lr), _stream(stream)), "kz_mlp_adam")
+
+
+def kz_collect_trace(g: int, per_sweep_cap: int, seed: int, cap: int):
+    """(features float32[count,16], labels uint8[count]) from plain sweeps."""
+    X = np.zeros((max(cap, 1), 16), np.float32)
+    y = np.zeros(max(cap, 1), np.uint8)
+    cnt = C.c_int64(0)
+    _check(_lib().kz_collect_trace(C.c_void_p(g), int(per_sweep_cap), C.c_uint64(seed), _ptr(X), _ptr(y), int(cap),
+                                   C.byref(cnt)), "kz_collect_trace")
+    return X[:cnt.value].copy(), y[:cnt.value].copy()
+
+
+def kz_attach_model(g: int, m: int, threshold: float = 0.5):
+    _check(_lib().kz_attach_model(C.c_void_p(g), C.c_void_p(m), C.c_float(threshold)), "kz_attach_model")

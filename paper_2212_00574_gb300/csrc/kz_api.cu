@@ -99,16 +99,22 @@ void release(kz_graph g) {
   // the graph's last work must be finished before its memory is handed back
   cudaStreamSynchronize(s);
   if (g->loop_exec) cudaGraphExecDestroy(g->loop_exec);
+  learned_release(g);
   for (auto &a : g->allocs) dev_free(a.p, a.bytes, s);
   g->allocs.clear();
   cudaStreamSynchronize(s);
   delete g;
 }
 
-// Common tail of both loaders: layout, packing, buffers.
-template <class Pack>
+// Bitset rows are built when their three copies fit this budget; larger
+// graphs (or graphs with very uneven colour classes) use the CSR path only.
+constexpr size_t kBitsetBudgetBytes = size_t(8) << 30;
+
+// Common tail of both loaders: relabelling, bitset layout and packing (when
+// the rows fit), CSR structures (edge-list input), buffers.
+template <class Pack, class Csr>
 kz_status load_common(int32_t n, int32_t k, const int32_t *colour, void *stream, kz_graph *out,
-                      Pack pack) {
+                      Pack pack, Csr csr, bool want_csr) {
   // no device, no fallback
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
@@ -122,18 +128,31 @@ kz_status load_common(int32_t n, int32_t k, const int32_t *colour, void *stream,
   g->stream = (cudaStream_t)stream;
   cudaGetDevice(&g->device);
   relabel(g, colour);
-  kz_status st = bitset_build_layout(g);
-  if (st == KZ_OK) st = graph_alloc(g, &g->d_perm, (size_t)std::max(n, 1), g->stream);
-  if (st == KZ_OK && n > 0)
-    st = cuda_status(cudaMemcpyAsync(g->d_perm, g->perm.data(), sizeof(int32_t) * n,
-                                     cudaMemcpyHostToDevice, g->stream));
-  if (st == KZ_OK) st = pack(g);
-  if (st == KZ_OK) st = bitset_finish_load(g, g->stream);
+  kz_status st = KZ_OK;
+  if (want_csr) st = csr(g);  // host-side duplicate check comes first
+  const kz_status lay = bitset_build_layout(g);
+  const size_t bitset_bytes = (size_t)3 * g->n * g->ldw * 4;
+  const bool want_bitset = lay == KZ_OK && bitset_bytes <= kBitsetBudgetBytes;
+  if (st == KZ_OK && want_bitset) {
+    st = graph_alloc(g, &g->d_perm, (size_t)std::max(n, 1), g->stream);
+    if (st == KZ_OK) st = graph_alloc(g, &g->d_inv, (size_t)std::max(n, 1), g->stream);
+    if (st == KZ_OK && n > 0)
+      st = cuda_status(cudaMemcpyAsync(g->d_perm, g->perm.data(), sizeof(int32_t) * n,
+                                       cudaMemcpyHostToDevice, g->stream));
+    if (st == KZ_OK && n > 0)
+      st = cuda_status(cudaMemcpyAsync(g->d_inv, g->inv.data(), sizeof(int32_t) * n,
+                                       cudaMemcpyHostToDevice, g->stream));
+    if (st == KZ_OK) st = pack(g);
+    if (st == KZ_OK) st = bitset_finish_load(g, g->stream);
+    if (st == KZ_OK) g->has_bitset = true;
+  }
+  if (st == KZ_OK && !g->has_bitset && !g->has_csr) st = KZ_ERR_UNSUPPORTED;
   if (st == KZ_OK) st = cuda_status(cudaStreamSynchronize(g->stream));
   if (st != KZ_OK) {
     release(g);
     return st;
   }
+  g->owner = g->has_bitset ? KZ_PATH_BITSET : KZ_PATH_SPARSE;
   *out = g;
   return KZ_OK;
 }
@@ -169,16 +188,19 @@ kz_status kz_load_graph(int32_t n, int32_t k, const int32_t *colour, int64_t m,
   if (flags & ~KZ_DEDUP) return KZ_ERR_ARG;
   KZ_TRY(check_colours(n, k, colour));
   KZ_TRY(check_edges(n, colour, m, edges));
-  return load_common(n, k, colour, stream, out, [&](kz_graph g) -> kz_status {
+  const bool dedup = (flags & KZ_DEDUP) != 0;
+  auto pack = [&](kz_graph g) -> kz_status {
     if (m == 0) return bitset_pack_edges(g, nullptr, 0, true, g->stream);
     int32_t *d_edges = (int32_t *)dev_alloc((size_t)m * 8, g->stream);
     if (!d_edges) return KZ_ERR_OOM;
     kz_status st = cuda_status(cudaMemcpyAsync(d_edges, edges, (size_t)m * 8,
                                                cudaMemcpyHostToDevice, g->stream));
-    if (st == KZ_OK) st = bitset_pack_edges(g, d_edges, m, (flags & KZ_DEDUP) != 0, g->stream);
+    if (st == KZ_OK) st = bitset_pack_edges(g, d_edges, m, dedup, g->stream);
     dev_free(d_edges, (size_t)m * 8, g->stream);
     return st;
-  });
+  };
+  auto csr = [&](kz_graph g) -> kz_status { return sparse_load(g, colour, m, edges, dedup, g->stream); };
+  return load_common(n, k, colour, stream, out, pack, csr, true);
 }
 
 kz_status kz_load_graph_dense(int32_t n, int32_t k, const int32_t *colour,
@@ -189,6 +211,7 @@ kz_status kz_load_graph_dense(int32_t n, int32_t k, const int32_t *colour,
   if (flags & ~KZ_DEDUP) return KZ_ERR_ARG;
   KZ_TRY(check_colours(n, k, colour));
   if (row_words < (int64_t)((n + 63) / 64) || (n > 0 && !adj_bits)) return KZ_ERR_ARG;
+  auto no_csr = [](kz_graph) -> kz_status { return KZ_OK; };
   return load_common(n, k, colour, stream, out, [&](kz_graph g) -> kz_status {
     const size_t bytes = (size_t)n * row_words * 8;
     if (bytes == 0) return bitset_pack_edges(g, nullptr, 0, true, g->stream);
@@ -203,12 +226,10 @@ kz_status kz_load_graph_dense(int32_t n, int32_t k, const int32_t *colour,
     if (d_bits) dev_free(d_bits, bytes, g->stream);
     if (d_col) dev_free(d_col, (size_t)n * 4, g->stream);
     return st;
-  });
+  }, no_csr, false);
 }
 
-kz_status kz_kernelize(kz_graph g, const kz_options *opt, void *stream) {
-  if (!g) return KZ_ERR_ARG;
-  kz_options o;
+static kz_status read_options(const kz_options *opt, kz_options &o) {
   if (opt) {
     o = *opt;
     for (int i = 0; i < 9; i++)
@@ -218,22 +239,104 @@ kz_status kz_kernelize(kz_graph g, const kz_options *opt, void *stream) {
   }
   if (o.path < KZ_PATH_AUTO || o.path > KZ_PATH_TENSOR) return KZ_ERR_ARG;
   if (o.schedule != KZ_SCHED_PLAIN && o.schedule != KZ_SCHED_LEARNED) return KZ_ERR_ARG;
-  if (o.path != KZ_PATH_AUTO && o.path != KZ_PATH_BITSET) return KZ_ERR_UNSUPPORTED;
-  if (o.schedule != KZ_SCHED_PLAIN) return KZ_ERR_UNSUPPORTED;
-  g->stream = (cudaStream_t)stream;
-  KZ_TRY(bitset_kernelize(g, o, g->stream));
-  g->kernelized = true;
-  g->path_ran = KZ_PATH_BITSET;
+  if (o.path == KZ_PATH_TENSOR) return KZ_ERR_UNSUPPORTED;
   return KZ_OK;
+}
+
+// The path a graph takes when the options leave the choice to the library:
+// bitset rows when they exist (inside one CTA when both ping-pong copies fit
+// in shared memory), else the CSR path.
+static int auto_path(kz_graph g) {
+  if (!g->has_bitset) return KZ_PATH_SPARSE;
+  return cta_fits_shared(g) ? KZ_PATH_SMALL : KZ_PATH_BITSET;
+}
+
+static kz_status run_one(kz_graph g, const kz_options &o, int path) {
+  if (path == KZ_PATH_SPARSE) {
+    if (!g->has_csr) return KZ_ERR_UNSUPPORTED;
+    KZ_TRY(state_to_sparse(g, g->stream));
+    KZ_TRY(sparse_kernelize(g, o, g->stream));
+  } else {
+    if (!g->has_bitset) return KZ_ERR_UNSUPPORTED;
+    KZ_TRY(state_to_bitset(g, g->stream));
+    if (path == KZ_PATH_SMALL) KZ_TRY(cta_kernelize_one(g, o, g->stream));
+    else KZ_TRY(bitset_kernelize(g, o, g->stream));
+  }
+  g->kernelized = true;
+  g->path_ran = path;
+  return KZ_OK;
+}
+
+kz_status kz_kernelize(kz_graph g, const kz_options *opt, void *stream) {
+  if (!g) return KZ_ERR_ARG;
+  kz_options o;
+  KZ_TRY(read_options(opt, o));
+  g->stream = (cudaStream_t)stream;
+  if (o.schedule == KZ_SCHED_LEARNED) {
+    // learned worklist rounds on the bitset rows, certified by plain sweeps
+    if (!g->has_bitset || !g->model) return KZ_ERR_UNSUPPORTED;
+    if (o.path != KZ_PATH_AUTO && o.path != KZ_PATH_BITSET) return KZ_ERR_UNSUPPORTED;
+    KZ_TRY(state_to_bitset(g, g->stream));
+    KZ_TRY(learned_kernelize(g, o, g->stream));
+    g->kernelized = true;
+    g->path_ran = KZ_PATH_BITSET;
+    return KZ_OK;
+  }
+  const int path = o.path == KZ_PATH_AUTO ? auto_path(g) : o.path;
+  return run_one(g, o, path);
 }
 
 kz_status kz_kernelize_batch(kz_graph *graphs, int32_t count, const kz_options *opt, void *stream) {
   if (count < 0 || (count > 0 && !graphs)) return KZ_ERR_ARG;
-  for (int32_t i = 0; i < count; i++) {
+  for (int32_t i = 0; i < count; i++)
     if (!graphs[i]) return KZ_ERR_ARG;
-    KZ_TRY(kz_kernelize(graphs[i], opt, stream));
+  kz_options o;
+  KZ_TRY(read_options(opt, o));
+  if (o.schedule != KZ_SCHED_PLAIN) {
+    for (int32_t i = 0; i < count; i++) KZ_TRY(kz_kernelize(graphs[i], &o, stream));
+    return KZ_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int32_t i = 0; i < count; i++) graphs[i]->stream = s;
+  if (o.path == KZ_PATH_BITSET || o.path == KZ_PATH_SPARSE) {
+    // the plain per-graph loop
+    for (int32_t i = 0; i < count; i++) KZ_TRY(run_one(graphs[i], o, o.path));
+    return KZ_OK;
+  }
+  // graphs without bitset rows go through the CSR path one by one
+  std::vector<kz_graph> rows;
+  for (int32_t i = 0; i < count; i++) {
+    if (!graphs[i]->has_bitset) {
+      KZ_TRY(run_one(graphs[i], o, KZ_PATH_SPARSE));
+      continue;
+    }
+    KZ_TRY(state_to_bitset(graphs[i], s));
+    rows.push_back(graphs[i]);
+  }
+  std::vector<kz_graph> loop, cta;
+  for (kz_graph g : rows) {
+    // SMALL: every graph in the in-CTA persistent launch; AUTO: the batched
+    // Jacobi loop for k <= 32, the in-CTA launch for more colours
+    if (o.path == KZ_PATH_SMALL || g->k > 32) cta.push_back(g);
+    else loop.push_back(g);
+  }
+  if (!loop.empty()) KZ_TRY(batch_kernelize(loop.data(), (int)loop.size(), o, s));
+  if (!cta.empty()) KZ_TRY(cta_kernelize(cta.data(), (int)cta.size(), o, s, 1));
+  for (kz_graph g : loop) {
+    g->kernelized = true;
+    g->path_ran = KZ_PATH_BITSET;
+  }
+  for (kz_graph g : cta) {
+    g->kernelized = true;
+    g->path_ran = KZ_PATH_SMALL;
   }
   return KZ_OK;
+}
+
+// Vertices alive, from whichever representation holds the state.
+static kz_status owner_vertex_alive(kz_graph g, uint8_t *alive, int64_t *n_live) {
+  if (g->owner == KZ_PATH_SPARSE) return sparse_vertex_alive(g, alive, n_live);
+  return bitset_vertex_alive(g, alive, n_live);
 }
 
 kz_status kz_fetch_stats(kz_graph g, kz_stats *stats) {
@@ -252,7 +355,7 @@ kz_status kz_fetch_stats(kz_graph g, kz_stats *stats) {
     stats->path = g->path_ran;
     stats->status = hs.status;
     stats->k = g->k;
-    KZ_TRY(bitset_vertex_alive(g, nullptr, &stats->n_live));
+    KZ_TRY(owner_vertex_alive(g, nullptr, &stats->n_live));
     stats->m_live = -1;  // filled by the fetch calls that count edges
   }
   return (kz_status)hs.status;
@@ -264,6 +367,28 @@ kz_status kz_fetch_kernel_dense(kz_graph g, uint8_t *vertex_alive, uint64_t *adj
   if (!g->kernelized) return KZ_ERR_NOT_READY;
   if (row_words < (int64_t)((g->n + 63) / 64) || (g->n > 0 && !adj_bits)) return KZ_ERR_ARG;
   KZ_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (g->owner == KZ_PATH_SPARSE) {
+    std::vector<int32_t> e;
+    int64_t ml = 0;
+    KZ_TRY(sparse_fetch(g, vertex_alive, nullptr, 0, &ml));
+    try {
+      e.resize((size_t)std::max<int64_t>(2 * ml, 2));
+    } catch (...) {
+      return KZ_ERR_OOM;
+    }
+    KZ_TRY(sparse_fetch(g, nullptr, e.data(), ml, &ml));
+    memset(adj_bits, 0, (size_t)g->n * row_words * 8);
+    for (int64_t i = 0; i < ml; i++) {
+      const int32_t u = e[2 * i], v = e[2 * i + 1];
+      adj_bits[(size_t)u * row_words + (v >> 6)] |= 1ull << (v & 63);
+      adj_bits[(size_t)v * row_words + (u >> 6)] |= 1ull << (u & 63);
+    }
+    kz_stats tmp;
+    kz_status dev_status = kz_fetch_stats(g, &tmp);
+    tmp.m_live = ml;
+    if (stats) *stats = tmp;
+    return dev_status;
+  }
   const size_t bytes = (size_t)g->n * row_words * 8;
   uint64_t *d_out = (uint64_t *)dev_alloc(std::max<size_t>(bytes, 16), g->stream);
   unsigned long long *d_cnt = (unsigned long long *)dev_alloc(16, g->stream);
@@ -280,7 +405,7 @@ kz_status kz_fetch_kernel_dense(kz_graph g, uint8_t *vertex_alive, uint64_t *adj
   if (st != KZ_OK) return st;
   kz_stats tmp;
   kz_status dev_status = kz_fetch_stats(g, &tmp);
-  if (vertex_alive) KZ_TRY(bitset_vertex_alive(g, vertex_alive, nullptr));
+  if (vertex_alive) KZ_TRY(owner_vertex_alive(g, vertex_alive, nullptr));
   tmp.m_live = (int64_t)(cnt / 2);
   if (stats) *stats = tmp;
   return dev_status;
@@ -290,6 +415,18 @@ kz_status kz_fetch_kernel(kz_graph g, uint8_t *vertex_alive, int32_t *edges_out,
                           int64_t *m_out, kz_stats *stats) {
   if (!g || !m_out || cap < 0 || (cap > 0 && !edges_out)) return KZ_ERR_ARG;
   if (!g->kernelized) return KZ_ERR_NOT_READY;
+  if (g->owner == KZ_PATH_SPARSE) {
+    kz_stats tmp;
+    kz_status dev_status = kz_fetch_stats(g, &tmp);
+    if (dev_status != KZ_OK && dev_status != KZ_ERR_LIMIT) return dev_status;
+    int64_t ml = 0;
+    KZ_TRY(sparse_fetch(g, vertex_alive, edges_out, cap, &ml));
+    *m_out = ml;
+    tmp.m_live = ml;
+    if (stats) *stats = tmp;
+    if (ml > cap) return KZ_ERR_BUFFER;
+    return dev_status;
+  }
   const int64_t rw = (g->n + 63) / 64;
   std::vector<uint64_t> bits;
   try {
@@ -338,10 +475,15 @@ kz_status kz_fetch_trace(kz_graph g, int64_t *dv, int64_t *de, int64_t cap, int3
   }
   if (v_sweep && g->n > 0) {
     std::vector<int32_t> vs((size_t)g->n);
-    KZ_CUDA_TRY(cudaMemcpy(vs.data(), g->v_sweep, sizeof(int32_t) * g->n, cudaMemcpyDeviceToHost));
-    for (int32_t x = 0; x < g->n; x++) {
-      // a pass stopped by the sweep limit is never applied
-      v_sweep[g->perm[x]] = vs[x] > hs.sweeps ? 0 : vs[x];
+    if (g->owner == KZ_PATH_SPARSE) {
+      KZ_TRY(sparse_v_sweep(g, vs.data()));
+      for (int32_t v = 0; v < g->n; v++) v_sweep[v] = vs[v] > hs.sweeps ? 0 : vs[v];
+    } else {
+      KZ_CUDA_TRY(cudaMemcpy(vs.data(), g->v_sweep, sizeof(int32_t) * g->n, cudaMemcpyDeviceToHost));
+      for (int32_t x = 0; x < g->n; x++) {
+        // a pass stopped by the sweep limit is never applied
+        v_sweep[g->perm[x]] = vs[x] > hs.sweeps ? 0 : vs[x];
+      }
     }
   }
   return KZ_OK;
@@ -350,7 +492,11 @@ kz_status kz_fetch_trace(kz_graph g, int64_t *dv, int64_t *de, int64_t cap, int3
 kz_status kz_reset(kz_graph g, void *stream) {
   if (!g) return KZ_ERR_ARG;
   g->stream = (cudaStream_t)stream;
-  return bitset_reset(g, g->stream);
+  if (g->has_bitset) KZ_TRY(bitset_reset(g, g->stream));
+  if (g->has_csr) KZ_TRY(sparse_reset(g, g->stream));
+  g->owner = g->has_bitset ? KZ_PATH_BITSET : KZ_PATH_SPARSE;
+  g->kernelized = false;
+  return KZ_OK;
 }
 
 void kz_free_graph(kz_graph g) { release(g); }

@@ -39,6 +39,7 @@
 #include <vector>
 
 #include "kz_internal.cuh"
+#include "kz_rules.cuh"
 
 namespace kz {
 
@@ -212,49 +213,6 @@ struct SweepArgs {
 
 constexpr int kSweepWarps = 4;
 
-// Exact colour cover of the pair (u, v) over all planes, classes cu and cv
-// excluded.
-__device__ __noinline__ int exact_edge_cover(const uint32_t *__restrict__ A, int ldw, int k,
-                                             const int32_t *__restrict__ rounds, int u, int v,
-                                             int cu, int cv) {
-  const uint32_t *ru = A + (int64_t)u * ldw;
-  const uint32_t *rv = A + (int64_t)v * ldw;
-  int cnt = 0;
-  for (int c = 0; c < k; c++) {
-    if (c == cu || c == cv) continue;
-    const int R = rounds[c];
-    for (int r = 0; r < R; r++) {
-      if (ru[r * k + c] & rv[r * k + c]) {
-        cnt++;
-        break;
-      }
-    }
-  }
-  return cnt;
-}
-
-// Exact colour cover of vertex u's live neighbourhood, class cu excluded.
-__device__ __noinline__ int exact_vertex_cover(const uint32_t *__restrict__ A, int ldw, int k,
-                                               const int32_t *__restrict__ rounds, int u, int cu) {
-  const uint32_t *ru = A + (int64_t)u * ldw;
-  int cnt = 0;
-  for (int c = 0; c < k; c++) {
-    if (c == cu) continue;
-    const int R = rounds[c];
-    for (int r = 0; r < R; r++) {
-      if (ru[r * k + c]) {
-        cnt++;
-        break;
-      }
-    }
-  }
-  return cnt;
-}
-
-__device__ __forceinline__ uint32_t min3u(uint32_t a, uint32_t b, uint32_t c) {
-  return __vimin3_u32(a, b, c);
-}
-
 template <int KMAX>
 __global__ void __launch_bounds__(kSweepWarps * 32)
     bitset_sweep_kernel(SweepArgs p) {
@@ -283,25 +241,15 @@ __global__ void __launch_bounds__(kSweepWarps * 32)
     const uint32_t *rowu = A + (int64_t)(valid_u ? u : X.base) * ldw;
 
     uint32_t Fu[KMAX];
-#pragma unroll
-    for (int q = 0; q < KMAX / 4; q++) {
-      uint4 w = make_uint4(0, 0, 0, 0);
-      if (valid_u && 4 * q < k) w = reinterpret_cast<const uint4 *>(rowu)[q];
-      Fu[4 * q + 0] = w.x;
-      Fu[4 * q + 1] = w.y;
-      Fu[4 * q + 2] = w.z;
-      Fu[4 * q + 3] = w.w;
-    }
+    load_plane0<KMAX>(Fu, rowu, k, valid_u);
 
     if (item.vflag) {
       // vertex rule for the members of X
       const int wx = X.r * k + cu;
       const uint32_t vword = Vc[wx];
       const bool live = valid_u && ((vword >> lane) & 1u);
-      int cnt = 0;
-#pragma unroll
-      for (int c = 0; c < KMAX; c++) cnt += (c < k && c != cu && Fu[c] != 0u) ? 1 : 0;
-      if (live && cnt < k - 1) cnt = exact_vertex_cover(A, ldw, k, p.rounds, u, cu);
+      int cnt = plane0_vertex_cover<KMAX>(Fu, k, cu);
+      if (live && cnt < k - 1) cnt = exact_vertex_cover_row(rowu, k, p.rounds, cu);
       const bool fail = live && cnt < k - 1;
       const uint32_t failmask = __ballot_sync(0xffffffffu, fail);
       if (lane == 0) {
@@ -311,63 +259,35 @@ __global__ void __launch_bounds__(kSweepWarps * 32)
       if (fail && p.v_sweep) p.v_sweep[u] = (int32_t)(sweep_no + 1);
     }
 
-    // own class and padding classes count as covered
-#pragma unroll
-    for (int c = 0; c < KMAX; c++)
-      if (c == cu || c >= k) Fu[c] = 0xffffffffu;
-
-    uint32_t Fu2[KMAX];
+    uint32_t P[KMAX];
     int prev_cv = -1;
     for (int y = item.y0; y < item.y1; y++) {
       const BlockDesc Y = p.blocks[y];
       const int cv = Y.c;
       if (cv != prev_cv) {
-#pragma unroll
-        for (int c = 0; c < KMAX; c++) Fu2[c] = (c == cv) ? 0xffffffffu : Fu[c];
+        pair_mask<KMAX>(P, k, cu, cv);
         prev_cv = cv;
       }
-      // stage plane 0 of the rows of Y, classes cu / cv / padding forced to ones
+      // stage plane 0 of the rows of Y (broadcast reads from shared memory)
       __syncwarp();
-      for (int idx = lane; idx < 32 * KMAX; idx += 32) {
-        const int b = idx / KMAX;
-        const int c = idx - b * KMAX;
-        uint32_t val = 0xffffffffu;
-        if (b < Y.size && c < k && c != cu && c != cv) val = A[(int64_t)(Y.base + b) * ldw + c];
-        sv[idx] = val;
+      const int kq = (k + 3) & ~3;  // columns the test reads
+      for (int idx = lane; idx < 32 * kq; idx += 32) {
+        const int b = idx / kq;
+        const int c = idx - b * kq;
+        sv[b * KMAX + c] = (b < Y.size && c < k) ? A[(int64_t)(Y.base + b) * ldw + c] : 0u;
       }
       __syncwarp();
       const int wy = Y.r * k + cv;
       const uint32_t adjw = valid_u ? A[(int64_t)u * ldw + wy] : 0u;
       my_tests += __popc(adjw);
-      uint32_t bits = __reduce_or_sync(0xffffffffu, adjw);
-      uint32_t del = 0;
-      while (bits) {
-        const int b = __ffs(bits) - 1;
-        bits &= bits - 1;
-        const uint4 *fv = reinterpret_cast<const uint4 *>(sv + b * KMAX);
-        uint32_t m0 = 0xffffffffu, m1 = 0xffffffffu;
-#pragma unroll
-        for (int q = 0; q < KMAX / 4; q++) {
-          const uint4 w = fv[q];
-          m0 = min3u(m0, Fu2[4 * q + 0] & w.x, Fu2[4 * q + 1] & w.y);
-          m1 = min3u(m1, Fu2[4 * q + 2] & w.z, Fu2[4 * q + 3] & w.w);
-        }
-        if (((adjw >> b) & 1u) && min(m0, m1) == 0u) {
-          const int cover = exact_edge_cover(A, ldw, k, p.rounds, u, Y.base + b, cu, cv);
-          if (cover < k - 2) del |= 1u << b;
-        }
-      }
+      const uint32_t del = edge_rule_block<KMAX>(
+          Fu, P, rowu, adjw, k, p.rounds, cu, cv,
+          [&](int b) { return (const uint32_t *)(sv + b * KMAX); },
+          [&](int b) { return A + (int64_t)(Y.base + b) * ldw; });
       if (valid_u) An[(int64_t)u * ldw + wy] = adjw & ~del;
       my_de += __popc(del);
       // row v's word for block X, with the deletions transposed by ballots
-      uint32_t delT = 0;
-      uint32_t anydel = __reduce_or_sync(0xffffffffu, del);
-      while (anydel) {
-        const int b = __ffs(anydel) - 1;
-        anydel &= anydel - 1;
-        const uint32_t col = __ballot_sync(0xffffffffu, (del >> b) & 1u);
-        if (lane == b) delT = col;
-      }
+      const uint32_t delT = transpose_deletions(del);
       if (lane < Y.size) {
         const int64_t wi = (int64_t)(Y.base + lane) * ldw + X.r * k + cu;
         An[wi] = A[wi] & ~delT;
@@ -392,38 +312,22 @@ __global__ void __launch_bounds__(kSweepWarps * 32)
       const unsigned long long dv = atomicAdd(&st->pass_dv, 0ull);
       const unsigned long long de = atomicAdd(&st->pass_de, 0ull);
       const unsigned long long tests = atomicAdd(&st->pass_tests, 0ull);
-      st->passes += 1;
-      st->tests += (int64_t)tests;
-      int cont = 0;
-      if (dv + de > 0) {
-        if (st->sweeps >= st->max_sweeps) {
-          st->status = KZ_ERR_LIMIT;
-        } else {
-          if (st->sweeps < kTraceCap) {
-            st->trace_dv[st->sweeps] = (int64_t)dv;
-            st->trace_de[st->sweeps] = (int64_t)de;
-          }
-          st->sweeps += 1;
-          st->cur ^= 1;
-          cont = 1;
-        }
-      }
+      const int cont = finish_pass(st, dv, de, tests);
       st->pass_dv = 0;
       st->pass_de = 0;
       st->pass_tests = 0;
       st->ticket = 0;
-      st->cont = cont;
       __threadfence();
       if (p.use_cond) cudaGraphSetConditional(p.cond, cont ? 1u : 0u);
     }
   }
 }
 
-__global__ void begin_run_kernel(DevState *st, int64_t max_sweeps) {
+__global__ void begin_run_kernel(DevState *st, int64_t max_sweeps, int64_t passes0) {
   st->status = KZ_OK;
   st->cont = 1;
   st->sweeps = 0;
-  st->passes = 0;
+  st->passes = passes0;
   st->tests = 0;
   st->max_sweeps = max_sweeps;
   st->pass_dv = st->pass_de = st->pass_tests = 0;
@@ -507,8 +411,12 @@ kz_status bitset_finish_load(kz_graph g, cudaStream_t s) {
   KZ_TRY(graph_alloc(g, &g->A[0], (size_t)g->n * g->ldw, s));
   KZ_TRY(graph_alloc(g, &g->A[1], (size_t)g->n * g->ldw, s));
   KZ_TRY(graph_alloc(g, &g->v_sweep, (size_t)std::max(g->n, 1), s));
-  KZ_TRY(graph_alloc(g, &g->st, 1, s));
-  KZ_CUDA_TRY(cudaMemsetAsync(g->st, 0, sizeof(DevState), s));
+  if (!g->st) {
+    KZ_TRY(graph_alloc(g, &g->st, 1, s));
+    KZ_CUDA_TRY(cudaMemsetAsync(g->st, 0, sizeof(DevState), s));
+  }
+  KZ_TRY(cta_prepare(g, s));
+  KZ_TRY(cta_upload_descriptor(g, s));
   return bitset_reset(g, s);
 }
 
@@ -562,7 +470,7 @@ static SweepArgs make_args(kz_graph g) {
 
 // Builds (once per graph) an executable CUDA graph whose while-node runs one
 // sweep-kernel launch per pass until the kernel clears the condition.
-static kz_status build_loop_graph(kz_graph g) {
+static kz_status build_loop_graph(kz_graph g, int64_t max_sweeps) {
   int kmax = 0;
   SweepFn fn = pick_sweep(g->k, kmax);
   if (!fn) return KZ_ERR_ARG;
@@ -585,8 +493,26 @@ static kz_status build_loop_graph(kz_graph g) {
   cp.conditional.handle = handle;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
+  // run-start kernel, then the while node
+  cudaGraphNode_t bnode;
+  {
+    DevState *stp = g->st;
+    int64_t ms = max_sweeps, p0 = 0;
+    void *bargs[] = {&stp, &ms, &p0};
+    cudaKernelNodeParams bp;
+    memset((void *)&bp, 0, sizeof(bp));
+    bp.func = (void *)begin_run_kernel;
+    bp.gridDim = dim3(1);
+    bp.blockDim = dim3(1);
+    bp.kernelParams = bargs;
+    e = cudaGraphAddKernelNode(&bnode, graph, nullptr, 0, &bp);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return cuda_status(e);
+    }
+  }
   cudaGraphNode_t wnode;
-  e = cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &cp);
+  e = cudaGraphAddNode(&wnode, graph, &bnode, nullptr, 1, &cp);
   if (e != cudaSuccess) {
     cudaGraphDestroy(graph);
     return cuda_status(e);
@@ -597,7 +523,7 @@ static kz_status build_loop_graph(kz_graph g) {
   args.use_cond = 1;
   void *kargs[] = {&args};
   cudaKernelNodeParams kp;
-  memset(&kp, 0, sizeof(kp));
+  memset((void *)&kp, 0, sizeof(kp));
   kp.func = (void *)fn;
   kp.gridDim = dim3(grid);
   kp.blockDim = dim3(kSweepWarps * 32);
@@ -615,20 +541,26 @@ static kz_status build_loop_graph(kz_graph g) {
   if (e != cudaSuccess) return cuda_status(e);
   g->loop_exec = exec;
   g->loop_grid = grid;
+  g->loop_max_sweeps = max_sweeps;
   return KZ_OK;
 }
 
 kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
   int64_t max_sweeps = opt.max_sweeps > 0 ? opt.max_sweeps : (int64_t)g->n + g->m + 1;
-  begin_run_kernel<<<1, 1, 0, s>>>(g->st, max_sweeps);
+  if (g->n > 0 && opt.use_graph) {
+    // one graph launch: run-start kernel, then the while node of sweep passes
+    if (g->loop_exec && g->loop_max_sweeps != max_sweeps) {
+      cudaGraphExecDestroy(g->loop_exec);
+      g->loop_exec = nullptr;
+    }
+    if (!g->loop_exec) KZ_TRY(build_loop_graph(g, max_sweeps));
+    KZ_CUDA_TRY(cudaGraphLaunch(g->loop_exec, s));
+    return KZ_OK;
+  }
+  begin_run_kernel<<<1, 1, 0, s>>>(g->st, max_sweeps, g->n == 0 ? 1 : 0);
   KZ_CUDA_TRY(cudaGetLastError());
   if (g->n == 0) {
     // nothing to test: one empty pass
-    return KZ_OK;
-  }
-  if (opt.use_graph) {
-    if (!g->loop_exec) KZ_TRY(build_loop_graph(g));
-    KZ_CUDA_TRY(cudaGraphLaunch(g->loop_exec, s));
     return KZ_OK;
   }
   // host-driven loop: one launch per pass, the host reads the continue flag
@@ -647,6 +579,30 @@ kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
     KZ_CUDA_TRY(cudaStreamSynchronize(s));
     if (!cont) break;
   }
+  return KZ_OK;
+}
+
+kz_status bitset_begin_run(kz_graph g, int64_t max_sweeps, cudaStream_t s) {
+  begin_run_kernel<<<1, 1, 0, s>>>(g->st, max_sweeps, g->n == 0 ? 1 : 0);
+  return cuda_status(cudaGetLastError());
+}
+
+kz_status bitset_one_pass(kz_graph g, cudaStream_t s, int *cont) {
+  *cont = 0;
+  if (g->n == 0) return KZ_OK;
+  int kmax = 0;
+  SweepFn fn = pick_sweep(g->k, kmax);
+  if (!fn) return KZ_ERR_ARG;
+  int grid = 0;
+  size_t smem = 0;
+  KZ_TRY(launch_config(g, fn, kmax, grid, smem));
+  SweepArgs args = make_args(g);
+  fn<<<grid, kSweepWarps * 32, smem, s>>>(args);
+  KZ_CUDA_TRY(cudaGetLastError());
+  int32_t c = 0;
+  KZ_CUDA_TRY(cudaMemcpyAsync(&c, &g->st->cont, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  KZ_CUDA_TRY(cudaStreamSynchronize(s));
+  *cont = c;
   return KZ_OK;
 }
 

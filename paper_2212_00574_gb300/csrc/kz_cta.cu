@@ -1,0 +1,407 @@
+// kz_cta.cu -- whole-fixpoint-in-one-CTA kernel: the small-graph path and
+// the batched persistent launch.
+//
+// One CTA runs every Jacobi pass of one graph (thesis Section 4.2 rules, see
+// kz_rules.cuh) with __syncthreads() between passes, so no pass needs a new
+// launch and no CTA ever waits on another.  A persistent grid (one CTA per
+// SM) pulls graphs from an atomic queue in longest-first order.  A graph
+// whose two ping-pong copies fit in shared memory is copied in once and
+// swept there ("shared" mode); a larger one is swept in place in its global
+// ping-pong buffers ("global" mode, L2-resident for the sizes of a batch).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "kz_internal.cuh"
+#include "kz_rules.cuh"
+
+namespace kz {
+
+constexpr int kCtaThreads = 512;
+constexpr int kCtaWarps = kCtaThreads / 32;
+
+struct CtaArgs {
+  const CtaGraph *graphs;
+  const int32_t *order;   // queue order (longest first)
+  int32_t count;
+  unsigned int *queue;    // next queue slot; null: CTA b takes order[b] only
+  int32_t smem_words;     // dynamic shared memory available, in words
+  int64_t max_sweeps;     // option value; <= 0 means n + m + 1 per graph
+};
+
+// First pair index of the warp's share, then the block X holding it.
+__device__ __forceinline__ int find_x(const int32_t *__restrict__ pair_off, int nb, int64_t p) {
+  int lo = 0, hi = nb;  // pair_off[lo] <= p < pair_off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pair_off[mid] <= p) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <int KMAX, bool SHARED>
+__device__ void cta_fixpoint(const CtaGraph &G, int64_t max_sweeps, uint32_t *smem, unsigned long long *s_cnt,
+                             int *s_flag) {
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int k = G.k, ldw = G.ldw, nb = G.nb;
+  DevState *st = G.st;
+  int cur = st->cur;
+  const size_t words = (size_t)G.n * ldw;
+
+  uint32_t *Ac, *An, *Vc, *Vn;
+  if (SHARED) {
+    Ac = smem;
+    An = smem + words;
+    Vc = An + words;
+    Vn = Vc + ldw;
+    const uint32_t *src = cur ? G.A1 : G.A0;
+    const uint32_t *vsrc = cur ? G.V1 : G.V0;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *a4 = reinterpret_cast<uint4 *>(Ac);
+    uint4 *n4 = reinterpret_cast<uint4 *>(An);
+    for (size_t i = tid; i < words / 4; i += kCtaThreads) {
+      const uint4 w = s4[i];
+      a4[i] = w;
+      n4[i] = w;
+    }
+    for (int i = tid; i < ldw; i += kCtaThreads) {
+      Vc[i] = vsrc[i];
+      Vn[i] = vsrc[i];
+    }
+  } else {
+    Ac = cur ? G.A1 : G.A0;
+    An = cur ? G.A0 : G.A1;
+    Vc = cur ? G.V1 : G.V0;
+    Vn = cur ? G.V0 : G.V1;
+  }
+  if (tid == 0) {
+    st->status = KZ_OK;
+    st->sweeps = 0;
+    st->passes = G.n == 0 ? 1 : 0;
+    st->tests = 0;
+    st->max_sweeps = max_sweeps > 0 ? max_sweeps : (int64_t)G.n + G.m + 1;
+    s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
+  }
+  __syncthreads();
+  if (G.n == 0) return;
+
+  const int64_t npairs = G.pair_off[nb];
+  const int64_t share = (npairs + kCtaWarps - 1) / kCtaWarps;
+  for (;;) {
+    const int64_t sweep_no = st->sweeps;
+    unsigned long long my_tests = 0, my_de = 0, my_dv = 0;
+    // vertex rule, one warp per block
+    for (int x = warp; x < nb; x += kCtaWarps) {
+      const BlockDesc X = G.blocks[x];
+      const bool valid_u = lane < X.size;
+      const int u = X.base + lane;
+      const uint32_t *rowu = Ac + (size_t)(valid_u ? u : X.base) * ldw;
+      uint32_t Fu[KMAX];
+      load_plane0<KMAX>(Fu, rowu, k, valid_u);
+      const int wx = X.r * k + X.c;
+      const uint32_t vword = Vc[wx];
+      const bool live = valid_u && ((vword >> lane) & 1u);
+      int cnt = plane0_vertex_cover<KMAX>(Fu, k, X.c);
+      if (live && cnt < k - 1) cnt = exact_vertex_cover_row(rowu, k, G.rounds, X.c);
+      const bool fail = live && cnt < k - 1;
+      const uint32_t failmask = __ballot_sync(0xffffffffu, fail);
+      if (lane == 0) {
+        Vn[wx] = vword & ~failmask;
+        my_dv += __popc(failmask);
+      }
+      if (fail && G.v_sweep) G.v_sweep[u] = (int32_t)(sweep_no + 1);
+    }
+    // edge rule over the warp's contiguous share of block pairs
+    const int64_t p0 = (int64_t)warp * share;
+    const int64_t p1 = min(npairs, p0 + share);
+    if (p0 < p1) {
+      int x = find_x(G.pair_off, nb, p0);
+      BlockDesc X = G.blocks[x];
+      int ybeg = G.boff[X.c + 1];
+      bool valid_u = lane < X.size;
+      int u = X.base + lane;
+      const uint32_t *rowu = Ac + (size_t)(valid_u ? u : X.base) * ldw;
+      uint32_t Fu[KMAX], P[KMAX];
+      load_plane0<KMAX>(Fu, rowu, k, valid_u);
+      int prev_cv = -1;
+      for (int64_t p = p0; p < p1; p++) {
+        while (p >= G.pair_off[x + 1]) {
+          x++;
+          X = G.blocks[x];
+          ybeg = G.boff[X.c + 1];
+          valid_u = lane < X.size;
+          u = X.base + lane;
+          rowu = Ac + (size_t)(valid_u ? u : X.base) * ldw;
+          load_plane0<KMAX>(Fu, rowu, k, valid_u);
+          prev_cv = -1;
+        }
+        const BlockDesc Y = G.blocks[ybeg + (int)(p - G.pair_off[x])];
+        if (Y.c != prev_cv) {
+          pair_mask<KMAX>(P, k, X.c, Y.c);
+          prev_cv = Y.c;
+        }
+        const int wy = Y.r * k + Y.c;
+        const uint32_t adjw = valid_u ? rowu[wy] : 0u;
+        my_tests += __popc(adjw);
+        const uint32_t *Ybase = Ac + (size_t)Y.base * ldw;
+        const uint32_t del = edge_rule_block<KMAX>(
+            Fu, P, rowu, adjw, k, G.rounds, X.c, Y.c,
+            [&](int b) { return Ybase + (size_t)b * ldw; },
+            [&](int b) { return Ybase + (size_t)b * ldw; });
+        if (valid_u) An[(size_t)u * ldw + wy] = adjw & ~del;
+        my_de += __popc(del);
+        const uint32_t delT = transpose_deletions(del);
+        if (lane < Y.size) {
+          const size_t wi = (size_t)(Y.base + lane) * ldw + X.r * k + X.c;
+          An[wi] = Ac[wi] & ~delT;
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      my_tests += __shfl_down_sync(0xffffffffu, my_tests, o);
+      my_de += __shfl_down_sync(0xffffffffu, my_de, o);
+      my_dv += __shfl_down_sync(0xffffffffu, my_dv, o);
+    }
+    if (lane == 0) {
+      if (my_tests) atomicAdd(&s_cnt[0], my_tests);
+      if (my_de) atomicAdd(&s_cnt[1], my_de);
+      if (my_dv) atomicAdd(&s_cnt[2], my_dv);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      *s_flag = finish_pass(st, s_cnt[2], s_cnt[1], s_cnt[0]);
+      s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
+    }
+    __syncthreads();
+    if (!*s_flag) break;
+    uint32_t *t = Ac;
+    Ac = An;
+    An = t;
+    t = Vc;
+    Vc = Vn;
+    Vn = t;
+    __syncthreads();
+  }
+  if (SHARED) {
+    // hand the final state back through buffer 0
+    uint4 *d4 = reinterpret_cast<uint4 *>(G.A0);
+    const uint4 *a4 = reinterpret_cast<const uint4 *>(Ac);
+    for (size_t i = tid; i < words / 4; i += kCtaThreads) d4[i] = a4[i];
+    for (int i = tid; i < ldw; i += kCtaThreads) G.V0[i] = Vc[i];
+    __syncthreads();
+    if (tid == 0) st->cur = 0;
+  }
+  // global mode: finish_pass already left st->cur on the live buffer
+  __syncthreads();
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(kCtaThreads, 1) cta_fixpoint_kernel(CtaArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ unsigned long long s_cnt[3];
+  __shared__ int s_flag;
+  __shared__ int s_g;
+  for (int round = 0;; round++) {
+    if (threadIdx.x == 0) s_g = a.queue ? (int)atomicAdd(a.queue, 1u) : (round == 0 ? (int)blockIdx.x : a.count);
+    __syncthreads();
+    const int g = s_g;
+    __syncthreads();
+    if (g >= a.count) break;
+    const CtaGraph G = a.graphs[a.order[g]];
+    if (G.k > KMAX) continue;  // never scheduled: the host groups graphs by KMAX
+    if (G.smem_words > 0 && G.smem_words <= a.smem_words)
+      cta_fixpoint<KMAX, true>(G, a.max_sweeps, smem, s_cnt, &s_flag);
+    else
+      cta_fixpoint<KMAX, false>(G, a.max_sweeps, smem, s_cnt, &s_flag);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+typedef void (*CtaFn)(CtaArgs);
+
+static CtaFn pick_cta(int k, int &kmax) {
+  if (k <= 8) { kmax = 8; return cta_fixpoint_kernel<8>; }
+  if (k <= 16) { kmax = 16; return cta_fixpoint_kernel<16>; }
+  if (k <= 32) { kmax = 32; return cta_fixpoint_kernel<32>; }
+  kmax = 64;
+  return cta_fixpoint_kernel<64>;
+}
+
+static int device_smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
+// Shared memory words a graph needs for the shared mode (two copies of the
+// rows and of the live words).
+size_t cta_smem_words(kz_graph g) { return 2 * ((size_t)g->n * g->ldw + (size_t)g->ldw); }
+
+kz_status cta_prepare(kz_graph g, cudaStream_t s) {
+  // prefix of the block pairs (x, y) with class(x) < class(y)
+  const int nb = (int)g->blocks.size();
+  std::vector<int32_t> poff((size_t)nb + 1, 0);
+  for (int x = 0; x < nb; x++) poff[x + 1] = poff[x] + (nb - g->boff[g->blocks[x].c + 1]);
+  KZ_TRY(graph_alloc(g, &g->d_pair_off, (size_t)nb + 1, s));
+  KZ_CUDA_TRY(cudaMemcpyAsync(g->d_pair_off, poff.data(), sizeof(int32_t) * (nb + 1),
+                              cudaMemcpyHostToDevice, s));
+  KZ_TRY(graph_alloc(g, &g->d_boff, (size_t)g->k + 1, s));
+  KZ_CUDA_TRY(cudaMemcpyAsync(g->d_boff, g->boff.data(), sizeof(int32_t) * (g->k + 1),
+                              cudaMemcpyHostToDevice, s));
+  g->n_pairs = poff[nb];
+  return KZ_OK;
+}
+
+static CtaGraph describe(kz_graph g, int64_t max_sweeps);
+
+// Descriptor of the graph for single-graph in-CTA launches (needs every
+// buffer of the graph allocated).
+kz_status cta_upload_descriptor(kz_graph g, cudaStream_t s) {
+  CtaGraph *d = nullptr;
+  KZ_TRY(graph_alloc(g, &d, 1, s));
+  g->d_cta_desc = d;
+  KZ_TRY(graph_alloc(g, &g->d_zero, 4, s));
+  KZ_CUDA_TRY(cudaMemsetAsync(g->d_zero, 0, 16, s));
+  CtaGraph h = describe(g, 0);
+  KZ_CUDA_TRY(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+  // the host struct is a local: wait for the copy
+  KZ_CUDA_TRY(cudaStreamSynchronize(s));
+  return KZ_OK;
+}
+
+static CtaGraph describe(kz_graph g, int64_t max_sweeps) {
+  CtaGraph d;
+  memset(&d, 0, sizeof(d));
+  d.A0 = g->A[0];
+  d.A1 = g->A[1];
+  d.V0 = g->V[0];
+  d.V1 = g->V[1];
+  d.v_sweep = g->v_sweep;
+  d.st = g->st;
+  d.blocks = g->d_blocks;
+  d.rounds = g->d_rounds;
+  d.pair_off = g->d_pair_off;
+  d.boff = g->d_boff;
+  d.n = g->n;
+  d.k = g->k;
+  d.ldw = g->ldw;
+  d.nb = (int32_t)g->blocks.size();
+  const size_t sw = cta_smem_words(g);
+  d.smem_words = sw > (size_t)INT32_MAX ? -1 : (int32_t)sw;
+  (void)max_sweeps;
+  d.m = g->m;
+  // cost estimate for the queue order: block pairs x class words
+  d.cost = (int64_t)g->n_pairs * 32 * g->k + (int64_t)g->blocks.size() * g->k;
+  return d;
+}
+
+bool cta_fits_shared(kz_graph g) {
+  const size_t limit = (size_t)(device_smem_optin() / 4);
+  return cta_smem_words(g) * 4 + 64 <= limit * 4;
+}
+
+// Kernelizes `count` graphs with persistent launches, one per KMAX group
+// (one launch when every k <= 32, as in a batch of k-partite graphs).
+kz_status cta_kernelize(kz_graph *gs, int count, const kz_options &opt, cudaStream_t s,
+                        int force_mode) {
+  if (count <= 0) return KZ_OK;
+  const int optin = device_smem_optin();
+  std::vector<CtaGraph> desc((size_t)count);
+  for (int i = 0; i < count; i++) {
+    desc[i] = describe(gs[i], opt.max_sweeps);
+    if (force_mode == 0) desc[i].smem_words = -1;  // global mode everywhere
+  }
+  // group by KMAX, longest first inside a group
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  CtaGraph *d_desc = (CtaGraph *)dev_alloc(sizeof(CtaGraph) * count, s);
+  int32_t *d_order = (int32_t *)dev_alloc(sizeof(int32_t) * count, s);
+  unsigned int *d_queue = (unsigned int *)dev_alloc(64, s);
+  kz_status st = (d_desc && d_order && d_queue) ? KZ_OK : KZ_ERR_OOM;
+  if (st == KZ_OK)
+    st = cuda_status(cudaMemcpyAsync(d_desc, desc.data(), sizeof(CtaGraph) * count,
+                                     cudaMemcpyHostToDevice, s));
+  if (st == KZ_OK) st = cuda_status(cudaMemsetAsync(d_queue, 0, 64, s));
+  std::vector<int32_t> order;
+  int group = 0;
+  for (int kmax_want : {8, 16, 32, 64}) {
+    if (st != KZ_OK) break;
+    std::vector<int32_t> idx;
+    for (int i = 0; i < count; i++) {
+      int km = 0;
+      pick_cta(desc[i].k, km);
+      if (km == kmax_want) idx.push_back(i);
+    }
+    if (idx.empty()) continue;
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return desc[a].cost > desc[b].cost; });
+    const size_t off = order.size();
+    order.insert(order.end(), idx.begin(), idx.end());
+    int km = 0;
+    CtaFn fn = pick_cta(desc[idx[0]].k, km);
+    const int smem_bytes = std::max(0, optin - 1024);  // static shared memory of the kernel
+    st = cuda_status(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          smem_bytes));
+    if (st != KZ_OK) break;
+    CtaArgs a;
+    a.graphs = d_desc;
+    a.order = d_order + off;
+    a.count = (int32_t)idx.size();
+    a.queue = d_queue + 4 * group;  // each group its own 16-byte counter
+    a.smem_words = smem_bytes / 4;
+    a.max_sweeps = opt.max_sweeps;
+    const int grid = std::max(1, std::min<int>((int)idx.size(), sms));
+    // order slice must be on the device before the launch
+    st = cuda_status(cudaMemcpyAsync(d_order + off, order.data() + off, sizeof(int32_t) * idx.size(),
+                                     cudaMemcpyHostToDevice, s));
+    if (st != KZ_OK) break;
+    fn<<<grid, kCtaThreads, smem_bytes, s>>>(a);
+    st = cuda_status(cudaGetLastError());
+    group++;
+  }
+  // (pageable host-to-device copies return once the source is staged, so
+  // the host vectors may go out of scope here)
+  if (d_desc) dev_free(d_desc, sizeof(CtaGraph) * count, s);
+  if (d_order) dev_free(d_order, sizeof(int32_t) * count, s);
+  if (d_queue) dev_free(d_queue, 64, s);
+  return st;
+}
+
+static bool configure_once(CtaFn fn, int kmax, int bytes) {
+  static bool done[4] = {false, false, false, false};
+  const int slot = kmax == 8 ? 0 : kmax == 16 ? 1 : kmax == 32 ? 2 : 3;
+  if (done[slot]) return true;
+  if (cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+      cudaSuccess)
+    return false;
+  done[slot] = true;
+  return true;
+}
+
+kz_status cta_kernelize_one(kz_graph g, const kz_options &opt, cudaStream_t s) {
+  int km = 0;
+  CtaFn fn = pick_cta(g->k, km);
+  const int smem_bytes = std::max(0, device_smem_optin() - 1024);
+  if (!configure_once(fn, km, smem_bytes)) return KZ_ERR_CUDA;
+  CtaArgs a;
+  a.graphs = g->d_cta_desc;
+  a.order = g->d_zero;
+  a.count = 1;
+  a.queue = nullptr;
+  a.smem_words = smem_bytes / 4;
+  a.max_sweeps = opt.max_sweeps;
+  fn<<<1, kCtaThreads, smem_bytes, s>>>(a);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace kz

@@ -69,11 +69,31 @@ struct DevState {
   int64_t trace_de[kTraceCap];
 };
 
+// Per-graph descriptor of the whole-fixpoint-in-one-CTA kernel.
+struct CtaGraph {
+  uint32_t *A0, *A1;      // ping-pong adjacency rows
+  uint32_t *V0, *V1;      // ping-pong vertex live words
+  int32_t *v_sweep;
+  DevState *st;
+  const BlockDesc *blocks;
+  const int32_t *rounds;
+  const int32_t *pair_off;  // nb + 1 prefix of block pairs per x
+  const int32_t *boff;      // k + 1 first block of each class
+  int32_t n, k, ldw, nb;
+  int32_t smem_words;       // words the shared mode needs (-1: too many)
+  int32_t pad;
+  int64_t m;                // edges (default sweep limit n + m + 1)
+  int64_t cost;
+};
+
 // Device allocation through the registered allocator.
 void *dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void *p, size_t bytes, cudaStream_t s);
 
 }  // namespace kz
+
+namespace kz { struct CtaGraph; }
+typedef kz::CtaGraph *CtaGraphPtr;
 
 // The handle behind kz_graph.
 struct kz_graph_s {
@@ -104,15 +124,51 @@ struct kz_graph_s {
   int32_t *v_sweep = nullptr;  // n (relabelled ids)
   int32_t *d_rounds = nullptr; // k
   int32_t *d_coff = nullptr;   // k + 1
+  int32_t *d_boff = nullptr;   // k + 1
+  int32_t *d_pair_off = nullptr;  // blocks + 1
+  int64_t n_pairs = 0;
+  CtaGraphPtr d_cta_desc = nullptr;  // this graph's in-CTA descriptor
+  int32_t *d_zero = nullptr;         // a device 0 (queue order of a single graph)
   int32_t *d_perm = nullptr;   // n
   kz::BlockDesc *d_blocks = nullptr;
   kz::WorkItem *d_items = nullptr;
   int32_t n_items = 0;
   kz::DevState *st = nullptr;
 
+  // which representation holds the live state: KZ_PATH_BITSET (bitset rows,
+  // also used by the in-CTA path) or KZ_PATH_SPARSE (CSR flags)
+  bool has_bitset = false;
+  bool has_csr = false;
+  int32_t owner = KZ_PATH_BITSET;
+  int32_t *d_inv = nullptr;    // caller id -> relabelled id (bitset layout)
+
+  // CSR path (caller ids)
+  int64_t *sp_row0 = nullptr;  // n + 1, all edges
+  int32_t *sp_adj0 = nullptr, *sp_eid0 = nullptr;
+  int64_t *sp_row[2] = {nullptr, nullptr};  // compacted live rows (ping-pong)
+  int32_t *sp_adj[2] = {nullptr, nullptr};
+  int32_t *sp_eid[2] = {nullptr, nullptr};
+  uint8_t *sp_elive[2] = {nullptr, nullptr};
+  uint8_t *sp_vlive[2] = {nullptr, nullptr};
+  int32_t sp_cur = 0;
+  int64_t *sp_orow = nullptr;  // oriented live CSR
+  int32_t *sp_oadj = nullptr, *sp_oeid = nullptr, *sp_osrc = nullptr;
+  int32_t *sp_eu = nullptr, *sp_ev = nullptr;  // canonical sorted edges
+  int32_t *sp_col = nullptr, *sp_rank = nullptr;
+  unsigned long long *sp_mask = nullptr;
+  int32_t *sp_cnt_live = nullptr, *sp_cnt_or = nullptr;
+  int64_t *sp_sums = nullptr, *sp_totals = nullptr;
+  int32_t *sp_v_sweep = nullptr;
+
+  // learned schedule: attached model, threshold, per-graph scratch
+  struct kz_model_s *model = nullptr;
+  float learned_threshold = 0.5f;
+  void *learned_bufs = nullptr;
+
   // executable CUDA graph of the device-side sweep loop (built lazily)
   cudaGraphExec_t loop_exec = nullptr;
   int loop_grid = 0;
+  int64_t loop_max_sweeps = 0;
 
   // every device allocation, for kz_free_graph
   struct Alloc { void *p; size_t bytes; };
@@ -133,6 +189,40 @@ kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s);
 kz_status bitset_unpack_dense(kz_graph g, uint64_t *d_out, int64_t row_words,
                               unsigned long long *d_edge_count, cudaStream_t s);
 kz_status bitset_vertex_alive(kz_graph g, uint8_t *host_alive, int64_t *n_live);
+
+// One plain multi-CTA sweep pass (no loop graph); *cont = 1 when it deleted
+// something and another pass should follow.
+kz_status bitset_one_pass(kz_graph g, cudaStream_t s, int *cont);
+// Run start (counters zero, sweep limit) without a pass.
+kz_status bitset_begin_run(kz_graph g, int64_t max_sweeps, cudaStream_t s);
+
+// Learned schedule (kz_learned.cu).
+kz_status learned_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s);
+void learned_release(kz_graph g);
+
+// Whole-fixpoint-in-one-CTA kernel (kz_cta.cu).
+kz_status cta_prepare(kz_graph g, cudaStream_t s);
+kz_status cta_upload_descriptor(kz_graph g, cudaStream_t s);
+bool cta_fits_shared(kz_graph g);
+// force_mode: 1 = shared mode where it fits, 0 = global mode for every graph
+kz_status cta_kernelize(kz_graph *gs, int count, const kz_options &opt, cudaStream_t s, int force_mode);
+// One graph, one CTA, no allocation or copy per call.
+kz_status cta_kernelize_one(kz_graph g, const kz_options &opt, cudaStream_t s);
+
+// CSR path (kz_sparse.cu).
+kz_status sparse_load(kz_graph g, const int32_t *colour, int64_t m, const int32_t *edges, bool dedup,
+                      cudaStream_t s);
+kz_status sparse_reset(kz_graph g, cudaStream_t s);
+kz_status sparse_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s);
+kz_status sparse_fetch(kz_graph g, uint8_t *vertex_alive, int32_t *edges_out, int64_t cap, int64_t *m_live);
+kz_status sparse_vertex_alive(kz_graph g, uint8_t *host_alive, int64_t *n_live);
+kz_status sparse_v_sweep(kz_graph g, int32_t *host);
+// Move the live state between the two representations.
+kz_status state_to_sparse(kz_graph g, cudaStream_t s);
+kz_status state_to_bitset(kz_graph g, cudaStream_t s);
+
+// Batched Jacobi loop over many graphs (kz_batch.cu); every k <= 32.
+kz_status batch_kernelize(kz_graph *gs, int count, const kz_options &opt, cudaStream_t s);
 
 // Allocation bookkeeping on the handle.
 template <class T>

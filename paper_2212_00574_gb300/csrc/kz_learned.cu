@@ -1,0 +1,827 @@
+// kz_learned.cu -- the learned schedule (include/kz_learned.h): an edge-
+// scoring MLP with hand-written forward / backward / Adam kernels, a trace
+// collector for its training data, and the worklist schedule that uses it.
+//
+// The schedule never changes the kernel (thesis Section 4.2 rules): every
+// deletion it makes is of an element that fails its rule on the current
+// graph, and it stops only after a full plain sweep deletes nothing, so the
+// result is the unique greatest fixpoint.
+//
+// Round structure of a learned kernelization (bitset rows):
+//   1. one full plain Jacobi sweep (the multi-CTA sweep kernel);
+//   2. learned rounds: per-vertex statistics of the live graph (degree,
+//      colour cover, smallest class count; the vertex rule falls out of them);
+//      the frontier = live edges at a vertex whose live degree changed since
+//      the previous round (no other edge can have started to fail); the MLP
+//      scores the frontier and only edges above the threshold are tested
+//      (warp per edge, exact over all planes); failing vertices and edges are
+//      removed in place;
+//   3. when a learned round finds nothing, a full plain sweep certifies; if it
+//      deletes something, learned rounds resume.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/kz_learned.h"
+#include "kz_internal.cuh"
+#include "kz_rules.cuh"
+
+struct kz_model_s {
+  float *w32 = nullptr;          // fp32 master weights
+  __nv_bfloat16 *w16 = nullptr;  // bf16 inference copy
+  float *m = nullptr, *v = nullptr;
+  int64_t t = 0;
+  int device = 0;
+};
+
+namespace kz {
+namespace learned {
+
+constexpr int F = KZ_MLP_FEATURES;
+constexpr int H = KZ_MLP_HIDDEN;
+constexpr int P = KZ_MLP_PARAMS;
+// offsets of the weight blocks in the flat array
+constexpr int oW1 = 0, ob1 = oW1 + H * F, oW2 = ob1 + H, ob2 = oW2 + H * H, ow3 = ob2 + H, ob3 = ow3 + H;
+static_assert(ob3 + 1 == P, "weight layout");
+
+// ---------------------------------------------------------------------------
+// MLP kernels
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float mlp_logit(const float *__restrict__ w, const float *x) {
+  float h1[H];
+#pragma unroll
+  for (int j = 0; j < H; j++) {
+    float a = w[ob1 + j];
+#pragma unroll
+    for (int i = 0; i < F; i++) a = fmaf(w[oW1 + j * F + i], x[i], a);
+    h1[j] = fmaxf(a, 0.f);
+  }
+  float out = w[ob3];
+  for (int j = 0; j < H; j++) {
+    float a = w[ob2 + j];
+#pragma unroll
+    for (int i = 0; i < H; i++) a = fmaf(w[oW2 + j * H + i], h1[i], a);
+    out = fmaf(w[ow3 + j], fmaxf(a, 0.f), out);
+  }
+  return out;
+}
+
+// bf16 weights widened into shared memory once per block; fp32 arithmetic.
+__global__ void mlp_forward_kernel(const __nv_bfloat16 *__restrict__ w16, const float *__restrict__ X, int64_t B,
+                                   float *__restrict__ logits) {
+  __shared__ float w[P];
+  for (int i = threadIdx.x; i < P; i += blockDim.x) w[i] = __bfloat162float(w16[i]);
+  __syncthreads();
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < B; s += (int64_t)gridDim.x * blockDim.x) {
+    float x[F];
+#pragma unroll
+    for (int i = 0; i < F; i++) x[i] = X[s * F + i];
+    logits[s] = mlp_logit(w, x);
+  }
+}
+
+constexpr int kGradThreads = 64;
+
+// Mean BCE and its gradient for one chunk of kGradThreads samples per block:
+// per-sample deltas go to shared memory, then the block forms the weight
+// gradients as sums of outer products and adds them to the global gradient.
+__global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(const float *__restrict__ w32,
+                                                                 const float *__restrict__ X,
+                                                                 const float *__restrict__ y, int64_t B,
+                                                                 float *__restrict__ grad, float *__restrict__ loss) {
+  extern __shared__ float sm[];
+  float *w = sm;                          // P
+  float *sx = w + P;                      // [T][F]
+  float *sh1 = sx + kGradThreads * F;     // [T][H]
+  float *sh2 = sh1 + kGradThreads * H;    // [T][H]
+  float *sdz1 = sh2 + kGradThreads * H;   // [T][H]
+  float *sdz2 = sdz1 + kGradThreads * H;  // [T][H]
+  float *sdl = sdz2 + kGradThreads * H;   // [T]
+  const int t = threadIdx.x;
+  for (int i = t; i < P; i += kGradThreads) w[i] = w32[i];
+  __syncthreads();
+  const int64_t s = blockIdx.x * (int64_t)kGradThreads + t;
+  const bool valid = s < B;
+  float x[F];
+#pragma unroll
+  for (int i = 0; i < F; i++) x[i] = valid ? X[s * F + i] : 0.f;
+  float z1[H], h2[H], z2[H];
+#pragma unroll
+  for (int j = 0; j < H; j++) {
+    float a = w[ob1 + j];
+#pragma unroll
+    for (int i = 0; i < F; i++) a = fmaf(w[oW1 + j * F + i], x[i], a);
+    z1[j] = a;
+  }
+  float out = w[ob3];
+  for (int j = 0; j < H; j++) {
+    float a = w[ob2 + j];
+#pragma unroll
+    for (int i = 0; i < H; i++) a = fmaf(w[oW2 + j * H + i], fmaxf(z1[i], 0.f), a);
+    z2[j] = a;
+    h2[j] = fmaxf(a, 0.f);
+    out = fmaf(w[ow3 + j], h2[j], out);
+  }
+  const float yy = valid ? y[s] : 0.f;
+  const float sig = 1.f / (1.f + expf(-out));
+  const float dl = valid ? (sig - yy) / (float)B : 0.f;
+  const float term = valid ? (fmaxf(out, 0.f) - out * yy + log1pf(expf(-fabsf(out)))) / (float)B : 0.f;
+  float dz2[H];
+#pragma unroll
+  for (int j = 0; j < H; j++) dz2[j] = z2[j] > 0.f ? dl * w[ow3 + j] : 0.f;
+  for (int i = 0; i < H; i++) {
+    float a = 0.f;
+#pragma unroll
+    for (int j = 0; j < H; j++) a = fmaf(w[oW2 + j * H + i], dz2[j], a);
+    sdz1[t * H + i] = z1[i] > 0.f ? a : 0.f;
+    sh1[t * H + i] = fmaxf(z1[i], 0.f);
+  }
+#pragma unroll
+  for (int j = 0; j < H; j++) {
+    sh2[t * H + j] = h2[j];
+    sdz2[t * H + j] = dz2[j];
+  }
+#pragma unroll
+  for (int i = 0; i < F; i++) sx[t * F + i] = x[i];
+  sdl[t] = dl;
+  // block sum of the loss terms
+  float lt = term;
+  for (int o = 16; o > 0; o >>= 1) lt += __shfl_down_sync(0xffffffffu, lt, o);
+  if ((t & 31) == 0) atomicAdd(loss, lt);
+  __syncthreads();
+  // dW2[j][i] = sum_s dz2[s][j] h1[s][i]
+  for (int e = t; e < H * H; e += kGradThreads) {
+    const int j = e / H, i = e % H;
+    float a = 0.f;
+    for (int q = 0; q < kGradThreads; q++) a = fmaf(sdz2[q * H + j], sh1[q * H + i], a);
+    atomicAdd(&grad[oW2 + e], a);
+  }
+  // dW1[j][i] = sum_s dz1[s][j] x[s][i]
+  for (int e = t; e < H * F; e += kGradThreads) {
+    const int j = e / F, i = e % F;
+    float a = 0.f;
+    for (int q = 0; q < kGradThreads; q++) a = fmaf(sdz1[q * H + j], sx[q * F + i], a);
+    atomicAdd(&grad[oW1 + e], a);
+  }
+  for (int j = t; j < H; j += kGradThreads) {
+    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    for (int q = 0; q < kGradThreads; q++) {
+      a1 += sdz1[q * H + j];
+      a2 += sdz2[q * H + j];
+      a3 = fmaf(sdl[q], sh2[q * H + j], a3);
+    }
+    atomicAdd(&grad[ob1 + j], a1);
+    atomicAdd(&grad[ob2 + j], a2);
+    atomicAdd(&grad[ow3 + j], a3);
+  }
+  if (t == 0) {
+    float a = 0.f;
+    for (int q = 0; q < kGradThreads; q++) a += sdl[q];
+    atomicAdd(&grad[ob3], a);
+  }
+}
+
+__global__ void adam_kernel(float *__restrict__ w32, __nv_bfloat16 *__restrict__ w16, float *__restrict__ m,
+                            float *__restrict__ v, const float *__restrict__ g, float lr, float bc1, float bc2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = 0.9f * m[i] + 0.1f * gi;
+    const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w32[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+    w32[i] = wi;
+    w16[i] = __float2bfloat16(wi);
+  }
+}
+
+__global__ void to_bf16_kernel(const float *__restrict__ w32, __nv_bfloat16 *__restrict__ w16) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x)
+    w16[i] = __float2bfloat16(w32[i]);
+}
+
+// ---------------------------------------------------------------------------
+// per-vertex statistics of the live graph (bitset rows)
+// ---------------------------------------------------------------------------
+
+struct Stats {
+  int32_t *deg;       // live degree
+  int32_t *prevdeg;   // live degree at the previous round
+  int32_t *cover;     // classes other than own with a live neighbour
+  int32_t *minc;      // smallest neighbour count over the other classes
+  uint8_t *vfail;     // vertex rule fails on this snapshot
+  uint8_t *changed;   // live degree changed since the previous round
+};
+
+struct RowView {
+  uint32_t *A;        // current rows (updated in place by learned rounds)
+  uint32_t *V;        // current live words
+  int32_t n, k, ldw, R;
+  const int32_t *col;   // relabelled colour
+  const int32_t *coff;  // k + 1
+};
+
+__device__ __forceinline__ bool vertex_live(const RowView &r, int x) {
+  const int c = r.col[x], i = x - r.coff[c];
+  return (r.V[(i >> 5) * r.k + c] >> (i & 31)) & 1u;
+}
+
+// One warp per vertex; per-class neighbour counts in shared memory.
+__global__ void stats_kernel(RowView r, Stats s, int first_round, unsigned long long *dv_out) {
+  __shared__ int cls[8][64];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long dv = 0;
+  for (int64_t x = warp0; x < r.n; x += warps) {
+    for (int c = lane; c < 64; c += 32) cls[wib][c] = 0;
+    __syncwarp();
+    const uint32_t *row = r.A + x * r.ldw;
+    const int rk = r.R * r.k;
+    for (int w = lane; w < rk; w += 32) {
+      const uint32_t word = row[w];
+      if (word) atomicAdd(&cls[wib][w % r.k], __popc(word));
+    }
+    __syncwarp();
+    if (lane == 0) {
+      const int own = r.col[x];
+      int deg = 0, cover = 0, minc = 0x7fffffff;
+      for (int c = 0; c < r.k; c++) {
+        deg += cls[wib][c];
+        if (c == own) continue;
+        cover += cls[wib][c] > 0;
+        minc = min(minc, cls[wib][c]);
+      }
+      if (r.k == 1) minc = 0;
+      const bool live = vertex_live(r, (int)x);
+      const bool fail = live && cover < r.k - 1;
+      s.vfail[x] = fail ? 1 : 0;
+      dv += fail;
+      s.changed[x] = first_round ? 1 : (uint8_t)(deg != s.deg[x]);
+      s.prevdeg[x] = first_round ? deg : s.deg[x];
+      s.deg[x] = deg;
+      s.cover[x] = cover;
+      s.minc[x] = minc;
+    }
+    __syncwarp();
+  }
+  for (int o = 16; o > 0; o >>= 1) dv += __shfl_down_sync(0xffffffffu, dv, o);
+  if (lane == 0 && dv) atomicAdd(dv_out, dv);
+}
+
+// Frontier: live edges {x, y} with a changed endpoint, each emitted once.
+__global__ void frontier_kernel(RowView r, Stats s, int2 *__restrict__ out, unsigned long long *count,
+                                int64_t cap) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t x = warp0; x < r.n; x += warps) {
+    if (!s.changed[x]) continue;
+    const uint32_t *row = r.A + x * r.ldw;
+    const int rk = r.R * r.k;
+    for (int w0 = 0; w0 < rk; w0 += 32) {
+      const int w = w0 + lane;
+      uint32_t word = w < rk ? row[w] : 0u;
+      const int c = w % r.k, rr = w / r.k;
+      // keep y when y is unchanged or x < y (each edge once)
+      uint32_t keep = 0;
+      while (word) {
+        const int b = __ffs(word) - 1;
+        word &= word - 1;
+        const int y = r.coff[c] + 32 * rr + b;
+        if (!s.changed[y] || x < y) keep |= 1u << b;
+      }
+      const int cnt = __popc(keep);
+      int incl = cnt;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      unsigned long long base = 0;
+      if (lane == 31 && total) base = atomicAdd(count, (unsigned long long)total);
+      base = __shfl_sync(0xffffffffu, base, 31);
+      unsigned long long pos = base + (incl - cnt);
+      while (keep) {
+        const int b = __ffs(keep) - 1;
+        keep &= keep - 1;
+        if ((int64_t)pos < cap) out[pos] = make_int2((int)x, r.coff[c] + 32 * rr + b);
+        pos++;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void edge_features(const RowView &r, const Stats &s, int x, int y, int round,
+                                              float density, float live_frac, float *f) {
+  const float n = (float)max(r.n, 1);
+  const float k = (float)r.k;
+  const float du = (float)s.deg[x], dvv = (float)s.deg[y];
+  f[0] = du / n;
+  f[1] = dvv / n;
+  f[2] = ((float)s.cover[x] - (k - 1.f)) / k;
+  f[3] = ((float)s.cover[y] - (k - 1.f)) / k;
+  f[4] = (float)s.minc[x] / fmaxf(n / k, 1.f);
+  f[5] = (float)s.minc[y] / fmaxf(n / k, 1.f);
+  f[6] = (du - (float)s.prevdeg[x]) / fmaxf((float)s.prevdeg[x], 1.f);
+  f[7] = (dvv - (float)s.prevdeg[y]) / fmaxf((float)s.prevdeg[y], 1.f);
+  f[8] = k / 64.f;
+  f[9] = (float)round / 32.f;
+  f[10] = density;
+  f[11] = fminf(du, dvv) / fmaxf(fmaxf(du, dvv), 1.f);
+  f[12] = (du + dvv) / (2.f * n);
+  f[13] = log2f(n) / 16.f;
+  f[14] = live_frac;
+  f[15] = 1.f;
+}
+
+// Scores the frontier and keeps the edges above the threshold.
+__global__ void score_kernel(RowView r, Stats s, const __nv_bfloat16 *__restrict__ w16, const int2 *__restrict__ fr,
+                             const unsigned long long *__restrict__ n_fr, float logit_threshold, int round,
+                             float density, float live_frac, int2 *__restrict__ work,
+                             unsigned long long *n_work) {
+  __shared__ float w[P];
+  for (int i = threadIdx.x; i < P; i += blockDim.x) w[i] = __bfloat162float(w16[i]);
+  __syncthreads();
+  const int64_t total = (int64_t)*n_fr;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int2 e = fr[q];
+    float f[F];
+    edge_features(r, s, e.x, e.y, round, density, live_frac, f);
+    if (mlp_logit(w, f) > logit_threshold) work[atomicAdd(n_work, 1ull)] = e;
+  }
+}
+
+// Exact edge rule for listed edges, one warp per edge, all planes.
+__global__ void test_edges_kernel(RowView r, const int2 *__restrict__ work, const unsigned long long *__restrict__ n_work,
+                                  int2 *__restrict__ dead, unsigned long long *n_dead) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = (int64_t)*n_work;
+  const int rk = r.R * r.k;
+  for (int64_t q = warp0; q < total; q += warps) {
+    const int2 e = work[q];
+    const uint32_t *ru = r.A + (int64_t)e.x * r.ldw, *rv = r.A + (int64_t)e.y * r.ldw;
+    uint64_t cov = 0;
+    for (int w = lane; w < rk; w += 32)
+      if (ru[w] & rv[w]) cov |= 1ull << (w % r.k);
+    uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)cov);
+    uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(cov >> 32));
+    const uint64_t all = ((uint64_t)hi << 32) | lo;
+    const uint64_t own = (1ull << r.col[e.x]) | (1ull << r.col[e.y]);
+    if (lane == 0 && __popcll(all & ~own) < r.k - 2) dead[atomicAdd(n_dead, 1ull)] = e;
+  }
+}
+
+// Removes the failing edges and the failing vertices (with all their edges)
+// in place.
+__global__ void apply_kernel(RowView r, const uint8_t *__restrict__ vfail, const int2 *__restrict__ dead,
+                             const unsigned long long *__restrict__ n_dead) {
+  const int lane = threadIdx.x & 31;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nd = (int64_t)*n_dead;
+  for (int64_t q = tid; q < nd; q += stride) {
+    const int x = dead[q].x, y = dead[q].y;
+    const int cx = r.col[x], cy = r.col[y], ix = x - r.coff[cx], iy = y - r.coff[cy];
+    atomicAnd(&r.A[(int64_t)x * r.ldw + (iy >> 5) * r.k + cy], ~(1u << (iy & 31)));
+    atomicAnd(&r.A[(int64_t)y * r.ldw + (ix >> 5) * r.k + cx], ~(1u << (ix & 31)));
+  }
+  const int64_t warp0 = tid >> 5, warps = stride >> 5;
+  const int rk = r.R * r.k;
+  for (int64_t x = warp0; x < r.n; x += warps) {
+    if (!vfail[x]) continue;
+    const int cx = r.col[x], ix = (int)x - r.coff[cx];
+    uint32_t *row = r.A + x * r.ldw;
+    for (int w = lane; w < rk; w += 32) {
+      uint32_t word = row[w];
+      const int c = w % r.k, rr = w / r.k;
+      while (word) {
+        const int b = __ffs(word) - 1;
+        word &= word - 1;
+        const int y = r.coff[c] + 32 * rr + b;
+        atomicAnd(&r.A[(int64_t)y * r.ldw + (ix >> 5) * r.k + cx], ~(1u << (ix & 31)));
+      }
+      row[w] = 0u;
+    }
+    if (lane == 0) atomicAnd(&r.V[(ix >> 5) * r.k + cx], ~(1u << (ix & 31)));
+  }
+}
+
+// Records a learned round (no buffer flip: learned rounds work in place).
+__global__ void learned_finish_kernel(DevState *st, const unsigned long long *dv, const unsigned long long *de,
+                                      const unsigned long long *tests, int32_t *v_sweep_unused) {
+  (void)v_sweep_unused;
+  st->passes += 1;
+  st->tests += (int64_t)*tests;
+  if (*dv + *de > 0) {
+    if (st->sweeps < kTraceCap) {
+      st->trace_dv[st->sweeps] = (int64_t)*dv;
+      st->trace_de[st->sweeps] = (int64_t)*de;
+    }
+    st->sweeps += 1;
+  }
+}
+
+// Live edges counted from the rows (for the density feature and the check).
+__global__ void count_live_kernel(RowView r, unsigned long long *edges2, unsigned long long *verts) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long e = 0, v = 0;
+  const int rk = r.R * r.k;
+  for (int64_t t = tid; t < (int64_t)r.n * rk; t += stride) e += __popc(r.A[(t / rk) * r.ldw + t % rk]);
+  for (int64_t x = tid; x < r.n; x += stride) v += vertex_live(r, (int)x);
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_down_sync(0xffffffffu, e, o);
+    v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (e) atomicAdd(edges2, e);
+    if (v) atomicAdd(verts, v);
+  }
+}
+
+// Trace records: features of a hashed subsample of the live edges of this
+// sweep with the label "fails the edge rule on this snapshot".
+__global__ void trace_kernel(RowView r, Stats s, int round, float density, float live_frac, uint64_t seed,
+                             uint32_t keep_below, float *__restrict__ X, uint8_t *__restrict__ y,
+                             unsigned long long *count, int64_t cap) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int rk = r.R * r.k;
+  for (int64_t x = warp0; x < r.n; x += warps) {
+    const uint32_t *ru = r.A + x * r.ldw;
+    for (int w0 = 0; w0 < rk; w0 += 32) {
+      const int w = w0 + lane;
+      uint32_t word = w < rk ? ru[w] : 0u;
+      const int c = w % r.k, rr = w / r.k;
+      while (word) {
+        const int b = __ffs(word) - 1;
+        word &= word - 1;
+        const int yv = r.coff[c] + 32 * rr + b;
+        if (yv <= x) continue;
+        uint64_t h = seed ^ ((uint64_t)x << 32 | (uint32_t)yv) ^ ((uint64_t)round * 0x9e3779b97f4a7c15ull);
+        h ^= h >> 33;
+        h *= 0xff51afd7ed558ccdull;
+        h ^= h >> 33;
+        if ((uint32_t)(h >> 32) >= keep_below) continue;
+        // label: exact edge rule on this snapshot (serial over the rows)
+        const uint32_t *rv = r.A + (int64_t)yv * r.ldw;
+        uint64_t cov = 0;
+        for (int q = 0; q < rk; q++)
+          if (ru[q] & rv[q]) cov |= 1ull << (q % r.k);
+        const uint64_t own = (1ull << r.col[x]) | (1ull << r.col[yv]);
+        const bool fails = __popcll(cov & ~own) < r.k - 2;
+        const unsigned long long pos = atomicAdd(count, 1ull);
+        if ((int64_t)pos < cap) {
+          float f[F];
+          edge_features(r, s, (int)x, yv, round, density, live_frac, f);
+#pragma unroll
+          for (int i = 0; i < F; i++) X[pos * F + i] = f[i];
+          y[pos] = fails ? 1 : 0;
+        }
+      }
+    }
+  }
+}
+
+}  // namespace learned
+}  // namespace kz
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+using namespace kz;
+using namespace kz::learned;
+
+namespace {
+
+int sms_now() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(sms, 1);
+}
+
+// Per-graph scratch of the learned schedule (allocated on first use).
+struct LearnedBufs {
+  Stats s;
+  int2 *fr = nullptr, *work = nullptr, *dead = nullptr;
+  unsigned long long *cnt = nullptr;  // [0] frontier [1] work [2] dead [3] dv [4] edges2 [5] verts
+  int32_t *col = nullptr;
+};
+
+kz_status ensure_bufs(kz_graph g, LearnedBufs &b, cudaStream_t s) {
+  const size_t n = (size_t)std::max(g->n, 1), m = (size_t)std::max<int64_t>(g->m, 1);
+  KZ_TRY(graph_alloc(g, &b.s.deg, n, s));
+  KZ_TRY(graph_alloc(g, &b.s.prevdeg, n, s));
+  KZ_TRY(graph_alloc(g, &b.s.cover, n, s));
+  KZ_TRY(graph_alloc(g, &b.s.minc, n, s));
+  KZ_TRY(graph_alloc(g, &b.s.vfail, n, s));
+  KZ_TRY(graph_alloc(g, &b.s.changed, n, s));
+  KZ_TRY(graph_alloc(g, &b.fr, m, s));
+  KZ_TRY(graph_alloc(g, &b.work, m, s));
+  KZ_TRY(graph_alloc(g, &b.dead, m, s));
+  KZ_TRY(graph_alloc(g, &b.cnt, 8, s));
+  std::vector<int32_t> col_new((size_t)g->n);
+  for (int c = 0; c < g->k; c++)
+    for (int x = g->coff[c]; x < g->coff[c + 1]; x++) col_new[x] = c;
+  KZ_TRY(graph_alloc(g, &b.col, n, s));
+  if (g->n) KZ_CUDA_TRY(cudaMemcpyAsync(b.col, col_new.data(), 4 * (size_t)g->n, cudaMemcpyHostToDevice, s));
+  KZ_CUDA_TRY(cudaStreamSynchronize(s));
+  return KZ_OK;
+}
+
+RowView view_of(kz_graph g, const LearnedBufs &b, int cur) {
+  RowView r;
+  r.A = g->A[cur & 1];
+  r.V = g->V[cur & 1];
+  r.n = g->n;
+  r.k = g->k;
+  r.ldw = g->ldw;
+  r.R = g->R;
+  r.col = b.col;
+  r.coff = g->d_coff;
+  return r;
+}
+
+kz_status read_u64(const unsigned long long *d, unsigned long long *h, int count, cudaStream_t s) {
+  KZ_CUDA_TRY(cudaMemcpyAsync(h, d, sizeof(unsigned long long) * count, cudaMemcpyDeviceToHost, s));
+  KZ_CUDA_TRY(cudaStreamSynchronize(s));
+  return KZ_OK;
+}
+
+int32_t read_cur(kz_graph g, cudaStream_t s) {
+  int32_t cur = 0;
+  cudaMemcpyAsync(&cur, &g->st->cur, 4, cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  return cur;
+}
+
+}  // namespace
+
+namespace kz {
+
+// Learned schedule on the bitset rows (see the file comment).
+kz_status learned_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
+  if (!g->model) return KZ_ERR_UNSUPPORTED;
+  if (!g->learned_bufs) {
+    LearnedBufs *b = new LearnedBufs();
+    kz_status st = ensure_bufs(g, *b, s);
+    if (st != KZ_OK) {
+      delete b;
+      return st;
+    }
+    g->learned_bufs = b;
+  }
+  LearnedBufs &b = *static_cast<LearnedBufs *>(g->learned_bufs);
+  const int64_t max_sweeps = opt.max_sweeps > 0 ? opt.max_sweeps : (int64_t)g->n + g->m + 1;
+  const float p = std::min(std::max(g->learned_threshold, 0.f), 0.999999f);
+  const float logit_thr = p <= 0.f ? -INFINITY : std::log(p / (1.f - p));
+  const int grid = 8 * sms_now();
+  KZ_TRY(bitset_begin_run(g, max_sweeps, s));
+  if (g->n == 0) return KZ_OK;
+  const int64_t cap = std::max<int64_t>(g->m, 1);
+  // degrees before the first sweep, so that the first learned round's
+  // frontier is what that sweep changed
+  {
+    RowView r0 = view_of(g, b, read_cur(g, s));
+    KZ_CUDA_TRY(cudaMemsetAsync(b.cnt, 0, sizeof(unsigned long long) * 8, s));
+    stats_kernel<<<grid, 256, 0, s>>>(r0, b.s, 1, b.cnt + 3);
+    KZ_CUDA_TRY(cudaGetLastError());
+  }
+  int round = 1;
+  bool need_full = true;
+  for (;;) {
+    if (need_full) {
+      // a full plain sweep: the first one, and the certifying ones
+      int cont = 0;
+      KZ_TRY(bitset_one_pass(g, s, &cont));
+      DevState hs;
+      KZ_CUDA_TRY(cudaMemcpy(&hs, g->st, offsetof(DevState, trace_dv), cudaMemcpyDeviceToHost));
+      if (!cont) return KZ_OK;  // nothing deleted (or the sweep limit): certified / stopped
+      need_full = false;
+    }
+    const int cur = read_cur(g, s);
+    RowView r = view_of(g, b, cur);
+    KZ_CUDA_TRY(cudaMemsetAsync(b.cnt, 0, sizeof(unsigned long long) * 8, s));
+    count_live_kernel<<<grid, 256, 0, s>>>(r, b.cnt + 4, b.cnt + 5);
+    stats_kernel<<<grid, 256, 0, s>>>(r, b.s, 0, b.cnt + 3);
+    frontier_kernel<<<grid, 256, 0, s>>>(r, b.s, b.fr, b.cnt + 0, cap);
+    unsigned long long h[8];
+    KZ_TRY(read_u64(b.cnt, h, 8, s));
+    const double n = std::max(g->n, 1);
+    const float density = (float)((double)h[4] / (n * std::max(n - 1.0, 1.0)));
+    const float live_frac = (float)(h[5] / n);
+    KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 1, 0, sizeof(unsigned long long) * 2, s));
+    score_kernel<<<grid, 256, 0, s>>>(r, b.s, g->model->w16, b.fr, b.cnt + 0, logit_thr, round, density,
+                                      live_frac, b.work, b.cnt + 1);
+    test_edges_kernel<<<grid, 256, 0, s>>>(r, b.work, b.cnt + 1, b.dead, b.cnt + 2);
+    KZ_TRY(read_u64(b.cnt, h, 8, s));
+    const unsigned long long dv = h[3], de = h[2], tests = h[1];
+    if (dv + de == 0) {
+      // nothing found by the scored worklist: certify with a full sweep
+      learned_finish_kernel<<<1, 1, 0, s>>>(g->st, b.cnt + 3, b.cnt + 2, b.cnt + 1, nullptr);
+      need_full = true;
+      continue;
+    }
+    DevState hs;
+    KZ_CUDA_TRY(cudaMemcpy(&hs, g->st, offsetof(DevState, trace_dv), cudaMemcpyDeviceToHost));
+    if (hs.sweeps >= max_sweeps) {
+      int32_t lim = KZ_ERR_LIMIT;
+      KZ_CUDA_TRY(cudaMemcpy(&g->st->status, &lim, 4, cudaMemcpyHostToDevice));
+      return KZ_OK;
+    }
+    apply_kernel<<<grid, 256, 0, s>>>(r, b.s.vfail, b.dead, b.cnt + 2);
+    learned_finish_kernel<<<1, 1, 0, s>>>(g->st, b.cnt + 3, b.cnt + 2, b.cnt + 1, nullptr);
+    KZ_CUDA_TRY(cudaGetLastError());
+    round++;
+  }
+}
+
+kz_status learned_collect(kz_graph g, int64_t per_sweep_cap, uint64_t seed, float *X, uint8_t *y, int64_t cap,
+                          int64_t *count) {
+  cudaStream_t s = g->stream;
+  if (!g->learned_bufs) {
+    LearnedBufs *b = new LearnedBufs();
+    kz_status st = ensure_bufs(g, *b, s);
+    if (st != KZ_OK) {
+      delete b;
+      return st;
+    }
+    g->learned_bufs = b;
+  }
+  LearnedBufs &b = *static_cast<LearnedBufs *>(g->learned_bufs);
+  float *dX = nullptr;
+  uint8_t *dy = nullptr;
+  unsigned long long *dcnt = nullptr;
+  const size_t capz = (size_t)std::max<int64_t>(cap, 1);
+  dX = (float *)dev_alloc(capz * F * 4, s);
+  dy = (uint8_t *)dev_alloc(capz, s);
+  dcnt = (unsigned long long *)dev_alloc(64, s);
+  kz_status st = (dX && dy && dcnt) ? KZ_OK : KZ_ERR_OOM;
+  if (st == KZ_OK) st = cuda_status(cudaMemsetAsync(dcnt, 0, 64, s));
+  if (st == KZ_OK) st = bitset_begin_run(g, (int64_t)g->n + g->m + 1, s);
+  const int grid = 8 * sms_now();
+  int round = 0;
+  while (st == KZ_OK) {
+    const int cur = read_cur(g, s);
+    RowView r = view_of(g, b, cur);
+    st = cuda_status(cudaMemsetAsync(b.cnt, 0, sizeof(unsigned long long) * 8, s));
+    count_live_kernel<<<grid, 256, 0, s>>>(r, b.cnt + 4, b.cnt + 5);
+    stats_kernel<<<grid, 256, 0, s>>>(r, b.s, round == 0 ? 1 : 0, b.cnt + 3);
+    unsigned long long h[8];
+    if (st == KZ_OK) st = read_u64(b.cnt, h, 8, s);
+    if (st != KZ_OK) break;
+    const double n = std::max(g->n, 1);
+    const double live_edges = (double)h[4] / 2.0;
+    const float density = (float)((double)h[4] / (n * std::max(n - 1.0, 1.0)));
+    const float live_frac = (float)(h[5] / n);
+    // keep about per_sweep_cap of this sweep's live edges
+    const double frac = live_edges > 0 ? std::min(1.0, (double)per_sweep_cap / live_edges) : 1.0;
+    const uint32_t keep_below = frac >= 1.0 ? 0xffffffffu : (uint32_t)(frac * 4294967295.0);
+    trace_kernel<<<grid, 256, 0, s>>>(r, b.s, round, density, live_frac, seed, keep_below, dX, dy, dcnt, cap);
+    int cont = 0;
+    st = bitset_one_pass(g, s, &cont);
+    if (st != KZ_OK || !cont) break;
+    round++;
+  }
+  unsigned long long total = 0;
+  if (st == KZ_OK) st = read_u64(dcnt, &total, 1, s);
+  const int64_t got = std::min<int64_t>((int64_t)total, cap);
+  if (st == KZ_OK && got > 0) {
+    st = cuda_status(cudaMemcpy(X, dX, (size_t)got * F * 4, cudaMemcpyDeviceToHost));
+    if (st == KZ_OK) st = cuda_status(cudaMemcpy(y, dy, (size_t)got, cudaMemcpyDeviceToHost));
+  }
+  if (count) *count = got;
+  if (dX) dev_free(dX, capz * F * 4, s);
+  if (dy) dev_free(dy, capz, s);
+  if (dcnt) dev_free(dcnt, 64, s);
+  if (st == KZ_OK) st = cuda_status(cudaStreamSynchronize(s));
+  return st;
+}
+
+void learned_release(kz_graph g) {
+  delete static_cast<LearnedBufs *>(g->learned_bufs);
+  g->learned_bufs = nullptr;
+}
+
+}  // namespace kz
+
+// ---------------------------------------------------------------------------
+// C ABI of the model
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+kz_status kz_model_create(const float *weights, kz_model *out) {
+  if (!out) return KZ_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return KZ_ERR_CUDA;
+  }
+  kz_model m = new (std::nothrow) kz_model_s();
+  if (!m) return KZ_ERR_OOM;
+  cudaGetDevice(&m->device);
+  cudaError_t e = cudaMalloc(&m->w32, P * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&m->w16, P * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&m->m, P * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&m->v, P * 4);
+  if (e == cudaSuccess) e = cudaMemset(m->m, 0, P * 4);
+  if (e == cudaSuccess) e = cudaMemset(m->v, 0, P * 4);
+  if (e == cudaSuccess)
+    e = weights ? cudaMemcpy(m->w32, weights, P * 4, cudaMemcpyHostToDevice) : cudaMemset(m->w32, 0, P * 4);
+  if (e == cudaSuccess) {
+    to_bf16_kernel<<<8, 256>>>(m->w32, m->w16);
+    e = cudaDeviceSynchronize();
+  }
+  if (e != cudaSuccess) {
+    kz_model_free(m);
+    return cuda_status(e);
+  }
+  *out = m;
+  return KZ_OK;
+}
+
+kz_status kz_model_get(kz_model m, float *weights) {
+  if (!m || !weights) return KZ_ERR_ARG;
+  KZ_CUDA_TRY(cudaDeviceSynchronize());
+  KZ_CUDA_TRY(cudaMemcpy(weights, m->w32, P * 4, cudaMemcpyDeviceToHost));
+  return KZ_OK;
+}
+
+void kz_model_free(kz_model m) {
+  if (!m) return;
+  cudaDeviceSynchronize();
+  cudaFree(m->w32);
+  cudaFree(m->w16);
+  cudaFree(m->m);
+  cudaFree(m->v);
+  delete m;
+}
+
+kz_status kz_mlp_forward(kz_model m, const float *X, int64_t B, float *logits, void *stream) {
+  if (!m || B < 0 || (B > 0 && (!X || !logits))) return KZ_ERR_ARG;
+  if (B == 0) return KZ_OK;
+  const int grid = (int)std::min<int64_t>((B + 127) / 128, 8 * sms_now());
+  mlp_forward_kernel<<<grid, 128, 0, (cudaStream_t)stream>>>(m->w16, X, B, logits);
+  return cuda_status(cudaGetLastError());
+}
+
+kz_status kz_mlp_grad(kz_model m, const float *X, const float *y, int64_t B, float *grad, float *loss,
+                      void *stream) {
+  if (!m || B <= 0 || !X || !y || !grad || !loss) return KZ_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t smem = sizeof(float) * (P + kGradThreads * F + 4 * kGradThreads * H + kGradThreads);
+  static bool configured = false;
+  if (!configured) {
+    KZ_CUDA_TRY(cudaFuncSetAttribute((const void *)mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    configured = true;
+  }
+  KZ_CUDA_TRY(cudaMemsetAsync(grad, 0, P * 4, s));
+  KZ_CUDA_TRY(cudaMemsetAsync(loss, 0, 4, s));
+  const int64_t blocks = (B + kGradThreads - 1) / kGradThreads;
+  mlp_grad_kernel<<<(unsigned)blocks, kGradThreads, smem, s>>>(m->w32, X, y, B, grad, loss);
+  return cuda_status(cudaGetLastError());
+}
+
+kz_status kz_mlp_adam(kz_model m, const float *grad, float lr, void *stream) {
+  if (!m || !grad) return KZ_ERR_ARG;
+  m->t += 1;
+  const float bc1 = 1.f - std::pow(0.9f, (float)m->t);
+  const float bc2 = 1.f - std::pow(0.999f, (float)m->t);
+  adam_kernel<<<8, 256, 0, (cudaStream_t)stream>>>(m->w32, m->w16, m->m, m->v, grad, lr, bc1, bc2);
+  return cuda_status(cudaGetLastError());
+}
+
+kz_status kz_collect_trace(kz_graph g, int64_t per_sweep_cap, uint64_t seed, float *X, uint8_t *y, int64_t cap,
+                           int64_t *count) {
+  if (!g || per_sweep_cap < 0 || cap < 0 || (cap > 0 && (!X || !y)) || !count) return KZ_ERR_ARG;
+  if (!g->has_bitset) return KZ_ERR_UNSUPPORTED;
+  KZ_TRY(state_to_bitset(g, g->stream));
+  KZ_TRY(learned_collect(g, per_sweep_cap, seed, X, y, cap, count));
+  g->kernelized = true;
+  g->path_ran = KZ_PATH_BITSET;
+  return KZ_OK;
+}
+
+kz_status kz_attach_model(kz_graph g, kz_model m, float threshold) {
+  if (!g) return KZ_ERR_ARG;
+  g->model = m;
+  g->learned_threshold = threshold;
+  return KZ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,211 @@
+// kz_rules.cuh -- warp-level evaluation of the two Section 4.2 rules on the
+// block-plane bitset layout (see kz_internal.cuh), shared by the multi-CTA
+// sweep kernel and the whole-fixpoint-in-one-CTA kernel.
+//
+// Vertex rule: a live vertex u fails when the classes other than col(u) that
+// hold a live neighbour number fewer than k-1.
+// Edge rule: a live edge {u,v} fails when the classes other than col(u),
+// col(v) that hold a live common neighbour number fewer than k-2.
+//
+// A warp works on a block X (lane = member u) against a block Y of a higher
+// class.  Plane 0 of row u (the first 32 members of every class) sits in
+// registers as Fu[c]; a per-pair mask P[c] is all ones for c = col(u),
+// c = col(v) and padding classes c >= k, zero elsewhere.  The pair is covered
+// in every needed class at once when
+//     min_c ((Fu[c] & Fv[c]) | P[c]) != 0,
+// one LOP3 and half a three-input min per class.  A live edge that fails this
+// plane-0 test is recounted exactly over all planes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kz_internal.cuh"
+
+namespace kz {
+
+__device__ __forceinline__ uint32_t kz_min3(uint32_t a, uint32_t b, uint32_t c) {
+  return __vimin3_u32(a, b, c);
+}
+
+// Exact count over all planes of the classes (other than cu) in which row u
+// has a set bit.
+static __device__ __noinline__ int exact_vertex_cover_row(const uint32_t *ru, int k,
+                                                   const int32_t *__restrict__ rounds, int cu) {
+  int cnt = 0;
+  for (int c = 0; c < k; c++) {
+    if (c == cu) continue;
+    const int R = rounds[c];
+    for (int r = 0; r < R; r++) {
+      if (ru[r * k + c]) {
+        cnt++;
+        break;
+      }
+    }
+  }
+  return cnt;
+}
+
+// Plane 0 of a row into registers (zero when the lane has no vertex).
+template <int KMAX>
+__device__ __forceinline__ void load_plane0(uint32_t (&Fu)[KMAX], const uint32_t *row, int k,
+                                            bool valid) {
+#pragma unroll
+  for (int q = 0; q < KMAX / 4; q++) {
+    uint4 w = make_uint4(0u, 0u, 0u, 0u);
+    if (valid && 4 * q < k) w = reinterpret_cast<const uint4 *>(row)[q];
+    // words at or beyond k belong to the next plane: never counted
+    if (4 * q + 0 >= k) w.x = 0u;
+    if (4 * q + 1 >= k) w.y = 0u;
+    if (4 * q + 2 >= k) w.z = 0u;
+    if (4 * q + 3 >= k) w.w = 0u;
+    Fu[4 * q + 0] = w.x;
+    Fu[4 * q + 1] = w.y;
+    Fu[4 * q + 2] = w.z;
+    Fu[4 * q + 3] = w.w;
+  }
+}
+
+template <int KMAX>
+__device__ __forceinline__ void pair_mask(uint32_t (&P)[KMAX], int k, int cu, int cv) {
+#pragma unroll
+  for (int c = 0; c < KMAX; c++) P[c] = (c == cu || c == cv || c >= k) ? 0xffffffffu : 0u;
+}
+
+// True when plane 0 alone shows every needed class covered.  fv points at
+// the first word of v's row (16-byte aligned); words at or beyond k are not
+// read.
+template <int KMAX>
+__device__ __forceinline__ bool plane0_covered(const uint32_t (&Fu)[KMAX], const uint32_t (&P)[KMAX],
+                                               const uint32_t *fv, int k) {
+  uint32_t m0 = 0xffffffffu, m1 = 0xffffffffu;
+#pragma unroll
+  for (int q = 0; q < KMAX / 4; q++) {
+    if (4 * q >= k) break;  // k is uniform: one kernel serves every k <= KMAX
+    const uint4 w = reinterpret_cast<const uint4 *>(fv)[q];
+    m0 = kz_min3(m0, (Fu[4 * q + 0] & w.x) | P[4 * q + 0], (Fu[4 * q + 1] & w.y) | P[4 * q + 1]);
+    m1 = kz_min3(m1, (Fu[4 * q + 2] & w.z) | P[4 * q + 2], (Fu[4 * q + 3] & w.w) | P[4 * q + 3]);
+  }
+  return min(m0, m1) != 0u;
+}
+
+// Number of classes other than cu whose plane-0 word of row u is non-zero.
+template <int KMAX>
+__device__ __forceinline__ int plane0_vertex_cover(const uint32_t (&Fu)[KMAX], int k, int cu) {
+  int cnt = 0;
+#pragma unroll
+  for (int c = 0; c < KMAX; c++) cnt += (c < k && c != cu && Fu[c] != 0u) ? 1 : 0;
+  return cnt;
+}
+
+// Classes (bit c) that plane 0 leaves uncovered for the pair: needed classes
+// whose plane-0 word AND is zero.
+template <int KMAX>
+__device__ __forceinline__ uint64_t plane0_missing(const uint32_t (&Fu)[KMAX], const uint32_t (&P)[KMAX],
+                                                   const uint32_t *fv, int k) {
+  uint64_t miss = 0;
+#pragma unroll
+  for (int c = 0; c < KMAX; c++) {
+    if (c >= k) break;
+    if (((Fu[c] & fv[c]) | P[c]) == 0u) miss |= 1ull << c;
+  }
+  return miss;
+}
+
+// Tests every live edge between the lane's vertex u (row ru, plane 0 in Fu)
+// and the members of block Y.  adjw = row u's word for Y (bit b = edge to
+// member b).  fv_row(b) returns plane 0 of member b's row; row_v(b) returns
+// member b's full row.  Returns the lane's deletion mask over Y's members.
+// Must be called by all 32 lanes.
+//
+// Pairs that plane 0 does not settle are recounted cooperatively: one pair at
+// a time, the whole warp splits the later planes of each class still missing
+// (a warp vote per class), so a sparse block costs a few instructions per
+// unsettled pair instead of a divergent per-lane loop.
+template <int KMAX, class FvRow, class FullRow>
+__device__ __forceinline__ uint32_t edge_rule_block(const uint32_t (&Fu)[KMAX], const uint32_t (&P)[KMAX],
+                                                    const uint32_t *ru, uint32_t adjw, int k,
+                                                    const int32_t *__restrict__ rounds, int cu, int cv,
+                                                    FvRow fv_row, FullRow row_v) {
+  (void)cu;
+  (void)cv;
+  const int lane = threadIdx.x & 31;
+  uint32_t bits = __reduce_or_sync(0xffffffffu, adjw);
+  uint32_t del = 0;
+  while (bits) {
+    const int b = __ffs(bits) - 1;
+    bits &= bits - 1;
+    const uint32_t *fv = fv_row(b);
+    const bool covered = plane0_covered<KMAX>(Fu, P, fv, k);
+    const bool need = ((adjw >> b) & 1u) && !covered;
+    uint32_t need_mask = __ballot_sync(0xffffffffu, need);
+    if (!need_mask) continue;
+    const uint64_t miss = need ? plane0_missing<KMAX>(Fu, P, fv, k) : 0ull;
+    const uint32_t *rv = row_v(b);
+    while (need_mask) {
+      const int L = __ffs(need_mask) - 1;
+      need_mask &= need_mask - 1;
+      uint64_t missL = __shfl_sync(0xffffffffu, miss, L);
+      const uint32_t *ruL = reinterpret_cast<const uint32_t *>(
+          __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(ru), L));
+      bool fails = false;
+      while (missL && !fails) {
+        const int c = __ffsll((long long)missL) - 1;
+        missL &= missL - 1;
+        const int R = rounds[c];
+        bool found = false;
+        for (int r0 = 1; r0 < R && !found; r0 += 32) {
+          const int r = r0 + lane;
+          const uint32_t x = r < R ? (ruL[r * k + c] & rv[r * k + c]) : 0u;
+          found = __any_sync(0xffffffffu, x != 0u);
+        }
+        fails = !found;
+      }
+      if (lane == L && fails) del |= 1u << b;
+    }
+  }
+  return del;
+}
+
+// Column view of the lanes' deletion masks: lane b receives the mask of the
+// lanes (members of X) whose edge to member b of Y was deleted.
+__device__ __forceinline__ uint32_t transpose_deletions(uint32_t del) {
+  uint32_t delT = 0;
+  uint32_t any = __reduce_or_sync(0xffffffffu, del);
+  const int lane = threadIdx.x & 31;
+  while (any) {
+    const int b = __ffs(any) - 1;
+    any &= any - 1;
+    const uint32_t col = __ballot_sync(0xffffffffu, (del >> b) & 1u);
+    if (lane == b) delT = col;
+  }
+  return delT;
+}
+
+// Records a finished pass in the device state and decides whether another
+// pass follows: a pass that deleted something is applied (sweeps + 1, the
+// ping-pong buffers flip) unless the sweep limit is reached, in which case it
+// is dropped and KZ_ERR_LIMIT recorded.  Returns 1 to continue.
+__device__ __forceinline__ int finish_pass(DevState *st, unsigned long long dv, unsigned long long de,
+                                           unsigned long long tests) {
+  st->passes += 1;
+  st->tests += (int64_t)tests;
+  int cont = 0;
+  if (dv + de > 0) {
+    if (st->sweeps >= st->max_sweeps) {
+      st->status = KZ_ERR_LIMIT;
+    } else {
+      if (st->sweeps < kTraceCap) {
+        st->trace_dv[st->sweeps] = (int64_t)dv;
+        st->trace_de[st->sweeps] = (int64_t)de;
+      }
+      st->sweeps += 1;
+      st->cur ^= 1;
+      cont = 1;
+    }
+  }
+  st->cont = cont;
+  return cont;
+}
+
+}  // namespace kz

@@ -58,11 +58,12 @@ def _tiny_cases():
     return cases
 
 
+@pytest.mark.parametrize("path", ["bitset", "small", "sparse"])
 @pytest.mark.parametrize("case", _tiny_cases(), ids=lambda c: f"s{c[0]}-n{c[1]}-k{c[2]}-p{c[3]:.2f}")
-def test_tiny_random(case):
+def test_tiny_random(case, path):
     seed, n, k, p, planted = case
     g = synth.tiny_random(5000 + seed, n, k, p, planted=planted and n >= k)
-    assert_parity(g, gpu_run(g))
+    assert_parity(g, gpu_run(g, path=path))
 
 
 # ---------------------------------------------------------------------------
@@ -117,12 +118,13 @@ def test_large_class_slow_path():
         assert_parity(g, gpu_run(g))
 
 
-def test_cascades():
+@pytest.mark.parametrize("path", ["bitset", "small", "sparse"])
+def test_cascades(path):
     """Sparse graphs that take many sweeps."""
     seen = 0
     for seed in range(12):
         g = synth.tiny_random(700 + seed, 400, 6, 0.06 + 0.01 * (seed % 5), planted=bool(seed % 2))
-        orc = assert_parity(g, gpu_run(g))
+        orc = assert_parity(g, gpu_run(g, path=path))
         seen = max(seen, orc["sweeps"])
     assert seen >= 3
 
@@ -229,10 +231,46 @@ def test_c5_reduced():
     assert_parity(g, gpu_run(g, dense=True))
 
 
-def test_c3_reduced_cascade():
+@pytest.mark.parametrize("path", ["auto", "sparse"])
+def test_c3_reduced_cascade(path):
     g = synth.workload("c3", 0.02)
-    orc = assert_parity(g, gpu_run(g))
+    orc = assert_parity(g, gpu_run(g, path=path))
     assert orc["sweeps"] >= 2
+
+
+def test_sparse_edge_cases():
+    for g in (_graph([], np.zeros((0, 2)), 3), _graph(np.arange(7) % 3, np.zeros((0, 2)), 3)):
+        assert_parity(g, gpu_run(g, path="sparse"))
+    for sizes in ([1, 1, 1], [31, 32, 33], [5, 0, 7], [2] * 33):
+        colour, edges = refs.complete_kpartite(sizes)
+        g = _graph(colour, edges, len(sizes))
+        assert_parity(g, gpu_run(g, path="sparse"))
+
+
+def test_sparse_limit():
+    g = synth.tiny_random(31, 60, 6, 0.35)
+    r = gpu_run(g, path="sparse", max_sweeps=1)
+    assert r["stats"]["status"] == kz.KZ_ERR_LIMIT and r["stats"]["sweeps"] == 1
+    orc = oracle.fixpoint(g.colour, g.edges, 6, max_sweeps=1, raise_on_limit=False)
+    assert np.array_equal(r["alive"], orc["vlive"])
+    assert np.array_equal(r["edges"], g.edges[orc["elive"].astype(bool)])
+
+
+def test_switching_paths_on_one_handle():
+    """Each path continues from the state another path left: a sweep limit
+    stops one path part-way, the next path finishes the fixpoint."""
+    g = synth.tiny_random(77, 500, 6, 0.05, planted=True)
+    orc = oracle.fixpoint(g.colour, g.edges, g.k)
+    want = g.edges[orc["elive"].astype(bool)]
+    for first, second in (("sparse", "bitset"), ("bitset", "sparse"), ("small", "sparse"), ("sparse", "small")):
+        with kz.KernelGraph.from_synth(g) as kg:
+            kg.kernelize(path=first, max_sweeps=1)
+            kg.kernelize(path=second)
+            alive, edges, st = kg.fetch()
+            assert np.array_equal(alive, orc["vlive"]) and np.array_equal(edges, want), (first, second)
+            kg.reset().kernelize(path=second)
+            alive, edges, st = kg.fetch()
+            assert np.array_equal(edges, want) and st["sweeps"] == orc["sweeps"]
 
 
 def test_c4_style_batch_members():
@@ -276,3 +314,97 @@ def test_c2_full_size_sampled():
     pairs = e[rng.choice(len(e), size=2000, replace=False)]
     _, ie = oracle.dense_indices(g.colour, g.get_bits(), g.k, pairs=pairs)
     assert (ie >= g.k - 2).all()
+
+
+# ---------------------------------------------------------------------------
+# whole fixpoint in one CTA, and the batched persistent launch
+# ---------------------------------------------------------------------------
+
+def test_small_path_global_mode():
+    """A graph too large for shared memory runs the in-CTA kernel on its
+    global ping-pong buffers."""
+    g = synth.tiny_random(77, 2000, 6, 0.02, planted=True)
+    r = gpu_run(g, path="small")
+    assert_parity(g, r)
+
+
+def test_small_path_limit_and_rerun():
+    g = synth.tiny_random(31, 60, 6, 0.35)
+    r = gpu_run(g, path="small", max_sweeps=1)
+    assert r["stats"]["status"] == kz.KZ_ERR_LIMIT and r["stats"]["sweeps"] == 1
+    orc = oracle.fixpoint(g.colour, g.edges, 6, max_sweeps=1, raise_on_limit=False)
+    assert np.array_equal(r["alive"], orc["vlive"])
+    with kz.KernelGraph.from_synth(g) as kg:
+        kg.kernelize(path="small")
+        a1, e1, s1 = kg.fetch()
+        kg.kernelize(path="bitset")      # continues from the in-CTA result
+        a2, e2, s2 = kg.fetch()
+        assert s2["sweeps"] == 0 and np.array_equal(a1, a2) and np.array_equal(e1, e2)
+
+
+def _batch_graphs():
+    gs = [synth.kpartite(n, k, p, seed, planted=pl) for (n, k, p, pl, seed) in synth.batch_specs(40, 4242, n_hi=1500)]
+    gs += [synth.tiny_random(900 + i, 300 + 40 * i, 5 + i, 0.08, planted=bool(i % 2)) for i in range(8)]
+    gs += [synth.tiny_random(950, 2000, 6, 0.02, planted=True)]     # global mode inside the batch
+    gs += [synth.tiny_random(951, 120, 40, 0.9, planted=True)]      # k > 32: its own KMAX group
+    return gs
+
+
+@pytest.mark.parametrize("path", ["auto", "bitset", "small"])
+def test_batch_matches_oracle(path):
+    gs = _batch_graphs()
+    handles = [kz.KernelGraph.from_synth(g) for g in gs]
+    try:
+        kz.kz_kernelize_batch([h.h for h in handles], kz.kz_default_options(path=path))
+        for g, h in zip(gs, handles):
+            alive, edges, stats = h.fetch()
+            dv, de, vs = h.trace()
+            res = dict(alive=alive, edges=edges, stats=stats, dv=dv[:stats["sweeps"]], de=de[:stats["sweeps"]],
+                       v_sweep=vs)
+            assert_parity(g, res)
+    finally:
+        for h in handles:
+            h.close()
+
+
+@pytest.mark.parametrize("path", ["auto", "small"])
+def test_batch_c4_reduced(path):
+    """The batched workload's recipe at reduced size (64 graphs, n <= 1024)."""
+    specs = synth.batch_specs(64, synth.SEED_BASE + 4, n_hi=1024)
+    gs = [synth.kpartite(n, k, p, seed, planted=pl) for (n, k, p, pl, seed) in specs]
+    handles = [kz.KernelGraph.from_synth(g) for g in gs]
+    try:
+        kz.kz_kernelize_batch([h.h for h in handles], kz.kz_default_options(path=path))
+        for g, h in zip(gs, handles):
+            alive, edges, stats = h.fetch()
+            orc = oracle.fixpoint(g.colour, g.get_edges(), g.k)
+            assert np.array_equal(alive, orc["vlive"])
+            assert np.array_equal(edges, g.get_edges()[orc["elive"].astype(bool)])
+            assert stats["sweeps"] == orc["sweeps"] and stats["edge_tests"] == orc["tests"]
+    finally:
+        for h in handles:
+            h.close()
+
+
+def test_batch_limit_and_repeat():
+    """A batch run twice without reset certifies in one pass per graph; a
+    sweep limit applies per graph."""
+    gs = [synth.tiny_random(1300 + i, 200, 6, 0.1, planted=True) for i in range(6)]
+    handles = [kz.KernelGraph.from_synth(g) for g in gs]
+    try:
+        hs = [h.h for h in handles]
+        kz.kz_kernelize_batch(hs, kz.kz_default_options(max_sweeps=1))
+        for g, h in zip(gs, handles):
+            alive, edges, st = h.fetch(allow=(kz.KZ_OK, kz.KZ_ERR_LIMIT))
+            orc = oracle.fixpoint(g.colour, g.edges, g.k, max_sweeps=1, raise_on_limit=False)
+            assert np.array_equal(alive, orc["vlive"]) and st["sweeps"] == orc["sweeps"]
+        for h in handles:
+            h.reset()
+        kz.kz_kernelize_batch(hs)
+        kz.kz_kernelize_batch(hs)
+        for h in handles:
+            st = h.stats()
+            assert st["sweeps"] == 0 and st["passes"] == 1
+    finally:
+        for h in handles:
+            h.close()
