@@ -215,6 +215,49 @@ void kz_free_graph(kz_graph g);
 /* Static, NUL-terminated description of a status. */
 const char *kz_status_string(kz_status s);
 
+/*
+ * kz_kernelize_dense_noalloc -- kernelize one graph without allocating any
+ * memory.  The thesis has no counterpart: this is an interface for callers
+ * that cannot allocate device memory.  Examples: a process whose device
+ * memory is wholly reserved by another allocator (a framework's memory pool
+ * that owns the GPU), code that runs inside such an allocator's callbacks,
+ * and latency-critical loops that must not call cudaMalloc because it can
+ * synchronise the device.  kz_load_graph and friends allocate per graph;
+ * this entry point uses one fixed scratch array instead.
+ *
+ * Every intermediate (relabelling, bitset rows, ping-pong buffers, loop
+ * state) lives in a static device array of about 9 MiB that each GPU loading
+ * the library holds until the process exits.  The first call on a device
+ * looks up that array's device address (once per device); make that first
+ * call outside any stream capture.  The call makes no cudaMalloc, cudaFree or
+ * other allocating call, host or device.
+ *
+ * All calls share the one array, which keeps the last call's contents (every
+ * call re-initialises what it reads).  Calls that overlap on the GPU (two
+ * host threads, or two streams) race on it and give wrong results: serialise
+ * them.
+ *
+ * Arguments (all buffers are DEVICE memory owned by the caller):
+ *   n, k          vertices (0 <= n <= KZ_NOALLOC_MAX_N) and colours (1..32)
+ *   colour        int32[n], legal colouring
+ *   adj_bits      uint64[n * row_words], as kz_load_graph_dense (strict upper
+ *                 triangle read)
+ *   max_sweeps    as kz_options.max_sweeps
+ *   vertex_alive  uint8[n] out: 1 if the vertex is in the kernel
+ *   adj_out       uint64[n * row_words] out: the kernel's symmetric bit matrix
+ *   counts        int64[4] out: sweeps, passes, edge tests, status
+ *   stream        stream for every launch; the call waits for it at the end
+ * Returns the status (also in counts[3]).  n > KZ_NOALLOC_MAX_N, or colour
+ * classes so uneven that the bitset rows exceed KZ_NOALLOC_MAX_WORDS words,
+ * give KZ_ERR_UNSUPPORTED.
+ */
+#define KZ_NOALLOC_MAX_N 4096
+#define KZ_NOALLOC_MAX_WORDS (1 << 20)
+kz_status kz_kernelize_dense_noalloc(int32_t n, int32_t k, const int32_t *colour,
+                                     const uint64_t *adj_bits, int64_t row_words, int64_t max_sweeps,
+                                     uint8_t *vertex_alive, uint64_t *adj_out, int64_t *counts,
+                                     void *stream);
+
 /* Library version as major * 10000 + minor * 100 + patch. */
 int32_t kz_version(void);
 

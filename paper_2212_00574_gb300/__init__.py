@@ -102,6 +102,7 @@ def _lib():
                 "kz_status_string": (C.c_char_p, [C.c_int]),
                 "kz_version": (i32, []),
                 "kz_probe_int_throughput": (C.c_int, [i32, P, P, P]),
+                "kz_kernelize_dense_noalloc": (C.c_int, [i32, i32, P, P, i64, i64, P, P, P, P]),
                 "kz_model_create": (C.c_int, [P, P]),
                 "kz_model_get": (C.c_int, [P, P]),
                 "kz_model_free": (None, [P]),
@@ -316,6 +317,19 @@ def kz_status_string(status: int) -> str:
 
 def kz_version() -> int:
     return int(_lib().kz_version())
+
+
+def kz_kernelize_dense_noalloc(n: int, k: int, colour_ptr: int, adj_bits_ptr: int, row_words: int,
+                               max_sweeps: int, alive_ptr: int, adj_out_ptr: int, counts_ptr: int,
+                               stream=None) -> int:
+    """Allocation-free kernelization of one graph; every pointer is a device
+    address owned by the caller.  Returns the status (not raised: KZ_ERR_LIMIT
+    still leaves a valid partial kernel)."""
+    return int(_lib().kz_kernelize_dense_noalloc(int(n), int(k), C.c_void_p(colour_ptr),
+                                                 C.c_void_p(adj_bits_ptr), int(row_words),
+                                                 int(max_sweeps), C.c_void_p(alive_ptr),
+                                                 C.c_void_p(adj_out_ptr), C.c_void_p(counts_ptr),
+                                                 _stream(stream)))
 
 
 def kz_probe_int_throughput(kind: int, stream=None):

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "kz_internal.cuh"
@@ -405,3 +406,374 @@ kz_status cta_kernelize_one(kz_graph g, const kz_options &opt, cudaStream_t s) {
 }
 
 }  // namespace kz
+
+// ---------------------------------------------------------------------------
+// kz_kernelize_dense_noalloc: one graph, start to finish, with no memory
+// allocation at all.  Every intermediate lives in one file-scope device array
+// (g_noalloc_scratch below) that each GPU loading the library keeps until the
+// process exits; the caller passes device buffers for inputs and outputs.
+// The fixpoint itself is the in-CTA kernel above, reading its descriptor from
+// that array.
+// ---------------------------------------------------------------------------
+
+namespace kz {
+namespace noalloc {
+
+constexpr int kMaxN = KZ_NOALLOC_MAX_N;
+constexpr int kMaxWords = KZ_NOALLOC_MAX_WORDS;  // words per adjacency buffer
+constexpr int kMaxLdw = 4096;                    // words per row
+constexpr int kMaxBlocks = 256;
+
+struct Header {
+  CtaGraph desc;
+  int32_t status;
+  int32_t pad;
+  unsigned long long m;
+  int32_t coff[65];
+  int32_t boff[65];
+  int32_t rounds[64];
+  int32_t fill[64];
+  int32_t pair_off[kMaxBlocks + 1];
+  BlockDesc blocks[kMaxBlocks];
+};
+
+struct Scratch {
+  alignas(256) Header h;
+  alignas(256) DevState st;
+  alignas(256) uint32_t A0[kMaxWords];
+  alignas(256) uint32_t A1[kMaxWords];
+  alignas(256) uint32_t V0[kMaxLdw];
+  alignas(256) uint32_t V1[kMaxLdw];
+  alignas(256) int32_t perm[kMaxN];
+  alignas(256) int32_t inv[kMaxN];
+  alignas(256) int32_t v_sweep[kMaxN];
+};
+
+}  // namespace noalloc
+}  // namespace kz
+
+// The scratch of kz_kernelize_dense_noalloc (about 9 MiB per device).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(kz::noalloc::Scratch)];
+
+namespace kz {
+namespace noalloc {
+
+__device__ __forceinline__ Scratch *S() { return reinterpret_cast<Scratch *>(g_noalloc_scratch); }
+
+// First index i in [0, len) with a[i] > x (a sorted ascending).
+__device__ __forceinline__ int upper_bound_int(const int32_t *a, int len, int32_t x) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] <= x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Layout of the caller's graph: colour classes, blocks, block pairs, the
+// descriptor of the in-CTA kernel.  One CTA.
+__global__ void setup_kernel(int32_t n, int32_t k, const int32_t *__restrict__ colour) {
+  Scratch *s = S();
+  Header &h = s->h;
+  __shared__ int cnt[64];
+  __shared__ int bad;
+  __shared__ int status;
+  const int tid = threadIdx.x;
+  if (tid < 64) cnt[tid] = 0;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int v = tid; v < n; v += blockDim.x) {
+    const int c = colour[v];
+    if (c < 0 || c >= k) atomicExch(&bad, (int)KZ_ERR_COLOUR_RANGE);
+    else atomicAdd(&cnt[c], 1);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int st = bad;
+    int R = 1, nb = 0;
+    h.coff[0] = 0;
+    for (int c = 0; c < k; c++) {
+      h.coff[c + 1] = h.coff[c] + cnt[c];
+      h.rounds[c] = (cnt[c] + 31) / 32;
+      R = max(R, h.rounds[c]);
+      nb += h.rounds[c];
+    }
+    const int64_t ldw = ((int64_t)R * k + 3) / 4 * 4;
+    if (!st && (ldw > kMaxLdw || (int64_t)n * ldw > kMaxWords || nb > kMaxBlocks)) st = KZ_ERR_UNSUPPORTED;
+    if (!st) {
+      h.boff[0] = 0;
+      int b = 0;
+      for (int c = 0; c < k; c++) {
+        h.boff[c + 1] = h.boff[c] + h.rounds[c];
+        for (int r = 0; r < h.rounds[c]; r++, b++) {
+          h.blocks[b].c = c;
+          h.blocks[b].r = r;
+          h.blocks[b].base = h.coff[c] + 32 * r;
+          h.blocks[b].size = min(32, cnt[c] - 32 * r);
+        }
+        h.fill[c] = h.coff[c];
+      }
+      h.pair_off[0] = 0;
+      for (int x = 0; x < nb; x++) h.pair_off[x + 1] = h.pair_off[x] + (nb - h.boff[h.blocks[x].c + 1]);
+      CtaGraph &d = h.desc;
+      d.A0 = s->A0;
+      d.A1 = s->A1;
+      d.V0 = s->V0;
+      d.V1 = s->V1;
+      d.v_sweep = s->v_sweep;
+      d.st = &s->st;
+      d.blocks = h.blocks;
+      d.rounds = h.rounds;
+      d.pair_off = h.pair_off;
+      d.boff = h.boff;
+      d.n = n;
+      d.k = k;
+      d.ldw = (int32_t)ldw;
+      d.nb = nb;
+      d.smem_words = (int32_t)(2 * ((int64_t)n * ldw + ldw));
+      d.m = 0;
+      d.cost = 0;
+      h.m = 0;
+      DevState &ds = s->st;
+      ds.cur = 0;
+      ds.status = KZ_OK;
+      ds.cont = 0;
+      ds.sweeps = ds.passes = ds.tests = 0;
+      ds.pass_dv = ds.pass_de = ds.pass_tests = 0;
+      ds.ticket = 0;
+    }
+    h.status = st;
+    status = st;
+  }
+  __syncthreads();
+  if (status) return;
+  // relabel: every class a contiguous id range (order inside a class is free:
+  // the fixpoint and every count reported do not depend on it)
+  for (int v = tid; v < n; v += blockDim.x) {
+    const int x = atomicAdd(&h.fill[colour[v]], 1);
+    s->inv[v] = x;
+    s->perm[x] = v;
+  }
+}
+
+// Zeroed rows, live words of every block, zeroed deletion sweeps.
+__global__ void clear_kernel() {
+  Scratch *s = S();
+  if (s->h.status) return;
+  const CtaGraph &d = s->h.desc;
+  const int64_t words = (int64_t)d.n * d.ldw;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = tid; i < words; i += stride) s->A0[i] = 0u;
+  for (int64_t i = tid; i < d.ldw; i += stride) s->V0[i] = 0u;
+  for (int64_t i = tid; i < d.n; i += stride) s->v_sweep[i] = 0;
+}
+
+__global__ void live_words_kernel() {
+  Scratch *s = S();
+  if (s->h.status) return;
+  const CtaGraph &d = s->h.desc;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < d.nb; b += gridDim.x * blockDim.x) {
+    const BlockDesc bd = s->h.blocks[b];
+    s->V0[bd.r * d.k + bd.c] = bd.size >= 32 ? 0xffffffffu : ((1u << bd.size) - 1u);
+  }
+}
+
+// Caller's dense bit matrix (strict upper triangle) into the block-plane rows.
+__global__ void pack_kernel(const uint64_t *__restrict__ bits, int64_t row_words,
+                            const int32_t *__restrict__ colour) {
+  Scratch *s = S();
+  Header &h = s->h;
+  if (h.status) return;
+  const int n = h.desc.n, k = h.desc.k, ldw = h.desc.ldw;
+  unsigned long long mine = 0;
+  const int64_t total = (int64_t)n * row_words;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = (int32_t)(t / row_words);
+    const int64_t w = t - (int64_t)i * row_words;
+    const int64_t j0 = w * 64;
+    if (j0 + 63 <= i || j0 >= n) continue;
+    uint64_t word = bits[t];
+    if (j0 <= i) {
+      const int sh = i - (int)j0 + 1;
+      word = sh >= 64 ? 0 : (word >> sh) << sh;
+    }
+    if (j0 + 64 > n) word &= (1ull << (n - (int)j0)) - 1;
+    if (!word) continue;
+    const int32_t ci = colour[i];
+    const int32_t x = s->inv[i];
+    const int32_t ix = x - h.coff[ci];
+    while (word) {
+      const int b = __ffsll((long long)word) - 1;
+      word &= word - 1;
+      const int32_t j = (int32_t)j0 + b;
+      const int32_t cj = colour[j];
+      if (cj == ci) {
+        atomicCAS(&h.status, 0, (int32_t)KZ_ERR_ILLEGAL_COLOURING);
+        continue;
+      }
+      const int32_t y = s->inv[j];
+      const int32_t iy = y - h.coff[cj];
+      atomicOr(&s->A0[(int64_t)x * ldw + (iy >> 5) * k + cj], 1u << (iy & 31));
+      atomicOr(&s->A0[(int64_t)y * ldw + (ix >> 5) * k + ci], 1u << (ix & 31));
+      mine++;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&h.m, mine);
+}
+
+// Both ping-pong copies start from the packed rows (own-class words zero).
+__global__ void mirror_kernel() {
+  Scratch *s = S();
+  if (s->h.status) return;
+  const CtaGraph &d = s->h.desc;
+  const int64_t words = (int64_t)d.n * d.ldw;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = tid; i < words; i += stride) s->A1[i] = s->A0[i];
+  for (int64_t i = tid; i < d.ldw; i += stride) s->V1[i] = s->V0[i];
+  if (tid == 0) s->h.desc.m = (int64_t)s->h.m;
+}
+
+// The in-CTA fixpoint on the scratch descriptor (k <= 32).
+__global__ void __launch_bounds__(kCtaThreads, 1) fixpoint_kernel(int64_t max_sweeps, int32_t smem_words) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ unsigned long long s_cnt[3];
+  __shared__ int s_flag;
+  Scratch *s = S();
+  if (s->h.status) return;
+  const CtaGraph G = s->h.desc;
+  if (G.smem_words > 0 && G.smem_words <= smem_words)
+    cta_fixpoint<32, true>(G, max_sweeps, smem, s_cnt, &s_flag);
+  else
+    cta_fixpoint<32, false>(G, max_sweeps, smem, s_cnt, &s_flag);
+}
+
+__global__ void zero_out_kernel(uint64_t *__restrict__ out, int64_t words) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = 0ull;
+}
+
+// Kernel rows back to caller ids: the symmetric bit matrix, the live
+// vertices, and (sweeps, passes, edge tests, status).
+__global__ void unpack_kernel(uint64_t *__restrict__ out, int64_t row_words, uint8_t *__restrict__ alive,
+                              int64_t *__restrict__ counts) {
+  Scratch *s = S();
+  const Header &h = s->h;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (h.status) {
+    if (tid == 0) {
+      counts[0] = counts[1] = counts[2] = 0;
+      counts[3] = h.status;
+    }
+    return;
+  }
+  const CtaGraph &d = h.desc;
+  const int cur = s->st.cur;
+  const uint32_t *A = cur ? s->A1 : s->A0;
+  const uint32_t *V = cur ? s->V1 : s->V0;
+  const int n = d.n, k = d.k, ldw = d.ldw;
+  const int rk = ldw;  // rows are scanned over their padded length; padding words are zero
+  for (int64_t t = tid; t < (int64_t)n * rk; t += stride) {
+    const int32_t x = (int32_t)(t / rk);
+    const int32_t w = (int32_t)(t - (int64_t)x * rk);
+    uint32_t word = A[(int64_t)x * ldw + w];
+    if (!word) continue;
+    const int32_t c = w % k, r = w / k;
+    const int32_t ox = s->perm[x];
+    while (word) {
+      const int b = __ffs(word) - 1;
+      word &= word - 1;
+      const int32_t oy = s->perm[h.coff[c] + 32 * r + b];
+      atomicOr(reinterpret_cast<unsigned long long *>(&out[(int64_t)ox * row_words + (oy >> 6)]),
+               1ull << (oy & 63));
+    }
+  }
+  for (int64_t v = tid; v < n; v += stride) {
+    const int32_t x = s->inv[v];
+    const int32_t c = (int32_t)(upper_bound_int(h.coff, k + 1, x) - 1);
+    const int32_t i = x - h.coff[c];
+    alive[v] = (uint8_t)((V[(i >> 5) * k + c] >> (i & 31)) & 1u);
+  }
+  if (tid == 0) {
+    counts[0] = s->st.sweeps;
+    counts[1] = s->st.passes;
+    counts[2] = s->st.tests;
+    counts[3] = s->st.status;
+  }
+}
+
+}  // namespace noalloc
+}  // namespace kz
+
+namespace {
+
+// Device address of the scratch array, looked up once per device (host code
+// cannot use the array's name as a device pointer).
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[64] = {nullptr};
+
+kz_status noalloc_scratch(void **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return KZ_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return KZ_ERR_CUDA;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return KZ_OK;
+}
+
+}  // namespace
+
+extern "C" kz_status kz_kernelize_dense_noalloc(int32_t n, int32_t k, const int32_t *colour,
+                                                const uint64_t *adj_bits, int64_t row_words,
+                                                int64_t max_sweeps, uint8_t *vertex_alive,
+                                                uint64_t *adj_out, int64_t *counts, void *stream) {
+  using namespace kz::noalloc;
+  if (n < 0 || k < 1 || k > 32) return KZ_ERR_ARG;
+  if (n > kMaxN) return KZ_ERR_UNSUPPORTED;
+  if (row_words < (int64_t)((n + 63) / 64) || !counts) return KZ_ERR_ARG;
+  if (n > 0 && (!colour || !adj_bits || !vertex_alive || !adj_out)) return KZ_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  void *scratch = nullptr;
+  KZ_TRY(noalloc_scratch(&scratch));
+  (void)scratch;  // set-up check: the kernels name the array directly
+  int dev = 0, sms = 1, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int smem_bytes = std::max(0, optin - 1024);
+  {
+    static std::mutex mu;
+    static bool configured[64] = {false};
+    std::lock_guard<std::mutex> lk(mu);
+    if (!configured[dev]) {
+      KZ_CUDA_TRY(cudaFuncSetAttribute((const void *)fixpoint_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes));
+      configured[dev] = true;
+    }
+  }
+  const int grid = 2 * std::max(sms, 1);
+  setup_kernel<<<1, 1024, 0, s>>>(n, k, colour);
+  clear_kernel<<<grid, 256, 0, s>>>();
+  live_words_kernel<<<1, 256, 0, s>>>();
+  if ((int64_t)n * row_words > 0) pack_kernel<<<grid, 256, 0, s>>>(adj_bits, row_words, colour);
+  mirror_kernel<<<grid, 256, 0, s>>>();
+  fixpoint_kernel<<<1, kz::kCtaThreads, smem_bytes, s>>>(max_sweeps, smem_bytes / 4);
+  if ((int64_t)n * row_words > 0) zero_out_kernel<<<grid, 256, 0, s>>>(adj_out, (int64_t)n * row_words);
+  unpack_kernel<<<grid, 256, 0, s>>>(adj_out, row_words, vertex_alive, counts);
+  KZ_CUDA_TRY(cudaGetLastError());
+  // synchronous: the device status decides the return value
+  int64_t status = 0;
+  KZ_CUDA_TRY(cudaMemcpyAsync(&status, counts + 3, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  KZ_CUDA_TRY(cudaStreamSynchronize(s));
+  return (kz_status)status;
+}
