@@ -50,9 +50,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU work budget of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--path", choices=["auto", "bitset", "small", "sparse"], default="auto")
-    ap.add_argument("--loop", choices=["graph", "host"], default="graph",
-                    help="host: one direct launch per pass (for profilers that cannot see graph kernels)")
+    ap.add_argument("--path", choices=["auto", "bitset", "small", "sparse", "tensor"], default="auto")
+    ap.add_argument("--loop", choices=["device", "graph", "host"], default="device",
+                    help="pass loop: device = one cooperative persistent launch, graph = CUDA-graph while "
+                         "node, host = one launch per pass from the host")
     return ap.parse_args()
 
 
@@ -252,7 +253,7 @@ def run_ours(args, world, rank, local, pg):
         pin_edges = torch.from_numpy(g.get_edges()).pin_memory()
         h_edges = pin_edges.numpy()
         h = kz.kz_load_graph(g.n, g.k, h_col, h_edges, stream=stream)
-    opts = kz.kz_default_options(path=args.path, use_graph=1 if args.loop == "graph" else 0)
+    opts = kz.kz_default_options(path=args.path, use_graph={"device": 1, "graph": 2, "host": 0}[args.loop])
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def step(i, ev0=None, ev1=None):
@@ -307,7 +308,8 @@ def run_ours(args, world, rank, local, pg):
     achieved = alg_ops / launch_s
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_derived / 1e12, "unit": "Tops/s",
                 "frac": achieved / peak_derived, "traffic": None,
-                "kernel": "bitset_sweep_kernel" if args.path != "small" else "cta_fixpoint_kernel",
+                "kernel": {1: "bitset_persistent_kernel", 2: "cta_fixpoint_kernel", 3: "sparse pass kernels",
+                           4: "tensor_edge_kernel"}.get(st["path"], "?"),
                 "probe_lop3_tops": probe_ops / 1e12,
                 "ops_per_launch": alg_ops,
                 "note": "ops = live edges tested x (k-2) class-word ANDs; peak = SMs x 64 logic lanes x "
@@ -370,7 +372,10 @@ def run_ours(args, world, rank, local, pg):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC[args.workload], "n": g.n, "k": g.k, "m": g.m,
-                       "path": args.path, "passes": passes, "sweeps": st["sweeps"],
+                       "path": {v: k for k, v in kz.PATHS.items()}.get(st["path"], str(st["path"])),
+                       "pass_loop": {"device": "one cooperative persistent launch", "graph": "CUDA-graph while node",
+                                     "host": "host-driven"}[args.loop],
+                       "passes": passes, "sweeps": st["sweeps"],
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); per-step CUDA events "
                              "around kz_kernelize only",
                        "parallelism": "replicas" if world > 1 else "single"},

@@ -89,12 +89,13 @@ typedef struct {
     int32_t path;         /* kz_path */
     int32_t schedule;     /* kz_schedule */
     int64_t max_sweeps;   /* productive sweeps allowed; <= 0 means n + m + 1 (always enough) */
-    int32_t use_graph;    /* 1 (default): device-side sweep loop in a CUDA graph; 0: host-driven loop */
+    int32_t use_graph;    /* device-side pass loop: 1 (default) one cooperative persistent launch,
+                             2 a CUDA-graph while node (one launch per pass), 0 host-driven loop */
     int32_t reserved[9];  /* must be zero */
 } kz_options;
 
 /* Fill *opt with the defaults (AUTO path, PLAIN schedule, no sweep limit,
- * CUDA-graph loop). */
+ * device-side pass loop in one persistent launch). */
 void kz_default_options(kz_options *opt);
 
 typedef struct {

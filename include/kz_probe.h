@@ -28,6 +28,17 @@ extern "C" {
  */
 kz_status kz_probe_int_throughput(int32_t kind, double *ops_per_s, double *ms, void *stream);
 
+/*
+ * Failure-path probe of the bounded grid barrier (asynchronous on `stream`).
+ * Runs the persistent sweep kernel on g with a barrier that waits for one
+ * arrival more than the grid has, so every wait gives up after spin_limit
+ * polls: the kernel records KZ_ERR_TIMEOUT in g's device status (read with
+ * kz_fetch_stats) and returns, leaving the CUDA context usable.  The graph's
+ * live state is not changed (no pass is applied).  Nothing here faults or
+ * hangs the device; it exercises the path a lost CTA would take.
+ */
+kz_status kz_probe_barrier_timeout(kz_graph g, uint32_t spin_limit, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

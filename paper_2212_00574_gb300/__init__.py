@@ -102,6 +102,7 @@ def _lib():
                 "kz_status_string": (C.c_char_p, [C.c_int]),
                 "kz_version": (i32, []),
                 "kz_probe_int_throughput": (C.c_int, [i32, P, P, P]),
+                "kz_probe_barrier_timeout": (C.c_int, [P, u32, P]),
                 "kz_kernelize_dense_noalloc": (C.c_int, [i32, i32, P, P, i64, i64, P, P, P, P]),
                 "kz_model_create": (C.c_int, [P, P]),
                 "kz_model_get": (C.c_int, [P, P]),
@@ -330,6 +331,11 @@ def kz_kernelize_dense_noalloc(n: int, k: int, colour_ptr: int, adj_bits_ptr: in
                                                  int(max_sweeps), C.c_void_p(alive_ptr),
                                                  C.c_void_p(adj_out_ptr), C.c_void_p(counts_ptr),
                                                  _stream(stream)))
+
+
+def kz_probe_barrier_timeout(g: int, spin_limit: int = 1 << 14, stream=None):
+    _check(_lib().kz_probe_barrier_timeout(C.c_void_p(g), int(spin_limit), _stream(stream)),
+           "kz_probe_barrier_timeout")
 
 
 def kz_probe_int_throughput(kind: int, stream=None):

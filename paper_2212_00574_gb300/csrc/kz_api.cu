@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -15,6 +16,7 @@ namespace {
 
 std::mutex g_alloc_mu;
 kz_allocator g_alloc = {nullptr, nullptr, nullptr};
+std::atomic<uint64_t> g_next_uid{1};
 
 }  // namespace
 
@@ -100,6 +102,7 @@ void release(kz_graph g) {
   cudaStreamSynchronize(s);
   if (g->loop_exec) cudaGraphExecDestroy(g->loop_exec);
   learned_release(g);
+  tensor_release(g);
   for (auto &a : g->allocs) dev_free(a.p, a.bytes, s);
   g->allocs.clear();
   cudaStreamSynchronize(s);
@@ -125,6 +128,7 @@ kz_status load_common(int32_t n, int32_t k, const int32_t *colour, void *stream,
   if (!g) return KZ_ERR_OOM;
   g->n = n;
   g->k = k;
+  g->uid = g_next_uid.fetch_add(1);
   g->stream = (cudaStream_t)stream;
   cudaGetDevice(&g->device);
   relabel(g, colour);
@@ -239,7 +243,6 @@ static kz_status read_options(const kz_options *opt, kz_options &o) {
   }
   if (o.path < KZ_PATH_AUTO || o.path > KZ_PATH_TENSOR) return KZ_ERR_ARG;
   if (o.schedule != KZ_SCHED_PLAIN && o.schedule != KZ_SCHED_LEARNED) return KZ_ERR_ARG;
-  if (o.path == KZ_PATH_TENSOR) return KZ_ERR_UNSUPPORTED;
   return KZ_OK;
 }
 
@@ -260,6 +263,7 @@ static kz_status run_one(kz_graph g, const kz_options &o, int path) {
     if (!g->has_bitset) return KZ_ERR_UNSUPPORTED;
     KZ_TRY(state_to_bitset(g, g->stream));
     if (path == KZ_PATH_SMALL) KZ_TRY(cta_kernelize_one(g, o, g->stream));
+    else if (path == KZ_PATH_TENSOR) KZ_TRY(tensor_kernelize(g, o, g->stream));
     else KZ_TRY(bitset_kernelize(g, o, g->stream));
   }
   g->kernelized = true;
@@ -298,7 +302,7 @@ kz_status kz_kernelize_batch(kz_graph *graphs, int32_t count, const kz_options *
   }
   cudaStream_t s = (cudaStream_t)stream;
   for (int32_t i = 0; i < count; i++) graphs[i]->stream = s;
-  if (o.path == KZ_PATH_BITSET || o.path == KZ_PATH_SPARSE) {
+  if (o.path == KZ_PATH_BITSET || o.path == KZ_PATH_SPARSE || o.path == KZ_PATH_TENSOR) {
     // the plain per-graph loop
     for (int32_t i = 0; i < count; i++) KZ_TRY(run_one(graphs[i], o, o.path));
     return KZ_OK;
@@ -523,5 +527,16 @@ const char *kz_status_string(kz_status s) {
 }
 
 int32_t kz_version(void) { return 100; }
+
+kz_status kz_probe_barrier_timeout(kz_graph g, uint32_t spin_limit, void *stream) {
+  if (!g || spin_limit == 0) return KZ_ERR_ARG;
+  if (!g->has_bitset) return KZ_ERR_UNSUPPORTED;
+  g->stream = (cudaStream_t)stream;
+  KZ_TRY(state_to_bitset(g, g->stream));
+  KZ_TRY(bitset_barrier_timeout_probe(g, spin_limit, g->stream));
+  g->kernelized = true;
+  g->path_ran = KZ_PATH_BITSET;
+  return KZ_OK;
+}
 
 }  // extern "C"

@@ -13,10 +13,12 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "kz_internal.cuh"
 #include "kz_rules.cuh"
+#include "kz_sweep.cuh"
 
 namespace kz {
 
@@ -55,120 +57,121 @@ struct BatchArgs {
 
 constexpr int kBatchWarps = 4;
 
+struct PersistCtl {
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  int32_t any_cont;
+  int32_t go;
+  int32_t abort;
+  int32_t pad;
+};
+
+constexpr uint32_t kBatchSpinLimit = 1u << 25;
+
+// Every pass of every graph in one cooperative launch.  A pass of the batch
+// processes the items of all unconverged graphs; the last item of a graph
+// closes that graph's pass; a bounded grid barrier separates the batch's
+// passes, and the last CTA to arrive decides whether another follows.
 template <int KMAX>
-__global__ void __launch_bounds__(kBatchWarps * 32) batch_sweep_kernel(BatchArgs p) {
+__global__ void __launch_bounds__(kBatchWarps * 32) batch_persistent_kernel(BatchArgs p, PersistCtl *ctl) {
   extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ int s_go;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  uint32_t *sv = smem + wib * 32 * KMAX;
+  uint32_t *buf0 = smem + wib * 2 * 32 * KMAX;
+  uint32_t *buf1 = buf0 + 32 * KMAX;
   const int warps_total = gridDim.x * kBatchWarps;
-  for (int it = blockIdx.x * kBatchWarps + wib; it < p.n_items; it += warps_total) {
-    const BatchItem item = p.items[it];
-    const BatchGraph &G = p.graphs[item.g];
-    DevState *st = G.st;
-    if (!*((volatile int32_t *)&st->cont)) continue;  // converged: its items are skipped
-    const int cur = *((volatile int32_t *)&st->cur);
-    const int64_t sweep_no = *((volatile int64_t *)&st->sweeps);
-    const uint32_t *__restrict__ A = cur ? G.A1 : G.A0;
-    uint32_t *__restrict__ An = cur ? G.A0 : G.A1;
-    const uint32_t *__restrict__ Vc = cur ? G.V1 : G.V0;
-    uint32_t *__restrict__ Vn = cur ? G.V0 : G.V1;
-    const int k = G.k, ldw = G.ldw;
-    const int y1 = item.y1v & 0x7fffffff;
-    const bool vflag = (item.y1v >> 31) & 1;
-    const BlockDesc X = G.blocks[item.x];
-    const int cu = X.c;
-    const bool valid_u = lane < X.size;
-    const int u = X.base + lane;
-    const uint32_t *rowu = A + (int64_t)(valid_u ? u : X.base) * ldw;
-    uint32_t Fu[KMAX];
-    load_plane0<KMAX>(Fu, rowu, k, valid_u);
-    unsigned long long my_tests = 0, my_de = 0, my_dv = 0;
-    if (vflag) {
-      const int wx = X.r * k + cu;
-      const uint32_t vword = Vc[wx];
-      const bool live = valid_u && ((vword >> lane) & 1u);
-      int cnt = plane0_vertex_cover<KMAX>(Fu, k, cu);
-      if (live && cnt < k - 1) cnt = exact_vertex_cover_row(rowu, k, G.rounds, cu);
-      const bool fail = live && cnt < k - 1;
-      const uint32_t failmask = __ballot_sync(0xffffffffu, fail);
+  for (;;) {
+    for (int it = blockIdx.x * kBatchWarps + wib; it < p.n_items; it += warps_total) {
+      const BatchItem bi = p.items[it];
+      const BatchGraph &B = p.graphs[bi.g];
+      DevState *st = B.st;
+      if (!*((volatile int32_t *)&st->cont)) continue;
+      const int cur = *((volatile int32_t *)&st->cur);
+      const int64_t sweep_no = *((volatile int64_t *)&st->sweeps);
+      GraphView G;
+      G.blocks = B.blocks;
+      G.rounds = B.rounds;
+      G.A0 = B.A0;
+      G.A1 = B.A1;
+      G.V0 = B.V0;
+      G.V1 = B.V1;
+      G.v_sweep = B.v_sweep;
+      G.k = B.k;
+      G.ldw = B.ldw;
+      WorkItem wi;
+      wi.x = bi.x;
+      wi.y0 = bi.y0;
+      wi.y1 = bi.y1v & 0x7fffffff;
+      wi.vflag = (bi.y1v >> 31) & 1;
+      PassCounters pc;
+      sweep_item<KMAX>(G, wi, cur, sweep_no, buf0, buf1, pc);
+      for (int o = 16; o > 0; o >>= 1) {
+        pc.tests += __shfl_down_sync(0xffffffffu, pc.tests, o);
+        pc.de += __shfl_down_sync(0xffffffffu, pc.de, o);
+        pc.dv += __shfl_down_sync(0xffffffffu, pc.dv, o);
+      }
       if (lane == 0) {
-        Vn[wx] = vword & ~failmask;
-        my_dv += __popc(failmask);
-      }
-      if (fail && G.v_sweep) G.v_sweep[u] = (int32_t)(sweep_no + 1);
-    }
-    uint32_t P[KMAX];
-    int prev_cv = -1;
-    for (int y = item.y0; y < y1; y++) {
-      const BlockDesc Y = G.blocks[y];
-      const int cv = Y.c;
-      if (cv != prev_cv) {
-        pair_mask<KMAX>(P, k, cu, cv);
-        prev_cv = cv;
+        if (pc.tests) atomicAdd(&st->pass_tests, pc.tests);
+        if (pc.de) atomicAdd(&st->pass_de, pc.de);
+        if (pc.dv) atomicAdd(&st->pass_dv, pc.dv);
+        __threadfence();
+        if (atomicAdd(&st->ticket, 1u) == (unsigned int)B.n_items - 1u) {
+          __threadfence();
+          const unsigned long long dv = atomicAdd(&st->pass_dv, 0ull);
+          const unsigned long long de = atomicAdd(&st->pass_de, 0ull);
+          const unsigned long long tests = atomicAdd(&st->pass_tests, 0ull);
+          const int cont = finish_pass(st, dv, de, tests);
+          st->pass_dv = st->pass_de = st->pass_tests = 0;
+          st->ticket = 0;
+          if (cont) atomicOr(&ctl->any_cont, 1);
+          __threadfence();
+        }
       }
       __syncwarp();
-      const int kq = (k + 3) & ~3;  // columns the test reads
-      for (int idx = lane; idx < 32 * kq; idx += 32) {
-        const int b = idx / kq;
-        const int c = idx - b * kq;
-        sv[b * KMAX + c] = (b < Y.size && c < k) ? A[(int64_t)(Y.base + b) * ldw + c] : 0u;
-      }
-      __syncwarp();
-      const int wy = Y.r * k + cv;
-      const uint32_t adjw = valid_u ? A[(int64_t)u * ldw + wy] : 0u;
-      my_tests += __popc(adjw);
-      const uint32_t del = edge_rule_block<KMAX>(
-          Fu, P, rowu, adjw, k, G.rounds, cu, cv,
-          [&](int b) { return (const uint32_t *)(sv + b * KMAX); },
-          [&](int b) { return A + (int64_t)(Y.base + b) * ldw; });
-      if (valid_u) An[(int64_t)u * ldw + wy] = adjw & ~del;
-      my_de += __popc(del);
-      const uint32_t delT = transpose_deletions(del);
-      if (lane < Y.size) {
-        const int64_t wi = (int64_t)(Y.base + lane) * ldw + X.r * k + cu;
-        An[wi] = A[wi] & ~delT;
-      }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      my_tests += __shfl_down_sync(0xffffffffu, my_tests, o);
-      my_de += __shfl_down_sync(0xffffffffu, my_de, o);
-      my_dv += __shfl_down_sync(0xffffffffu, my_dv, o);
-    }
-    if (lane == 0) {
-      if (my_tests) atomicAdd(&st->pass_tests, my_tests);
-      if (my_de) atomicAdd(&st->pass_de, my_de);
-      if (my_dv) atomicAdd(&st->pass_dv, my_dv);
+    __syncthreads();
+    if (threadIdx.x == 0) {
       __threadfence();
-      const unsigned int t = atomicAdd(&st->ticket, 1u);
-      if (t == (unsigned int)G.n_items - 1u) {
-        // last item of this graph's pass
+      const unsigned int gen = *((volatile unsigned int *)&ctl->bar_gen);
+      if (atomicAdd(&ctl->bar_count, 1u) == gridDim.x - 1u) {
         __threadfence();
-        const unsigned long long dv = atomicAdd(&st->pass_dv, 0ull);
-        const unsigned long long de = atomicAdd(&st->pass_de, 0ull);
-        const unsigned long long tests = atomicAdd(&st->pass_tests, 0ull);
-        const int cont = finish_pass(st, dv, de, tests);
-        st->pass_dv = 0;
-        st->pass_de = 0;
-        st->pass_tests = 0;
-        st->ticket = 0;
-        if (cont) atomicOr(&p.ctl->any_cont, 1);
+        ctl->go = atomicExch(&ctl->any_cont, 0);
+        ctl->bar_count = 0;
         __threadfence();
+        atomicExch(&ctl->bar_gen, gen + 1u);
+      } else {
+        uint32_t spins = 0;
+        while (*((volatile unsigned int *)&ctl->bar_gen) == gen) {
+          if (*((volatile int32_t *)&ctl->abort)) break;
+          __nanosleep(64);
+          if (++spins > kBatchSpinLimit) {
+            atomicExch(&ctl->abort, 1);
+            break;
+          }
+        }
       }
-    }
-    __syncwarp();
-  }
-  if (lane == 0) {
-    __threadfence();
-    const unsigned int t = atomicAdd(&p.ctl->ticket, 1u);
-    if (t == (unsigned int)warps_total - 1u) {
       __threadfence();
-      const int cont = atomicExch(&p.ctl->any_cont, 0);
-      p.ctl->ticket = 0;
-      __threadfence();
-      if (p.use_cond) cudaGraphSetConditional(p.cond, cont ? 1u : 0u);
+      s_go = *((volatile int32_t *)&ctl->go) && !*((volatile int32_t *)&ctl->abort);
     }
+    __syncthreads();
+    if (!s_go) break;
   }
+}
+
+// After a batch: graphs whose barrier wait ran out are marked.
+__global__ void batch_timeout_kernel(const BatchGraph *graphs, int count, const PersistCtl *ctl) {
+  if (!ctl->abort) return;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < count; g += gridDim.x * blockDim.x)
+    atomicCAS(&graphs[g].st->status, (int32_t)KZ_OK, (int32_t)KZ_ERR_TIMEOUT);
+}
+
+__global__ void persist_ctl_reset_kernel(PersistCtl *ctl) {
+  ctl->bar_count = 0;
+  ctl->bar_gen = 0;
+  ctl->any_cont = 0;
+  ctl->go = 0;
+  ctl->abort = 0;
 }
 
 // Run start for every graph of the batch: counters zero, every graph active.
@@ -184,7 +187,7 @@ __global__ void batch_begin_kernel(const BatchGraph *graphs, int count, BatchCtl
     st->ticket = 0;
     st->cont = graphs[g].n_items > 0 ? 1 : 0;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (ctl && blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->ticket = 0;
     ctl->any_cont = 0;
   }
@@ -236,101 +239,110 @@ static void build_batch_items(kz_graph *gs, int count, std::vector<BatchItem> &i
   }
 }
 
+// The plan of the last batch (descriptors, items, control block), kept on
+// the device so that running the same batch again does no host work.  A plan
+// is identified by the graphs' load identities and the sweep limit.
+struct BatchPlan {
+  std::vector<uint64_t> key;
+  BatchGraph *desc = nullptr;
+  BatchItem *items = nullptr;
+  PersistCtl *ctl = nullptr;
+  size_t desc_bytes = 0, item_bytes = 0;
+  int32_t n_items = 0;
+  int device = -1;
+};
+
+static std::mutex g_plan_mu;
+static BatchPlan g_plan;
+
+static void plan_release(BatchPlan &pl) {
+  if (pl.desc) cudaFree(pl.desc);
+  if (pl.items) cudaFree(pl.items);
+  if (pl.ctl) cudaFree(pl.ctl);
+  pl = BatchPlan();
+}
+
 kz_status batch_kernelize(kz_graph *gs, int count, const kz_options &opt, cudaStream_t s) {
   if (count <= 0) return KZ_OK;
   for (int i = 0; i < count; i++)
     if (gs[i]->k > 32) return KZ_ERR_UNSUPPORTED;  // caller routes k > 32 elsewhere
-  std::vector<BatchItem> items;
-  std::vector<int32_t> per_graph;
-  build_batch_items(gs, count, items, per_graph);
-  std::vector<BatchGraph> desc((size_t)count);
-  for (int i = 0; i < count; i++) {
-    kz_graph g = gs[i];
-    BatchGraph &d = desc[i];
-    memset(&d, 0, sizeof(d));
-    d.A0 = g->A[0];
-    d.A1 = g->A[1];
-    d.V0 = g->V[0];
-    d.V1 = g->V[1];
-    d.v_sweep = g->v_sweep;
-    d.st = g->st;
-    d.blocks = g->d_blocks;
-    d.rounds = g->d_rounds;
-    d.k = g->k;
-    d.ldw = g->ldw;
-    d.n_items = per_graph[i];
-    d.n = g->n;
-    d.max_sweeps = opt.max_sweeps > 0 ? opt.max_sweeps : (int64_t)g->n + g->m + 1;
-  }
-  const size_t bytes_g = sizeof(BatchGraph) * count;
-  const size_t bytes_i = sizeof(BatchItem) * std::max<size_t>(items.size(), 1);
-  BatchGraph *d_desc = (BatchGraph *)dev_alloc(bytes_g, s);
-  BatchItem *d_items = (BatchItem *)dev_alloc(bytes_i, s);
-  BatchCtl *d_ctl = (BatchCtl *)dev_alloc(sizeof(BatchCtl), s);
-  kz_status st = (d_desc && d_items && d_ctl) ? KZ_OK : KZ_ERR_OOM;
-  if (st == KZ_OK)
-    st = cuda_status(cudaMemcpyAsync(d_desc, desc.data(), bytes_g, cudaMemcpyHostToDevice, s));
-  if (st == KZ_OK && !items.empty())
-    st = cuda_status(cudaMemcpyAsync(d_items, items.data(), sizeof(BatchItem) * items.size(),
-                                     cudaMemcpyHostToDevice, s));
-  if (st == KZ_OK) {
-    batch_begin_kernel<<<(count + 255) / 256, 256, 0, s>>>(d_desc, count, d_ctl);
-    st = cuda_status(cudaGetLastError());
-  }
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  if (st == KZ_OK && !items.empty()) {
-    const int kmax = 32;
-    auto fn = batch_sweep_kernel<32>;
-    const size_t smem = (size_t)kBatchWarps * 32 * kmax * 4;
-    int per_sm = 0;
-    st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn,
-                                                                   kBatchWarps * 32, smem));
-    const int want = (int)((items.size() + kBatchWarps - 1) / kBatchWarps);
-    const int grid = std::max(1, std::min(want, std::max(per_sm, 1) * sm_count_here()));
-    if (st == KZ_OK) st = cuda_status(cudaGraphCreate(&graph, 0));
-    cudaGraphConditionalHandle handle;
-    if (st == KZ_OK)
-      st = cuda_status(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
-    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
-    memset(cp_raw, 0, sizeof(cp_raw));
-    cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cp_raw);
-    cudaGraphNode_t wnode;
-    if (st == KZ_OK) {
-      cp.type = cudaGraphNodeTypeConditional;
-      cp.conditional.handle = handle;
-      cp.conditional.type = cudaGraphCondTypeWhile;
-      cp.conditional.size = 1;
-      st = cuda_status(cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &cp));
+  std::vector<uint64_t> key;
+  key.reserve((size_t)count + 1);
+  for (int i = 0; i < count; i++) key.push_back(gs[i]->uid);
+  key.push_back((uint64_t)opt.max_sweeps);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  if (g_plan.key != key || g_plan.device != dev) {
+    // the plan must not be freed while an earlier launch may still read it
+    if (g_plan.desc) KZ_CUDA_TRY(cudaDeviceSynchronize());
+    plan_release(g_plan);
+    std::vector<BatchItem> items;
+    std::vector<int32_t> per_graph;
+    build_batch_items(gs, count, items, per_graph);
+    std::vector<BatchGraph> desc((size_t)count);
+    for (int i = 0; i < count; i++) {
+      kz_graph g = gs[i];
+      BatchGraph &d = desc[i];
+      memset(&d, 0, sizeof(d));
+      d.A0 = g->A[0];
+      d.A1 = g->A[1];
+      d.V0 = g->V[0];
+      d.V1 = g->V[1];
+      d.v_sweep = g->v_sweep;
+      d.st = g->st;
+      d.blocks = g->d_blocks;
+      d.rounds = g->d_rounds;
+      d.k = g->k;
+      d.ldw = g->ldw;
+      d.n_items = per_graph[i];
+      d.n = g->n;
+      d.max_sweeps = opt.max_sweeps > 0 ? opt.max_sweeps : (int64_t)g->n + g->m + 1;
     }
-    if (st == KZ_OK) {
-      BatchArgs a;
-      a.graphs = d_desc;
-      a.items = d_items;
-      a.n_items = (int32_t)items.size();
-      a.ctl = d_ctl;
-      a.cond = handle;
-      a.use_cond = 1;
-      void *kargs[] = {&a};
-      cudaKernelNodeParams kp;
-      memset((void *)&kp, 0, sizeof(kp));
-      kp.func = (void *)fn;
-      kp.gridDim = dim3(grid);
-      kp.blockDim = dim3(kBatchWarps * 32);
-      kp.sharedMemBytes = (unsigned)smem;
-      kp.kernelParams = kargs;
-      cudaGraphNode_t knode;
-      st = cuda_status(cudaGraphAddKernelNode(&knode, cp.conditional.phGraph_out[0], nullptr, 0, &kp));
+    BatchPlan pl;
+    pl.key = key;
+    pl.device = dev;
+    pl.desc_bytes = sizeof(BatchGraph) * count;
+    pl.item_bytes = sizeof(BatchItem) * std::max<size_t>(items.size(), 1);
+    pl.n_items = (int32_t)items.size();
+    cudaError_t e = cudaMalloc(&pl.desc, pl.desc_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&pl.items, pl.item_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&pl.ctl, sizeof(PersistCtl));
+    if (e == cudaSuccess) e = cudaMemcpy(pl.desc, desc.data(), pl.desc_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !items.empty())
+      e = cudaMemcpy(pl.items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      plan_release(pl);
+      return cuda_status(e);
     }
-    if (st == KZ_OK) st = cuda_status(cudaGraphInstantiate(&exec, graph, 0));
-    if (st == KZ_OK) st = cuda_status(cudaGraphLaunch(exec, s));
+    g_plan = pl;
   }
-  if (exec) cudaGraphExecDestroy(exec);  // safe: destruction waits for nothing, launch keeps its copy
-  if (graph) cudaGraphDestroy(graph);
-  if (d_desc) dev_free(d_desc, bytes_g, s);
-  if (d_items) dev_free(d_items, bytes_i, s);
-  if (d_ctl) dev_free(d_ctl, sizeof(BatchCtl), s);
-  return st;
+  BatchPlan &pl = g_plan;
+  batch_begin_kernel<<<(count + 255) / 256, 256, 0, s>>>(pl.desc, count, nullptr);
+  persist_ctl_reset_kernel<<<1, 1, 0, s>>>(pl.ctl);
+  KZ_CUDA_TRY(cudaGetLastError());
+  if (pl.n_items == 0) return KZ_OK;
+  auto fn = batch_persistent_kernel<32>;
+  const size_t smem = (size_t)kBatchWarps * 2 * 32 * 32 * 4;
+  KZ_CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  KZ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, kBatchWarps * 32, smem));
+  const int want = (pl.n_items + kBatchWarps - 1) / kBatchWarps;
+  const int grid = std::max(1, std::min(want, std::max(per_sm, 1) * sm_count_here()));
+  BatchArgs a;
+  memset(&a, 0, sizeof(a));
+  a.graphs = pl.desc;
+  a.items = pl.items;
+  a.n_items = pl.n_items;
+  a.ctl = nullptr;
+  a.use_cond = 0;
+  PersistCtl *ctl = pl.ctl;
+  void *kargs[] = {&a, &ctl};
+  KZ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(kBatchWarps * 32), kargs, smem, s));
+  batch_timeout_kernel<<<(count + 255) / 256, 256, 0, s>>>(pl.desc, count, pl.ctl);
+  KZ_CUDA_TRY(cudaGetLastError());
+  return KZ_OK;
 }
 
 }  // namespace kz

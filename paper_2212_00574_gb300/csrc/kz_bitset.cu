@@ -40,6 +40,7 @@
 
 #include "kz_internal.cuh"
 #include "kz_rules.cuh"
+#include "kz_sweep.cuh"
 
 namespace kz {
 
@@ -209,102 +210,58 @@ struct SweepArgs {
   DevState *st;
   cudaGraphConditionalHandle cond;
   int32_t use_cond;
+  uint32_t bar_extra;    // arrivals the grid barrier waits for beyond the grid (0; tests use 1)
+  uint32_t spin_limit;   // polls before a barrier wait gives up
 };
 
 constexpr int kSweepWarps = 4;
 
+template <int KMAX>
+__device__ __forceinline__ void sweep_items(const SweepArgs &p, int cur, int64_t sweep_no, uint32_t *buf0,
+                                            uint32_t *buf1, int first_item, int item_stride, PassCounters &pc) {
+  GraphView G;
+  G.blocks = p.blocks;
+  G.rounds = p.rounds;
+  G.A0 = p.A0;
+  G.A1 = p.A1;
+  G.V0 = p.V0;
+  G.V1 = p.V1;
+  G.v_sweep = p.v_sweep;
+  G.k = p.k;
+  G.ldw = p.ldw;
+  for (int it = first_item; it < p.n_items; it += item_stride)
+    sweep_item<KMAX>(G, p.items[it], cur, sweep_no, buf0, buf1, pc);
+}
+
+template <int KMAX>
+__device__ __forceinline__ void reduce_counters(PassCounters &pc) {
+  for (int o = 16; o > 0; o >>= 1) {
+    pc.tests += __shfl_down_sync(0xffffffffu, pc.tests, o);
+    pc.de += __shfl_down_sync(0xffffffffu, pc.de, o);
+    pc.dv += __shfl_down_sync(0xffffffffu, pc.dv, o);
+  }
+}
+
+// One Jacobi pass per launch (the CUDA-graph loop and the host-driven loop).
 template <int KMAX>
 __global__ void __launch_bounds__(kSweepWarps * 32)
     bitset_sweep_kernel(SweepArgs p) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  uint32_t *sv = smem + wib * 32 * KMAX;
+  uint32_t *buf0 = smem + wib * 2 * 32 * KMAX;
+  uint32_t *buf1 = buf0 + 32 * KMAX;
   DevState *st = p.st;
   const int cur = *((volatile int32_t *)&st->cur);
   const int64_t sweep_no = *((volatile int64_t *)&st->sweeps);
-  const uint32_t *__restrict__ A = cur ? p.A1 : p.A0;
-  uint32_t *__restrict__ An = cur ? p.A0 : p.A1;
-  const uint32_t *__restrict__ Vc = cur ? p.V1 : p.V0;
-  uint32_t *__restrict__ Vn = cur ? p.V0 : p.V1;
-  const int k = p.k;
-  const int ldw = p.ldw;
-
-  unsigned long long my_tests = 0, my_de = 0, my_dv = 0;
   const int warps_total = gridDim.x * kSweepWarps;
-  for (int it = blockIdx.x * kSweepWarps + wib; it < p.n_items; it += warps_total) {
-    const WorkItem item = p.items[it];
-    const BlockDesc X = p.blocks[item.x];
-    const int cu = X.c;
-    const bool valid_u = lane < X.size;
-    const int u = X.base + lane;
-    const uint32_t *rowu = A + (int64_t)(valid_u ? u : X.base) * ldw;
-
-    uint32_t Fu[KMAX];
-    load_plane0<KMAX>(Fu, rowu, k, valid_u);
-
-    if (item.vflag) {
-      // vertex rule for the members of X
-      const int wx = X.r * k + cu;
-      const uint32_t vword = Vc[wx];
-      const bool live = valid_u && ((vword >> lane) & 1u);
-      int cnt = plane0_vertex_cover<KMAX>(Fu, k, cu);
-      if (live && cnt < k - 1) cnt = exact_vertex_cover_row(rowu, k, p.rounds, cu);
-      const bool fail = live && cnt < k - 1;
-      const uint32_t failmask = __ballot_sync(0xffffffffu, fail);
-      if (lane == 0) {
-        Vn[wx] = vword & ~failmask;
-        my_dv += __popc(failmask);
-      }
-      if (fail && p.v_sweep) p.v_sweep[u] = (int32_t)(sweep_no + 1);
-    }
-
-    uint32_t P[KMAX];
-    int prev_cv = -1;
-    for (int y = item.y0; y < item.y1; y++) {
-      const BlockDesc Y = p.blocks[y];
-      const int cv = Y.c;
-      if (cv != prev_cv) {
-        pair_mask<KMAX>(P, k, cu, cv);
-        prev_cv = cv;
-      }
-      // stage plane 0 of the rows of Y (broadcast reads from shared memory)
-      __syncwarp();
-      const int kq = (k + 3) & ~3;  // columns the test reads
-      for (int idx = lane; idx < 32 * kq; idx += 32) {
-        const int b = idx / kq;
-        const int c = idx - b * kq;
-        sv[b * KMAX + c] = (b < Y.size && c < k) ? A[(int64_t)(Y.base + b) * ldw + c] : 0u;
-      }
-      __syncwarp();
-      const int wy = Y.r * k + cv;
-      const uint32_t adjw = valid_u ? A[(int64_t)u * ldw + wy] : 0u;
-      my_tests += __popc(adjw);
-      const uint32_t del = edge_rule_block<KMAX>(
-          Fu, P, rowu, adjw, k, p.rounds, cu, cv,
-          [&](int b) { return (const uint32_t *)(sv + b * KMAX); },
-          [&](int b) { return A + (int64_t)(Y.base + b) * ldw; });
-      if (valid_u) An[(int64_t)u * ldw + wy] = adjw & ~del;
-      my_de += __popc(del);
-      // row v's word for block X, with the deletions transposed by ballots
-      const uint32_t delT = transpose_deletions(del);
-      if (lane < Y.size) {
-        const int64_t wi = (int64_t)(Y.base + lane) * ldw + X.r * k + cu;
-        An[wi] = A[wi] & ~delT;
-      }
-    }
-  }
-
-  // pass counters and the last-warp bookkeeping
-  for (int o = 16; o > 0; o >>= 1) {
-    my_tests += __shfl_down_sync(0xffffffffu, my_tests, o);
-    my_de += __shfl_down_sync(0xffffffffu, my_de, o);
-    my_dv += __shfl_down_sync(0xffffffffu, my_dv, o);
-  }
+  PassCounters pc;
+  sweep_items<KMAX>(p, cur, sweep_no, buf0, buf1, blockIdx.x * kSweepWarps + wib, warps_total, pc);
+  reduce_counters<KMAX>(pc);
   if (lane == 0) {
-    if (my_tests) atomicAdd(&st->pass_tests, my_tests);
-    if (my_de) atomicAdd(&st->pass_de, my_de);
-    if (my_dv) atomicAdd(&st->pass_dv, my_dv);
+    if (pc.tests) atomicAdd(&st->pass_tests, pc.tests);
+    if (pc.de) atomicAdd(&st->pass_de, pc.de);
+    if (pc.dv) atomicAdd(&st->pass_dv, pc.dv);
     __threadfence();
     const unsigned int t = atomicAdd(&st->ticket, 1u);
     if (t == (unsigned int)warps_total - 1u) {
@@ -323,7 +280,75 @@ __global__ void __launch_bounds__(kSweepWarps * 32)
   }
 }
 
+constexpr uint32_t kBarrierSpinLimit = 1u << 25;
+
+// Every pass of the fixpoint in one cooperative launch (all CTAs resident):
+// after its share of a pass each CTA arrives at a grid barrier; the last one
+// closes the pass (counters, buffer flip) and releases the others.  Every
+// barrier wait is bounded: one that runs out records KZ_ERR_TIMEOUT and all
+// CTAs leave.
+template <int KMAX>
+__global__ void __launch_bounds__(kSweepWarps * 32)
+    bitset_persistent_kernel(SweepArgs p) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ int s_go;
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  uint32_t *buf0 = smem + wib * 2 * 32 * KMAX;
+  uint32_t *buf1 = buf0 + 32 * KMAX;
+  DevState *st = p.st;
+  const int warps_total = gridDim.x * kSweepWarps;
+  for (;;) {
+    const int cur = *((volatile int32_t *)&st->cur);
+    const int64_t sweep_no = *((volatile int64_t *)&st->sweeps);
+    PassCounters pc;
+    sweep_items<KMAX>(p, cur, sweep_no, buf0, buf1, blockIdx.x * kSweepWarps + wib, warps_total, pc);
+    reduce_counters<KMAX>(pc);
+    if (lane == 0) {
+      if (pc.tests) atomicAdd(&st->pass_tests, pc.tests);
+      if (pc.de) atomicAdd(&st->pass_de, pc.de);
+      if (pc.dv) atomicAdd(&st->pass_dv, pc.dv);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned int gen = *((volatile unsigned int *)&st->bar_gen);
+      if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1u + p.bar_extra) {
+        __threadfence();
+        const unsigned long long dv = atomicAdd(&st->pass_dv, 0ull);
+        const unsigned long long de = atomicAdd(&st->pass_de, 0ull);
+        const unsigned long long tests = atomicAdd(&st->pass_tests, 0ull);
+        finish_pass(st, dv, de, tests);
+        st->pass_dv = 0;
+        st->pass_de = 0;
+        st->pass_tests = 0;
+        st->bar_count = 0;
+        __threadfence();
+        atomicExch(&st->bar_gen, gen + 1u);
+      } else {
+        uint32_t spins = 0;
+        while (*((volatile unsigned int *)&st->bar_gen) == gen) {
+          if (*((volatile int32_t *)&st->bar_abort)) break;
+          __nanosleep(64);
+          if (++spins > p.spin_limit) {
+            atomicCAS(&st->status, (int32_t)KZ_OK, (int32_t)KZ_ERR_TIMEOUT);
+            atomicExch(&st->bar_abort, 1);
+            break;
+          }
+        }
+      }
+      __threadfence();
+      s_go = *((volatile int32_t *)&st->cont) && !*((volatile int32_t *)&st->bar_abort);
+    }
+    __syncthreads();
+    if (!s_go) break;
+  }
+}
+
 __global__ void begin_run_kernel(DevState *st, int64_t max_sweeps, int64_t passes0) {
+  st->bar_count = 0;
+  st->bar_gen = 0;
+  st->bar_abort = 0;
   st->status = KZ_OK;
   st->cont = 1;
   st->sweeps = 0;
@@ -354,6 +379,27 @@ static SweepFn pick_sweep(int k, int &kmax) {
   if (k <= K) {                           \
     kmax = K;                             \
     return bitset_sweep_kernel<K>;        \
+  }
+  KZ_CASE(4)
+  KZ_CASE(8)
+  KZ_CASE(12)
+  KZ_CASE(16)
+  KZ_CASE(20)
+  KZ_CASE(24)
+  KZ_CASE(28)
+  KZ_CASE(32)
+  KZ_CASE(48)
+  KZ_CASE(64)
+#undef KZ_CASE
+  kmax = 0;
+  return nullptr;
+}
+
+static SweepFn pick_persistent(int k, int &kmax) {
+#define KZ_CASE(K)                           \
+  if (k <= K) {                              \
+    kmax = K;                                \
+    return bitset_persistent_kernel<K>;      \
   }
   KZ_CASE(4)
   KZ_CASE(8)
@@ -436,10 +482,9 @@ kz_status bitset_reset(kz_graph g, cudaStream_t s) {
 }
 
 static kz_status launch_config(kz_graph g, SweepFn fn, int kmax, int &grid, size_t &smem) {
-  smem = (size_t)kSweepWarps * 32 * kmax * 4;
-  if (smem > 48 * 1024)
-    KZ_CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+  smem = (size_t)kSweepWarps * 2 * 32 * kmax * 4;
+  // always raise the limit: the kernels' static shared memory comes on top
+  KZ_CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   KZ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn,
                                                             kSweepWarps * 32, smem));
@@ -465,6 +510,8 @@ static SweepArgs make_args(kz_graph g) {
   a.st = g->st;
   a.cond = 0;
   a.use_cond = 0;
+  a.bar_extra = 0;
+  a.spin_limit = kBarrierSpinLimit;
   return a;
 }
 
@@ -547,7 +594,22 @@ static kz_status build_loop_graph(kz_graph g, int64_t max_sweeps) {
 
 kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
   int64_t max_sweeps = opt.max_sweeps > 0 ? opt.max_sweeps : (int64_t)g->n + g->m + 1;
-  if (g->n > 0 && opt.use_graph) {
+  if (g->n > 0 && opt.use_graph == 1) {
+    // every pass in one cooperative launch (grid sized to be fully resident)
+    begin_run_kernel<<<1, 1, 0, s>>>(g->st, max_sweeps, 0);
+    KZ_CUDA_TRY(cudaGetLastError());
+    int kmax = 0;
+    SweepFn fn = pick_persistent(g->k, kmax);
+    if (!fn) return KZ_ERR_ARG;
+    int grid = 0;
+    size_t smem = 0;
+    KZ_TRY(launch_config(g, fn, kmax, grid, smem));
+    SweepArgs args = make_args(g);
+    void *kargs[] = {&args};
+    KZ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(kSweepWarps * 32), kargs, smem, s));
+    return KZ_OK;
+  }
+  if (g->n > 0 && opt.use_graph == 2) {
     // one graph launch: run-start kernel, then the while node of sweep passes
     if (g->loop_exec && g->loop_max_sweeps != max_sweeps) {
       cudaGraphExecDestroy(g->loop_exec);
@@ -603,6 +665,27 @@ kz_status bitset_one_pass(kz_graph g, cudaStream_t s, int *cont) {
   KZ_CUDA_TRY(cudaMemcpyAsync(&c, &g->st->cont, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   KZ_CUDA_TRY(cudaStreamSynchronize(s));
   *cont = c;
+  return KZ_OK;
+}
+
+// Runs the persistent sweep kernel with a grid barrier that waits for one
+// arrival more than the grid has, so every bounded wait runs out: the kernel
+// must record KZ_ERR_TIMEOUT and return.  For tests of the failure path.
+kz_status bitset_barrier_timeout_probe(kz_graph g, uint32_t spin_limit, cudaStream_t s) {
+  if (g->n == 0) return KZ_ERR_ARG;
+  begin_run_kernel<<<1, 1, 0, s>>>(g->st, (int64_t)g->n + g->m + 1, 0);
+  KZ_CUDA_TRY(cudaGetLastError());
+  int kmax = 0;
+  SweepFn fn = pick_persistent(g->k, kmax);
+  if (!fn) return KZ_ERR_ARG;
+  int grid = 0;
+  size_t smem = 0;
+  KZ_TRY(launch_config(g, fn, kmax, grid, smem));
+  SweepArgs args = make_args(g);
+  args.bar_extra = 1;
+  args.spin_limit = spin_limit;
+  void *kargs[] = {&args};
+  KZ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(kSweepWarps * 32), kargs, smem, s));
   return KZ_OK;
 }
 
@@ -681,7 +764,7 @@ kz_status bitset_vertex_alive(kz_graph g, uint8_t *host_alive, int64_t *n_live) 
 // zeroed pristine adjacency.  Returns the temporaries to free after the sync.
 static kz_status pack_setup(kz_graph g, cudaStream_t s, PackArgs &a, std::vector<void *> &tmp) {
   KZ_TRY(graph_alloc(g, &g->A0, (size_t)g->n * g->ldw, s));
-  if ((size_t)g->n * g->ldw)
+  if (g->n > 0 && g->ldw > 0)
     KZ_CUDA_TRY(cudaMemsetAsync(g->A0, 0, (size_t)g->n * g->ldw * 4, s));
   std::vector<int32_t> col_new((size_t)g->n);
   for (int c = 0; c < g->k; c++)

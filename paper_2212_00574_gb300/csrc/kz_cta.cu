@@ -392,8 +392,12 @@ static bool configure_once(CtaFn fn, int kmax, int bytes) {
 kz_status cta_kernelize_one(kz_graph g, const kz_options &opt, cudaStream_t s) {
   int km = 0;
   CtaFn fn = pick_cta(g->k, km);
-  const int smem_bytes = std::max(0, device_smem_optin() - 1024);
-  if (!configure_once(fn, km, smem_bytes)) return KZ_ERR_CUDA;
+  const int max_bytes = std::max(0, device_smem_optin() - 1024);
+  if (!configure_once(fn, km, max_bytes)) return KZ_ERR_CUDA;
+  // ask only for what this graph's shared mode needs (a small graph should
+  // not force the largest shared-memory carve-out)
+  const size_t need = cta_smem_words(g) * 4;
+  const int smem_bytes = need <= (size_t)max_bytes ? (int)((need + 15) / 16 * 16) : 0;
   CtaArgs a;
   a.graphs = g->d_cta_desc;
   a.order = g->d_zero;

@@ -65,6 +65,10 @@ struct DevState {
   unsigned long long pass_tests;
   unsigned int ticket;            // warps finished in the running pass
   unsigned int pad1;
+  unsigned int bar_count;         // grid barrier of the persistent sweep kernel
+  unsigned int bar_gen;
+  int32_t bar_abort;              // a bounded barrier wait ran out
+  int32_t pad2;
   int64_t trace_dv[kTraceCap];
   int64_t trace_de[kTraceCap];
 };
@@ -99,6 +103,7 @@ typedef kz::CtaGraph *CtaGraphPtr;
 struct kz_graph_s {
   int32_t n = 0, k = 0;
   int64_t m = 0;          // edges after merging duplicates
+  uint64_t uid = 0;       // unique per loaded graph (batch plans are keyed by it)
   int device = 0;
   cudaStream_t stream = nullptr;  // stream of the last enqueued work
   bool kernelized = false;
@@ -164,6 +169,7 @@ struct kz_graph_s {
   struct kz_model_s *model = nullptr;
   float learned_threshold = 0.5f;
   void *learned_bufs = nullptr;
+  void *tensor_bufs = nullptr;  // tensor-core path scratch
 
   // executable CUDA graph of the device-side sweep loop (built lazily)
   cudaGraphExec_t loop_exec = nullptr;
@@ -193,8 +199,14 @@ kz_status bitset_vertex_alive(kz_graph g, uint8_t *host_alive, int64_t *n_live);
 // One plain multi-CTA sweep pass (no loop graph); *cont = 1 when it deleted
 // something and another pass should follow.
 kz_status bitset_one_pass(kz_graph g, cudaStream_t s, int *cont);
+// Failure-path probe of the persistent kernel's bounded grid barrier.
+kz_status bitset_barrier_timeout_probe(kz_graph g, uint32_t spin_limit, cudaStream_t s);
 // Run start (counters zero, sweep limit) without a pass.
 kz_status bitset_begin_run(kz_graph g, int64_t max_sweeps, cudaStream_t s);
+
+// Tensor-core edge rule (kz_tensor.cu).
+kz_status tensor_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s);
+void tensor_release(kz_graph g);
 
 // Learned schedule (kz_learned.cu).
 kz_status learned_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s);
@@ -247,10 +259,15 @@ inline kz_status cuda_status(cudaError_t e) {
 
 }  // namespace kz
 
+// On failure the runtime's last-error state is consumed, so that a refused
+// launch (a non-sticky error) does not resurface in a later, unrelated call.
 #define KZ_CUDA_TRY(expr)                            \
   do {                                               \
     cudaError_t _e = (expr);                         \
-    if (_e != cudaSuccess) return kz::cuda_status(_e); \
+    if (_e != cudaSuccess) {                         \
+      cudaGetLastError();                            \
+      return kz::cuda_status(_e);                    \
+    }                                                \
   } while (0)
 
 #define KZ_TRY(expr)                  \

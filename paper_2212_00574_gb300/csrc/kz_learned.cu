@@ -341,20 +341,67 @@ __device__ __forceinline__ void edge_features(const RowView &r, const Stats &s, 
   f[15] = 1.f;
 }
 
-// Scores the frontier and keeps the edges above the threshold.
+// Pending-set bit of the (unordered) pair {x, y}: kept in the row of the
+// smaller id, at the word and bit of the larger one.
+__device__ __forceinline__ void pend_bit(const RowView &r, int x, int y, int64_t &word, uint32_t &bit) {
+  const int a = min(x, y), b = max(x, y);
+  const int cb = r.col[b], ib = b - r.coff[cb];
+  word = (int64_t)a * r.ldw + (ib >> 5) * r.k + cb;
+  bit = 1u << (ib & 31);
+}
+
+// Scores the frontier: edges above the threshold are tested this round (and
+// leave the pending set); the others join the pending set, to be tested in
+// a later flush unless they die first.
 __global__ void score_kernel(RowView r, Stats s, const __nv_bfloat16 *__restrict__ w16, const int2 *__restrict__ fr,
                              const unsigned long long *__restrict__ n_fr, float logit_threshold, int round,
                              float density, float live_frac, int2 *__restrict__ work,
-                             unsigned long long *n_work) {
+                             unsigned long long *n_work, uint32_t *__restrict__ pend) {
   __shared__ float w[P];
   for (int i = threadIdx.x; i < P; i += blockDim.x) w[i] = __bfloat162float(w16[i]);
   __syncthreads();
   const int64_t total = (int64_t)*n_fr;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     const int2 e = fr[q];
-    float f[F];
-    edge_features(r, s, e.x, e.y, round, density, live_frac, f);
-    if (mlp_logit(w, f) > logit_threshold) work[atomicAdd(n_work, 1ull)] = e;
+    int64_t pw;
+    uint32_t pb;
+    pend_bit(r, e.x, e.y, pw, pb);
+    bool take = true;
+    if (logit_threshold > -INFINITY) {
+      float f[F];
+      edge_features(r, s, e.x, e.y, round, density, live_frac, f);
+      take = mlp_logit(w, f) > logit_threshold;
+    }
+    if (take) {
+      work[atomicAdd(n_work, 1ull)] = e;
+      atomicAnd(&pend[pw], ~pb);
+    } else {
+      atomicOr(&pend[pw], pb);
+    }
+  }
+}
+
+// Flush: every pending edge that is still live, listed once; the pending
+// set is cleared.
+__global__ void flush_pending_kernel(RowView r, uint32_t *__restrict__ pend, int2 *__restrict__ out,
+                                     unsigned long long *count, int64_t cap) {
+  const int rk = r.R * r.k;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = tid; t < (int64_t)r.n * rk; t += stride) {
+    const int64_t x = t / rk;
+    const int w = (int)(t - x * rk);
+    const int64_t idx = x * r.ldw + w;
+    uint32_t bits = pend[idx] & r.A[idx];
+    if (!pend[idx]) continue;
+    pend[idx] = 0u;
+    const int c = w % r.k, rr = w / r.k;
+    while (bits) {
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1;
+      const unsigned long long pos = atomicAdd(count, 1ull);
+      if ((int64_t)pos < cap) out[pos] = make_int2((int)x, r.coff[c] + 32 * rr + b);
+    }
   }
 }
 
@@ -516,6 +563,7 @@ int sms_now() {
 struct LearnedBufs {
   Stats s;
   int2 *fr = nullptr, *work = nullptr, *dead = nullptr;
+  uint32_t *pend = nullptr;  // pending edges (bitset rows, pair kept in the smaller id's row)
   unsigned long long *cnt = nullptr;  // [0] frontier [1] work [2] dead [3] dv [4] edges2 [5] verts
   int32_t *col = nullptr;
 };
@@ -532,6 +580,8 @@ kz_status ensure_bufs(kz_graph g, LearnedBufs &b, cudaStream_t s) {
   KZ_TRY(graph_alloc(g, &b.work, m, s));
   KZ_TRY(graph_alloc(g, &b.dead, m, s));
   KZ_TRY(graph_alloc(g, &b.cnt, 8, s));
+  KZ_TRY(graph_alloc(g, &b.pend, (size_t)std::max(g->n, 1) * g->ldw, s));
+  KZ_CUDA_TRY(cudaMemsetAsync(b.pend, 0, (size_t)std::max(g->n, 1) * g->ldw * 4, s));
   std::vector<int32_t> col_new((size_t)g->n);
   for (int c = 0; c < g->k; c++)
     for (int x = g->coff[c]; x < g->coff[c + 1]; x++) col_new[x] = c;
@@ -601,13 +651,12 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
   }
   int round = 1;
   bool need_full = true;
+  KZ_CUDA_TRY(cudaMemsetAsync(b.pend, 0, (size_t)g->n * g->ldw * 4, s));
   for (;;) {
     if (need_full) {
       // a full plain sweep: the first one, and the certifying ones
       int cont = 0;
       KZ_TRY(bitset_one_pass(g, s, &cont));
-      DevState hs;
-      KZ_CUDA_TRY(cudaMemcpy(&hs, g->st, offsetof(DevState, trace_dv), cudaMemcpyDeviceToHost));
       if (!cont) return KZ_OK;  // nothing deleted (or the sweep limit): certified / stopped
       need_full = false;
     }
@@ -622,17 +671,27 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
     const double n = std::max(g->n, 1);
     const float density = (float)((double)h[4] / (n * std::max(n - 1.0, 1.0)));
     const float live_frac = (float)(h[5] / n);
-    KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 1, 0, sizeof(unsigned long long) * 2, s));
     score_kernel<<<grid, 256, 0, s>>>(r, b.s, g->model->w16, b.fr, b.cnt + 0, logit_thr, round, density,
-                                      live_frac, b.work, b.cnt + 1);
+                                      live_frac, b.work, b.cnt + 1, b.pend);
     test_edges_kernel<<<grid, 256, 0, s>>>(r, b.work, b.cnt + 1, b.dead, b.cnt + 2);
     KZ_TRY(read_u64(b.cnt, h, 8, s));
-    const unsigned long long dv = h[3], de = h[2], tests = h[1];
+    unsigned long long dv = h[3], de = h[2];
     if (dv + de == 0) {
-      // nothing found by the scored worklist: certify with a full sweep
+      // the scored edges found nothing: test the pending ones
       learned_finish_kernel<<<1, 1, 0, s>>>(g->st, b.cnt + 3, b.cnt + 2, b.cnt + 1, nullptr);
-      need_full = true;
-      continue;
+      KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 1, 0, sizeof(unsigned long long) * 2, s));
+      flush_pending_kernel<<<grid, 256, 0, s>>>(r, b.pend, b.work, b.cnt + 1, cap);
+      test_edges_kernel<<<grid, 256, 0, s>>>(r, b.work, b.cnt + 1, b.dead, b.cnt + 2);
+      KZ_TRY(read_u64(b.cnt, h, 8, s));
+      dv = 0;
+      de = h[2];
+      if (de == 0) {
+        // nothing pending fails either: certify with a full sweep
+        learned_finish_kernel<<<1, 1, 0, s>>>(g->st, b.cnt + 3, b.cnt + 2, b.cnt + 1, nullptr);
+        need_full = true;
+        continue;
+      }
+      KZ_CUDA_TRY(cudaMemsetAsync(b.s.vfail, 0, (size_t)g->n, s));
     }
     DevState hs;
     KZ_CUDA_TRY(cudaMemcpy(&hs, g->st, offsetof(DevState, trace_dv), cudaMemcpyDeviceToHost));
@@ -641,6 +700,7 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
       KZ_CUDA_TRY(cudaMemcpy(&g->st->status, &lim, 4, cudaMemcpyHostToDevice));
       return KZ_OK;
     }
+    if (dv == 0) KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 3, 0, sizeof(unsigned long long), s));
     apply_kernel<<<grid, 256, 0, s>>>(r, b.s.vfail, b.dead, b.cnt + 2);
     learned_finish_kernel<<<1, 1, 0, s>>>(g->st, b.cnt + 3, b.cnt + 2, b.cnt + 1, nullptr);
     KZ_CUDA_TRY(cudaGetLastError());

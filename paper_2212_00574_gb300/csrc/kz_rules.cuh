@@ -112,16 +112,34 @@ __device__ __forceinline__ uint64_t plane0_missing(const uint32_t (&Fu)[KMAX], c
   return miss;
 }
 
+// Exact edge rule for a pair that plane 0 did not settle: every class in
+// `miss` must show a common neighbour in some later plane.  Returns true
+// when the edge fails (some needed class has none in any plane).
+__device__ __forceinline__ bool edge_fails_beyond_plane0(const uint32_t *ru, const uint32_t *rv, int k,
+                                                         const int32_t *__restrict__ rounds, uint64_t miss) {
+  while (miss) {
+    const int c = __ffsll((long long)miss) - 1;
+    miss &= miss - 1;
+    const int R = rounds[c];
+    bool found = false;
+    for (int r = 1; r < R; r++) {
+      if (ru[r * k + c] & rv[r * k + c]) {
+        found = true;
+        break;
+      }
+    }
+    if (!found) return true;
+  }
+  return false;
+}
+
 // Tests every live edge between the lane's vertex u (row ru, plane 0 in Fu)
 // and the members of block Y.  adjw = row u's word for Y (bit b = edge to
 // member b).  fv_row(b) returns plane 0 of member b's row; row_v(b) returns
 // member b's full row.  Returns the lane's deletion mask over Y's members.
-// Must be called by all 32 lanes.
-//
-// Pairs that plane 0 does not settle are recounted cooperatively: one pair at
-// a time, the whole warp splits the later planes of each class still missing
-// (a warp vote per class), so a sparse block costs a few instructions per
-// unsettled pair instead of a divergent per-lane loop.
+// Must be called by all 32 lanes.  A pair that plane 0 does not settle is
+// recounted by its own lane over the later planes of the uncovered classes
+// only; the lanes' recounts run side by side, so their loads overlap.
 template <int KMAX, class FvRow, class FullRow>
 __device__ __forceinline__ uint32_t edge_rule_block(const uint32_t (&Fu)[KMAX], const uint32_t (&P)[KMAX],
                                                     const uint32_t *ru, uint32_t adjw, int k,
@@ -129,7 +147,6 @@ __device__ __forceinline__ uint32_t edge_rule_block(const uint32_t (&Fu)[KMAX], 
                                                     FvRow fv_row, FullRow row_v) {
   (void)cu;
   (void)cv;
-  const int lane = threadIdx.x & 31;
   uint32_t bits = __reduce_or_sync(0xffffffffu, adjw);
   uint32_t del = 0;
   while (bits) {
@@ -137,32 +154,75 @@ __device__ __forceinline__ uint32_t edge_rule_block(const uint32_t (&Fu)[KMAX], 
     bits &= bits - 1;
     const uint32_t *fv = fv_row(b);
     const bool covered = plane0_covered<KMAX>(Fu, P, fv, k);
-    const bool need = ((adjw >> b) & 1u) && !covered;
-    uint32_t need_mask = __ballot_sync(0xffffffffu, need);
-    if (!need_mask) continue;
-    const uint64_t miss = need ? plane0_missing<KMAX>(Fu, P, fv, k) : 0ull;
-    const uint32_t *rv = row_v(b);
-    while (need_mask) {
-      const int L = __ffs(need_mask) - 1;
-      need_mask &= need_mask - 1;
-      uint64_t missL = __shfl_sync(0xffffffffu, miss, L);
-      const uint32_t *ruL = reinterpret_cast<const uint32_t *>(
-          __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(ru), L));
-      bool fails = false;
-      while (missL && !fails) {
-        const int c = __ffsll((long long)missL) - 1;
-        missL &= missL - 1;
-        const int R = rounds[c];
-        bool found = false;
-        for (int r0 = 1; r0 < R && !found; r0 += 32) {
-          const int r = r0 + lane;
-          const uint32_t x = r < R ? (ruL[r * k + c] & rv[r * k + c]) : 0u;
-          found = __any_sync(0xffffffffu, x != 0u);
-        }
-        fails = !found;
-      }
-      if (lane == L && fails) del |= 1u << b;
+    if (((adjw >> b) & 1u) && !covered) {
+      const uint64_t miss = plane0_missing<KMAX>(Fu, P, fv, k);
+      if (edge_fails_beyond_plane0(ru, row_v(b), k, rounds, miss)) del |= 1u << b;
     }
+  }
+  return del;
+}
+
+// Hot loop of the sweep kernels: the plane-0 test of every member of block Y
+// (rows staged in shared memory, KMAX words apart) against every lane's u,
+// two members at a time (four independent min chains).  Returns the lane's
+// live edges that plane 0 does not settle; the recount is done afterwards
+// by recount_unsettled, outside this loop.
+template <int KMAX>
+__device__ __forceinline__ uint32_t plane0_unsettled(const uint32_t (&Fu)[KMAX], const uint32_t (&P)[KMAX],
+                                                     const uint32_t *sv, uint32_t adjw, int k) {
+  uint32_t bits = __reduce_or_sync(0xffffffffu, adjw);
+  uint32_t open = 0;
+  while (bits) {
+    const int b0 = __ffs(bits) - 1;
+    bits &= bits - 1;
+    const uint4 *f0 = reinterpret_cast<const uint4 *>(sv + b0 * KMAX);
+    if (bits) {
+      const int b1 = __ffs(bits) - 1;
+      bits &= bits - 1;
+      const uint4 *f1 = reinterpret_cast<const uint4 *>(sv + b1 * KMAX);
+      uint32_t m0 = 0xffffffffu, m1 = 0xffffffffu, m2 = 0xffffffffu, m3 = 0xffffffffu;
+#pragma unroll
+      for (int q = 0; q < KMAX / 4; q++) {
+        if (4 * q >= k) break;
+        const uint4 w0 = f0[q], w1 = f1[q];
+        m0 = kz_min3(m0, (Fu[4 * q + 0] & w0.x) | P[4 * q + 0], (Fu[4 * q + 1] & w0.y) | P[4 * q + 1]);
+        m1 = kz_min3(m1, (Fu[4 * q + 2] & w0.z) | P[4 * q + 2], (Fu[4 * q + 3] & w0.w) | P[4 * q + 3]);
+        m2 = kz_min3(m2, (Fu[4 * q + 0] & w1.x) | P[4 * q + 0], (Fu[4 * q + 1] & w1.y) | P[4 * q + 1]);
+        m3 = kz_min3(m3, (Fu[4 * q + 2] & w1.z) | P[4 * q + 2], (Fu[4 * q + 3] & w1.w) | P[4 * q + 3]);
+      }
+      if (min(m0, m1) == 0u) open |= 1u << b0;
+      if (min(m2, m3) == 0u) open |= 1u << b1;
+    } else {
+      uint32_t m0 = 0xffffffffu, m1 = 0xffffffffu;
+#pragma unroll
+      for (int q = 0; q < KMAX / 4; q++) {
+        if (4 * q >= k) break;
+        const uint4 w0 = f0[q];
+        m0 = kz_min3(m0, (Fu[4 * q + 0] & w0.x) | P[4 * q + 0], (Fu[4 * q + 1] & w0.y) | P[4 * q + 1]);
+        m1 = kz_min3(m1, (Fu[4 * q + 2] & w0.z) | P[4 * q + 2], (Fu[4 * q + 3] & w0.w) | P[4 * q + 3]);
+      }
+      if (min(m0, m1) == 0u) open |= 1u << b0;
+    }
+  }
+  return open & adjw;
+}
+
+// Recount, lane by lane, the edges plane 0 left open: the classes plane 0
+// leaves uncovered (from the row of u and the staged row of v) are searched
+// in their later planes.  Returns the lane's deletion mask.  Takes pointers
+// only, so the hot loop's register arrays stay in registers.
+static __device__ __noinline__ uint32_t recount_unsettled(const uint32_t *ru, const uint32_t *sv, int kmax_stride,
+                                                         const uint32_t *ybase, int ldw, uint32_t open, int k,
+                                                         int cu, int cv, const int32_t *__restrict__ rounds) {
+  uint32_t del = 0;
+  while (open) {
+    const int b = __ffs(open) - 1;
+    open &= open - 1;
+    const uint32_t *fv = sv + b * kmax_stride;
+    uint64_t miss = 0;
+    for (int c = 0; c < k; c++)
+      if (c != cu && c != cv && (ru[c] & fv[c]) == 0u) miss |= 1ull << c;
+    if (edge_fails_beyond_plane0(ru, ybase + (int64_t)b * ldw, k, rounds, miss)) del |= 1u << b;
   }
   return del;
 }

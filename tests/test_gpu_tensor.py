@@ -1,0 +1,47 @@
+"""Tensor-core edge rule (tcgen05.mma kind::f8f6f4) against the oracle, through
+the C ABI (GPU only).  Bit-exact: survivors, sweeps, per-sweep counts."""
+import numpy as np
+import pytest
+
+from paper_2212_00574_gb300 import synth
+from tests import refs
+from tests.test_gpu_parity import _graph, _tiny_cases, assert_parity, gpu_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("case", _tiny_cases()[::2], ids=lambda c: f"s{c[0]}-n{c[1]}-k{c[2]}")
+def test_tensor_tiny(case):
+    seed, n, k, p, planted = case
+    g = synth.tiny_random(5000 + seed, n, k, p, planted=planted and n >= k)
+    assert_parity(g, gpu_run(g, path="tensor"))
+
+
+@pytest.mark.parametrize("sizes", [[31, 32, 33], [64, 65, 1, 96], [5, 0, 7], [2] * 33])
+def test_tensor_shapes(sizes):
+    colour, edges = refs.complete_kpartite(sizes)
+    g = _graph(colour, edges, len(sizes))
+    assert_parity(g, gpu_run(g, path="tensor"))
+
+
+def test_tensor_cascades_and_large_classes():
+    for seed in range(4):
+        g = synth.tiny_random(700 + seed, 400, 6, 0.06 + 0.01 * seed, planted=bool(seed % 2))
+        assert_parity(g, gpu_run(g, path="tensor"))
+    g = synth.tiny_random(61, 600, 4, 0.03, planted=True)
+    assert_parity(g, gpu_run(g, path="tensor"))
+
+
+@pytest.mark.parametrize("scale", [0.0625, 0.125])
+def test_tensor_dense_workload_reduced(scale):
+    g = synth.workload("c2", scale)
+    assert_parity(g, gpu_run(g, path="tensor", dense=True))
+
+
+def test_tensor_matches_bitset_on_batch_members():
+    for (n, k, p, planted, seed) in synth.batch_specs(6, 515, n_hi=900):
+        g = synth.kpartite(n, k, p, seed, planted=planted)
+        a = gpu_run(g, path="tensor", dense=True)
+        b = gpu_run(g, path="bitset", dense=True)
+        assert np.array_equal(a["alive"], b["alive"]) and np.array_equal(a["edges"], b["edges"])
+        assert a["stats"]["sweeps"] == b["stats"]["sweeps"]
