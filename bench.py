@@ -38,6 +38,13 @@ WORKLOAD_DESC = {
 METRIC = "edge-rule tests/s to fixpoint (time-to-fixpoint per graph)"
 UNIT = "edge tests/s"
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes read + written by one launch of the dominant kernel, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum); the summaries with
+# the commands are in profiles/.  An entry is removed when its kernel changes.
+MEASURED_TRAFFIC = {
+    ("c2", "bitset_persistent_kernel"): 2463744,
+    ("c2", "tensor_edge_kernel"): 19928064,
+}
 
 
 def parse():
@@ -306,15 +313,20 @@ def run_ours(args, world, rank, local, pg):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_derived = sms * 64 * 2.070e9  # 64 32-bit logic lanes per SM (probe-confirmed) x max SM clock
     achieved = alg_ops / launch_s
+    kernel = {1: "bitset_persistent_kernel", 2: "cta_fixpoint_kernel", 3: "sparse pass kernels",
+              4: "tensor_edge_kernel"}.get(st["path"], "?")
+    if kernel == "bitset_persistent_kernel" and args.loop != "device":
+        kernel = "bitset_sweep_kernel"
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_derived / 1e12, "unit": "Tops/s",
-                "frac": achieved / peak_derived, "traffic": None,
-                "kernel": {1: "bitset_persistent_kernel", 2: "cta_fixpoint_kernel", 3: "sparse pass kernels",
-                           4: "tensor_edge_kernel"}.get(st["path"], "?"),
+                "frac": achieved / peak_derived, "traffic": MEASURED_TRAFFIC.get((args.workload, kernel)),
+                "kernel": kernel,
                 "probe_lop3_tops": probe_ops / 1e12,
                 "ops_per_launch": alg_ops,
                 "note": "ops = live edges tested x (k-2) class-word ANDs; peak = SMs x 64 logic lanes x "
                         "2070 MHz (derived; the LOP3 probe measures it); launch time = CUDA events around "
-                        "kz_kernelize / passes (includes graph-launch overhead)"}
+                        "kz_kernelize / passes (includes graph-launch overhead); traffic = DRAM bytes read + "
+                        "written per launch from one ncu capture of this kernel on this workload (null where "
+                        "none was taken for the current kernel)"}
 
     # end-to-end through the C ABI: host buffers in, host buffers out
     e2e = None
