@@ -21,8 +21,13 @@ extern "C" {
  *   kind  0: 32-bit three-input logic ops (lop3.b32)
  *         1: 32-bit unsigned min (min.u32)
  *         2: three-input unsigned min (__vimin3_u32)
+ *         3: one lop3.b32 feeding one min.u32 (2 operations per step)
+ *         4: two lop3.b32 feeding one three-input min (3 operations per step)
  *   ops_per_s  receives the measured per-lane operations per second over the
- *              whole device (every SM busy, independent dependency chains)
+ *              whole device (every SM busy, independent dependency chains);
+ *              kinds 3 and 4 count every instruction of a step, so a rate
+ *              above kind 0's shows the two instruction kinds issuing to
+ *              different pipes
  *   ms         receives the measured kernel time
  * Returns KZ_ERR_ARG for a bad kind or null output, KZ_ERR_CUDA on failure.
  */

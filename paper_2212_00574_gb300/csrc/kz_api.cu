@@ -262,6 +262,8 @@ static kz_status run_one(kz_graph g, const kz_options &o, int path) {
   } else {
     if (!g->has_bitset) return KZ_ERR_UNSUPPORTED;
     KZ_TRY(state_to_bitset(g, g->stream));
+    // only the multi-CTA sweep kernels keep the two row buffers in step
+    if (path != KZ_PATH_BITSET) g->ab_synced = false;
     if (path == KZ_PATH_SMALL) KZ_TRY(cta_kernelize_one(g, o, g->stream));
     else if (path == KZ_PATH_TENSOR) KZ_TRY(tensor_kernelize(g, o, g->stream));
     else KZ_TRY(bitset_kernelize(g, o, g->stream));
@@ -281,6 +283,7 @@ kz_status kz_kernelize(kz_graph g, const kz_options *opt, void *stream) {
     if (!g->has_bitset || !g->model) return KZ_ERR_UNSUPPORTED;
     if (o.path != KZ_PATH_AUTO && o.path != KZ_PATH_BITSET) return KZ_ERR_UNSUPPORTED;
     KZ_TRY(state_to_bitset(g, g->stream));
+    g->ab_synced = false;
     KZ_TRY(learned_kernelize(g, o, g->stream));
     g->kernelized = true;
     g->path_ran = KZ_PATH_BITSET;
@@ -315,6 +318,7 @@ kz_status kz_kernelize_batch(kz_graph *graphs, int32_t count, const kz_options *
       continue;
     }
     KZ_TRY(state_to_bitset(graphs[i], s));
+    graphs[i]->ab_synced = false;
     rows.push_back(graphs[i]);
   }
   std::vector<kz_graph> loop, cta;

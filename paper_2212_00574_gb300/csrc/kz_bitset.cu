@@ -14,23 +14,28 @@
 // the failing edges already removes every edge of a failing vertex: the
 // adjacency rows never need masking with the vertex live set.
 //
-// Sweep kernel design (one launch per pass, warp-granular work items):
-//   * A warp owns a block X of 32 vertices u (lane = u) of class cu and holds
-//     plane 0 of their rows (k words) in registers.
-//   * It walks blocks Y of higher classes cv > cu.  For each Y it stages plane
-//     0 of the 32 rows v in shared memory, and for every v tests all lanes'
-//     pairs (u, v) at once: the pair is covered in class c when
+// Sweep kernel design:
+//   * The work of a pass is a sequence of units (X, Y): a block X of 32
+//     vertices u (lane = u) of class cu against one block Y of a higher class
+//     cv > cu.  The host cuts the sequence into one range of about equal cost
+//     per warp, so every warp of the grid ends its pass at about the same time.
+//   * A warp holds plane 0 of its X rows (k words per lane) in registers.  For
+//     each unit it stages plane 0 of the 32 rows v of Y in shared memory (the
+//     next unit's copy is in flight meanwhile) and for every v tests all
+//     lanes' pairs (u, v) at once: the pair is covered in class c when
 //     row_u[c] & row_v[c] != 0.  The classes cu and cv are forced to "covered"
 //     on both sides, so "every class covered" is one min-reduction over the
 //     k word-ANDs.  A live edge whose plane-0 test fails is recounted exactly
 //     over all planes (rare on dense graphs).
-//   * Results go to the other ping-pong buffer: the warp writes row u's word
-//     for block Y and (transposed with ballots) row v's word for block X.
-//     Every (X, Y) pair with class(X) < class(Y) belongs to exactly one work
-//     item, so every word of the next state is written exactly once.
-//   * The last warp to finish (atomic ticket) records the pass counters,
-//     flips the buffers when something was deleted and sets the CUDA-graph
-//     while-condition.
+//   * The two words a unit owns (row u's word for Y, and row v's word for X,
+//     the warp transpose of the first) go to the other ping-pong buffer only
+//     when they change in this pass or changed in the previous one: the other
+//     buffer already holds every other word.  A per-unit tag records the sweep
+//     of the last change.  After another path has written the rows, one pass
+//     writes every word.
+//   * The last CTA (persistent kernel) or warp (one-pass kernel) to finish
+//     records the pass counters, flips the buffers when something was deleted
+//     and, in the CUDA-graph loop, sets the while-condition.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -77,26 +82,49 @@ kz_status bitset_build_layout(kz_graph g) {
   return KZ_OK;
 }
 
-// Work list: each block x against the blocks of higher classes, cut into
-// pieces so that there are enough warps to fill the GPU.
-static void build_items(kz_graph g, int target_items, std::vector<WorkItem> &items) {
+// Work ranges of the sweep kernels: the units of a pass in order (x
+// ascending; for each x the blocks y of higher classes, or one vertex-only
+// unit y = nb for a block of the last class), cut into `warps` consecutive
+// ranges of about equal estimated cost.  A unit costs the members of Y it
+// tests plus a fixed part for staging and bookkeeping; the first unit of each
+// x also evaluates the vertex rule.
+static void build_ranges(kz_graph g, int warps, std::vector<WarpRange> &out, int64_t &n_units) {
+  constexpr int64_t kUnitFixed = 8, kVertexCost = 8;
   const int nb = (int)g->blocks.size();
-  int64_t pairs = 0;
-  for (int x = 0; x < nb; x++) pairs += nb - g->boff[g->blocks[x].c + 1];
-  int64_t S = std::max<int64_t>(1, (pairs + target_items - 1) / std::max(1, target_items));
-  items.clear();
+  auto ybegin = [&](int x) { return std::min(g->boff[g->blocks[x].c + 1], nb); };
+  int64_t total = 0;
+  n_units = 0;
   for (int x = 0; x < nb; x++) {
-    const int y_begin = g->boff[g->blocks[x].c + 1];
-    if (y_begin >= nb) {
-      items.push_back({x, nb, nb, 1});
+    const int yb = ybegin(x);
+    total += kVertexCost;
+    if (yb >= nb) {
+      total += kUnitFixed;
+      n_units += 1;
       continue;
     }
-    bool first = true;
-    for (int64_t y = y_begin; y < nb; y += S) {
-      items.push_back({x, (int32_t)y, (int32_t)std::min<int64_t>(nb, y + S), first ? 1 : 0});
-      first = false;
+    for (int y = yb; y < nb; y++) total += g->blocks[y].size + kUnitFixed;
+    n_units += nb - yb;
+  }
+  out.assign((size_t)warps, WarpRange{nb, nb, (int32_t)n_units, 0});
+  int w = 0;
+  int64_t acc = 0, unit = 0;
+  WarpRange cur{0, 0, 0, 0};
+  for (int x = 0; x < nb; x++) {
+    const int yb = ybegin(x);
+    const int y_end = yb >= nb ? nb + 1 : nb;
+    for (int y = yb; y < y_end; y++, unit++) {
+      acc += (y < nb ? g->blocks[y].size : 0) + kUnitFixed + (y == yb ? kVertexCost : 0);
+      if (cur.count == 0) cur = WarpRange{x, y, (int32_t)unit, 0};
+      cur.count++;
+      // close this warp's range once the running cost reaches its share
+      if (w < warps - 1 && acc * warps >= (int64_t)(w + 1) * total) {
+        out[(size_t)w++] = cur;
+        cur.count = 0;
+        while (w < warps - 1 && acc * warps >= (int64_t)(w + 1) * total) w++;  // empty ranges
+      }
     }
   }
+  if (cur.count) out[(size_t)w] = cur;
 }
 
 // ---------------------------------------------------------------------------
@@ -200,13 +228,15 @@ __global__ void init_vlive_kernel(uint32_t *V, const BlockDesc *blocks, int nb, 
 
 struct SweepArgs {
   const BlockDesc *blocks;
-  const WorkItem *items;
-  int32_t n_items;
+  const WarpRange *ranges;  // one per warp of the grid
+  int32_t nb;               // blocks
   int32_t k, ldw;
   const int32_t *rounds;  // blocks per class
+  const int32_t *boff;    // first block of each class, k + 1
   uint32_t *A0, *A1;      // ping-pong adjacency
   uint32_t *V0, *V1;      // ping-pong vertex live words
   int32_t *v_sweep;       // relabelled ids, may be null
+  uint8_t *changed;       // per unit: low byte of the sweep that last changed its words
   DevState *st;
   cudaGraphConditionalHandle cond;
   int32_t use_cond;
@@ -215,22 +245,153 @@ struct SweepArgs {
 };
 
 constexpr int kSweepWarps = 4;
+// density (edges / pairs of vertices in different classes) from which the
+// sweep kernels use the half-word plane-0 test
+constexpr double kHalfDensity = 0.6;
+// resident CTAs per SM the compiler is asked to fit: the half-word form
+// needs fewer registers, so it runs five 4-warp CTAs per SM
+template <int KMAX, bool HALF>
+constexpr int kMinCtas = (HALF && KMAX <= 32) ? 5 : 1;
 
-template <int KMAX>
-__device__ __forceinline__ void sweep_items(const SweepArgs &p, int cur, int64_t sweep_no, uint32_t *buf0,
-                                            uint32_t *buf1, int first_item, int item_stride, PassCounters &pc) {
-  GraphView G;
-  G.blocks = p.blocks;
-  G.rounds = p.rounds;
-  G.A0 = p.A0;
-  G.A1 = p.A1;
-  G.V0 = p.V0;
-  G.V1 = p.V1;
-  G.v_sweep = p.v_sweep;
-  G.k = p.k;
-  G.ldw = p.ldw;
-  for (int it = first_item; it < p.n_items; it += item_stride)
-    sweep_item<KMAX>(G, p.items[it], cur, sweep_no, buf0, buf1, pc);
+__device__ __forceinline__ void prefetch_l1(const uint32_t *p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// One warp's range of units in one Jacobi pass.  `cur` is the current
+// ping-pong buffer, `sweep_no` the productive sweeps so far, `full` asks for
+// every owned word to be written.  HALF selects the half-word plane-0 test
+// (first 16 members of each class; for dense graphs).
+template <int KMAX, bool HALF>
+__device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange r, int cur, int64_t sweep_no,
+                                            bool full, uint32_t *buf0, uint32_t *buf1, PassCounters &pc) {
+  if (r.count <= 0) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t *__restrict__ A = cur ? p.A1 : p.A0;
+  uint32_t *__restrict__ An = cur ? p.A0 : p.A1;
+  const uint32_t *__restrict__ Vc = cur ? p.V1 : p.V0;
+  uint32_t *__restrict__ Vn = cur ? p.V0 : p.V1;
+  const int k = p.k, ldw = p.ldw, nb = p.nb;
+  const int kq4 = (k + 3) >> 2;
+  const uint8_t tag_now = (uint8_t)(sweep_no & 0xff);
+  const uint8_t tag_next = (uint8_t)((sweep_no + 1) & 0xff);
+
+  // cursor (x, y): the next unit to stage; its adjacency word, change tag and
+  // live word are loaded one unit ahead
+  int x = r.x, y = r.y;
+  BlockDesc X = p.blocks[x];
+  int ybeg = min(p.boff[X.c + 1], nb);
+  BlockDesc Y = X;
+  if (y < nb) {
+    Y = p.blocks[y];
+    stage_block<KMAX>(A, ldw, Y, kq4, buf0, lane);
+  }
+  cp_async_commit();
+  uint32_t adj_n = (y < nb && lane < X.size) ? A[(int64_t)(X.base + lane) * ldw + Y.r * k + Y.c] : 0u;
+  uint8_t chg_n = y < nb ? p.changed[r.unit] : (uint8_t)0;
+  uint32_t vw_n = y == ybeg ? Vc[X.r * k + X.c] : 0u;
+
+  constexpr int KH = ((KMAX / 2) + 3) / 4 * 4;
+  constexpr int KW = HALF ? KH : KMAX;
+  const int kh = (k + 1) >> 1;
+  uint32_t F[KW], P[KW];  // plane 0 of the lanes' rows (full or half-word form), forced classes
+  int fu_x = -1, prev_cv = -1, vcnt = 0;
+  for (int i = 0; i < r.count; i++) {
+    const int xc = x, yc = y;
+    const BlockDesc Xc = X, Yc = Y;
+    const bool vflag = yc == ybeg;
+    const uint32_t adjw = adj_n, vword = vw_n;
+    const uint8_t chg = chg_n;
+    const int unit = r.unit + i;
+    uint32_t *sv = (i & 1) ? buf1 : buf0;
+    if (i + 1 < r.count) {
+      if (y + 1 < nb) {
+        y++;
+      } else {
+        x++;
+        X = p.blocks[x];
+        ybeg = min(p.boff[X.c + 1], nb);
+        y = ybeg;
+        if (lane < X.size) {  // warm L1 with plane 0 of the next block's rows
+          const uint32_t *row = A + (int64_t)(X.base + lane) * ldw;
+          prefetch_l1(row);
+          prefetch_l1(row + k - 1);
+        }
+      }
+      if (y < nb) {
+        Y = p.blocks[y];
+        stage_block<KMAX>(A, ldw, Y, kq4, (i & 1) ? buf0 : buf1, lane);
+      }
+      adj_n = (y < nb && lane < X.size) ? A[(int64_t)(X.base + lane) * ldw + Y.r * k + Y.c] : 0u;
+      chg_n = y < nb ? p.changed[unit + 1] : (uint8_t)0;
+      vw_n = y == ybeg ? Vc[X.r * k + X.c] : 0u;
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncwarp();
+
+    const int cu = Xc.c;
+    const bool valid = lane < Xc.size;
+    const int u = Xc.base + lane;
+    const uint32_t *rowu = A + (int64_t)(valid ? u : Xc.base) * ldw;
+    if (xc != fu_x) {  // always true at a vertex-rule unit (the first unit of its block)
+      if constexpr (HALF) {
+        uint32_t Fu[KMAX];
+        load_plane0<KMAX>(Fu, rowu, k, valid);
+        vcnt = plane0_vertex_cover<KMAX>(Fu, k, cu);
+        halve_plane0<KMAX, KH>(F, Fu);
+      } else {
+        load_plane0<KMAX>(F, rowu, k, valid);
+        vcnt = plane0_vertex_cover<KMAX>(F, k, cu);
+      }
+      fu_x = xc;
+      prev_cv = -1;
+    }
+    if (vflag) {
+      const bool live = valid && ((vword >> lane) & 1u);
+      int cnt = vcnt;
+      if (live && cnt < k - 1) cnt = exact_vertex_cover_row(rowu, k, p.rounds, cu);
+      const bool fail = live && cnt < k - 1;
+      const uint32_t failmask = __ballot_sync(0xffffffffu, fail);
+      if (lane == 0) {
+        Vn[Xc.r * k + cu] = vword & ~failmask;
+        pc.dv += __popc(failmask);
+      }
+      if (fail && p.v_sweep) p.v_sweep[u] = (int32_t)(sweep_no + 1);
+    }
+    if (yc < nb) {
+      const int cv = Yc.c;
+      if (cv != prev_cv) {
+        if constexpr (HALF) half_mask<KH>(P, k, cu, cv);
+        else pair_mask<KMAX>(P, k, cu, cv);
+        prev_cv = cv;
+      }
+      pc.tests += __popc(adjw);
+      const uint32_t *ybase = A + (int64_t)Yc.base * ldw;
+      uint32_t open, del = 0;
+      if constexpr (HALF) {
+        halve_staged_rows<KMAX>(sv, Yc.size, k, lane);
+        __syncwarp();
+        open = half_unsettled<KH>(F, P, sv, KMAX, adjw, kh);
+        // the staged rows now hold half-words: the recount reads plane 0 from the rows
+        if (open) del = recount_unsettled(rowu, ybase, ldw, ybase, ldw, open, k, cu, cv, p.rounds);
+      } else {
+        open = plane0_unsettled<KMAX>(F, P, sv, adjw, k);
+        if (open) del = recount_unsettled(rowu, sv, KMAX, ybase, ldw, open, k, cu, cv, p.rounds);
+      }
+      const bool anydel = __any_sync(0xffffffffu, del != 0u);
+      if (anydel || full || chg == tag_now) {
+        const uint32_t keep = adjw & ~del;
+        if (valid) An[(int64_t)u * ldw + Yc.r * k + cv] = keep;
+        const uint32_t col = transpose32(keep);
+        if (lane < Yc.size) An[(int64_t)(Yc.base + lane) * ldw + Xc.r * k + cu] = col;
+        if (anydel && lane == 0) p.changed[unit] = tag_next;
+        pc.de += __popc(del);
+      }
+    }
+    __syncwarp();
+  }
+  cp_async_wait<0>();
+  __syncwarp();
 }
 
 template <int KMAX>
@@ -243,8 +404,8 @@ __device__ __forceinline__ void reduce_counters(PassCounters &pc) {
 }
 
 // One Jacobi pass per launch (the CUDA-graph loop and the host-driven loop).
-template <int KMAX>
-__global__ void __launch_bounds__(kSweepWarps * 32)
+template <int KMAX, bool HALF>
+__global__ void __launch_bounds__(kSweepWarps * 32, kMinCtas<KMAX, HALF>)
     bitset_sweep_kernel(SweepArgs p) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int lane = threadIdx.x & 31;
@@ -254,9 +415,10 @@ __global__ void __launch_bounds__(kSweepWarps * 32)
   DevState *st = p.st;
   const int cur = *((volatile int32_t *)&st->cur);
   const int64_t sweep_no = *((volatile int64_t *)&st->sweeps);
+  const bool full = *((volatile int32_t *)&st->full_write) != 0;
   const int warps_total = gridDim.x * kSweepWarps;
   PassCounters pc;
-  sweep_items<KMAX>(p, cur, sweep_no, buf0, buf1, blockIdx.x * kSweepWarps + wib, warps_total, pc);
+  sweep_range<KMAX, HALF>(p, p.ranges[blockIdx.x * kSweepWarps + wib], cur, sweep_no, full, buf0, buf1, pc);
   reduce_counters<KMAX>(pc);
   if (lane == 0) {
     if (pc.tests) atomicAdd(&st->pass_tests, pc.tests);
@@ -287,8 +449,8 @@ constexpr uint32_t kBarrierSpinLimit = 1u << 25;
 // closes the pass (counters, buffer flip) and releases the others.  Every
 // barrier wait is bounded: one that runs out records KZ_ERR_TIMEOUT and all
 // CTAs leave.
-template <int KMAX>
-__global__ void __launch_bounds__(kSweepWarps * 32)
+template <int KMAX, bool HALF>
+__global__ void __launch_bounds__(kSweepWarps * 32, kMinCtas<KMAX, HALF>)
     bitset_persistent_kernel(SweepArgs p) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ int s_go;
@@ -297,12 +459,12 @@ __global__ void __launch_bounds__(kSweepWarps * 32)
   uint32_t *buf0 = smem + wib * 2 * 32 * KMAX;
   uint32_t *buf1 = buf0 + 32 * KMAX;
   DevState *st = p.st;
-  const int warps_total = gridDim.x * kSweepWarps;
   for (;;) {
     const int cur = *((volatile int32_t *)&st->cur);
     const int64_t sweep_no = *((volatile int64_t *)&st->sweeps);
+    const bool full = *((volatile int32_t *)&st->full_write) != 0;
     PassCounters pc;
-    sweep_items<KMAX>(p, cur, sweep_no, buf0, buf1, blockIdx.x * kSweepWarps + wib, warps_total, pc);
+    sweep_range<KMAX, HALF>(p, p.ranges[blockIdx.x * kSweepWarps + wib], cur, sweep_no, full, buf0, buf1, pc);
     reduce_counters<KMAX>(pc);
     if (lane == 0) {
       if (pc.tests) atomicAdd(&st->pass_tests, pc.tests);
@@ -374,43 +536,29 @@ __global__ void reset_state_kernel(DevState *st) {
 
 typedef void (*SweepFn)(SweepArgs);
 
-static SweepFn pick_sweep(int k, int &kmax) {
-#define KZ_CASE(K)                        \
-  if (k <= K) {                           \
-    kmax = K;                             \
-    return bitset_sweep_kernel<K>;        \
+#define KZ_KMAX_LIST(X) X(4) X(8) X(12) X(16) X(20) X(24) X(28) X(32) X(48) X(64)
+
+// One-pass kernel for k colours (kmax receives the template width); HALF
+// selects the half-word plane-0 test.
+static SweepFn pick_sweep(int k, bool half, int &kmax) {
+#define KZ_CASE(K)                                                      \
+  if (k <= K) {                                                         \
+    kmax = K;                                                           \
+    return half ? bitset_sweep_kernel<K, true> : bitset_sweep_kernel<K, false>; \
   }
-  KZ_CASE(4)
-  KZ_CASE(8)
-  KZ_CASE(12)
-  KZ_CASE(16)
-  KZ_CASE(20)
-  KZ_CASE(24)
-  KZ_CASE(28)
-  KZ_CASE(32)
-  KZ_CASE(48)
-  KZ_CASE(64)
+  KZ_KMAX_LIST(KZ_CASE)
 #undef KZ_CASE
   kmax = 0;
   return nullptr;
 }
 
-static SweepFn pick_persistent(int k, int &kmax) {
-#define KZ_CASE(K)                           \
-  if (k <= K) {                              \
-    kmax = K;                                \
-    return bitset_persistent_kernel<K>;      \
+static SweepFn pick_persistent(int k, bool half, int &kmax) {
+#define KZ_CASE(K)                                                                \
+  if (k <= K) {                                                                   \
+    kmax = K;                                                                     \
+    return half ? bitset_persistent_kernel<K, true> : bitset_persistent_kernel<K, false>; \
   }
-  KZ_CASE(4)
-  KZ_CASE(8)
-  KZ_CASE(12)
-  KZ_CASE(16)
-  KZ_CASE(20)
-  KZ_CASE(24)
-  KZ_CASE(28)
-  KZ_CASE(32)
-  KZ_CASE(48)
-  KZ_CASE(64)
+  KZ_KMAX_LIST(KZ_CASE)
 #undef KZ_CASE
   kmax = 0;
   return nullptr;
@@ -426,6 +574,8 @@ static int sm_count() {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   return sms > 0 ? sms : 1;
 }
+
+static kz_status sweep_grid_size(kz_graph g, int &grid);
 
 kz_status bitset_finish_load(kz_graph g, cudaStream_t s) {
   const int nb = (int)g->blocks.size();
@@ -446,14 +596,28 @@ kz_status bitset_finish_load(kz_graph g, cudaStream_t s) {
   KZ_TRY(graph_alloc(g, &g->d_rounds, (size_t)g->k, s));
   KZ_CUDA_TRY(cudaMemcpyAsync(g->d_rounds, g->rounds.data(), sizeof(int32_t) * g->k,
                               cudaMemcpyHostToDevice, s));
-  // work items: aim for ~16 warps per SM scheduler
-  std::vector<WorkItem> items;
-  build_items(g, 16 * 4 * sm_count(), items);
-  g->n_items = (int32_t)items.size();
-  KZ_TRY(graph_alloc(g, &g->d_items, std::max<size_t>(items.size(), 1), s));
-  if (!items.empty())
-    KZ_CUDA_TRY(cudaMemcpyAsync(g->d_items, items.data(), sizeof(WorkItem) * items.size(),
+  // the half-word plane-0 test pays off when 16 members of a class almost
+  // always hold a common neighbour: dense graphs
+  {
+    double cross = 0, tot = 0;
+    for (int c = 0; c < g->k; c++) {
+      const double sz = g->coff[c + 1] - g->coff[c];
+      cross += tot * sz;
+      tot += sz;
+    }
+    g->half_plane0 = cross > 0 && (double)g->m >= kHalfDensity * cross;
+  }
+  // one work range per warp of a grid that is resident all at once
+  if (g->k <= 64) {
+    KZ_TRY(sweep_grid_size(g, g->sweep_grid));
+    std::vector<WarpRange> ranges;
+    build_ranges(g, g->sweep_grid * kSweepWarps, ranges, g->n_units);
+    KZ_TRY(graph_alloc(g, &g->d_ranges, ranges.size(), s));
+    KZ_CUDA_TRY(cudaMemcpyAsync(g->d_ranges, ranges.data(), sizeof(WarpRange) * ranges.size(),
                                 cudaMemcpyHostToDevice, s));
+    KZ_TRY(graph_alloc(g, &g->d_changed, (size_t)std::max<int64_t>(g->n_units, 1), s));
+    KZ_CUDA_TRY(cudaMemsetAsync(g->d_changed, 0xff, (size_t)std::max<int64_t>(g->n_units, 1), s));
+  }
   KZ_TRY(graph_alloc(g, &g->A[0], (size_t)g->n * g->ldw, s));
   KZ_TRY(graph_alloc(g, &g->A[1], (size_t)g->n * g->ldw, s));
   KZ_TRY(graph_alloc(g, &g->v_sweep, (size_t)std::max(g->n, 1), s));
@@ -478,30 +642,57 @@ kz_status bitset_reset(kz_graph g, cudaStream_t s) {
   reset_state_kernel<<<1, 1, 0, s>>>(g->st);
   KZ_CUDA_TRY(cudaGetLastError());
   g->kernelized = false;
+  g->ab_synced = true;  // both row buffers now equal the loaded graph
+  return KZ_OK;
+}
+
+// Shared memory of a sweep kernel and its resident CTAs per SM.
+static kz_status kernel_fit(SweepFn fn, int kmax, size_t &smem, int &per_sm) {
+  smem = (size_t)kSweepWarps * 2 * 32 * kmax * 4;
+  // always raise the limit: the kernels' static shared memory comes on top
+  KZ_CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  per_sm = 0;
+  KZ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn,
+                                                            kSweepWarps * 32, smem));
+  return KZ_OK;
+}
+
+// The grid of both sweep kernels: every CTA resident at once (the persistent
+// kernel's grid barrier needs that), and no more warps than units.
+static kz_status sweep_grid_size(kz_graph g, int &grid) {
+  int kmax = 0, kmax2 = 0, per_a = 0, per_b = 0;
+  size_t smem = 0;
+  SweepFn fa = pick_persistent(g->k, g->half_plane0, kmax), fb = pick_sweep(g->k, g->half_plane0, kmax2);
+  if (!fa || !fb) return KZ_ERR_ARG;
+  KZ_TRY(kernel_fit(fa, kmax, smem, per_a));
+  KZ_TRY(kernel_fit(fb, kmax2, smem, per_b));
+  const int per_sm = std::max(1, std::min(per_a, per_b));
+  int64_t units = 0;
+  const int nb = (int)g->blocks.size();
+  for (int x = 0; x < nb; x++) units += std::max(1, nb - std::min(g->boff[g->blocks[x].c + 1], nb));
+  const int64_t want = (std::max<int64_t>(units, 1) + kSweepWarps - 1) / kSweepWarps;
+  grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)per_sm * sm_count()));
   return KZ_OK;
 }
 
 static kz_status launch_config(kz_graph g, SweepFn fn, int kmax, int &grid, size_t &smem) {
-  smem = (size_t)kSweepWarps * 2 * 32 * kmax * 4;
-  // always raise the limit: the kernels' static shared memory comes on top
-  KZ_CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  KZ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn,
-                                                            kSweepWarps * 32, smem));
-  per_sm = std::max(per_sm, 1);
-  const int want = (g->n_items + kSweepWarps - 1) / kSweepWarps;
-  grid = std::max(1, std::min(want, per_sm * sm_count()));
+  KZ_TRY(kernel_fit(fn, kmax, smem, per_sm));
+  grid = g->sweep_grid;
+  if (grid <= 0 || grid > std::max(per_sm, 1) * sm_count()) return KZ_ERR_INTERNAL;
   return KZ_OK;
 }
 
 static SweepArgs make_args(kz_graph g) {
   SweepArgs a;
   a.blocks = g->d_blocks;
-  a.items = g->d_items;
-  a.n_items = g->n_items;
+  a.ranges = g->d_ranges;
+  a.nb = (int32_t)g->blocks.size();
   a.k = g->k;
   a.ldw = g->ldw;
   a.rounds = g->d_rounds;
+  a.boff = g->d_boff;
+  a.changed = g->d_changed;
   a.A0 = g->A[0];
   a.A1 = g->A[1];
   a.V0 = g->V[0];
@@ -519,7 +710,7 @@ static SweepArgs make_args(kz_graph g) {
 // sweep-kernel launch per pass until the kernel clears the condition.
 static kz_status build_loop_graph(kz_graph g, int64_t max_sweeps) {
   int kmax = 0;
-  SweepFn fn = pick_sweep(g->k, kmax);
+  SweepFn fn = pick_sweep(g->k, g->half_plane0, kmax);
   if (!fn) return KZ_ERR_ARG;
   int grid = 0;
   size_t smem = 0;
@@ -592,14 +783,25 @@ static kz_status build_loop_graph(kz_graph g, int64_t max_sweeps) {
   return KZ_OK;
 }
 
+// Asks the next pass to write every word of the next buffer (after anything
+// but a sweep kernel wrote the rows).
+static kz_status request_full_write(kz_graph g, cudaStream_t s) {
+  KZ_CUDA_TRY(cudaMemsetAsync(&g->st->full_write, 1, sizeof(int32_t), s));
+  return KZ_OK;
+}
+
 kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
   int64_t max_sweeps = opt.max_sweeps > 0 ? opt.max_sweeps : (int64_t)g->n + g->m + 1;
+  if (!g->ab_synced) {
+    KZ_TRY(request_full_write(g, s));
+    g->ab_synced = true;
+  }
   if (g->n > 0 && opt.use_graph == 1) {
     // every pass in one cooperative launch (grid sized to be fully resident)
     begin_run_kernel<<<1, 1, 0, s>>>(g->st, max_sweeps, 0);
     KZ_CUDA_TRY(cudaGetLastError());
     int kmax = 0;
-    SweepFn fn = pick_persistent(g->k, kmax);
+    SweepFn fn = pick_persistent(g->k, g->half_plane0, kmax);
     if (!fn) return KZ_ERR_ARG;
     int grid = 0;
     size_t smem = 0;
@@ -627,7 +829,7 @@ kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
   }
   // host-driven loop: one launch per pass, the host reads the continue flag
   int kmax = 0;
-  SweepFn fn = pick_sweep(g->k, kmax);
+  SweepFn fn = pick_sweep(g->k, g->half_plane0, kmax);
   if (!fn) return KZ_ERR_ARG;
   int grid = 0;
   size_t smem = 0;
@@ -652,8 +854,11 @@ kz_status bitset_begin_run(kz_graph g, int64_t max_sweeps, cudaStream_t s) {
 kz_status bitset_one_pass(kz_graph g, cudaStream_t s, int *cont) {
   *cont = 0;
   if (g->n == 0) return KZ_OK;
+  // the caller may have changed the rows in place between passes
+  KZ_TRY(request_full_write(g, s));
+  g->ab_synced = false;
   int kmax = 0;
-  SweepFn fn = pick_sweep(g->k, kmax);
+  SweepFn fn = pick_sweep(g->k, g->half_plane0, kmax);
   if (!fn) return KZ_ERR_ARG;
   int grid = 0;
   size_t smem = 0;
@@ -676,7 +881,7 @@ kz_status bitset_barrier_timeout_probe(kz_graph g, uint32_t spin_limit, cudaStre
   begin_run_kernel<<<1, 1, 0, s>>>(g->st, (int64_t)g->n + g->m + 1, 0);
   KZ_CUDA_TRY(cudaGetLastError());
   int kmax = 0;
-  SweepFn fn = pick_persistent(g->k, kmax);
+  SweepFn fn = pick_persistent(g->k, g->half_plane0, kmax);
   if (!fn) return KZ_ERR_ARG;
   int grid = 0;
   size_t smem = 0;

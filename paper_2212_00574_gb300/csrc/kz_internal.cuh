@@ -49,13 +49,26 @@ struct WorkItem {
   int32_t vflag;
 };
 
+// A warp's share of one pass of the single-graph sweep kernels: `count`
+// consecutive units starting at unit number `unit` = (x, y).  Units run over
+// x in order, and for each x over the blocks y of higher classes (a block x
+// of the last class has one unit with y = number of blocks, which only
+// evaluates the vertex rule).  The host cuts the unit sequence into equal-cost
+// ranges, one per warp.
+struct WarpRange {
+  int32_t x;
+  int32_t y;
+  int32_t unit;
+  int32_t count;
+};
+
 // Device-resident loop state of one graph.  Written by the sweep kernels'
 // last warp; read by the host only after a synchronisation.
 struct DevState {
   int32_t cur;        // which ping-pong buffer holds the live state
   int32_t status;     // kz_status of the running / last kernelize
   int32_t cont;       // 1 while another pass is needed
-  int32_t pad0;
+  int32_t full_write; // next pass writes every word of the next buffer (cleared after a pass)
   int64_t sweeps;     // productive sweeps so far
   int64_t passes;     // passes so far
   int64_t tests;      // live edges tested, all passes
@@ -136,8 +149,15 @@ struct kz_graph_s {
   int32_t *d_zero = nullptr;         // a device 0 (queue order of a single graph)
   int32_t *d_perm = nullptr;   // n
   kz::BlockDesc *d_blocks = nullptr;
-  kz::WorkItem *d_items = nullptr;
-  int32_t n_items = 0;
+  kz::WarpRange *d_ranges = nullptr;  // one per warp of the sweep kernels' grid
+  int32_t sweep_grid = 0;             // CTAs of that grid
+  uint8_t *d_changed = nullptr;       // per unit: low byte of the sweep that last changed it
+  int64_t n_units = 0;
+  // true when the two row buffers differ only in the words of units whose
+  // change tag names the current sweep (false after any other path or a
+  // conversion wrote the rows; the next bitset pass then writes every word)
+  bool ab_synced = false;
+  bool half_plane0 = false;           // sweep kernels use the half-word plane-0 test
   kz::DevState *st = nullptr;
 
   // which representation holds the live state: KZ_PATH_BITSET (bitset rows,

@@ -871,6 +871,7 @@ kz_status kz_collect_trace(kz_graph g, int64_t per_sweep_cap, uint64_t seed, flo
   if (!g || per_sweep_cap < 0 || cap < 0 || (cap > 0 && (!X || !y)) || !count) return KZ_ERR_ARG;
   if (!g->has_bitset) return KZ_ERR_UNSUPPORTED;
   KZ_TRY(state_to_bitset(g, g->stream));
+  g->ab_synced = false;
   KZ_TRY(learned_collect(g, per_sweep_cap, seed, X, y, cap, count));
   g->kernelized = true;
   g->path_ran = KZ_PATH_BITSET;

@@ -25,7 +25,12 @@ template <int KIND>
 __global__ void int_probe_kernel(uint32_t seed, uint32_t *out) {
   uint32_t x[kChains];
 #pragma unroll
-  for (int i = 0; i < kChains; i++) x[i] = seed * (threadIdx.x + 7 * i + 1);
+  uint32_t m[kChains];
+#pragma unroll
+  for (int i = 0; i < kChains; i++) {
+    x[i] = seed * (threadIdx.x + 7 * i + 1);
+    m[i] = 0xffffffffu - (uint32_t)i;
+  }
   const uint32_t y = seed ^ blockIdx.x, z = seed + 3u;
   for (int it = 0; it < kIters; it++) {
 #pragma unroll
@@ -33,18 +38,27 @@ __global__ void int_probe_kernel(uint32_t seed, uint32_t *out) {
       if (KIND == 0) x[i] = lop3_and_or(x[i], y, z);
       if (KIND == 1) x[i] = umin_asm(x[i], y + (uint32_t)i);
       if (KIND == 2) x[i] = __vimin3_u32(x[i], y, z + (uint32_t)i);
+      if (KIND == 3) {  // one logic op feeding one two-input min
+        x[i] = lop3_and_or(x[i], y, z);
+        m[i] = umin_asm(m[i], x[i]);
+      }
+      if (KIND == 4) {  // two logic ops feeding one three-input min
+        const uint32_t a = lop3_and_or(x[i], y, z), b = lop3_and_or(x[i], z, y);
+        m[i] = __vimin3_u32(m[i], a, b);
+        x[i] = a;
+      }
     }
   }
   uint32_t acc = 0;
 #pragma unroll
-  for (int i = 0; i < kChains; i++) acc ^= x[i];
+  for (int i = 0; i < kChains; i++) acc ^= x[i] ^ m[i];
   if (acc == 0x9e3779b9u) out[0] = acc;  // keeps the chains live
 }
 
 }  // namespace
 
 extern "C" kz_status kz_probe_int_throughput(int32_t kind, double *ops_per_s, double *ms, void *stream) {
-  if (!ops_per_s || !ms || kind < 0 || kind > 2) return KZ_ERR_ARG;
+  if (!ops_per_s || !ms || kind < 0 || kind > 4) return KZ_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return KZ_ERR_CUDA;
@@ -55,8 +69,9 @@ extern "C" kz_status kz_probe_int_throughput(int32_t kind, double *ops_per_s, do
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  void (*fn)(uint32_t, uint32_t *) =
-      kind == 0 ? int_probe_kernel<0> : (kind == 1 ? int_probe_kernel<1> : int_probe_kernel<2>);
+  void (*const fns[5])(uint32_t, uint32_t *) = {int_probe_kernel<0>, int_probe_kernel<1>, int_probe_kernel<2>,
+                                                 int_probe_kernel<3>, int_probe_kernel<4>};
+  void (*fn)(uint32_t, uint32_t *) = fns[kind];
   fn<<<blocks, threads, 0, s>>>(12345u, out);  // warm-up
   cudaEventRecord(e0, s);
   fn<<<blocks, threads, 0, s>>>(54321u, out);
@@ -68,7 +83,8 @@ extern "C" kz_status kz_probe_int_throughput(int32_t kind, double *ops_per_s, do
   cudaEventDestroy(e1);
   cudaFreeAsync(out, s);
   if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return KZ_ERR_CUDA;
-  const double ops = (double)blocks * threads * kIters * kChains;
+  const double per_chain_step = kind == 3 ? 2.0 : (kind == 4 ? 3.0 : 1.0);
+  const double ops = (double)blocks * threads * kIters * kChains * per_chain_step;
   *ms = t;
   *ops_per_s = ops / (t * 1e-3);
   return KZ_OK;

@@ -207,6 +207,113 @@ __device__ __forceinline__ uint32_t plane0_unsettled(const uint32_t (&Fu)[KMAX],
   return open & adjw;
 }
 
+// ---------------------------------------------------------------------------
+// Half-word form of plane 0, for dense graphs: word j holds the first 16
+// members of class 2j (low half) and of class 2j+1 (high half), so one LOP3
+// tests two classes and one three-input 16x2 min reduces four.  A pair is
+// settled when every needed class has a common neighbour among the first 16
+// members; anything else goes to the exact recount over the full rows.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t pack_halves(uint32_t lo, uint32_t hi) {
+  return __byte_perm(lo, hi, 0x5410);  // low 16 bits of lo, then low 16 bits of hi
+}
+
+// Half-word plane 0 of a full-word plane 0 (KH = KMAX/2 rounded up to 4).
+template <int KMAX, int KH>
+__device__ __forceinline__ void halve_plane0(uint32_t (&H)[KH], const uint32_t (&F)[KMAX]) {
+#pragma unroll
+  for (int j = 0; j < KH; j++) {
+    const uint32_t lo = 2 * j < KMAX ? F[2 * j] : 0u;
+    const uint32_t hi = 2 * j + 1 < KMAX ? F[2 * j + 1] : 0u;
+    H[j] = pack_halves(lo, hi);
+  }
+}
+
+// Forced half-words: all ones for the classes of u and v and for classes >= k.
+template <int KH>
+__device__ __forceinline__ void half_mask(uint32_t (&P)[KH], int k, int cu, int cv) {
+#pragma unroll
+  for (int j = 0; j < KH; j++) {
+    const int c0 = 2 * j, c1 = 2 * j + 1;
+    const bool f0 = c0 == cu || c0 == cv || c0 >= k;
+    const bool f1 = c1 == cu || c1 == cv || c1 >= k;
+    P[j] = (f0 ? 0x0000ffffu : 0u) | (f1 ? 0xffff0000u : 0u);
+  }
+}
+
+// In-place conversion of staged plane-0 rows (k words each, KMAX apart) to the
+// half-word form: lane b converts row b.
+template <int KMAX>
+__device__ __forceinline__ void halve_staged_rows(uint32_t *buf, int rows, int k, int lane) {
+  constexpr int KH = ((KMAX / 2) + 3) / 4 * 4;
+  if (lane < rows) {
+    uint32_t *row = buf + lane * KMAX;
+    uint32_t w[KMAX];
+#pragma unroll
+    for (int q = 0; q < KMAX / 4; q++) {
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (4 * q < k) v = reinterpret_cast<const uint4 *>(row)[q];
+      w[4 * q + 0] = v.x;
+      w[4 * q + 1] = v.y;
+      w[4 * q + 2] = v.z;
+      w[4 * q + 3] = v.w;
+    }
+    uint32_t h[KH];
+    halve_plane0<KMAX, KH>(h, w);
+    const int kh = (k + 1) >> 1;
+#pragma unroll
+    for (int q = 0; q < KH / 4; q++) {
+      if (4 * q >= kh) break;
+      reinterpret_cast<uint4 *>(row)[q] = make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+    }
+  }
+}
+
+__device__ __forceinline__ bool has_zero_half(uint32_t m) { return (m & 0xffffu) == 0u || m < 0x10000u; }
+
+// Hot loop of the half-word form (see plane0_unsettled): returns the lane's
+// live edges that the first 16 members of each class do not settle.
+template <int KH>
+__device__ __forceinline__ uint32_t half_unsettled(const uint32_t (&F)[KH], const uint32_t (&P)[KH],
+                                                   const uint32_t *sv, int stride, uint32_t adjw, int kh) {
+  uint32_t bits = __reduce_or_sync(0xffffffffu, adjw);
+  uint32_t open = 0;
+  while (bits) {
+    const int b0 = __ffs(bits) - 1;
+    bits &= bits - 1;
+    const uint4 *f0 = reinterpret_cast<const uint4 *>(sv + b0 * stride);
+    if (bits) {
+      const int b1 = __ffs(bits) - 1;
+      bits &= bits - 1;
+      const uint4 *f1 = reinterpret_cast<const uint4 *>(sv + b1 * stride);
+      uint32_t m0 = 0xffffffffu, m1 = 0xffffffffu, m2 = 0xffffffffu, m3 = 0xffffffffu;
+#pragma unroll
+      for (int q = 0; q < KH / 4; q++) {
+        if (4 * q >= kh) break;
+        const uint4 w0 = f0[q], w1 = f1[q];
+        m0 = __vimin3_u16x2(m0, (F[4 * q + 0] & w0.x) | P[4 * q + 0], (F[4 * q + 1] & w0.y) | P[4 * q + 1]);
+        m1 = __vimin3_u16x2(m1, (F[4 * q + 2] & w0.z) | P[4 * q + 2], (F[4 * q + 3] & w0.w) | P[4 * q + 3]);
+        m2 = __vimin3_u16x2(m2, (F[4 * q + 0] & w1.x) | P[4 * q + 0], (F[4 * q + 1] & w1.y) | P[4 * q + 1]);
+        m3 = __vimin3_u16x2(m3, (F[4 * q + 2] & w1.z) | P[4 * q + 2], (F[4 * q + 3] & w1.w) | P[4 * q + 3]);
+      }
+      if (has_zero_half(__vimin3_u16x2(m0, m1, 0xffffffffu))) open |= 1u << b0;
+      if (has_zero_half(__vimin3_u16x2(m2, m3, 0xffffffffu))) open |= 1u << b1;
+    } else {
+      uint32_t m0 = 0xffffffffu, m1 = 0xffffffffu;
+#pragma unroll
+      for (int q = 0; q < KH / 4; q++) {
+        if (4 * q >= kh) break;
+        const uint4 w0 = f0[q];
+        m0 = __vimin3_u16x2(m0, (F[4 * q + 0] & w0.x) | P[4 * q + 0], (F[4 * q + 1] & w0.y) | P[4 * q + 1]);
+        m1 = __vimin3_u16x2(m1, (F[4 * q + 2] & w0.z) | P[4 * q + 2], (F[4 * q + 3] & w0.w) | P[4 * q + 3]);
+      }
+      if (has_zero_half(__vimin3_u16x2(m0, m1, 0xffffffffu))) open |= 1u << b0;
+    }
+  }
+  return open & adjw;
+}
+
 // Recount, lane by lane, the edges plane 0 left open: the classes plane 0
 // leaves uncovered (from the row of u and the staged row of v) are searched
 // in their later planes.  Returns the lane's deletion mask.  Takes pointers
@@ -242,6 +349,22 @@ __device__ __forceinline__ uint32_t transpose_deletions(uint32_t del) {
   return delT;
 }
 
+// 32 x 32 bit-matrix transpose across the warp: lane i holds row i (bit j =
+// entry (i, j)); lane j receives column j (bit i = entry (i, j)).  Five
+// butterfly stages swap the off-diagonal half-blocks of 16, 8, 4, 2 and 1.
+__device__ __forceinline__ uint32_t transpose32(uint32_t w) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t masks[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    const int sft = 16 >> i;
+    const uint32_t m = masks[i];
+    const uint32_t q = __shfl_xor_sync(0xffffffffu, w, sft);
+    w = (lane & sft) ? ((w & ~m) | ((q >> sft) & m)) : ((w & m) | ((q << sft) & ~m));
+  }
+  return w;
+}
+
 // Records a finished pass in the device state and decides whether another
 // pass follows: a pass that deleted something is applied (sweeps + 1, the
 // ping-pong buffers flip) unless the sweep limit is reached, in which case it
@@ -250,6 +373,7 @@ __device__ __forceinline__ int finish_pass(DevState *st, unsigned long long dv, 
                                            unsigned long long tests) {
   st->passes += 1;
   st->tests += (int64_t)tests;
+  st->full_write = 0;
   int cont = 0;
   if (dv + de > 0) {
     if (st->sweeps >= st->max_sweeps) {

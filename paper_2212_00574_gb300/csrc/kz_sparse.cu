@@ -625,6 +625,7 @@ kz_status state_to_bitset(kz_graph g, cudaStream_t s) {
                                                         g->sp_vlive[g->sp_cur]);
   KZ_CUDA_TRY(cudaGetLastError());
   g->owner = KZ_PATH_BITSET;
+  g->ab_synced = false;  // only the current buffer was rebuilt
   return KZ_OK;
 }
 

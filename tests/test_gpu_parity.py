@@ -408,3 +408,75 @@ def test_batch_limit_and_repeat():
     finally:
         for h in handles:
             h.close()
+
+
+# ---------------------------------------------------------------------------
+# multi-CTA sweep: equal-cost warp ranges and change-tagged writes
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("loop", [0, 1, 2])
+def test_warp_ranges_multi_sweep(loop):
+    """Graphs with thousands of units (several per warp, ranges crossing block
+    boundaries) that take several sweeps: only words that changed in this or
+    the previous sweep are rewritten, so every sweep checks the protocol."""
+    for (n, k, p, seed) in ((3000, 10, 0.1, 5), (2500, 8, 0.07, 5)):
+        g = synth.tiny_random(seed, n, k, p, planted=True)
+        orc = assert_parity(g, gpu_run(g, path="bitset", use_graph=loop))
+        assert orc["sweeps"] >= 3
+
+
+def test_sweep_by_sweep_continuation():
+    """One sweep per call, continued on the same handle until the fixpoint:
+    the state after each call equals the oracle's after that many sweeps."""
+    g = synth.tiny_random(5, 2500, 8, 0.07, planted=True)
+    edges = g.get_edges()
+    orc = oracle.fixpoint(g.colour, edges, g.k)
+    with kz.KernelGraph.from_synth(g) as kg:
+        for s in range(1, orc["sweeps"] + 2):
+            kg.kernelize(path="bitset", max_sweeps=1)
+            alive, got, st = kg.fetch(allow=(kz.KZ_OK, kz.KZ_ERR_LIMIT))
+            want = oracle.fixpoint(g.colour, edges, g.k, max_sweeps=s, raise_on_limit=False)
+            assert np.array_equal(alive, want["vlive"]), s
+            assert np.array_equal(got, edges[want["elive"].astype(bool)]), s
+        assert st["status"] == kz.KZ_OK and st["sweeps"] == 0
+
+
+@pytest.mark.parametrize("first", ["small", "tensor", "sparse"])
+def test_bitset_after_other_path(first):
+    """Another path writes the rows part-way (one sweep); the multi-CTA sweep
+    then writes every word once and finishes the fixpoint."""
+    g = synth.tiny_random(5, 2500, 8, 0.07, planted=True)
+    edges = g.get_edges()
+    orc = oracle.fixpoint(g.colour, edges, g.k)
+    with kz.KernelGraph.from_synth(g) as kg:
+        kg.kernelize(path="bitset")          # rows in step after a converged run
+        kg.reset()
+        kg.kernelize(path=first, max_sweeps=1)
+        kg.kernelize(path="bitset")
+        alive, got, st = kg.fetch()
+    assert np.array_equal(alive, orc["vlive"])
+    assert np.array_equal(got, edges[orc["elive"].astype(bool)])
+
+
+def _two_density_graph(seed, n, k, n_dense, p_dense, p_sparse):
+    """k-partite graph whose first n_dense classes are joined densely and the
+    rest sparsely: dense overall (the half-word plane-0 test is taken) while
+    many pairs need the recount and the sparse classes cascade."""
+    rng = np.random.default_rng(seed)
+    colour = np.sort(rng.integers(0, k, size=n)).astype(np.int32)
+    iu, iv = np.triu_indices(n, 1)
+    cu, cv = colour[iu], colour[iv]
+    p = np.where((cu < n_dense) & (cv < n_dense), p_dense, p_sparse)
+    keep = (cu != cv) & (rng.random(len(iu)) < p)
+    edges = np.stack([iu[keep], iv[keep]], axis=1).astype(np.int32)
+    return synth.Graph(n=n, k=k, colour=colour, edges=synth.canonical_edges(edges), name="two-density")
+
+
+@pytest.mark.parametrize("loop", [0, 1])
+def test_half_word_plane0_with_recounts(loop):
+    for seed, (n, k, nd, pd, ps) in enumerate(((1200, 12, 10, 0.95, 0.05), (900, 8, 6, 0.97, 0.3),
+                                               (700, 20, 18, 0.9, 0.1))):
+        g = _two_density_graph(seed, n, k, nd, pd, ps)
+        cross = (n * n - np.sum(np.bincount(g.colour, minlength=k) ** 2)) / 2
+        assert len(g.edges) >= 0.6 * cross  # dense enough for the half-word test
+        assert_parity(g, gpu_run(g, path="bitset", use_graph=loop))
