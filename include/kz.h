@@ -85,13 +85,36 @@ typedef enum {
     KZ_SCHED_LEARNED = 1  /* MLP-ranked worklist, then a full certifying sweep */
 } kz_schedule;
 
+/* First test of a pair in the BITSET path's sweep kernels (kz_options.plane0).
+ * Both are exact: a pair the first test leaves open is recounted over all
+ * planes.  Only the speed differs. */
+typedef enum {
+    KZ_PLANE0_AUTO = 0, /* by edge density: half words from density 0.8 */
+    KZ_PLANE0_FULL = 1, /* the first 32 members of each class, one word per class */
+    KZ_PLANE0_HALF = 2  /* the first 16 members of each class, two classes per word */
+} kz_plane0;
+
+/* How kz_kernelize_batch runs its graphs (kz_options.batch).  All give the
+ * same results; only the scheduling differs. */
+typedef enum {
+    KZ_BATCH_CONCURRENT = 0, /* each graph on its own path (kz_options.path; AUTO per graph), spread
+                                over the library's internal streams longest first, joined back
+                                into the caller's stream */
+    KZ_BATCH_SEQUENTIAL = 1, /* each graph on its own path, one after another on the caller's stream */
+    KZ_BATCH_FUSED = 2       /* one launch for all graphs: the in-CTA persistent kernel (path SMALL,
+                                and graphs with k > 32), otherwise the batched multi-graph Jacobi
+                                kernel; graphs without bitset rows run on the CSR path first */
+} kz_batch_mode;
+
 typedef struct {
     int32_t path;         /* kz_path */
     int32_t schedule;     /* kz_schedule */
     int64_t max_sweeps;   /* productive sweeps allowed; <= 0 means n + m + 1 (always enough) */
     int32_t use_graph;    /* device-side pass loop: 1 (default) one cooperative persistent launch,
                              2 a CUDA-graph while node (one launch per pass), 0 host-driven loop */
-    int32_t reserved[9];  /* must be zero */
+    int32_t plane0;       /* kz_plane0 (BITSET path only) */
+    int32_t batch;        /* kz_batch_mode (kz_kernelize_batch only) */
+    int32_t reserved[7];  /* must be zero */
 } kz_options;
 
 /* Fill *opt with the defaults (AUTO path, PLAIN schedule, no sweep limit,

@@ -38,6 +38,8 @@ globals().update({v: k for k, v in STATUS_NAMES.items()})
 KZ_DEDUP = 0x1
 PATHS = {"auto": 0, "bitset": 1, "small": 2, "sparse": 3, "tensor": 4}
 SCHEDULES = {"plain": 0, "learned": 1}
+PLANE0 = {"auto": 0, "full": 1, "half": 2}
+BATCH = {"concurrent": 0, "sequential": 1, "fused": 2}
 
 
 class KzError(RuntimeError):
@@ -50,7 +52,8 @@ class KzError(RuntimeError):
 
 class kz_options(C.Structure):
     _fields_ = [("path", C.c_int32), ("schedule", C.c_int32), ("max_sweeps", C.c_int64),
-                ("use_graph", C.c_int32), ("reserved", C.c_int32 * 9)]
+                ("use_graph", C.c_int32), ("plane0", C.c_int32), ("batch", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
 
 
 class kz_stats(C.Structure):
@@ -213,6 +216,10 @@ def kz_default_options(**kw) -> kz_options:
             val = PATHS[val]
         if key == "schedule" and isinstance(val, str):
             val = SCHEDULES[val]
+        if key == "plane0" and isinstance(val, str):
+            val = PLANE0[val]
+        if key == "batch" and isinstance(val, str):
+            val = BATCH[val]
         setattr(o, key, int(val))
     return o
 

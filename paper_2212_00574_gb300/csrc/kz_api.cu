@@ -4,10 +4,12 @@
 #include <stdint.h>
 
 #include <algorithm>
-#include <cstring>
 #include <atomic>
+#include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <numeric>
 #include <vector>
 
 #include "kz_internal.cuh"
@@ -236,22 +238,27 @@ kz_status kz_load_graph_dense(int32_t n, int32_t k, const int32_t *colour,
 static kz_status read_options(const kz_options *opt, kz_options &o) {
   if (opt) {
     o = *opt;
-    for (int i = 0; i < 9; i++)
+    for (int i = 0; i < 7; i++)
       if (o.reserved[i]) return KZ_ERR_ARG;
   } else {
     kz_default_options(&o);
   }
   if (o.path < KZ_PATH_AUTO || o.path > KZ_PATH_TENSOR) return KZ_ERR_ARG;
   if (o.schedule != KZ_SCHED_PLAIN && o.schedule != KZ_SCHED_LEARNED) return KZ_ERR_ARG;
+  if (o.plane0 < KZ_PLANE0_AUTO || o.plane0 > KZ_PLANE0_HALF) return KZ_ERR_ARG;
+  if (o.batch < KZ_BATCH_CONCURRENT || o.batch > KZ_BATCH_FUSED) return KZ_ERR_ARG;
   return KZ_OK;
 }
 
 // The path a graph takes when the options leave the choice to the library:
-// bitset rows when they exist (inside one CTA when both ping-pong copies fit
-// in shared memory), else the CSR path.
+// bitset rows when they exist, else the CSR path.  A graph of at most 64
+// vertices runs inside one CTA from shared memory (a multi-CTA pass would be
+// all launch and barrier); anything larger is spread over the GPU.
+constexpr int kSmallAutoMaxN = 64;
+
 static int auto_path(kz_graph g) {
   if (!g->has_bitset) return KZ_PATH_SPARSE;
-  return cta_fits_shared(g) ? KZ_PATH_SMALL : KZ_PATH_BITSET;
+  return g->n <= kSmallAutoMaxN && cta_fits_shared(g) ? KZ_PATH_SMALL : KZ_PATH_BITSET;
 }
 
 static kz_status run_one(kz_graph g, const kz_options &o, int path) {
@@ -293,24 +300,88 @@ kz_status kz_kernelize(kz_graph g, const kz_options *opt, void *stream) {
   return run_one(g, o, path);
 }
 
-kz_status kz_kernelize_batch(kz_graph *graphs, int32_t count, const kz_options *opt, void *stream) {
-  if (count < 0 || (count > 0 && !graphs)) return KZ_ERR_ARG;
-  for (int32_t i = 0; i < count; i++)
-    if (!graphs[i]) return KZ_ERR_ARG;
-  kz_options o;
-  KZ_TRY(read_options(opt, o));
-  if (o.schedule != KZ_SCHED_PLAIN) {
-    for (int32_t i = 0; i < count; i++) KZ_TRY(kz_kernelize(graphs[i], &o, stream));
+}  // extern "C"
+
+namespace {
+
+// Streams (and their events) on which kz_kernelize_batch spreads graphs,
+// created once per device.
+constexpr int kBatchStreams = 16;
+
+struct StreamPool {
+  std::mutex mu;  // one batch enqueues on the pool at a time
+  cudaStream_t streams[kBatchStreams];
+  cudaEvent_t done[kBatchStreams];
+  cudaEvent_t fork;
+};
+
+std::mutex g_pools_mu;
+std::map<int, StreamPool *> g_pools;
+
+kz_status stream_pool(StreamPool *&out) {
+  int dev = 0;
+  KZ_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_pools_mu);
+  auto it = g_pools.find(dev);
+  if (it != g_pools.end()) {
+    out = it->second;
     return KZ_OK;
   }
-  cudaStream_t s = (cudaStream_t)stream;
-  for (int32_t i = 0; i < count; i++) graphs[i]->stream = s;
-  if (o.path == KZ_PATH_BITSET || o.path == KZ_PATH_SPARSE || o.path == KZ_PATH_TENSOR) {
-    // the plain per-graph loop
-    for (int32_t i = 0; i < count; i++) KZ_TRY(run_one(graphs[i], o, o.path));
-    return KZ_OK;
+  StreamPool *p = new (std::nothrow) StreamPool;
+  if (!p) return KZ_ERR_OOM;
+  for (int i = 0; i < kBatchStreams; i++) {
+    KZ_CUDA_TRY(cudaStreamCreateWithFlags(&p->streams[i], cudaStreamNonBlocking));
+    KZ_CUDA_TRY(cudaEventCreateWithFlags(&p->done[i], cudaEventDisableTiming));
   }
-  // graphs without bitset rows go through the CSR path one by one
+  KZ_CUDA_TRY(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
+  g_pools[dev] = p;  // kept until the process exits
+  out = p;
+  return KZ_OK;
+}
+
+// Estimated work of one pass of a graph: tested pairs (dense graphs) or
+// stored edges, whichever representation it has.
+double pass_cost(kz_graph g) {
+  if (g->has_bitset) return (double)g->n * (double)g->n * (double)std::max(g->k, 1) + 1e5;
+  return (double)g->m * 16.0 + 1e5;
+}
+
+// Each graph on its own path, on the pool's streams: longest first, each to
+// the stream with the least estimated work so far; the caller's stream then
+// waits for all of them.
+kz_status batch_concurrent(kz_graph *graphs, int32_t count, const kz_options &o, cudaStream_t s) {
+  StreamPool *pool = nullptr;
+  KZ_TRY(stream_pool(pool));
+  std::lock_guard<std::mutex> lk(pool->mu);
+  std::vector<int32_t> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  std::vector<double> cost(count);
+  for (int32_t i = 0; i < count; i++) cost[i] = pass_cost(graphs[i]);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+  const int used = std::min<int>(kBatchStreams, std::max(count, 1));
+  KZ_CUDA_TRY(cudaEventRecord(pool->fork, s));
+  for (int i = 0; i < used; i++) KZ_CUDA_TRY(cudaStreamWaitEvent(pool->streams[i], pool->fork, 0));
+  std::vector<double> load(used, 0.0);
+  kz_status st = KZ_OK;
+  for (int32_t j = 0; j < count && st == KZ_OK; j++) {
+    kz_graph g = graphs[order[j]];
+    const int i = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[i] += cost[order[j]];
+    g->stream = pool->streams[i];
+    st = run_one(g, o, o.path == KZ_PATH_AUTO ? auto_path(g) : o.path);
+  }
+  // join every stream that may hold work, even after a failure
+  for (int i = 0; i < used; i++) {
+    cudaError_t e = cudaEventRecord(pool->done[i], pool->streams[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, pool->done[i], 0);
+    if (e != cudaSuccess && st == KZ_OK) st = kz::cuda_status(e);
+  }
+  for (int32_t j = 0; j < count; j++) graphs[j]->stream = s;
+  return st;
+}
+
+// One launch for all graphs (after the CSR-only graphs, one by one).
+kz_status batch_fused(kz_graph *graphs, int32_t count, const kz_options &o, cudaStream_t s) {
   std::vector<kz_graph> rows;
   for (int32_t i = 0; i < count; i++) {
     if (!graphs[i]->has_bitset) {
@@ -323,8 +394,8 @@ kz_status kz_kernelize_batch(kz_graph *graphs, int32_t count, const kz_options *
   }
   std::vector<kz_graph> loop, cta;
   for (kz_graph g : rows) {
-    // SMALL: every graph in the in-CTA persistent launch; AUTO: the batched
-    // Jacobi loop for k <= 32, the in-CTA launch for more colours
+    // SMALL: every graph in the in-CTA persistent launch; otherwise the
+    // batched Jacobi kernel for k <= 32, the in-CTA launch for more colours
     if (o.path == KZ_PATH_SMALL || g->k > 32) cta.push_back(g);
     else loop.push_back(g);
   }
@@ -339,6 +410,37 @@ kz_status kz_kernelize_batch(kz_graph *graphs, int32_t count, const kz_options *
     g->path_ran = KZ_PATH_SMALL;
   }
   return KZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kz_status kz_kernelize_batch(kz_graph *graphs, int32_t count, const kz_options *opt, void *stream) {
+  if (count < 0 || (count > 0 && !graphs)) return KZ_ERR_ARG;
+  for (int32_t i = 0; i < count; i++)
+    if (!graphs[i]) return KZ_ERR_ARG;
+  kz_options o;
+  KZ_TRY(read_options(opt, o));
+  if (o.schedule != KZ_SCHED_PLAIN) {
+    for (int32_t i = 0; i < count; i++) KZ_TRY(kz_kernelize(graphs[i], &o, stream));
+    return KZ_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int32_t i = 0; i < count; i++) graphs[i]->stream = s;
+  if (count == 0) return KZ_OK;
+  if (o.batch == KZ_BATCH_FUSED) {
+    if (o.path == KZ_PATH_BITSET || o.path == KZ_PATH_SPARSE || o.path == KZ_PATH_TENSOR) return KZ_ERR_ARG;
+    return batch_fused(graphs, count, o, s);
+  }
+  if (o.batch == KZ_BATCH_SEQUENTIAL) {
+    for (int32_t i = 0; i < count; i++) {
+      kz_graph g = graphs[i];
+      KZ_TRY(run_one(g, o, o.path == KZ_PATH_AUTO ? auto_path(g) : o.path));
+    }
+    return KZ_OK;
+  }
+  return batch_concurrent(graphs, count, o, s);
 }
 
 // Vertices alive, from whichever representation holds the state.

@@ -41,6 +41,9 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "kz_internal.cuh"
@@ -82,30 +85,38 @@ kz_status bitset_build_layout(kz_graph g) {
   return KZ_OK;
 }
 
-// Work ranges of the sweep kernels: the units of a pass in order (x
-// ascending; for each x the blocks y of higher classes, or one vertex-only
-// unit y = nb for a block of the last class), cut into `warps` consecutive
-// ranges of about equal estimated cost.  A unit costs the members of Y it
-// tests plus a fixed part for staging and bookkeeping; the first unit of each
-// x also evaluates the vertex rule.
-static void build_ranges(kz_graph g, int warps, std::vector<WarpRange> &out, int64_t &n_units) {
+// Work of the sweep kernels: the units of a pass in order (x ascending; for
+// each x the blocks y of higher classes, or one vertex-only unit y = nb for a
+// block of the last class).  The units holding the first `static_share` of
+// the estimated cost are cut into `warps` consecutive ranges of about equal
+// cost; the rest form the tail, which warps take one unit at a time once
+// their range is done.  A unit costs the members of Y it tests plus a fixed
+// part for staging and bookkeeping; the first unit of each x also evaluates
+// the vertex rule.  The estimate is good for dense graphs (the half-word
+// form: everything static); sparser graphs spend unpredictable time in
+// recounts, so a quarter of their work is left to the tail.
+constexpr double kStaticShareHalf = 1.0;
+constexpr double kStaticShareFull = 0.75;
+
+static void build_ranges(kz_graph g, int warps, double static_share, std::vector<WarpRange> &out,
+                         std::vector<int2> &tail, int64_t &n_units, int64_t &tail_begin) {
   constexpr int64_t kUnitFixed = 8, kVertexCost = 8;
   const int nb = (int)g->blocks.size();
   auto ybegin = [&](int x) { return std::min(g->boff[g->blocks[x].c + 1], nb); };
+  auto cost = [&](int y, bool first) {
+    return (y < nb ? g->blocks[y].size : 0) + kUnitFixed + (first ? kVertexCost : 0);
+  };
   int64_t total = 0;
   n_units = 0;
   for (int x = 0; x < nb; x++) {
     const int yb = ybegin(x);
-    total += kVertexCost;
-    if (yb >= nb) {
-      total += kUnitFixed;
-      n_units += 1;
-      continue;
-    }
-    for (int y = yb; y < nb; y++) total += g->blocks[y].size + kUnitFixed;
-    n_units += nb - yb;
+    const int y_end = yb >= nb ? nb + 1 : nb;
+    for (int y = yb; y < y_end; y++, n_units++) total += cost(y, y == yb);
   }
-  out.assign((size_t)warps, WarpRange{nb, nb, (int32_t)n_units, 0});
+  const int64_t share = static_share >= 1.0 ? total : (int64_t)(static_share * (double)total);
+  out.assign((size_t)warps, WarpRange{nb, nb, 0, 0});
+  tail.clear();
+  tail_begin = n_units;
   int w = 0;
   int64_t acc = 0, unit = 0;
   WarpRange cur{0, 0, 0, 0};
@@ -113,14 +124,19 @@ static void build_ranges(kz_graph g, int warps, std::vector<WarpRange> &out, int
     const int yb = ybegin(x);
     const int y_end = yb >= nb ? nb + 1 : nb;
     for (int y = yb; y < y_end; y++, unit++) {
-      acc += (y < nb ? g->blocks[y].size : 0) + kUnitFixed + (y == yb ? kVertexCost : 0);
+      if (acc >= share && share < total) {  // tail
+        if (tail.empty()) tail_begin = unit;
+        tail.push_back(make_int2(x, y));
+        continue;
+      }
+      acc += cost(y, y == yb);
       if (cur.count == 0) cur = WarpRange{x, y, (int32_t)unit, 0};
       cur.count++;
       // close this warp's range once the running cost reaches its share
-      if (w < warps - 1 && acc * warps >= (int64_t)(w + 1) * total) {
+      if (w < warps - 1 && acc * warps >= (int64_t)(w + 1) * share) {
         out[(size_t)w++] = cur;
         cur.count = 0;
-        while (w < warps - 1 && acc * warps >= (int64_t)(w + 1) * total) w++;  // empty ranges
+        while (w < warps - 1 && acc * warps >= (int64_t)(w + 1) * share) w++;  // empty ranges
       }
     }
   }
@@ -237,6 +253,10 @@ struct SweepArgs {
   uint32_t *V0, *V1;      // ping-pong vertex live words
   int32_t *v_sweep;       // relabelled ids, may be null
   uint8_t *changed;       // per unit: low byte of the sweep that last changed its words
+  int32_t fast_half;      // half-word form: try the whole-block fold first (very dense graphs)
+  const int2 *tail;       // (x, y) of the tail units
+  int32_t tail_begin;     // unit number of the first tail unit
+  int32_t tail_count;
   DevState *st;
   cudaGraphConditionalHandle cond;
   int32_t use_cond;
@@ -247,24 +267,37 @@ struct SweepArgs {
 constexpr int kSweepWarps = 4;
 // density (edges / pairs of vertices in different classes) from which the
 // sweep kernels use the half-word plane-0 test
-constexpr double kHalfDensity = 0.6;
-// resident CTAs per SM the compiler is asked to fit: the half-word form
-// needs fewer registers, so it runs five 4-warp CTAs per SM
+constexpr double kHalfDensity = 0.8;
+// density from which a whole block is first folded without per-pair results
+// (almost every 32 x 32 block then has every pair covered); below it the
+// half-word form (when forced) tests pair by pair
+constexpr double kFastHalfDensity = 0.8;
+// resident CTAs per SM the compiler is asked to fit (4-warp CTAs): five for
+// the half-word form up to k = 24, four otherwise up to k = 32
 template <int KMAX, bool HALF>
-constexpr int kMinCtas = (HALF && KMAX <= 32) ? 5 : 1;
+constexpr int kMinCtas = !HALF ? (KMAX <= 32 ? 4 : 1) : (KMAX <= 24 ? 5 : (KMAX <= 32 ? 4 : 1));
+// Shared memory of one warp: two staging buffers of plane-0 rows (KMAX words
+// each) and, in the half-word form, the converted rows of the current unit.
+template <int KMAX, bool HALF>
+__host__ __device__ constexpr int warp_smem_words() {
+  return 2 * 32 * KMAX + (HALF ? 32 * half_stride<KMAX>() : 0);
+}
 
 __device__ __forceinline__ void prefetch_l1(const uint32_t *p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
-// One warp's range of units in one Jacobi pass.  `cur` is the current
-// ping-pong buffer, `sweep_no` the productive sweeps so far, `full` asks for
-// every owned word to be written.  HALF selects the half-word plane-0 test
-// (first 16 members of each class; for dense graphs).
+// One warp's share of one Jacobi pass: its static range of units, then tail
+// units taken one at a time from the pass's shared counter until none is
+// left, so the warps of the grid end their pass within about one unit of
+// each other.  `cur` is the current ping-pong buffer, `sweep_no` the
+// productive sweeps so far, `full` asks for every owned word to be written.
+// HALF selects the half-word plane-0 test (first 16 members of each class;
+// for dense graphs).
 template <int KMAX, bool HALF>
 __device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange r, int cur, int64_t sweep_no,
-                                            bool full, uint32_t *buf0, uint32_t *buf1, PassCounters &pc) {
-  if (r.count <= 0) return;
+                                            bool full, uint32_t *buf0, uint32_t *buf1, uint32_t *bufh,
+                                            const int32_t *rounds, PassCounters &pc) {
   const int lane = threadIdx.x & 31;
   const uint32_t *__restrict__ A = cur ? p.A1 : p.A0;
   uint32_t *__restrict__ An = cur ? p.A0 : p.A1;
@@ -274,10 +307,33 @@ __device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange 
   const int kq4 = (k + 3) >> 2;
   const uint8_t tag_now = (uint8_t)(sweep_no & 0xff);
   const uint8_t tag_next = (uint8_t)((sweep_no + 1) & 0xff);
+  unsigned int *tail_ctr = &p.st->tail_next;
 
-  // cursor (x, y): the next unit to stage; its adjacency word, change tag and
-  // live word are loaded one unit ahead
-  int x = r.x, y = r.y;
+  // cursor (x, y, unit): the next unit to stage.  Its adjacency word, change
+  // tag and live word are loaded one unit ahead; a tail ticket is requested
+  // one unit before it is needed (lane 0 holds it until then).
+  int x = 0, y = 0, unit = 0, left = r.count;
+  unsigned int ticket = 0;
+  bool have = false;
+  if (left > 0) {
+    x = r.x;
+    y = r.y;
+    unit = r.unit;
+    left--;
+    have = true;
+    if (left == 0 && p.tail_count && lane == 0) ticket = atomicAdd(tail_ctr, 1u);
+  } else if (p.tail_count) {
+    const unsigned int t = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(tail_ctr, 1u) : 0u, 0);
+    if (t < (unsigned int)p.tail_count) {
+      const int2 e = p.tail[t];
+      x = e.x;
+      y = e.y;
+      unit = p.tail_begin + (int)t;
+      have = true;
+      if (lane == 0) ticket = atomicAdd(tail_ctr, 1u);
+    }
+  }
+  if (!have) return;
   BlockDesc X = p.blocks[x];
   int ybeg = min(p.boff[X.c + 1], nb);
   BlockDesc Y = X;
@@ -287,30 +343,50 @@ __device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange 
   }
   cp_async_commit();
   uint32_t adj_n = (y < nb && lane < X.size) ? A[(int64_t)(X.base + lane) * ldw + Y.r * k + Y.c] : 0u;
-  uint8_t chg_n = y < nb ? p.changed[r.unit] : (uint8_t)0;
+  uint8_t chg_n = y < nb ? p.changed[unit] : (uint8_t)0;
   uint32_t vw_n = y == ybeg ? Vc[X.r * k + X.c] : 0u;
 
-  constexpr int KH = ((KMAX / 2) + 3) / 4 * 4;
+  constexpr int KH = KMAX / 2;
   constexpr int KW = HALF ? KH : KMAX;
-  const int kh = (k + 1) >> 1;
   uint32_t F[KW], P[KW];  // plane 0 of the lanes' rows (full or half-word form), forced classes
   int fu_x = -1, prev_cv = -1, vcnt = 0;
-  for (int i = 0; i < r.count; i++) {
-    const int xc = x, yc = y;
+  uint64_t vmiss = 0;  // classes plane 0 leaves uncovered for the lane's vertex
+  for (int i = 0;; i++) {
+    const int xc = x, yc = y, uc_unit = unit;
     const BlockDesc Xc = X, Yc = Y;
     const bool vflag = yc == ybeg;
     const uint32_t adjw = adj_n, vword = vw_n;
     const uint8_t chg = chg_n;
-    const int unit = r.unit + i;
     uint32_t *sv = (i & 1) ? buf1 : buf0;
-    if (i + 1 < r.count) {
+    // advance the cursor and stage the next unit
+    bool more = false, next_block = false;
+    if (left > 0) {
       if (y + 1 < nb) {
         y++;
       } else {
-        x++;
+        x++;  // first unit of the next block: y is its first higher-class block
+        next_block = true;
+      }
+      unit++;
+      left--;
+      more = true;
+      if (left == 0 && p.tail_count && lane == 0) ticket = atomicAdd(tail_ctr, 1u);
+    } else if (p.tail_count) {
+      const unsigned int t = __shfl_sync(0xffffffffu, ticket, 0);
+      if (t < (unsigned int)p.tail_count) {
+        const int2 e = p.tail[t];
+        x = e.x;
+        y = e.y;
+        unit = p.tail_begin + (int)t;
+        more = true;
+        if (lane == 0) ticket = atomicAdd(tail_ctr, 1u);
+      }
+    }
+    if (more) {
+      if (x != xc) {
         X = p.blocks[x];
         ybeg = min(p.boff[X.c + 1], nb);
-        y = ybeg;
+        if (next_block) y = ybeg;
         if (lane < X.size) {  // warm L1 with plane 0 of the next block's rows
           const uint32_t *row = A + (int64_t)(X.base + lane) * ldw;
           prefetch_l1(row);
@@ -322,7 +398,7 @@ __device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange 
         stage_block<KMAX>(A, ldw, Y, kq4, (i & 1) ? buf0 : buf1, lane);
       }
       adj_n = (y < nb && lane < X.size) ? A[(int64_t)(X.base + lane) * ldw + Y.r * k + Y.c] : 0u;
-      chg_n = y < nb ? p.changed[unit + 1] : (uint8_t)0;
+      chg_n = y < nb ? p.changed[unit] : (uint8_t)0;
       vw_n = y == ybeg ? Vc[X.r * k + X.c] : 0u;
     }
     cp_async_commit();
@@ -337,19 +413,24 @@ __device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange 
       if constexpr (HALF) {
         uint32_t Fu[KMAX];
         load_plane0<KMAX>(Fu, rowu, k, valid);
-        vcnt = plane0_vertex_cover<KMAX>(Fu, k, cu);
+        vmiss = plane0_vertex_missing<KMAX>(Fu, k, cu);
         halve_plane0<KMAX, KH>(F, Fu);
+        if (!valid) {  // no vertex: never uncovered, so the fast fold is not disturbed
+#pragma unroll
+          for (int j = 0; j < KH; j++) F[j] = 0xffffffffu;
+        }
       } else {
         load_plane0<KMAX>(F, rowu, k, valid);
-        vcnt = plane0_vertex_cover<KMAX>(F, k, cu);
+        vmiss = plane0_vertex_missing<KMAX>(F, k, cu);
       }
+      vcnt = (k - 1) - __popcll(vmiss);
       fu_x = xc;
       prev_cv = -1;
     }
     if (vflag) {
       const bool live = valid && ((vword >> lane) & 1u);
       int cnt = vcnt;
-      if (live && cnt < k - 1) cnt = exact_vertex_cover_row(rowu, k, p.rounds, cu);
+      if (live && cnt < k - 1) cnt += vertex_cover_beyond_plane0(rowu, k, rounds, vmiss);
       const bool fail = live && cnt < k - 1;
       const uint32_t failmask = __ballot_sync(0xffffffffu, fail);
       if (lane == 0) {
@@ -369,14 +450,14 @@ __device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange 
       const uint32_t *ybase = A + (int64_t)Yc.base * ldw;
       uint32_t open, del = 0;
       if constexpr (HALF) {
-        halve_staged_rows<KMAX>(sv, Yc.size, k, lane);
+        halve_staged_rows<KMAX>(sv, bufh, Yc.size, lane);
         __syncwarp();
-        open = half_unsettled<KH>(F, P, sv, KMAX, adjw, kh);
-        // the staged rows now hold half-words: the recount reads plane 0 from the rows
-        if (open) del = recount_unsettled(rowu, ybase, ldw, ybase, ldw, open, k, cu, cv, p.rounds);
+        open = half_unsettled<KMAX, KH>(F, P, bufh, adjw, p.fast_half != 0);
+        // the recount starts from the full staged plane 0
+        if (open) del = recount_unsettled(rowu, sv, KMAX, ybase, ldw, open, k, cu, cv, rounds);
       } else {
         open = plane0_unsettled<KMAX>(F, P, sv, adjw, k);
-        if (open) del = recount_unsettled(rowu, sv, KMAX, ybase, ldw, open, k, cu, cv, p.rounds);
+        if (open) del = recount_unsettled(rowu, sv, KMAX, ybase, ldw, open, k, cu, cv, rounds);
       }
       const bool anydel = __any_sync(0xffffffffu, del != 0u);
       if (anydel || full || chg == tag_now) {
@@ -384,22 +465,44 @@ __device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange 
         if (valid) An[(int64_t)u * ldw + Yc.r * k + cv] = keep;
         const uint32_t col = transpose32(keep);
         if (lane < Yc.size) An[(int64_t)(Yc.base + lane) * ldw + Xc.r * k + cu] = col;
-        if (anydel && lane == 0) p.changed[unit] = tag_next;
+        if (anydel && lane == 0) p.changed[uc_unit] = tag_next;
         pc.de += __popc(del);
       }
     }
     __syncwarp();
+    if (!more) break;
   }
   cp_async_wait<0>();
   __syncwarp();
 }
 
-template <int KMAX>
-__device__ __forceinline__ void reduce_counters(PassCounters &pc) {
+// The CTA's pass counters, summed over its warps and added to the graph's
+// running pass totals with one atomic per counter (thread 0).  Ends with the
+// CTA synchronised.
+__device__ __forceinline__ void add_cta_counters(PassCounters pc, DevState *st) {
+  __shared__ unsigned long long s_pc[kSweepWarps][3];
   for (int o = 16; o > 0; o >>= 1) {
     pc.tests += __shfl_down_sync(0xffffffffu, pc.tests, o);
     pc.de += __shfl_down_sync(0xffffffffu, pc.de, o);
     pc.dv += __shfl_down_sync(0xffffffffu, pc.dv, o);
+  }
+  const int wib = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    s_pc[wib][0] = pc.tests;
+    s_pc[wib][1] = pc.de;
+    s_pc[wib][2] = pc.dv;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0, de = 0, dv = 0;
+    for (int w = 0; w < kSweepWarps; w++) {
+      t += s_pc[w][0];
+      de += s_pc[w][1];
+      dv += s_pc[w][2];
+    }
+    if (t) atomicAdd(&st->pass_tests, t);
+    if (de) atomicAdd(&st->pass_de, de);
+    if (dv) atomicAdd(&st->pass_dv, dv);
   }
 }
 
@@ -408,25 +511,24 @@ template <int KMAX, bool HALF>
 __global__ void __launch_bounds__(kSweepWarps * 32, kMinCtas<KMAX, HALF>)
     bitset_sweep_kernel(SweepArgs p) {
   extern __shared__ __align__(16) uint32_t smem[];
-  const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  uint32_t *buf0 = smem + wib * 2 * 32 * KMAX;
+  uint32_t *buf0 = smem + wib * warp_smem_words<KMAX, HALF>();
   uint32_t *buf1 = buf0 + 32 * KMAX;
+  uint32_t *bufh = buf1 + 32 * KMAX;  // half-word rows (HALF only)
+  __shared__ int32_t s_rounds[KMAX];
+  for (int c = threadIdx.x; c < p.k; c += blockDim.x) s_rounds[c] = p.rounds[c];
+  __syncthreads();
   DevState *st = p.st;
   const int cur = *((volatile int32_t *)&st->cur);
   const int64_t sweep_no = *((volatile int64_t *)&st->sweeps);
   const bool full = *((volatile int32_t *)&st->full_write) != 0;
-  const int warps_total = gridDim.x * kSweepWarps;
   PassCounters pc;
-  sweep_range<KMAX, HALF>(p, p.ranges[blockIdx.x * kSweepWarps + wib], cur, sweep_no, full, buf0, buf1, pc);
-  reduce_counters<KMAX>(pc);
-  if (lane == 0) {
-    if (pc.tests) atomicAdd(&st->pass_tests, pc.tests);
-    if (pc.de) atomicAdd(&st->pass_de, pc.de);
-    if (pc.dv) atomicAdd(&st->pass_dv, pc.dv);
+  sweep_range<KMAX, HALF>(p, p.ranges[blockIdx.x * kSweepWarps + wib], cur, sweep_no, full, buf0, buf1, bufh, s_rounds, pc);
+  add_cta_counters(pc, st);
+  if (threadIdx.x == 0) {
     __threadfence();
     const unsigned int t = atomicAdd(&st->ticket, 1u);
-    if (t == (unsigned int)warps_total - 1u) {
+    if (t == gridDim.x - 1u) {  // the last CTA closes the pass
       __threadfence();
       const unsigned long long dv = atomicAdd(&st->pass_dv, 0ull);
       const unsigned long long de = atomicAdd(&st->pass_de, 0ull);
@@ -453,63 +555,77 @@ template <int KMAX, bool HALF>
 __global__ void __launch_bounds__(kSweepWarps * 32, kMinCtas<KMAX, HALF>)
     bitset_persistent_kernel(SweepArgs p) {
   extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ int s_go;
-  const int lane = threadIdx.x & 31;
+  __shared__ unsigned long long s_word;
   const int wib = threadIdx.x >> 5;
-  uint32_t *buf0 = smem + wib * 2 * 32 * KMAX;
+  uint32_t *buf0 = smem + wib * warp_smem_words<KMAX, HALF>();
   uint32_t *buf1 = buf0 + 32 * KMAX;
+  uint32_t *bufh = buf1 + 32 * KMAX;  // half-word rows (HALF only)
+  __shared__ int32_t s_rounds[KMAX];
+  for (int c = threadIdx.x; c < p.k; c += blockDim.x) s_rounds[c] = p.rounds[c];
+  __syncthreads();
   DevState *st = p.st;
+  // the first pass reads the run's start state; every later one takes it from
+  // the word the pass-closing CTA publishes with the barrier release
+  int cur = *((volatile int32_t *)&st->cur);
+  int64_t sweep_no = *((volatile int64_t *)&st->sweeps);
+  bool full = *((volatile int32_t *)&st->full_write) != 0;
   for (;;) {
-    const int cur = *((volatile int32_t *)&st->cur);
-    const int64_t sweep_no = *((volatile int64_t *)&st->sweeps);
-    const bool full = *((volatile int32_t *)&st->full_write) != 0;
     PassCounters pc;
-    sweep_range<KMAX, HALF>(p, p.ranges[blockIdx.x * kSweepWarps + wib], cur, sweep_no, full, buf0, buf1, pc);
-    reduce_counters<KMAX>(pc);
-    if (lane == 0) {
-      if (pc.tests) atomicAdd(&st->pass_tests, pc.tests);
-      if (pc.de) atomicAdd(&st->pass_de, pc.de);
-      if (pc.dv) atomicAdd(&st->pass_dv, pc.dv);
-    }
-    __syncthreads();
+    sweep_range<KMAX, HALF>(p, p.ranges[blockIdx.x * kSweepWarps + wib], cur, sweep_no, full, buf0, buf1, bufh,
+                            s_rounds, pc);
+    add_cta_counters(pc, st);
     if (threadIdx.x == 0) {
       __threadfence();
-      const unsigned int gen = *((volatile unsigned int *)&st->bar_gen);
+      const unsigned long long w0 = *((volatile unsigned long long *)&st->pass_word);
+      unsigned long long w = w0;
+      bool abort = false;
       if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1u + p.bar_extra) {
         __threadfence();
         const unsigned long long dv = atomicAdd(&st->pass_dv, 0ull);
         const unsigned long long de = atomicAdd(&st->pass_de, 0ull);
         const unsigned long long tests = atomicAdd(&st->pass_tests, 0ull);
-        finish_pass(st, dv, de, tests);
+        const int cont = finish_pass(st, dv, de, tests);
         st->pass_dv = 0;
         st->pass_de = 0;
         st->pass_tests = 0;
         st->bar_count = 0;
+        w = pass_word(pass_word_gen(w0) + 1u, cont, cont ? cur ^ 1 : cur, cont ? sweep_no + 1 : sweep_no);
         __threadfence();
-        atomicExch(&st->bar_gen, gen + 1u);
+        atomicExch(&st->pass_word, w);
       } else {
         uint32_t spins = 0;
-        while (*((volatile unsigned int *)&st->bar_gen) == gen) {
-          if (*((volatile int32_t *)&st->bar_abort)) break;
+        for (;;) {
+          w = *((volatile unsigned long long *)&st->pass_word);
+          if (pass_word_gen(w) != pass_word_gen(w0)) break;
+          if (*((volatile int32_t *)&st->bar_abort)) {
+            abort = true;
+            break;
+          }
           __nanosleep(64);
           if (++spins > p.spin_limit) {
             atomicCAS(&st->status, (int32_t)KZ_OK, (int32_t)KZ_ERR_TIMEOUT);
             atomicExch(&st->bar_abort, 1);
+            abort = true;
             break;
           }
         }
       }
       __threadfence();
-      s_go = *((volatile int32_t *)&st->cont) && !*((volatile int32_t *)&st->bar_abort);
+      s_word = abort ? 0ull : w;  // a cleared continue bit ends the kernel
     }
     __syncthreads();
-    if (!s_go) break;
+    const unsigned long long w = s_word;
+    if (!pass_word_cont(w)) break;
+    cur = pass_word_cur(w);
+    sweep_no = pass_word_sweeps(w);
+    full = false;  // a finished pass leaves the buffers in step
   }
 }
 
 __global__ void begin_run_kernel(DevState *st, int64_t max_sweeps, int64_t passes0) {
   st->bar_count = 0;
   st->bar_gen = 0;
+  st->pass_word = 0;
   st->bar_abort = 0;
   st->status = KZ_OK;
   st->cont = 1;
@@ -519,6 +635,7 @@ __global__ void begin_run_kernel(DevState *st, int64_t max_sweeps, int64_t passe
   st->max_sweeps = max_sweeps;
   st->pass_dv = st->pass_de = st->pass_tests = 0;
   st->ticket = 0;
+  st->tail_next = 0;
 }
 
 __global__ void reset_state_kernel(DevState *st) {
@@ -528,6 +645,7 @@ __global__ void reset_state_kernel(DevState *st) {
   st->sweeps = st->passes = st->tests = 0;
   st->pass_dv = st->pass_de = st->pass_tests = 0;
   st->ticket = 0;
+  st->tail_next = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -569,13 +687,20 @@ static SweepFn pick_persistent(int k, bool half, int &kmax) {
 // ---------------------------------------------------------------------------
 
 static int sm_count() {
+  static std::mutex mu;
+  static std::map<int, int> counts;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  const auto it = counts.find(dev);
+  if (it != counts.end()) return it->second;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return sms > 0 ? sms : 1;
+  sms = sms > 0 ? sms : 1;
+  counts[dev] = sms;
+  return sms;
 }
 
-static kz_status sweep_grid_size(kz_graph g, int &grid);
+static kz_status ensure_plan(kz_graph g, bool half, cudaStream_t s);
 
 kz_status bitset_finish_load(kz_graph g, cudaStream_t s) {
   const int nb = (int)g->blocks.size();
@@ -606,17 +731,16 @@ kz_status bitset_finish_load(kz_graph g, cudaStream_t s) {
       tot += sz;
     }
     g->half_plane0 = cross > 0 && (double)g->m >= kHalfDensity * cross;
+    g->fast_half = cross > 0 && (double)g->m >= kFastHalfDensity * cross;
   }
-  // one work range per warp of a grid that is resident all at once
+  // per-unit change tags, and the work split of the form the density picks
   if (g->k <= 64) {
-    KZ_TRY(sweep_grid_size(g, g->sweep_grid));
-    std::vector<WarpRange> ranges;
-    build_ranges(g, g->sweep_grid * kSweepWarps, ranges, g->n_units);
-    KZ_TRY(graph_alloc(g, &g->d_ranges, ranges.size(), s));
-    KZ_CUDA_TRY(cudaMemcpyAsync(g->d_ranges, ranges.data(), sizeof(WarpRange) * ranges.size(),
-                                cudaMemcpyHostToDevice, s));
+    g->n_units = 0;
+    for (int x = 0; x < nb; x++) g->n_units += std::max(1, nb - std::min(g->boff[g->blocks[x].c + 1], nb));
+    if (g->n_units > INT32_MAX) return KZ_ERR_UNSUPPORTED;
     KZ_TRY(graph_alloc(g, &g->d_changed, (size_t)std::max<int64_t>(g->n_units, 1), s));
     KZ_CUDA_TRY(cudaMemsetAsync(g->d_changed, 0xff, (size_t)std::max<int64_t>(g->n_units, 1), s));
+    KZ_TRY(ensure_plan(g, g->half_plane0, s));
   }
   KZ_TRY(graph_alloc(g, &g->A[0], (size_t)g->n * g->ldw, s));
   KZ_TRY(graph_alloc(g, &g->A[1], (size_t)g->n * g->ldw, s));
@@ -647,52 +771,93 @@ kz_status bitset_reset(kz_graph g, cudaStream_t s) {
 }
 
 // Shared memory of a sweep kernel and its resident CTAs per SM.
-static kz_status kernel_fit(SweepFn fn, int kmax, size_t &smem, int &per_sm) {
-  smem = (size_t)kSweepWarps * 2 * 32 * kmax * 4;
+// (Set up and queried once per kernel and device: the attribute persists.)
+static kz_status kernel_fit(SweepFn fn, int kmax, bool half, size_t &smem, int &per_sm) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void *, int>, int> fitted;  // (kernel, device) -> CTAs per SM
+  const int half_stride_words = (kmax / 2 + 3) / 4 * 4;
+  smem = (size_t)kSweepWarps * 4 * (2 * 32 * kmax + (half ? 32 * half_stride_words : 0));
+  int dev = 0;
+  KZ_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_tuple((const void *)fn, dev);
+  const auto it = fitted.find(key);
+  if (it != fitted.end()) {
+    per_sm = it->second;
+    return KZ_OK;
+  }
   // always raise the limit: the kernels' static shared memory comes on top
   KZ_CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   per_sm = 0;
   KZ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn,
                                                             kSweepWarps * 32, smem));
+  fitted[key] = per_sm;
   return KZ_OK;
 }
 
-// The grid of both sweep kernels: every CTA resident at once (the persistent
-// kernel's grid barrier needs that), and no more warps than units.
-static kz_status sweep_grid_size(kz_graph g, int &grid) {
+// The grid of both sweep kernels of one form: every CTA resident at once
+// (the persistent kernel's grid barrier needs that), and no more warps than
+// units.
+static kz_status sweep_grid_size(kz_graph g, bool half, int &grid) {
   int kmax = 0, kmax2 = 0, per_a = 0, per_b = 0;
   size_t smem = 0;
-  SweepFn fa = pick_persistent(g->k, g->half_plane0, kmax), fb = pick_sweep(g->k, g->half_plane0, kmax2);
+  SweepFn fa = pick_persistent(g->k, half, kmax), fb = pick_sweep(g->k, half, kmax2);
   if (!fa || !fb) return KZ_ERR_ARG;
-  KZ_TRY(kernel_fit(fa, kmax, smem, per_a));
-  KZ_TRY(kernel_fit(fb, kmax2, smem, per_b));
+  KZ_TRY(kernel_fit(fa, kmax, half, smem, per_a));
+  KZ_TRY(kernel_fit(fb, kmax2, half, smem, per_b));
   const int per_sm = std::max(1, std::min(per_a, per_b));
-  int64_t units = 0;
-  const int nb = (int)g->blocks.size();
-  for (int x = 0; x < nb; x++) units += std::max(1, nb - std::min(g->boff[g->blocks[x].c + 1], nb));
-  const int64_t want = (std::max<int64_t>(units, 1) + kSweepWarps - 1) / kSweepWarps;
+  const int64_t want = (std::max<int64_t>(g->n_units, 1) + kSweepWarps - 1) / kSweepWarps;
   grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)per_sm * sm_count()));
   return KZ_OK;
 }
 
-static kz_status launch_config(kz_graph g, SweepFn fn, int kmax, int &grid, size_t &smem) {
+// Builds the grid, static ranges and tail of one form, once per graph.
+static kz_status ensure_plan(kz_graph g, bool half, cudaStream_t s) {
+  SweepPlan &pl = g->plan[half ? 1 : 0];
+  if (pl.grid > 0) return KZ_OK;
+  int grid = 0;
+  KZ_TRY(sweep_grid_size(g, half, grid));
+  std::vector<WarpRange> ranges;
+  std::vector<int2> tail;
+  int64_t units = 0, tail_begin = 0;
+  build_ranges(g, grid * kSweepWarps, half ? kStaticShareHalf : kStaticShareFull, ranges, tail, units,
+               tail_begin);
+  if (units != g->n_units) return KZ_ERR_INTERNAL;
+  KZ_TRY(graph_alloc(g, &pl.d_ranges, ranges.size(), s));
+  KZ_CUDA_TRY(cudaMemcpyAsync(pl.d_ranges, ranges.data(), sizeof(WarpRange) * ranges.size(),
+                              cudaMemcpyHostToDevice, s));
+  KZ_TRY(graph_alloc(g, &pl.d_tail, std::max<size_t>(tail.size(), 1), s));
+  if (!tail.empty())
+    KZ_CUDA_TRY(cudaMemcpyAsync(pl.d_tail, tail.data(), sizeof(int2) * tail.size(), cudaMemcpyHostToDevice, s));
+  pl.tail_begin = (int32_t)tail_begin;
+  pl.tail_count = (int32_t)tail.size();
+  pl.grid = grid;
+  return KZ_OK;
+}
+
+static kz_status launch_config(kz_graph g, SweepFn fn, int kmax, bool half, int &grid, size_t &smem) {
   int per_sm = 0;
-  KZ_TRY(kernel_fit(fn, kmax, smem, per_sm));
-  grid = g->sweep_grid;
+  KZ_TRY(kernel_fit(fn, kmax, half, smem, per_sm));
+  grid = g->plan[half ? 1 : 0].grid;
   if (grid <= 0 || grid > std::max(per_sm, 1) * sm_count()) return KZ_ERR_INTERNAL;
   return KZ_OK;
 }
 
-static SweepArgs make_args(kz_graph g) {
+static SweepArgs make_args(kz_graph g, bool half) {
+  const SweepPlan &pl = g->plan[half ? 1 : 0];
   SweepArgs a;
   a.blocks = g->d_blocks;
-  a.ranges = g->d_ranges;
+  a.ranges = pl.d_ranges;
   a.nb = (int32_t)g->blocks.size();
   a.k = g->k;
   a.ldw = g->ldw;
   a.rounds = g->d_rounds;
   a.boff = g->d_boff;
   a.changed = g->d_changed;
+  a.fast_half = g->fast_half ? 1 : 0;
+  a.tail = pl.d_tail;
+  a.tail_begin = pl.tail_begin;
+  a.tail_count = pl.tail_count;
   a.A0 = g->A[0];
   a.A1 = g->A[1];
   a.V0 = g->V[0];
@@ -708,13 +873,13 @@ static SweepArgs make_args(kz_graph g) {
 
 // Builds (once per graph) an executable CUDA graph whose while-node runs one
 // sweep-kernel launch per pass until the kernel clears the condition.
-static kz_status build_loop_graph(kz_graph g, int64_t max_sweeps) {
+static kz_status build_loop_graph(kz_graph g, int64_t max_sweeps, bool half) {
   int kmax = 0;
-  SweepFn fn = pick_sweep(g->k, g->half_plane0, kmax);
+  SweepFn fn = pick_sweep(g->k, half, kmax);
   if (!fn) return KZ_ERR_ARG;
   int grid = 0;
   size_t smem = 0;
-  KZ_TRY(launch_config(g, fn, kmax, grid, smem));
+  KZ_TRY(launch_config(g, fn, kmax, half, grid, smem));
   cudaGraph_t graph = nullptr;
   KZ_CUDA_TRY(cudaGraphCreate(&graph, 0));
   cudaGraphConditionalHandle handle;
@@ -756,7 +921,7 @@ static kz_status build_loop_graph(kz_graph g, int64_t max_sweeps) {
     return cuda_status(e);
   }
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  SweepArgs args = make_args(g);
+  SweepArgs args = make_args(g, half);
   args.cond = handle;
   args.use_cond = 1;
   void *kargs[] = {&args};
@@ -780,6 +945,7 @@ static kz_status build_loop_graph(kz_graph g, int64_t max_sweeps) {
   g->loop_exec = exec;
   g->loop_grid = grid;
   g->loop_max_sweeps = max_sweeps;
+  g->loop_half = half;
   return KZ_OK;
 }
 
@@ -792,6 +958,8 @@ static kz_status request_full_write(kz_graph g, cudaStream_t s) {
 
 kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
   int64_t max_sweeps = opt.max_sweeps > 0 ? opt.max_sweeps : (int64_t)g->n + g->m + 1;
+  const bool half = opt.plane0 == KZ_PLANE0_AUTO ? g->half_plane0 : opt.plane0 == KZ_PLANE0_HALF;
+  if (g->n > 0) KZ_TRY(ensure_plan(g, half, s));
   if (!g->ab_synced) {
     KZ_TRY(request_full_write(g, s));
     g->ab_synced = true;
@@ -801,23 +969,23 @@ kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
     begin_run_kernel<<<1, 1, 0, s>>>(g->st, max_sweeps, 0);
     KZ_CUDA_TRY(cudaGetLastError());
     int kmax = 0;
-    SweepFn fn = pick_persistent(g->k, g->half_plane0, kmax);
+    SweepFn fn = pick_persistent(g->k, half, kmax);
     if (!fn) return KZ_ERR_ARG;
     int grid = 0;
     size_t smem = 0;
-    KZ_TRY(launch_config(g, fn, kmax, grid, smem));
-    SweepArgs args = make_args(g);
+    KZ_TRY(launch_config(g, fn, kmax, half, grid, smem));
+    SweepArgs args = make_args(g, half);
     void *kargs[] = {&args};
     KZ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(kSweepWarps * 32), kargs, smem, s));
     return KZ_OK;
   }
   if (g->n > 0 && opt.use_graph == 2) {
     // one graph launch: run-start kernel, then the while node of sweep passes
-    if (g->loop_exec && g->loop_max_sweeps != max_sweeps) {
+    if (g->loop_exec && (g->loop_max_sweeps != max_sweeps || g->loop_half != half)) {
       cudaGraphExecDestroy(g->loop_exec);
       g->loop_exec = nullptr;
     }
-    if (!g->loop_exec) KZ_TRY(build_loop_graph(g, max_sweeps));
+    if (!g->loop_exec) KZ_TRY(build_loop_graph(g, max_sweeps, half));
     KZ_CUDA_TRY(cudaGraphLaunch(g->loop_exec, s));
     return KZ_OK;
   }
@@ -829,12 +997,12 @@ kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
   }
   // host-driven loop: one launch per pass, the host reads the continue flag
   int kmax = 0;
-  SweepFn fn = pick_sweep(g->k, g->half_plane0, kmax);
+  SweepFn fn = pick_sweep(g->k, half, kmax);
   if (!fn) return KZ_ERR_ARG;
   int grid = 0;
   size_t smem = 0;
-  KZ_TRY(launch_config(g, fn, kmax, grid, smem));
-  SweepArgs args = make_args(g);
+  KZ_TRY(launch_config(g, fn, kmax, half, grid, smem));
+  SweepArgs args = make_args(g, half);
   for (;;) {
     fn<<<grid, kSweepWarps * 32, smem, s>>>(args);
     KZ_CUDA_TRY(cudaGetLastError());
@@ -862,8 +1030,8 @@ kz_status bitset_one_pass(kz_graph g, cudaStream_t s, int *cont) {
   if (!fn) return KZ_ERR_ARG;
   int grid = 0;
   size_t smem = 0;
-  KZ_TRY(launch_config(g, fn, kmax, grid, smem));
-  SweepArgs args = make_args(g);
+  KZ_TRY(launch_config(g, fn, kmax, g->half_plane0, grid, smem));
+  SweepArgs args = make_args(g, g->half_plane0);
   fn<<<grid, kSweepWarps * 32, smem, s>>>(args);
   KZ_CUDA_TRY(cudaGetLastError());
   int32_t c = 0;
@@ -885,8 +1053,8 @@ kz_status bitset_barrier_timeout_probe(kz_graph g, uint32_t spin_limit, cudaStre
   if (!fn) return KZ_ERR_ARG;
   int grid = 0;
   size_t smem = 0;
-  KZ_TRY(launch_config(g, fn, kmax, grid, smem));
-  SweepArgs args = make_args(g);
+  KZ_TRY(launch_config(g, fn, kmax, g->half_plane0, grid, smem));
+  SweepArgs args = make_args(g, g->half_plane0);
   args.bar_extra = 1;
   args.spin_limit = spin_limit;
   void *kargs[] = {&args};

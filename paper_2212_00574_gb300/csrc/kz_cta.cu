@@ -44,9 +44,16 @@ __device__ __forceinline__ int find_x(const int32_t *__restrict__ pair_off, int 
   return lo;
 }
 
+// The running record of one graph's fixpoint, kept in shared memory while
+// its CTA works on it and written to the graph's DevState at the end.
+struct CtaRun {
+  int64_t sweeps, passes, tests, max_sweeps;
+  int32_t cur, status;
+};
+
 template <int KMAX, bool SHARED>
 __device__ void cta_fixpoint(const CtaGraph &G, int64_t max_sweeps, uint32_t *smem, unsigned long long *s_cnt,
-                             int *s_flag) {
+                             int *s_flag, int32_t *s_rounds, CtaRun *run) {
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
@@ -81,21 +88,22 @@ __device__ void cta_fixpoint(const CtaGraph &G, int64_t max_sweeps, uint32_t *sm
     Vc = cur ? G.V1 : G.V0;
     Vn = cur ? G.V0 : G.V1;
   }
+  for (int c = tid; c < k; c += kCtaThreads) s_rounds[c] = G.rounds[c];
   if (tid == 0) {
-    st->status = KZ_OK;
-    st->sweeps = 0;
-    st->passes = G.n == 0 ? 1 : 0;
-    st->tests = 0;
-    st->max_sweeps = max_sweeps > 0 ? max_sweeps : (int64_t)G.n + G.m + 1;
+    run->sweeps = 0;
+    run->passes = G.n == 0 ? 1 : 0;
+    run->tests = 0;
+    run->max_sweeps = max_sweeps > 0 ? max_sweeps : (int64_t)G.n + G.m + 1;
+    run->cur = cur;
+    run->status = KZ_OK;
     s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
   }
   __syncthreads();
-  if (G.n == 0) return;
 
   const int64_t npairs = G.pair_off[nb];
   const int64_t share = (npairs + kCtaWarps - 1) / kCtaWarps;
-  for (;;) {
-    const int64_t sweep_no = st->sweeps;
+  for (; G.n > 0;) {
+    const int64_t sweep_no = run->sweeps;
     unsigned long long my_tests = 0, my_de = 0, my_dv = 0;
     // vertex rule, one warp per block
     for (int x = warp; x < nb; x += kCtaWarps) {
@@ -108,8 +116,9 @@ __device__ void cta_fixpoint(const CtaGraph &G, int64_t max_sweeps, uint32_t *sm
       const int wx = X.r * k + X.c;
       const uint32_t vword = Vc[wx];
       const bool live = valid_u && ((vword >> lane) & 1u);
-      int cnt = plane0_vertex_cover<KMAX>(Fu, k, X.c);
-      if (live && cnt < k - 1) cnt = exact_vertex_cover_row(rowu, k, G.rounds, X.c);
+      const uint64_t miss0 = plane0_vertex_missing<KMAX>(Fu, k, X.c);
+      int cnt = (k - 1) - __popcll(miss0);
+      if (live && cnt < k - 1) cnt += vertex_cover_beyond_plane0(rowu, k, s_rounds, miss0);
       const bool fail = live && cnt < k - 1;
       const uint32_t failmask = __ballot_sync(0xffffffffu, fail);
       if (lane == 0) {
@@ -152,7 +161,7 @@ __device__ void cta_fixpoint(const CtaGraph &G, int64_t max_sweeps, uint32_t *sm
         my_tests += __popc(adjw);
         const uint32_t *Ybase = Ac + (size_t)Y.base * ldw;
         const uint32_t del = edge_rule_block<KMAX>(
-            Fu, P, rowu, adjw, k, G.rounds, X.c, Y.c,
+            Fu, P, rowu, adjw, k, s_rounds, X.c, Y.c,
             [&](int b) { return Ybase + (size_t)b * ldw; },
             [&](int b) { return Ybase + (size_t)b * ldw; });
         if (valid_u) An[(size_t)u * ldw + wy] = adjw & ~del;
@@ -175,8 +184,25 @@ __device__ void cta_fixpoint(const CtaGraph &G, int64_t max_sweeps, uint32_t *sm
       if (my_dv) atomicAdd(&s_cnt[2], my_dv);
     }
     __syncthreads();
-    if (tid == 0) {
-      *s_flag = finish_pass(st, s_cnt[2], s_cnt[1], s_cnt[0]);
+    if (tid == 0) {  // close the pass in shared memory (the trace goes straight out)
+      const unsigned long long dv = s_cnt[2], de = s_cnt[1];
+      run->passes += 1;
+      run->tests += (int64_t)s_cnt[0];
+      int cont = 0;
+      if (dv + de > 0) {
+        if (run->sweeps >= run->max_sweeps) {
+          run->status = KZ_ERR_LIMIT;
+        } else {
+          if (run->sweeps < kTraceCap) {
+            st->trace_dv[run->sweeps] = (int64_t)dv;
+            st->trace_de[run->sweeps] = (int64_t)de;
+          }
+          run->sweeps += 1;
+          run->cur ^= 1;
+          cont = 1;
+        }
+      }
+      *s_flag = cont;
       s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
     }
     __syncthreads();
@@ -189,16 +215,22 @@ __device__ void cta_fixpoint(const CtaGraph &G, int64_t max_sweeps, uint32_t *sm
     Vn = t;
     __syncthreads();
   }
-  if (SHARED) {
+  if (SHARED && G.n > 0) {
     // hand the final state back through buffer 0
     uint4 *d4 = reinterpret_cast<uint4 *>(G.A0);
     const uint4 *a4 = reinterpret_cast<const uint4 *>(Ac);
     for (size_t i = tid; i < words / 4; i += kCtaThreads) d4[i] = a4[i];
     for (int i = tid; i < ldw; i += kCtaThreads) G.V0[i] = Vc[i];
-    __syncthreads();
-    if (tid == 0) st->cur = 0;
   }
-  // global mode: finish_pass already left st->cur on the live buffer
+  if (tid == 0) {  // the run's record (global mode: the live buffer is run->cur)
+    st->sweeps = run->sweeps;
+    st->passes = run->passes;
+    st->tests = run->tests;
+    st->max_sweeps = run->max_sweeps;
+    st->status = run->status;
+    st->cont = 0;
+    st->cur = SHARED ? 0 : run->cur;
+  }
   __syncthreads();
 }
 
@@ -208,6 +240,8 @@ __global__ void __launch_bounds__(kCtaThreads, 1) cta_fixpoint_kernel(CtaArgs a)
   __shared__ unsigned long long s_cnt[3];
   __shared__ int s_flag;
   __shared__ int s_g;
+  __shared__ int32_t s_rounds[KMAX];
+  __shared__ CtaRun s_run;
   for (int round = 0;; round++) {
     if (threadIdx.x == 0) s_g = a.queue ? (int)atomicAdd(a.queue, 1u) : (round == 0 ? (int)blockIdx.x : a.count);
     __syncthreads();
@@ -217,9 +251,9 @@ __global__ void __launch_bounds__(kCtaThreads, 1) cta_fixpoint_kernel(CtaArgs a)
     const CtaGraph G = a.graphs[a.order[g]];
     if (G.k > KMAX) continue;  // never scheduled: the host groups graphs by KMAX
     if (G.smem_words > 0 && G.smem_words <= a.smem_words)
-      cta_fixpoint<KMAX, true>(G, a.max_sweeps, smem, s_cnt, &s_flag);
+      cta_fixpoint<KMAX, true>(G, a.max_sweeps, smem, s_cnt, &s_flag, s_rounds, &s_run);
     else
-      cta_fixpoint<KMAX, false>(G, a.max_sweeps, smem, s_cnt, &s_flag);
+      cta_fixpoint<KMAX, false>(G, a.max_sweeps, smem, s_cnt, &s_flag, s_rounds, &s_run);
   }
 }
 
@@ -647,13 +681,15 @@ __global__ void __launch_bounds__(kCtaThreads, 1) fixpoint_kernel(int64_t max_sw
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long s_cnt[3];
   __shared__ int s_flag;
+  __shared__ int32_t s_rounds[32];
+  __shared__ CtaRun s_run;
   Scratch *s = S();
   if (s->h.status) return;
   const CtaGraph G = s->h.desc;
   if (G.smem_words > 0 && G.smem_words <= smem_words)
-    cta_fixpoint<32, true>(G, max_sweeps, smem, s_cnt, &s_flag);
+    cta_fixpoint<32, true>(G, max_sweeps, smem, s_cnt, &s_flag, s_rounds, &s_run);
   else
-    cta_fixpoint<32, false>(G, max_sweeps, smem, s_cnt, &s_flag);
+    cta_fixpoint<32, false>(G, max_sweeps, smem, s_cnt, &s_flag, s_rounds, &s_run);
 }
 
 __global__ void zero_out_kernel(uint64_t *__restrict__ out, int64_t words) {

@@ -77,14 +77,27 @@ struct DevState {
   unsigned long long pass_de;
   unsigned long long pass_tests;
   unsigned int ticket;            // warps finished in the running pass
-  unsigned int pad1;
+  unsigned int tail_next;          // next tail unit of the running pass (sweep kernels)
   unsigned int bar_count;         // grid barrier of the persistent sweep kernel
   unsigned int bar_gen;
   int32_t bar_abort;              // a bounded barrier wait ran out
   int32_t pad2;
+  unsigned long long pass_word;   // persistent sweep kernel: barrier generation and next-pass state
   int64_t trace_dv[kTraceCap];
   int64_t trace_de[kTraceCap];
 };
+
+// The persistent sweep kernel's barrier word: the generation (20 bits), then
+// whether another pass follows, the buffer it reads and its sweep number.
+// The pass-closing CTA writes it once; waiting CTAs need no other read.
+__host__ __device__ inline unsigned long long pass_word(uint32_t gen, int cont, int cur, int64_t sweeps) {
+  return (unsigned long long)(gen & 0xfffffu) | ((unsigned long long)(cont & 1) << 20) |
+         ((unsigned long long)(cur & 1) << 21) | ((unsigned long long)sweeps << 22);
+}
+__host__ __device__ inline uint32_t pass_word_gen(unsigned long long w) { return (uint32_t)(w & 0xfffffu); }
+__host__ __device__ inline int pass_word_cont(unsigned long long w) { return (int)((w >> 20) & 1u); }
+__host__ __device__ inline int pass_word_cur(unsigned long long w) { return (int)((w >> 21) & 1u); }
+__host__ __device__ inline int64_t pass_word_sweeps(unsigned long long w) { return (int64_t)(w >> 22); }
 
 // Per-graph descriptor of the whole-fixpoint-in-one-CTA kernel.
 struct CtaGraph {
@@ -109,7 +122,17 @@ void dev_free(void *p, size_t bytes, cudaStream_t s);
 
 }  // namespace kz
 
-namespace kz { struct CtaGraph; }
+namespace kz {
+struct CtaGraph;
+// Grid and work split of the multi-CTA sweep kernels for one plane-0 form
+// (built when the form is first used).
+struct SweepPlan {
+  int32_t grid = 0;              // CTAs, all resident at once (0: not built)
+  WarpRange *d_ranges = nullptr; // one static range per warp
+  int2 *d_tail = nullptr;        // (x, y) of the tail units, taken one at a time
+  int32_t tail_begin = 0, tail_count = 0;
+};
+}  // namespace kz
 typedef kz::CtaGraph *CtaGraphPtr;
 
 // The handle behind kz_graph.
@@ -149,8 +172,7 @@ struct kz_graph_s {
   int32_t *d_zero = nullptr;         // a device 0 (queue order of a single graph)
   int32_t *d_perm = nullptr;   // n
   kz::BlockDesc *d_blocks = nullptr;
-  kz::WarpRange *d_ranges = nullptr;  // one per warp of the sweep kernels' grid
-  int32_t sweep_grid = 0;             // CTAs of that grid
+  kz::SweepPlan plan[2];              // work of the sweep kernels: [0] full-word, [1] half-word test
   uint8_t *d_changed = nullptr;       // per unit: low byte of the sweep that last changed it
   int64_t n_units = 0;
   // true when the two row buffers differ only in the words of units whose
@@ -158,6 +180,7 @@ struct kz_graph_s {
   // conversion wrote the rows; the next bitset pass then writes every word)
   bool ab_synced = false;
   bool half_plane0 = false;           // sweep kernels use the half-word plane-0 test
+  bool fast_half = false;             // ... and fold whole blocks first (very dense graphs)
   kz::DevState *st = nullptr;
 
   // which representation holds the live state: KZ_PATH_BITSET (bitset rows,
@@ -195,6 +218,7 @@ struct kz_graph_s {
   cudaGraphExec_t loop_exec = nullptr;
   int loop_grid = 0;
   int64_t loop_max_sweeps = 0;
+  bool loop_half = false;
 
   // every device allocation, for kz_free_graph
   struct Alloc { void *p; size_t bytes; };

@@ -98,6 +98,36 @@ __device__ __forceinline__ int plane0_vertex_cover(const uint32_t (&Fu)[KMAX], i
   return cnt;
 }
 
+// Classes (bit c) other than cu whose plane-0 word of row u is zero.
+template <int KMAX>
+__device__ __forceinline__ uint64_t plane0_vertex_missing(const uint32_t (&Fu)[KMAX], int k, int cu) {
+  uint64_t miss = 0;
+#pragma unroll
+  for (int c = 0; c < KMAX; c++)
+    if (c < k && c != cu && Fu[c] == 0u) miss |= 1ull << c;
+  return miss;
+}
+
+// Classes in miss0 (none of their first 32 members is a neighbour of u) that
+// a later plane of row u covers.  Reads only the later planes of those
+// classes; `rounds` (blocks per class) is best in shared memory.
+static __device__ __noinline__ int vertex_cover_beyond_plane0(const uint32_t *ru, int k,
+                                                             const int32_t *__restrict__ rounds, uint64_t miss0) {
+  int cnt = 0;
+  while (miss0) {
+    const int c = __ffsll((long long)miss0) - 1;
+    miss0 &= miss0 - 1;
+    const int R = rounds[c];
+    for (int r = 1; r < R; r++) {
+      if (ru[r * k + c]) {
+        cnt++;
+        break;
+      }
+    }
+  }
+  return cnt;
+}
+
 // Classes (bit c) that plane 0 leaves uncovered for the pair: needed classes
 // whose plane-0 word AND is zero.
 template <int KMAX>
@@ -183,6 +213,8 @@ __device__ __forceinline__ uint32_t plane0_unsettled(const uint32_t (&Fu)[KMAX],
       uint32_t m0 = 0xffffffffu, m1 = 0xffffffffu, m2 = 0xffffffffu, m3 = 0xffffffffu;
 #pragma unroll
       for (int q = 0; q < KMAX / 4; q++) {
+        // words >= k are forced by P, but the bound check keeps the compiler
+        // from rebuilding P inside the loop (measured: 1.6x the instructions)
         if (4 * q >= k) break;
         const uint4 w0 = f0[q], w1 = f1[q];
         m0 = kz_min3(m0, (Fu[4 * q + 0] & w0.x) | P[4 * q + 0], (Fu[4 * q + 1] & w0.y) | P[4 * q + 1]);
@@ -219,15 +251,11 @@ __device__ __forceinline__ uint32_t pack_halves(uint32_t lo, uint32_t hi) {
   return __byte_perm(lo, hi, 0x5410);  // low 16 bits of lo, then low 16 bits of hi
 }
 
-// Half-word plane 0 of a full-word plane 0 (KH = KMAX/2 rounded up to 4).
+// Half-word plane 0 of a full-word plane 0 (KH = KMAX / 2 words).
 template <int KMAX, int KH>
 __device__ __forceinline__ void halve_plane0(uint32_t (&H)[KH], const uint32_t (&F)[KMAX]) {
 #pragma unroll
-  for (int j = 0; j < KH; j++) {
-    const uint32_t lo = 2 * j < KMAX ? F[2 * j] : 0u;
-    const uint32_t hi = 2 * j + 1 < KMAX ? F[2 * j + 1] : 0u;
-    H[j] = pack_halves(lo, hi);
-  }
+  for (int j = 0; j < KH; j++) H[j] = pack_halves(F[2 * j], F[2 * j + 1]);
 }
 
 // Forced half-words: all ones for the classes of u and v and for classes >= k.
@@ -242,18 +270,26 @@ __device__ __forceinline__ void half_mask(uint32_t (&P)[KH], int k, int cu, int 
   }
 }
 
-// In-place conversion of staged plane-0 rows (k words each, KMAX apart) to the
-// half-word form: lane b converts row b.
+// Row stride (words) of the half-word staging buffer: KMAX / 2 rounded up to
+// a multiple of 4, so that every row starts on 16 bytes.
 template <int KMAX>
-__device__ __forceinline__ void halve_staged_rows(uint32_t *buf, int rows, int k, int lane) {
-  constexpr int KH = ((KMAX / 2) + 3) / 4 * 4;
+__host__ __device__ constexpr int half_stride() {
+  return (KMAX / 2 + 3) / 4 * 4;
+}
+
+// Half-word form of staged plane-0 rows (KMAX words apart in src) into dst
+// (half_stride<KMAX>() words apart): lane b converts row b.  Words of classes
+// >= k come out as anything; the forced mask covers them.
+template <int KMAX>
+__device__ __forceinline__ void halve_staged_rows(const uint32_t *src, uint32_t *dst, int rows, int lane) {
+  constexpr int KH = KMAX / 2;
   if (lane < rows) {
-    uint32_t *row = buf + lane * KMAX;
+    const uint32_t *row = src + lane * KMAX;
+    uint32_t *out = dst + lane * half_stride<KMAX>();
     uint32_t w[KMAX];
 #pragma unroll
     for (int q = 0; q < KMAX / 4; q++) {
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (4 * q < k) v = reinterpret_cast<const uint4 *>(row)[q];
+      const uint4 v = reinterpret_cast<const uint4 *>(row)[q];
       w[4 * q + 0] = v.x;
       w[4 * q + 1] = v.y;
       w[4 * q + 2] = v.z;
@@ -261,55 +297,67 @@ __device__ __forceinline__ void halve_staged_rows(uint32_t *buf, int rows, int k
     }
     uint32_t h[KH];
     halve_plane0<KMAX, KH>(h, w);
-    const int kh = (k + 1) >> 1;
 #pragma unroll
-    for (int q = 0; q < KH / 4; q++) {
-      if (4 * q >= kh) break;
-      reinterpret_cast<uint4 *>(row)[q] = make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
-    }
+    for (int q = 0; q < KH / 4; q++)
+      reinterpret_cast<uint4 *>(out)[q] = make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+    if constexpr (KH % 4 == 2)
+      reinterpret_cast<uint2 *>(out)[KH / 2 - 1] = make_uint2(h[KH - 2], h[KH - 1]);
   }
 }
 
 __device__ __forceinline__ bool has_zero_half(uint32_t m) { return (m & 0xffffu) == 0u || m < 0x10000u; }
 
-// Hot loop of the half-word form (see plane0_unsettled): returns the lane's
-// live edges that the first 16 members of each class do not settle.
+// Folds the forced half-word ANDs of one staged member row f into a0, a1.
 template <int KH>
+__device__ __forceinline__ void half_fold(const uint32_t (&F)[KH], const uint32_t (&P)[KH], const uint32_t *f,
+                                          uint32_t &a0, uint32_t &a1) {
+#pragma unroll
+  for (int q = 0; q < KH / 4; q++) {
+    const uint4 w = reinterpret_cast<const uint4 *>(f)[q];
+    a0 = __vimin3_u16x2(a0, (F[4 * q + 0] & w.x) | P[4 * q + 0], (F[4 * q + 1] & w.y) | P[4 * q + 1]);
+    a1 = __vimin3_u16x2(a1, (F[4 * q + 2] & w.z) | P[4 * q + 2], (F[4 * q + 3] & w.w) | P[4 * q + 3]);
+  }
+  if constexpr (KH % 4 == 2) {
+    const uint2 w = reinterpret_cast<const uint2 *>(f)[KH / 2 - 1];
+    a0 = __vimin3_u16x2(a0, (F[KH - 2] & w.x) | P[KH - 2], (F[KH - 1] & w.y) | P[KH - 1]);
+  }
+}
+
+// Hot loop of the half-word form (see plane0_unsettled) over half-word rows
+// sv (half_stride<KMAX>() words apart): returns the lane's live edges that
+// the first 16 members of each class do not settle.  When
+// `try_fast` is set and all 32 members of Y are in play, one pass folds every
+// pair of the block into the lanes' running minima; only a block in which
+// some pair (edge or not) shows an uncovered class is redone member by
+// member.  Lanes without a vertex must hold all-ones in F.
+template <int KMAX, int KH>
 __device__ __forceinline__ uint32_t half_unsettled(const uint32_t (&F)[KH], const uint32_t (&P)[KH],
-                                                   const uint32_t *sv, int stride, uint32_t adjw, int kh) {
+                                                   const uint32_t *sv, uint32_t adjw, bool try_fast) {
   uint32_t bits = __reduce_or_sync(0xffffffffu, adjw);
+  if (try_fast && bits == 0xffffffffu) {
+    uint32_t a0 = 0xffffffffu, a1 = 0xffffffffu, a2 = 0xffffffffu, a3 = 0xffffffffu;
+#pragma unroll 2
+    for (int b = 0; b < 32; b += 2) {
+      half_fold<KH>(F, P, sv + b * half_stride<KMAX>(), a0, a1);
+      half_fold<KH>(F, P, sv + (b + 1) * half_stride<KMAX>(), a2, a3);
+    }
+    const uint32_t a = __vimin3_u16x2(__vimin3_u16x2(a0, a1, a2), a3, 0xffffffffu);
+    if (!__any_sync(0xffffffffu, has_zero_half(a))) return 0u;
+  }
   uint32_t open = 0;
   while (bits) {
     const int b0 = __ffs(bits) - 1;
     bits &= bits - 1;
-    const uint4 *f0 = reinterpret_cast<const uint4 *>(sv + b0 * stride);
+    uint32_t m0 = 0xffffffffu, m1 = 0xffffffffu;
+    half_fold<KH>(F, P, sv + b0 * half_stride<KMAX>(), m0, m1);
     if (bits) {
       const int b1 = __ffs(bits) - 1;
       bits &= bits - 1;
-      const uint4 *f1 = reinterpret_cast<const uint4 *>(sv + b1 * stride);
-      uint32_t m0 = 0xffffffffu, m1 = 0xffffffffu, m2 = 0xffffffffu, m3 = 0xffffffffu;
-#pragma unroll
-      for (int q = 0; q < KH / 4; q++) {
-        if (4 * q >= kh) break;
-        const uint4 w0 = f0[q], w1 = f1[q];
-        m0 = __vimin3_u16x2(m0, (F[4 * q + 0] & w0.x) | P[4 * q + 0], (F[4 * q + 1] & w0.y) | P[4 * q + 1]);
-        m1 = __vimin3_u16x2(m1, (F[4 * q + 2] & w0.z) | P[4 * q + 2], (F[4 * q + 3] & w0.w) | P[4 * q + 3]);
-        m2 = __vimin3_u16x2(m2, (F[4 * q + 0] & w1.x) | P[4 * q + 0], (F[4 * q + 1] & w1.y) | P[4 * q + 1]);
-        m3 = __vimin3_u16x2(m3, (F[4 * q + 2] & w1.z) | P[4 * q + 2], (F[4 * q + 3] & w1.w) | P[4 * q + 3]);
-      }
-      if (has_zero_half(__vimin3_u16x2(m0, m1, 0xffffffffu))) open |= 1u << b0;
+      uint32_t m2 = 0xffffffffu, m3 = 0xffffffffu;
+      half_fold<KH>(F, P, sv + b1 * half_stride<KMAX>(), m2, m3);
       if (has_zero_half(__vimin3_u16x2(m2, m3, 0xffffffffu))) open |= 1u << b1;
-    } else {
-      uint32_t m0 = 0xffffffffu, m1 = 0xffffffffu;
-#pragma unroll
-      for (int q = 0; q < KH / 4; q++) {
-        if (4 * q >= kh) break;
-        const uint4 w0 = f0[q];
-        m0 = __vimin3_u16x2(m0, (F[4 * q + 0] & w0.x) | P[4 * q + 0], (F[4 * q + 1] & w0.y) | P[4 * q + 1]);
-        m1 = __vimin3_u16x2(m1, (F[4 * q + 2] & w0.z) | P[4 * q + 2], (F[4 * q + 3] & w0.w) | P[4 * q + 3]);
-      }
-      if (has_zero_half(__vimin3_u16x2(m0, m1, 0xffffffffu))) open |= 1u << b0;
     }
+    if (has_zero_half(__vimin3_u16x2(m0, m1, 0xffffffffu))) open |= 1u << b0;
   }
   return open & adjw;
 }
@@ -371,22 +419,25 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t w) {
 // is dropped and KZ_ERR_LIMIT recorded.  Returns 1 to continue.
 __device__ __forceinline__ int finish_pass(DevState *st, unsigned long long dv, unsigned long long de,
                                            unsigned long long tests) {
-  st->passes += 1;
-  st->tests += (int64_t)tests;
+  // every field is read before any is written, so the reads travel together
+  // (one memory round trip instead of a chain of read-modify-writes)
+  const int64_t passes = st->passes, total = st->tests, sweeps = st->sweeps, max_sweeps = st->max_sweeps;
+  const int32_t cur = st->cur;
+  const bool productive = dv + de > 0;
+  const bool limited = productive && sweeps >= max_sweeps;
+  const int cont = productive && !limited ? 1 : 0;
+  st->passes = passes + 1;
+  st->tests = total + (int64_t)tests;
   st->full_write = 0;
-  int cont = 0;
-  if (dv + de > 0) {
-    if (st->sweeps >= st->max_sweeps) {
-      st->status = KZ_ERR_LIMIT;
-    } else {
-      if (st->sweeps < kTraceCap) {
-        st->trace_dv[st->sweeps] = (int64_t)dv;
-        st->trace_de[st->sweeps] = (int64_t)de;
-      }
-      st->sweeps += 1;
-      st->cur ^= 1;
-      cont = 1;
+  st->tail_next = 0;
+  if (limited) st->status = KZ_ERR_LIMIT;
+  if (cont) {
+    if (sweeps < kTraceCap) {
+      st->trace_dv[sweeps] = (int64_t)dv;
+      st->trace_de[sweeps] = (int64_t)de;
     }
+    st->sweeps = sweeps + 1;
+    st->cur = cur ^ 1;
   }
   st->cont = cont;
   return cont;

@@ -37,14 +37,19 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Stage plane 0 of the member rows of block Y (round_up(k, 4) words each,
-// KMAX words apart) with asynchronous 16-byte copies.
+// KMAX words apart) with asynchronous 16-byte copies.  Lane l copies chunk
+// l % (KMAX / 4) of rows l / (KMAX / 4), l / (KMAX / 4) + 32 / (KMAX / 4), ...
+// (compile-time divisions only).
 template <int KMAX>
 __device__ __forceinline__ void stage_block(const uint32_t *__restrict__ A, int ldw, const BlockDesc &Y, int kq4,
                                             uint32_t *buf, int lane) {
-  const int total = Y.size * kq4;
-  for (int idx = lane; idx < total; idx += 32) {
-    const int b = idx / kq4, q = idx - b * kq4;
-    cp_async16(buf + b * KMAX + 4 * q, A + (int64_t)(Y.base + b) * ldw + 4 * q);
+  constexpr int C = KMAX / 4;   // 16-byte chunks per staged row
+  constexpr int RPI = 32 / C;   // rows per round of the warp
+  const int rr = lane / C, q = lane - rr * C;
+  if (rr < RPI && q < kq4) {
+    const uint32_t *src = A + (int64_t)Y.base * ldw + 4 * q;
+    uint32_t *dst = buf + 4 * q;
+    for (int b = rr; b < Y.size; b += RPI) cp_async16(dst + b * KMAX, src + (int64_t)b * ldw);
   }
 }
 

@@ -350,12 +350,16 @@ def _batch_graphs():
     return gs
 
 
-@pytest.mark.parametrize("path", ["auto", "bitset", "small"])
-def test_batch_matches_oracle(path):
+@pytest.mark.parametrize("path,batch", [("auto", "concurrent"), ("auto", "sequential"), ("auto", "fused"),
+                                        ("bitset", "concurrent"), ("small", "concurrent"), ("small", "fused"),
+                                        ("sparse", "concurrent")])
+def test_batch_matches_oracle(path, batch):
     gs = _batch_graphs()
-    handles = [kz.KernelGraph.from_synth(g) for g in gs]
+    if path == "sparse":
+        gs = gs[:20]
+    handles = [kz.KernelGraph.from_synth(g, dense=False) for g in gs]
     try:
-        kz.kz_kernelize_batch([h.h for h in handles], kz.kz_default_options(path=path))
+        kz.kz_kernelize_batch([h.h for h in handles], kz.kz_default_options(path=path, batch=batch))
         for g, h in zip(gs, handles):
             alive, edges, stats = h.fetch()
             dv, de, vs = h.trace()
@@ -367,14 +371,14 @@ def test_batch_matches_oracle(path):
             h.close()
 
 
-@pytest.mark.parametrize("path", ["auto", "small"])
-def test_batch_c4_reduced(path):
+@pytest.mark.parametrize("path,batch", [("auto", "concurrent"), ("auto", "fused"), ("small", "fused")])
+def test_batch_c4_reduced(path, batch):
     """The batched workload's recipe at reduced size (64 graphs, n <= 1024)."""
     specs = synth.batch_specs(64, synth.SEED_BASE + 4, n_hi=1024)
     gs = [synth.kpartite(n, k, p, seed, planted=pl) for (n, k, p, pl, seed) in specs]
     handles = [kz.KernelGraph.from_synth(g) for g in gs]
     try:
-        kz.kz_kernelize_batch([h.h for h in handles], kz.kz_default_options(path=path))
+        kz.kz_kernelize_batch([h.h for h in handles], kz.kz_default_options(path=path, batch=batch))
         for g, h in zip(gs, handles):
             alive, edges, stats = h.fetch()
             orc = oracle.fixpoint(g.colour, g.get_edges(), g.k)
@@ -405,6 +409,8 @@ def test_batch_limit_and_repeat():
         for h in handles:
             st = h.stats()
             assert st["sweeps"] == 0 and st["passes"] == 1
+        with pytest.raises(kz.KzError):  # a fused batch has no multi-CTA per-graph form
+            kz.kz_kernelize_batch(hs, kz.kz_default_options(path="bitset", batch="fused"))
     finally:
         for h in handles:
             h.close()
@@ -472,11 +478,23 @@ def _two_density_graph(seed, n, k, n_dense, p_dense, p_sparse):
     return synth.Graph(n=n, k=k, colour=colour, edges=synth.canonical_edges(edges), name="two-density")
 
 
-@pytest.mark.parametrize("loop", [0, 1])
-def test_half_word_plane0_with_recounts(loop):
+@pytest.mark.parametrize("loop,plane0", [(0, 0), (1, 0), (1, 1), (2, 2)])
+def test_half_word_plane0_with_recounts(loop, plane0):
+    """Densities 0.65 to 0.95: the half-word test with and without the
+    whole-block fold, blocks that fall back to per-pair results."""
     for seed, (n, k, nd, pd, ps) in enumerate(((1200, 12, 10, 0.95, 0.05), (900, 8, 6, 0.97, 0.3),
-                                               (700, 20, 18, 0.9, 0.1))):
+                                               (700, 20, 18, 0.9, 0.1), (800, 24, 23, 0.95, 0.05),
+                                               (1500, 16, 14, 0.99, 0.4))):
         g = _two_density_graph(seed, n, k, nd, pd, ps)
         cross = (n * n - np.sum(np.bincount(g.colour, minlength=k) ** 2)) / 2
-        assert len(g.edges) >= 0.6 * cross  # dense enough for the half-word test
-        assert_parity(g, gpu_run(g, path="bitset", use_graph=loop))
+        assert len(g.edges) >= 0.6 * cross  # dense
+        assert_parity(g, gpu_run(g, path="bitset", use_graph=loop, plane0=plane0))
+
+
+@pytest.mark.parametrize("plane0", [1, 2])
+def test_forced_plane0_forms(plane0):
+    """Either first test on graphs of any density, sparse ones included (the
+    half-word form then sends most pairs to the recount)."""
+    for (n, k, p, seed) in ((3000, 10, 0.1, 5), (600, 7, 0.5, 6), (400, 33, 0.9, 7), (1000, 64, 0.97, 8)):
+        g = synth.tiny_random(seed, n, k, p, planted=True)
+        assert_parity(g, gpu_run(g, path="bitset", plane0=plane0))
