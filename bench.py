@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--path", choices=["auto", "bitset", "small", "sparse", "tensor"], default="auto")
-    ap.add_argument("--plane0", choices=["auto", "full", "half"], default="auto",
+    ap.add_argument("--plane0", choices=["auto", "full", "half", "two"], default="auto",
                     help="first test of the bitset sweep kernels (full words or half words per class)")
     ap.add_argument("--loop", choices=["device", "graph", "host"], default="device",
                     help="pass loop: device = one cooperative persistent launch, graph = CUDA-graph while "
@@ -262,7 +262,7 @@ def run_ours(args, world, rank, local, pg):
         h_edges = pin_edges.numpy()
         h = kz.kz_load_graph(g.n, g.k, h_col, h_edges, stream=stream)
     opts = kz.kz_default_options(path=args.path, use_graph={"device": 1, "graph": 2, "host": 0}[args.loop],
-                                 plane0={"auto": 0, "full": 1, "half": 2}[args.plane0])
+                                 plane0={"auto": 0, "full": 1, "half": 2, "two": 3}[args.plane0])
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def step(i, ev0=None, ev1=None):

@@ -89,9 +89,11 @@ typedef enum {
  * Both are exact: a pair the first test leaves open is recounted over all
  * planes.  Only the speed differs. */
 typedef enum {
-    KZ_PLANE0_AUTO = 0, /* by edge density: half words from density 0.8 */
+    KZ_PLANE0_AUTO = 0, /* by edge density: half words from 0.8, two planes below 0.42 */
     KZ_PLANE0_FULL = 1, /* the first 32 members of each class, one word per class */
-    KZ_PLANE0_HALF = 2  /* the first 16 members of each class, two classes per word */
+    KZ_PLANE0_HALF = 2, /* the first 16 members of each class, two classes per word */
+    KZ_PLANE0_TWO = 3   /* the first 64 members of each class (k <= 32 and classes of more than
+                           32 members; otherwise FULL) */
 } kz_plane0;
 
 /* How kz_kernelize_batch runs its graphs (kz_options.batch).  All give the

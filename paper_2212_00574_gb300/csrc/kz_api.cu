@@ -245,7 +245,7 @@ static kz_status read_options(const kz_options *opt, kz_options &o) {
   }
   if (o.path < KZ_PATH_AUTO || o.path > KZ_PATH_TENSOR) return KZ_ERR_ARG;
   if (o.schedule != KZ_SCHED_PLAIN && o.schedule != KZ_SCHED_LEARNED) return KZ_ERR_ARG;
-  if (o.plane0 < KZ_PLANE0_AUTO || o.plane0 > KZ_PLANE0_HALF) return KZ_ERR_ARG;
+  if (o.plane0 < KZ_PLANE0_AUTO || o.plane0 > KZ_PLANE0_TWO) return KZ_ERR_ARG;
   if (o.batch < KZ_BATCH_CONCURRENT || o.batch > KZ_BATCH_FUSED) return KZ_ERR_ARG;
   return KZ_OK;
 }

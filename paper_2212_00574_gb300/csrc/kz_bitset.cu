@@ -265,22 +265,32 @@ struct SweepArgs {
 };
 
 constexpr int kSweepWarps = 4;
+// First test of a pair in the sweep kernels (the FORM template argument).
+constexpr int kFormFull = 0;  // plane 0: the first 32 members of each class, one word per class
+constexpr int kFormHalf = 1;  // the first 16 members, two classes per word (dense graphs)
+constexpr int kFormTwo = 2;   // planes 0 and 1: the first 64 members (sparser graphs)
 // density (edges / pairs of vertices in different classes) from which the
 // sweep kernels use the half-word plane-0 test
 constexpr double kHalfDensity = 0.8;
+// density below which a graph of at least two planes (and k <= 32) tests the
+// first 64 members of each class first
+constexpr double kTwoPlaneDensity = 0.42;
 // density from which a whole block is first folded without per-pair results
 // (almost every 32 x 32 block then has every pair covered); below it the
 // half-word form (when forced) tests pair by pair
 constexpr double kFastHalfDensity = 0.8;
 // resident CTAs per SM the compiler is asked to fit (4-warp CTAs): five for
-// the half-word form up to k = 24, four otherwise up to k = 32
-template <int KMAX, bool HALF>
-constexpr int kMinCtas = !HALF ? (KMAX <= 32 ? 4 : 1) : (KMAX <= 24 ? 5 : (KMAX <= 32 ? 4 : 1));
+// the half-word form up to k = 24, three for the two-plane form from k = 25,
+// four otherwise up to k = 32
+template <int KMAX, int FORM>
+constexpr int kMinCtas = FORM == kFormHalf ? (KMAX <= 24 ? 5 : (KMAX <= 32 ? 4 : 1))
+                         : FORM == kFormTwo ? (KMAX <= 24 ? 4 : (KMAX <= 32 ? 3 : 1))
+                                            : (KMAX <= 32 ? 4 : 1);
 // Shared memory of one warp: two staging buffers of plane-0 rows (KMAX words
 // each) and, in the half-word form, the converted rows of the current unit.
-template <int KMAX, bool HALF>
+template <int KMAX, int FORM>
 __host__ __device__ constexpr int warp_smem_words() {
-  return 2 * 32 * KMAX + (HALF ? 32 * half_stride<KMAX>() : 0);
+  return FORM == kFormTwo ? 2 * 32 * 2 * KMAX : 2 * 32 * KMAX + (FORM == kFormHalf ? 32 * half_stride<KMAX>() : 0);
 }
 
 __device__ __forceinline__ void prefetch_l1(const uint32_t *p) {
@@ -292,9 +302,8 @@ __device__ __forceinline__ void prefetch_l1(const uint32_t *p) {
 // left, so the warps of the grid end their pass within about one unit of
 // each other.  `cur` is the current ping-pong buffer, `sweep_no` the
 // productive sweeps so far, `full` asks for every owned word to be written.
-// HALF selects the half-word plane-0 test (first 16 members of each class;
-// for dense graphs).
-template <int KMAX, bool HALF>
+// FORM selects the first test of a pair (kFormFull, kFormHalf, kFormTwo).
+template <int KMAX, int FORM>
 __device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange r, int cur, int64_t sweep_no,
                                             bool full, uint32_t *buf0, uint32_t *buf1, uint32_t *bufh,
                                             const int32_t *rounds, PassCounters &pc) {
@@ -303,8 +312,10 @@ __device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange 
   uint32_t *__restrict__ An = cur ? p.A0 : p.A1;
   const uint32_t *__restrict__ Vc = cur ? p.V1 : p.V0;
   uint32_t *__restrict__ Vn = cur ? p.V0 : p.V1;
+  constexpr bool HALF = FORM == kFormHalf;
+  constexpr bool TWO = FORM == kFormTwo;
   const int k = p.k, ldw = p.ldw, nb = p.nb;
-  const int kq4 = (k + 3) >> 2;
+  const int kq4 = TWO ? (2 * k + 3) >> 2 : (k + 3) >> 2;  // 16-byte chunks staged per row
   const uint8_t tag_now = (uint8_t)(sweep_no & 0xff);
   const uint8_t tag_next = (uint8_t)((sweep_no + 1) & 0xff);
   unsigned int *tail_ctr = &p.st->tail_next;
@@ -339,7 +350,8 @@ __device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange 
   BlockDesc Y = X;
   if (y < nb) {
     Y = p.blocks[y];
-    stage_block<KMAX>(A, ldw, Y, kq4, buf0, lane);
+    if constexpr (TWO) stage_block2<KMAX>(A, ldw, Y, kq4, buf0, lane);
+    else stage_block<KMAX>(A, ldw, Y, kq4, buf0, lane);
   }
   cp_async_commit();
   uint32_t adj_n = (y < nb && lane < X.size) ? A[(int64_t)(X.base + lane) * ldw + Y.r * k + Y.c] : 0u;
@@ -349,6 +361,7 @@ __device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange 
   constexpr int KH = KMAX / 2;
   constexpr int KW = HALF ? KH : KMAX;
   uint32_t F[KW], P[KW];  // plane 0 of the lanes' rows (full or half-word form), forced classes
+  uint32_t F1[TWO ? KMAX : 1];  // plane 1 (two-plane form)
   int fu_x = -1, prev_cv = -1, vcnt = 0;
   uint64_t vmiss = 0;  // classes plane 0 leaves uncovered for the lane's vertex
   for (int i = 0;; i++) {
@@ -395,7 +408,8 @@ __device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange 
       }
       if (y < nb) {
         Y = p.blocks[y];
-        stage_block<KMAX>(A, ldw, Y, kq4, (i & 1) ? buf0 : buf1, lane);
+        if constexpr (TWO) stage_block2<KMAX>(A, ldw, Y, kq4, (i & 1) ? buf0 : buf1, lane);
+        else stage_block<KMAX>(A, ldw, Y, kq4, (i & 1) ? buf0 : buf1, lane);
       }
       adj_n = (y < nb && lane < X.size) ? A[(int64_t)(X.base + lane) * ldw + Y.r * k + Y.c] : 0u;
       chg_n = y < nb ? p.changed[unit] : (uint8_t)0;
@@ -422,6 +436,7 @@ __device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange 
       } else {
         load_plane0<KMAX>(F, rowu, k, valid);
         vmiss = plane0_vertex_missing<KMAX>(F, k, cu);
+        if constexpr (TWO) load_plane1<KMAX>(F1, rowu, k, valid);
       }
       vcnt = (k - 1) - __popcll(vmiss);
       fu_x = xc;
@@ -455,6 +470,12 @@ __device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange 
         open = half_unsettled<KMAX, KH>(F, P, bufh, adjw, p.fast_half != 0);
         // the recount starts from the full staged plane 0
         if (open) del = recount_unsettled(rowu, sv, KMAX, ybase, ldw, open, k, cu, cv, rounds);
+      } else if constexpr (TWO) {
+        spread_plane1<KMAX>(sv, Yc.size, k, lane);
+        __syncwarp();
+        open = two_unsettled<KMAX>(F, F1, P, sv, adjw, k);
+        // the recount starts from plane 0 of the staged rows, then reads the rows
+        if (open) del = recount_unsettled(rowu, sv, 2 * KMAX, ybase, ldw, open, k, cu, cv, rounds);
       } else {
         open = plane0_unsettled<KMAX>(F, P, sv, adjw, k);
         if (open) del = recount_unsettled(rowu, sv, KMAX, ybase, ldw, open, k, cu, cv, rounds);
@@ -507,14 +528,15 @@ __device__ __forceinline__ void add_cta_counters(PassCounters pc, DevState *st) 
 }
 
 // One Jacobi pass per launch (the CUDA-graph loop and the host-driven loop).
-template <int KMAX, bool HALF>
-__global__ void __launch_bounds__(kSweepWarps * 32, kMinCtas<KMAX, HALF>)
+template <int KMAX, int FORM>
+__global__ void __launch_bounds__(kSweepWarps * 32, kMinCtas<KMAX, FORM>)
     bitset_sweep_kernel(SweepArgs p) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int wib = threadIdx.x >> 5;
-  uint32_t *buf0 = smem + wib * warp_smem_words<KMAX, HALF>();
-  uint32_t *buf1 = buf0 + 32 * KMAX;
-  uint32_t *bufh = buf1 + 32 * KMAX;  // half-word rows (HALF only)
+  constexpr int kRow = FORM == kFormTwo ? 2 * KMAX : KMAX;  // staged row stride
+  uint32_t *buf0 = smem + wib * warp_smem_words<KMAX, FORM>();
+  uint32_t *buf1 = buf0 + 32 * kRow;
+  uint32_t *bufh = buf1 + 32 * kRow;  // half-word rows (half-word form only)
   __shared__ int32_t s_rounds[KMAX];
   for (int c = threadIdx.x; c < p.k; c += blockDim.x) s_rounds[c] = p.rounds[c];
   __syncthreads();
@@ -523,7 +545,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32, kMinCtas<KMAX, HALF>)
   const int64_t sweep_no = *((volatile int64_t *)&st->sweeps);
   const bool full = *((volatile int32_t *)&st->full_write) != 0;
   PassCounters pc;
-  sweep_range<KMAX, HALF>(p, p.ranges[blockIdx.x * kSweepWarps + wib], cur, sweep_no, full, buf0, buf1, bufh, s_rounds, pc);
+  sweep_range<KMAX, FORM>(p, p.ranges[blockIdx.x * kSweepWarps + wib], cur, sweep_no, full, buf0, buf1, bufh, s_rounds, pc);
   add_cta_counters(pc, st);
   if (threadIdx.x == 0) {
     __threadfence();
@@ -551,15 +573,16 @@ constexpr uint32_t kBarrierSpinLimit = 1u << 25;
 // closes the pass (counters, buffer flip) and releases the others.  Every
 // barrier wait is bounded: one that runs out records KZ_ERR_TIMEOUT and all
 // CTAs leave.
-template <int KMAX, bool HALF>
-__global__ void __launch_bounds__(kSweepWarps * 32, kMinCtas<KMAX, HALF>)
+template <int KMAX, int FORM>
+__global__ void __launch_bounds__(kSweepWarps * 32, kMinCtas<KMAX, FORM>)
     bitset_persistent_kernel(SweepArgs p) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long s_word;
   const int wib = threadIdx.x >> 5;
-  uint32_t *buf0 = smem + wib * warp_smem_words<KMAX, HALF>();
-  uint32_t *buf1 = buf0 + 32 * KMAX;
-  uint32_t *bufh = buf1 + 32 * KMAX;  // half-word rows (HALF only)
+  constexpr int kRow = FORM == kFormTwo ? 2 * KMAX : KMAX;  // staged row stride
+  uint32_t *buf0 = smem + wib * warp_smem_words<KMAX, FORM>();
+  uint32_t *buf1 = buf0 + 32 * kRow;
+  uint32_t *bufh = buf1 + 32 * kRow;  // half-word rows (half-word form only)
   __shared__ int32_t s_rounds[KMAX];
   for (int c = threadIdx.x; c < p.k; c += blockDim.x) s_rounds[c] = p.rounds[c];
   __syncthreads();
@@ -571,7 +594,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32, kMinCtas<KMAX, HALF>)
   bool full = *((volatile int32_t *)&st->full_write) != 0;
   for (;;) {
     PassCounters pc;
-    sweep_range<KMAX, HALF>(p, p.ranges[blockIdx.x * kSweepWarps + wib], cur, sweep_no, full, buf0, buf1, bufh,
+    sweep_range<KMAX, FORM>(p, p.ranges[blockIdx.x * kSweepWarps + wib], cur, sweep_no, full, buf0, buf1, bufh,
                             s_rounds, pc);
     add_cta_counters(pc, st);
     if (threadIdx.x == 0) {
@@ -656,13 +679,15 @@ typedef void (*SweepFn)(SweepArgs);
 
 #define KZ_KMAX_LIST(X) X(4) X(8) X(12) X(16) X(20) X(24) X(28) X(32) X(48) X(64)
 
-// One-pass kernel for k colours (kmax receives the template width); HALF
-// selects the half-word plane-0 test.
-static SweepFn pick_sweep(int k, bool half, int &kmax) {
-#define KZ_CASE(K)                                                      \
-  if (k <= K) {                                                         \
-    kmax = K;                                                           \
-    return half ? bitset_sweep_kernel<K, true> : bitset_sweep_kernel<K, false>; \
+// One-pass and persistent kernels for k colours and a form (kmax receives the
+// template width).  The two-plane form exists for k <= 32.
+static SweepFn pick_sweep(int k, int form, int &kmax) {
+#define KZ_CASE(K)                                                                              \
+  if (k <= K) {                                                                                 \
+    kmax = K;                                                                                   \
+    if (form == kFormHalf) return bitset_sweep_kernel<K, kFormHalf>;                            \
+    if (form == kFormTwo) return K <= 32 ? bitset_sweep_kernel<(K <= 32 ? K : 32), kFormTwo> : nullptr; \
+    return bitset_sweep_kernel<K, kFormFull>;                                                   \
   }
   KZ_KMAX_LIST(KZ_CASE)
 #undef KZ_CASE
@@ -670,11 +695,13 @@ static SweepFn pick_sweep(int k, bool half, int &kmax) {
   return nullptr;
 }
 
-static SweepFn pick_persistent(int k, bool half, int &kmax) {
-#define KZ_CASE(K)                                                                \
-  if (k <= K) {                                                                   \
-    kmax = K;                                                                     \
-    return half ? bitset_persistent_kernel<K, true> : bitset_persistent_kernel<K, false>; \
+static SweepFn pick_persistent(int k, int form, int &kmax) {
+#define KZ_CASE(K)                                                                                   \
+  if (k <= K) {                                                                                      \
+    kmax = K;                                                                                        \
+    if (form == kFormHalf) return bitset_persistent_kernel<K, kFormHalf>;                            \
+    if (form == kFormTwo) return K <= 32 ? bitset_persistent_kernel<(K <= 32 ? K : 32), kFormTwo> : nullptr; \
+    return bitset_persistent_kernel<K, kFormFull>;                                                   \
   }
   KZ_KMAX_LIST(KZ_CASE)
 #undef KZ_CASE
@@ -700,7 +727,7 @@ static int sm_count() {
   return sms;
 }
 
-static kz_status ensure_plan(kz_graph g, bool half, cudaStream_t s);
+static kz_status ensure_plan(kz_graph g, int form, cudaStream_t s);
 
 kz_status bitset_finish_load(kz_graph g, cudaStream_t s) {
   const int nb = (int)g->blocks.size();
@@ -730,8 +757,11 @@ kz_status bitset_finish_load(kz_graph g, cudaStream_t s) {
       cross += tot * sz;
       tot += sz;
     }
-    g->half_plane0 = cross > 0 && (double)g->m >= kHalfDensity * cross;
-    g->fast_half = cross > 0 && (double)g->m >= kFastHalfDensity * cross;
+    const double density = cross > 0 ? (double)g->m / cross : 0.0;
+    g->fast_half = density >= kFastHalfDensity;
+    g->form = density >= kHalfDensity ? kFormHalf
+              : (density < kTwoPlaneDensity && g->R >= 2 && g->k <= 32) ? kFormTwo
+                                                                        : kFormFull;
   }
   // per-unit change tags, and the work split of the form the density picks
   if (g->k <= 64) {
@@ -740,7 +770,7 @@ kz_status bitset_finish_load(kz_graph g, cudaStream_t s) {
     if (g->n_units > INT32_MAX) return KZ_ERR_UNSUPPORTED;
     KZ_TRY(graph_alloc(g, &g->d_changed, (size_t)std::max<int64_t>(g->n_units, 1), s));
     KZ_CUDA_TRY(cudaMemsetAsync(g->d_changed, 0xff, (size_t)std::max<int64_t>(g->n_units, 1), s));
-    KZ_TRY(ensure_plan(g, g->half_plane0, s));
+    KZ_TRY(ensure_plan(g, g->form, s));
   }
   KZ_TRY(graph_alloc(g, &g->A[0], (size_t)g->n * g->ldw, s));
   KZ_TRY(graph_alloc(g, &g->A[1], (size_t)g->n * g->ldw, s));
@@ -772,11 +802,13 @@ kz_status bitset_reset(kz_graph g, cudaStream_t s) {
 
 // Shared memory of a sweep kernel and its resident CTAs per SM.
 // (Set up and queried once per kernel and device: the attribute persists.)
-static kz_status kernel_fit(SweepFn fn, int kmax, bool half, size_t &smem, int &per_sm) {
+static kz_status kernel_fit(SweepFn fn, int kmax, int form, size_t &smem, int &per_sm) {
   static std::mutex mu;
   static std::map<std::tuple<const void *, int>, int> fitted;  // (kernel, device) -> CTAs per SM
   const int half_stride_words = (kmax / 2 + 3) / 4 * 4;
-  smem = (size_t)kSweepWarps * 4 * (2 * 32 * kmax + (half ? 32 * half_stride_words : 0));
+  const size_t warp_words = form == kFormTwo ? 2 * 32 * 2 * (size_t)kmax
+                                              : 2 * 32 * (size_t)kmax + (form == kFormHalf ? 32 * half_stride_words : 0);
+  smem = (size_t)kSweepWarps * 4 * warp_words;
   int dev = 0;
   KZ_CUDA_TRY(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lk(mu);
@@ -798,13 +830,13 @@ static kz_status kernel_fit(SweepFn fn, int kmax, bool half, size_t &smem, int &
 // The grid of both sweep kernels of one form: every CTA resident at once
 // (the persistent kernel's grid barrier needs that), and no more warps than
 // units.
-static kz_status sweep_grid_size(kz_graph g, bool half, int &grid) {
+static kz_status sweep_grid_size(kz_graph g, int form, int &grid) {
   int kmax = 0, kmax2 = 0, per_a = 0, per_b = 0;
   size_t smem = 0;
-  SweepFn fa = pick_persistent(g->k, half, kmax), fb = pick_sweep(g->k, half, kmax2);
+  SweepFn fa = pick_persistent(g->k, form, kmax), fb = pick_sweep(g->k, form, kmax2);
   if (!fa || !fb) return KZ_ERR_ARG;
-  KZ_TRY(kernel_fit(fa, kmax, half, smem, per_a));
-  KZ_TRY(kernel_fit(fb, kmax2, half, smem, per_b));
+  KZ_TRY(kernel_fit(fa, kmax, form, smem, per_a));
+  KZ_TRY(kernel_fit(fb, kmax2, form, smem, per_b));
   const int per_sm = std::max(1, std::min(per_a, per_b));
   const int64_t want = (std::max<int64_t>(g->n_units, 1) + kSweepWarps - 1) / kSweepWarps;
   grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)per_sm * sm_count()));
@@ -812,15 +844,15 @@ static kz_status sweep_grid_size(kz_graph g, bool half, int &grid) {
 }
 
 // Builds the grid, static ranges and tail of one form, once per graph.
-static kz_status ensure_plan(kz_graph g, bool half, cudaStream_t s) {
-  SweepPlan &pl = g->plan[half ? 1 : 0];
+static kz_status ensure_plan(kz_graph g, int form, cudaStream_t s) {
+  SweepPlan &pl = g->plan[form];
   if (pl.grid > 0) return KZ_OK;
   int grid = 0;
-  KZ_TRY(sweep_grid_size(g, half, grid));
+  KZ_TRY(sweep_grid_size(g, form, grid));
   std::vector<WarpRange> ranges;
   std::vector<int2> tail;
   int64_t units = 0, tail_begin = 0;
-  build_ranges(g, grid * kSweepWarps, half ? kStaticShareHalf : kStaticShareFull, ranges, tail, units,
+  build_ranges(g, grid * kSweepWarps, form == kFormHalf ? kStaticShareHalf : kStaticShareFull, ranges, tail, units,
                tail_begin);
   if (units != g->n_units) return KZ_ERR_INTERNAL;
   KZ_TRY(graph_alloc(g, &pl.d_ranges, ranges.size(), s));
@@ -835,16 +867,16 @@ static kz_status ensure_plan(kz_graph g, bool half, cudaStream_t s) {
   return KZ_OK;
 }
 
-static kz_status launch_config(kz_graph g, SweepFn fn, int kmax, bool half, int &grid, size_t &smem) {
+static kz_status launch_config(kz_graph g, SweepFn fn, int kmax, int form, int &grid, size_t &smem) {
   int per_sm = 0;
-  KZ_TRY(kernel_fit(fn, kmax, half, smem, per_sm));
-  grid = g->plan[half ? 1 : 0].grid;
+  KZ_TRY(kernel_fit(fn, kmax, form, smem, per_sm));
+  grid = g->plan[form].grid;
   if (grid <= 0 || grid > std::max(per_sm, 1) * sm_count()) return KZ_ERR_INTERNAL;
   return KZ_OK;
 }
 
-static SweepArgs make_args(kz_graph g, bool half) {
-  const SweepPlan &pl = g->plan[half ? 1 : 0];
+static SweepArgs make_args(kz_graph g, int form) {
+  const SweepPlan &pl = g->plan[form];
   SweepArgs a;
   a.blocks = g->d_blocks;
   a.ranges = pl.d_ranges;
@@ -873,13 +905,13 @@ static SweepArgs make_args(kz_graph g, bool half) {
 
 // Builds (once per graph) an executable CUDA graph whose while-node runs one
 // sweep-kernel launch per pass until the kernel clears the condition.
-static kz_status build_loop_graph(kz_graph g, int64_t max_sweeps, bool half) {
+static kz_status build_loop_graph(kz_graph g, int64_t max_sweeps, int form) {
   int kmax = 0;
-  SweepFn fn = pick_sweep(g->k, half, kmax);
+  SweepFn fn = pick_sweep(g->k, form, kmax);
   if (!fn) return KZ_ERR_ARG;
   int grid = 0;
   size_t smem = 0;
-  KZ_TRY(launch_config(g, fn, kmax, half, grid, smem));
+  KZ_TRY(launch_config(g, fn, kmax, form, grid, smem));
   cudaGraph_t graph = nullptr;
   KZ_CUDA_TRY(cudaGraphCreate(&graph, 0));
   cudaGraphConditionalHandle handle;
@@ -921,7 +953,7 @@ static kz_status build_loop_graph(kz_graph g, int64_t max_sweeps, bool half) {
     return cuda_status(e);
   }
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  SweepArgs args = make_args(g, half);
+  SweepArgs args = make_args(g, form);
   args.cond = handle;
   args.use_cond = 1;
   void *kargs[] = {&args};
@@ -945,7 +977,7 @@ static kz_status build_loop_graph(kz_graph g, int64_t max_sweeps, bool half) {
   g->loop_exec = exec;
   g->loop_grid = grid;
   g->loop_max_sweeps = max_sweeps;
-  g->loop_half = half;
+  g->loop_form = form;
   return KZ_OK;
 }
 
@@ -958,8 +990,11 @@ static kz_status request_full_write(kz_graph g, cudaStream_t s) {
 
 kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
   int64_t max_sweeps = opt.max_sweeps > 0 ? opt.max_sweeps : (int64_t)g->n + g->m + 1;
-  const bool half = opt.plane0 == KZ_PLANE0_AUTO ? g->half_plane0 : opt.plane0 == KZ_PLANE0_HALF;
-  if (g->n > 0) KZ_TRY(ensure_plan(g, half, s));
+  int form = g->form;
+  if (opt.plane0 == KZ_PLANE0_FULL) form = kFormFull;
+  if (opt.plane0 == KZ_PLANE0_HALF) form = kFormHalf;
+  if (opt.plane0 == KZ_PLANE0_TWO) form = g->R >= 2 && g->k <= 32 ? kFormTwo : kFormFull;
+  if (g->n > 0) KZ_TRY(ensure_plan(g, form, s));
   if (!g->ab_synced) {
     KZ_TRY(request_full_write(g, s));
     g->ab_synced = true;
@@ -969,23 +1004,23 @@ kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
     begin_run_kernel<<<1, 1, 0, s>>>(g->st, max_sweeps, 0);
     KZ_CUDA_TRY(cudaGetLastError());
     int kmax = 0;
-    SweepFn fn = pick_persistent(g->k, half, kmax);
+    SweepFn fn = pick_persistent(g->k, form, kmax);
     if (!fn) return KZ_ERR_ARG;
     int grid = 0;
     size_t smem = 0;
-    KZ_TRY(launch_config(g, fn, kmax, half, grid, smem));
-    SweepArgs args = make_args(g, half);
+    KZ_TRY(launch_config(g, fn, kmax, form, grid, smem));
+    SweepArgs args = make_args(g, form);
     void *kargs[] = {&args};
     KZ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(kSweepWarps * 32), kargs, smem, s));
     return KZ_OK;
   }
   if (g->n > 0 && opt.use_graph == 2) {
     // one graph launch: run-start kernel, then the while node of sweep passes
-    if (g->loop_exec && (g->loop_max_sweeps != max_sweeps || g->loop_half != half)) {
+    if (g->loop_exec && (g->loop_max_sweeps != max_sweeps || g->loop_form != form)) {
       cudaGraphExecDestroy(g->loop_exec);
       g->loop_exec = nullptr;
     }
-    if (!g->loop_exec) KZ_TRY(build_loop_graph(g, max_sweeps, half));
+    if (!g->loop_exec) KZ_TRY(build_loop_graph(g, max_sweeps, form));
     KZ_CUDA_TRY(cudaGraphLaunch(g->loop_exec, s));
     return KZ_OK;
   }
@@ -997,12 +1032,12 @@ kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
   }
   // host-driven loop: one launch per pass, the host reads the continue flag
   int kmax = 0;
-  SweepFn fn = pick_sweep(g->k, half, kmax);
+  SweepFn fn = pick_sweep(g->k, form, kmax);
   if (!fn) return KZ_ERR_ARG;
   int grid = 0;
   size_t smem = 0;
-  KZ_TRY(launch_config(g, fn, kmax, half, grid, smem));
-  SweepArgs args = make_args(g, half);
+  KZ_TRY(launch_config(g, fn, kmax, form, grid, smem));
+  SweepArgs args = make_args(g, form);
   for (;;) {
     fn<<<grid, kSweepWarps * 32, smem, s>>>(args);
     KZ_CUDA_TRY(cudaGetLastError());
@@ -1026,12 +1061,12 @@ kz_status bitset_one_pass(kz_graph g, cudaStream_t s, int *cont) {
   KZ_TRY(request_full_write(g, s));
   g->ab_synced = false;
   int kmax = 0;
-  SweepFn fn = pick_sweep(g->k, g->half_plane0, kmax);
+  SweepFn fn = pick_sweep(g->k, g->form, kmax);
   if (!fn) return KZ_ERR_ARG;
   int grid = 0;
   size_t smem = 0;
-  KZ_TRY(launch_config(g, fn, kmax, g->half_plane0, grid, smem));
-  SweepArgs args = make_args(g, g->half_plane0);
+  KZ_TRY(launch_config(g, fn, kmax, g->form, grid, smem));
+  SweepArgs args = make_args(g, g->form);
   fn<<<grid, kSweepWarps * 32, smem, s>>>(args);
   KZ_CUDA_TRY(cudaGetLastError());
   int32_t c = 0;
@@ -1049,12 +1084,12 @@ kz_status bitset_barrier_timeout_probe(kz_graph g, uint32_t spin_limit, cudaStre
   begin_run_kernel<<<1, 1, 0, s>>>(g->st, (int64_t)g->n + g->m + 1, 0);
   KZ_CUDA_TRY(cudaGetLastError());
   int kmax = 0;
-  SweepFn fn = pick_persistent(g->k, g->half_plane0, kmax);
+  SweepFn fn = pick_persistent(g->k, g->form, kmax);
   if (!fn) return KZ_ERR_ARG;
   int grid = 0;
   size_t smem = 0;
-  KZ_TRY(launch_config(g, fn, kmax, g->half_plane0, grid, smem));
-  SweepArgs args = make_args(g, g->half_plane0);
+  KZ_TRY(launch_config(g, fn, kmax, g->form, grid, smem));
+  SweepArgs args = make_args(g, g->form);
   args.bar_extra = 1;
   args.spin_limit = spin_limit;
   void *kargs[] = {&args};

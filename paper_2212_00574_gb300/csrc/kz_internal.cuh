@@ -172,15 +172,15 @@ struct kz_graph_s {
   int32_t *d_zero = nullptr;         // a device 0 (queue order of a single graph)
   int32_t *d_perm = nullptr;   // n
   kz::BlockDesc *d_blocks = nullptr;
-  kz::SweepPlan plan[2];              // work of the sweep kernels: [0] full-word, [1] half-word test
+  kz::SweepPlan plan[3];              // work of the sweep kernels per form (full, half-word, two-plane)
   uint8_t *d_changed = nullptr;       // per unit: low byte of the sweep that last changed it
   int64_t n_units = 0;
   // true when the two row buffers differ only in the words of units whose
   // change tag names the current sweep (false after any other path or a
   // conversion wrote the rows; the next bitset pass then writes every word)
   bool ab_synced = false;
-  bool half_plane0 = false;           // sweep kernels use the half-word plane-0 test
-  bool fast_half = false;             // ... and fold whole blocks first (very dense graphs)
+  int32_t form = 0;                   // the sweep kernels' first test chosen by density
+  bool fast_half = false;             // half-word form: fold whole blocks first (very dense graphs)
   kz::DevState *st = nullptr;
 
   // which representation holds the live state: KZ_PATH_BITSET (bitset rows,
@@ -218,7 +218,7 @@ struct kz_graph_s {
   cudaGraphExec_t loop_exec = nullptr;
   int loop_grid = 0;
   int64_t loop_max_sweeps = 0;
-  bool loop_half = false;
+  int32_t loop_form = 0;
 
   // every device allocation, for kz_free_graph
   struct Alloc { void *p; size_t bytes; };

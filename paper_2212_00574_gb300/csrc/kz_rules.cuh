@@ -362,6 +362,63 @@ __device__ __forceinline__ uint32_t half_unsettled(const uint32_t (&F)[KH], cons
   return open & adjw;
 }
 
+// ---------------------------------------------------------------------------
+// Two-plane form, for sparser graphs: the first test looks at the first 64
+// members of each class (planes 0 and 1), so far fewer pairs go to the
+// recount.  A staged row holds plane 0 in words [0, KMAX) and plane 1 in
+// words [KMAX, 2 KMAX).
+// ---------------------------------------------------------------------------
+
+// Plane 1 of a row into registers (k words from row + k; zero when the lane
+// has no vertex).  Plane 1 need not start on 16 bytes: scalar loads.
+template <int KMAX>
+__device__ __forceinline__ void load_plane1(uint32_t (&F1)[KMAX], const uint32_t *row, int k, bool valid) {
+#pragma unroll
+  for (int c = 0; c < KMAX; c++) F1[c] = (valid && c < k) ? row[k + c] : 0u;
+}
+
+// Staged rows hold the first round_up(2k, 4) words of each row at their own
+// offsets; lane b moves plane 1 of row b from word k to word KMAX.
+template <int KMAX>
+__device__ __forceinline__ void spread_plane1(uint32_t *buf, int rows, int k, int lane) {
+  if (k == KMAX || lane >= rows) return;
+  uint32_t *row = buf + lane * 2 * KMAX;
+  uint32_t t[KMAX];
+#pragma unroll
+  for (int c = 0; c < KMAX; c++) t[c] = c < k ? row[k + c] : 0u;
+#pragma unroll
+  for (int q = 0; q < KMAX / 4; q++)
+    reinterpret_cast<uint4 *>(row + KMAX)[q] = make_uint4(t[4 * q], t[4 * q + 1], t[4 * q + 2], t[4 * q + 3]);
+}
+
+// Hot loop of the two-plane form (see plane0_unsettled): per class
+// (F0 & w0) | (F1 & w1) | P, two LOP3s.  Returns the lane's live edges that
+// the first 64 members of each class do not settle.
+template <int KMAX>
+__device__ __forceinline__ uint32_t two_unsettled(const uint32_t (&F0)[KMAX], const uint32_t (&F1)[KMAX],
+                                                  const uint32_t (&P)[KMAX], const uint32_t *sv, uint32_t adjw,
+                                                  int k) {
+  uint32_t bits = __reduce_or_sync(0xffffffffu, adjw);
+  uint32_t open = 0;
+  while (bits) {
+    const int b0 = __ffs(bits) - 1;
+    bits &= bits - 1;
+    const uint4 *f0 = reinterpret_cast<const uint4 *>(sv + b0 * 2 * KMAX);
+    uint32_t m0 = 0xffffffffu, m1 = 0xffffffffu;
+#pragma unroll
+    for (int q = 0; q < KMAX / 4; q++) {
+      if (4 * q >= k) break;  // see plane0_unsettled
+      const uint4 a = f0[q], b = f0[KMAX / 4 + q];
+      m0 = kz_min3(m0, (F0[4 * q + 0] & a.x) | (F1[4 * q + 0] & b.x) | P[4 * q + 0],
+                   (F0[4 * q + 1] & a.y) | (F1[4 * q + 1] & b.y) | P[4 * q + 1]);
+      m1 = kz_min3(m1, (F0[4 * q + 2] & a.z) | (F1[4 * q + 2] & b.z) | P[4 * q + 2],
+                   (F0[4 * q + 3] & a.w) | (F1[4 * q + 3] & b.w) | P[4 * q + 3]);
+    }
+    if (min(m0, m1) == 0u) open |= 1u << b0;
+  }
+  return open & adjw;
+}
+
 // Recount, lane by lane, the edges plane 0 left open: the classes plane 0
 // leaves uncovered (from the row of u and the staged row of v) are searched
 // in their later planes.  Returns the lane's deletion mask.  Takes pointers

@@ -53,6 +53,22 @@ __device__ __forceinline__ void stage_block(const uint32_t *__restrict__ A, int 
   }
 }
 
+// Stage planes 0 and 1 of the member rows of block Y: the first
+// round_up(2k, 4) words of each row at their own offsets, rows 2 KMAX words
+// apart (the rows hold at least two planes).
+template <int KMAX>
+__device__ __forceinline__ void stage_block2(const uint32_t *__restrict__ A, int ldw, const BlockDesc &Y, int kq8,
+                                             uint32_t *buf, int lane) {
+  constexpr int C = KMAX / 2;   // 16-byte chunks per staged row
+  constexpr int RPI = 32 / C;   // rows per round of the warp
+  const int rr = lane / C, q = lane - rr * C;
+  if (rr < RPI && q < kq8) {
+    const uint32_t *src = A + (int64_t)Y.base * ldw + 4 * q;
+    uint32_t *dst = buf + 4 * q;
+    for (int b = rr; b < Y.size; b += RPI) cp_async16(dst + b * 2 * KMAX, src + (int64_t)b * ldw);
+  }
+}
+
 struct PassCounters {
   unsigned long long tests = 0, de = 0, dv = 0;
 };

@@ -478,7 +478,7 @@ def _two_density_graph(seed, n, k, n_dense, p_dense, p_sparse):
     return synth.Graph(n=n, k=k, colour=colour, edges=synth.canonical_edges(edges), name="two-density")
 
 
-@pytest.mark.parametrize("loop,plane0", [(0, 0), (1, 0), (1, 1), (2, 2)])
+@pytest.mark.parametrize("loop,plane0", [(0, 0), (1, 0), (1, 1), (2, 2), (1, 3), (2, 3)])
 def test_half_word_plane0_with_recounts(loop, plane0):
     """Densities 0.65 to 0.95: the half-word test with and without the
     whole-block fold, blocks that fall back to per-pair results."""
@@ -491,10 +491,12 @@ def test_half_word_plane0_with_recounts(loop, plane0):
         assert_parity(g, gpu_run(g, path="bitset", use_graph=loop, plane0=plane0))
 
 
-@pytest.mark.parametrize("plane0", [1, 2])
+@pytest.mark.parametrize("plane0", [1, 2, 3])
 def test_forced_plane0_forms(plane0):
-    """Either first test on graphs of any density, sparse ones included (the
-    half-word form then sends most pairs to the recount)."""
-    for (n, k, p, seed) in ((3000, 10, 0.1, 5), (600, 7, 0.5, 6), (400, 33, 0.9, 7), (1000, 64, 0.97, 8)):
+    """Every first test on graphs of any density, sparse ones included (the
+    half-word form then sends most pairs to the recount; the two-plane form
+    falls back to full words where a class has one block or k > 32)."""
+    for (n, k, p, seed) in ((3000, 10, 0.1, 5), (600, 7, 0.5, 6), (400, 33, 0.9, 7), (1000, 64, 0.97, 8),
+                            (1100, 29, 0.35, 9), (1500, 6, 0.3, 10)):
         g = synth.tiny_random(seed, n, k, p, planted=True)
         assert_parity(g, gpu_run(g, path="bitset", plane0=plane0))
