@@ -87,60 +87,36 @@ kz_status bitset_build_layout(kz_graph g) {
 
 // Work of the sweep kernels: the units of a pass in order (x ascending; for
 // each x the blocks y of higher classes, or one vertex-only unit y = nb for a
-// block of the last class).  The units holding the first `static_share` of
-// the estimated cost are cut into `warps` consecutive ranges of about equal
-// cost; the rest form the tail, which warps take one unit at a time once
-// their range is done.  A unit costs the members of Y it tests plus a fixed
-// part for staging and bookkeeping; the first unit of each x also evaluates
-// the vertex rule.  The estimate is good for dense graphs (the half-word
-// form: everything static); sparser graphs spend unpredictable time in
-// recounts, so a quarter of their work is left to the tail.
-constexpr double kStaticShareHalf = 1.0;
-constexpr double kStaticShareFull = 0.75;
-
-static void build_ranges(kz_graph g, int warps, double static_share, std::vector<WarpRange> &out,
-                         std::vector<int2> &tail, int64_t &n_units, int64_t &tail_begin) {
+// block of the last class), listed as (x, y) pairs and cut into `ctas`
+// consecutive ranges of about equal estimated cost.  A CTA owns one range and
+// its warps take the range's units one at a time, so every warp of the CTA
+// stays busy until the CTA's share is done.  A unit costs the members of Y it
+// tests plus a fixed part for staging and bookkeeping; the first unit of each
+// x also evaluates the vertex rule.
+static void build_units(kz_graph g, int ctas, std::vector<int2> &units, std::vector<int32_t> &cta_begin) {
   constexpr int64_t kUnitFixed = 8, kVertexCost = 8;
   const int nb = (int)g->blocks.size();
   auto ybegin = [&](int x) { return std::min(g->boff[g->blocks[x].c + 1], nb); };
-  auto cost = [&](int y, bool first) {
-    return (y < nb ? g->blocks[y].size : 0) + kUnitFixed + (first ? kVertexCost : 0);
-  };
+  units.clear();
+  std::vector<int64_t> acc;  // running cost after each unit
   int64_t total = 0;
-  n_units = 0;
   for (int x = 0; x < nb; x++) {
     const int yb = ybegin(x);
     const int y_end = yb >= nb ? nb + 1 : nb;
-    for (int y = yb; y < y_end; y++, n_units++) total += cost(y, y == yb);
-  }
-  const int64_t share = static_share >= 1.0 ? total : (int64_t)(static_share * (double)total);
-  out.assign((size_t)warps, WarpRange{nb, nb, 0, 0});
-  tail.clear();
-  tail_begin = n_units;
-  int w = 0;
-  int64_t acc = 0, unit = 0;
-  WarpRange cur{0, 0, 0, 0};
-  for (int x = 0; x < nb; x++) {
-    const int yb = ybegin(x);
-    const int y_end = yb >= nb ? nb + 1 : nb;
-    for (int y = yb; y < y_end; y++, unit++) {
-      if (acc >= share && share < total) {  // tail
-        if (tail.empty()) tail_begin = unit;
-        tail.push_back(make_int2(x, y));
-        continue;
-      }
-      acc += cost(y, y == yb);
-      if (cur.count == 0) cur = WarpRange{x, y, (int32_t)unit, 0};
-      cur.count++;
-      // close this warp's range once the running cost reaches its share
-      if (w < warps - 1 && acc * warps >= (int64_t)(w + 1) * share) {
-        out[(size_t)w++] = cur;
-        cur.count = 0;
-        while (w < warps - 1 && acc * warps >= (int64_t)(w + 1) * share) w++;  // empty ranges
-      }
+    for (int y = yb; y < y_end; y++) {
+      total += (y < nb ? g->blocks[y].size : 0) + kUnitFixed + (y == yb ? kVertexCost : 0);
+      units.push_back(make_int2(x, y));
+      acc.push_back(total);
     }
   }
-  if (cur.count) out[(size_t)w] = cur;
+  // CTA c takes the units whose running cost ends in (c, c + 1] * total / ctas
+  cta_begin.assign((size_t)ctas + 1, (int32_t)units.size());
+  cta_begin[0] = 0;
+  size_t u = 0;
+  for (int c = 1; c < ctas; c++) {
+    while (u < units.size() && acc[u] * ctas <= (int64_t)c * total) u++;
+    cta_begin[(size_t)c] = (int32_t)u;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -244,7 +220,8 @@ __global__ void init_vlive_kernel(uint32_t *V, const BlockDesc *blocks, int nb, 
 
 struct SweepArgs {
   const BlockDesc *blocks;
-  const WarpRange *ranges;  // one per warp of the grid
+  const int2 *units;        // (x, y) of every unit of a pass
+  const int32_t *cta_begin; // first unit of each CTA's range (grid + 1)
   int32_t nb;               // blocks
   int32_t k, ldw;
   const int32_t *rounds;  // blocks per class
@@ -254,9 +231,6 @@ struct SweepArgs {
   int32_t *v_sweep;       // relabelled ids, may be null
   uint8_t *changed;       // per unit: low byte of the sweep that last changed its words
   int32_t fast_half;      // half-word form: try the whole-block fold first (very dense graphs)
-  const int2 *tail;       // (x, y) of the tail units
-  int32_t tail_begin;     // unit number of the first tail unit
-  int32_t tail_count;
   DevState *st;
   cudaGraphConditionalHandle cond;
   int32_t use_cond;
@@ -264,7 +238,6 @@ struct SweepArgs {
   uint32_t spin_limit;   // polls before a barrier wait gives up
 };
 
-constexpr int kSweepWarps = 4;
 // First test of a pair in the sweep kernels (the FORM template argument).
 constexpr int kFormFull = 0;  // plane 0: the first 32 members of each class, one word per class
 constexpr int kFormHalf = 1;  // the first 16 members, two classes per word (dense graphs)
@@ -279,13 +252,14 @@ constexpr double kTwoPlaneDensity = 0.42;
 // (almost every 32 x 32 block then has every pair covered); below it the
 // half-word form (when forced) tests pair by pair
 constexpr double kFastHalfDensity = 0.8;
-// resident CTAs per SM the compiler is asked to fit (4-warp CTAs): five for
-// the half-word form up to k = 24, three for the two-plane form from k = 25,
-// four otherwise up to k = 32
-template <int KMAX, int FORM>
-constexpr int kMinCtas = FORM == kFormHalf ? (KMAX <= 24 ? 5 : (KMAX <= 32 ? 4 : 1))
-                         : FORM == kFormTwo ? (KMAX <= 24 ? 4 : (KMAX <= 32 ? 3 : 1))
-                                            : (KMAX <= 32 ? 4 : 1);
+// Warps of a sweep CTA (one CTA per SM): as many as the registers of the
+// form allow -- 20 for the half-word form up to k = 24 (96 registers), 16 at
+// up to 128 registers, 8 for the widest kernels.
+__host__ __device__ constexpr int cta_warps(int kmax, int form) {
+  return form == kFormHalf ? (kmax <= 24 ? 20 : (kmax <= 32 ? 16 : 8))
+         : form == kFormTwo ? (kmax <= 24 ? 16 : 8)
+                            : (kmax <= 32 ? 16 : 8);
+}
 // Shared memory of one warp: two staging buffers of plane-0 rows (KMAX words
 // each) and, in the half-word form, the converted rows of the current unit.
 template <int KMAX, int FORM>
@@ -297,16 +271,16 @@ __device__ __forceinline__ void prefetch_l1(const uint32_t *p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
-// One warp's share of one Jacobi pass: its static range of units, then tail
-// units taken one at a time from the pass's shared counter until none is
-// left, so the warps of the grid end their pass within about one unit of
-// each other.  `cur` is the current ping-pong buffer, `sweep_no` the
-// productive sweeps so far, `full` asks for every owned word to be written.
-// FORM selects the first test of a pair (kFormFull, kFormHalf, kFormTwo).
+// One warp's share of one Jacobi pass: units taken one at a time from its
+// CTA's range [u_begin, u_end) through the shared counter *s_next, so the
+// CTA's warps stay busy until its whole range is done.  `cur` is the current
+// ping-pong buffer, `sweep_no` the productive sweeps so far, `full` asks for
+// every owned word to be written.  FORM selects the first test of a pair
+// (kFormFull, kFormHalf, kFormTwo).
 template <int KMAX, int FORM>
-__device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange r, int cur, int64_t sweep_no,
-                                            bool full, uint32_t *buf0, uint32_t *buf1, uint32_t *bufh,
-                                            const int32_t *rounds, PassCounters &pc) {
+__device__ __forceinline__ void sweep_cta(const SweepArgs &p, int u_begin, int u_end, unsigned int *s_next,
+                                          int cur, int64_t sweep_no, bool full, uint32_t *buf0, uint32_t *buf1,
+                                          uint32_t *bufh, const int32_t *rounds, PassCounters &pc) {
   const int lane = threadIdx.x & 31;
   const uint32_t *__restrict__ A = cur ? p.A1 : p.A0;
   uint32_t *__restrict__ An = cur ? p.A0 : p.A1;
@@ -318,33 +292,13 @@ __device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange 
   const int kq4 = TWO ? (2 * k + 3) >> 2 : (k + 3) >> 2;  // 16-byte chunks staged per row
   const uint8_t tag_now = (uint8_t)(sweep_no & 0xff);
   const uint8_t tag_next = (uint8_t)((sweep_no + 1) & 0xff);
-  unsigned int *tail_ctr = &p.st->tail_next;
 
   // cursor (x, y, unit): the next unit to stage.  Its adjacency word, change
-  // tag and live word are loaded one unit ahead; a tail ticket is requested
-  // one unit before it is needed (lane 0 holds it until then).
-  int x = 0, y = 0, unit = 0, left = r.count;
-  unsigned int ticket = 0;
-  bool have = false;
-  if (left > 0) {
-    x = r.x;
-    y = r.y;
-    unit = r.unit;
-    left--;
-    have = true;
-    if (left == 0 && p.tail_count && lane == 0) ticket = atomicAdd(tail_ctr, 1u);
-  } else if (p.tail_count) {
-    const unsigned int t = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(tail_ctr, 1u) : 0u, 0);
-    if (t < (unsigned int)p.tail_count) {
-      const int2 e = p.tail[t];
-      x = e.x;
-      y = e.y;
-      unit = p.tail_begin + (int)t;
-      have = true;
-      if (lane == 0) ticket = atomicAdd(tail_ctr, 1u);
-    }
-  }
-  if (!have) return;
+  // tag and live word are loaded one unit ahead.
+  int unit = u_begin + (int)__shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(s_next, 1u) : 0u, 0);
+  if (unit >= u_end) return;
+  int2 e = p.units[unit];
+  int x = e.x, y = e.y;
   BlockDesc X = p.blocks[x];
   int ybeg = min(p.boff[X.c + 1], nb);
   BlockDesc Y = X;
@@ -371,35 +325,16 @@ __device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange 
     const uint32_t adjw = adj_n, vword = vw_n;
     const uint8_t chg = chg_n;
     uint32_t *sv = (i & 1) ? buf1 : buf0;
-    // advance the cursor and stage the next unit
-    bool more = false, next_block = false;
-    if (left > 0) {
-      if (y + 1 < nb) {
-        y++;
-      } else {
-        x++;  // first unit of the next block: y is its first higher-class block
-        next_block = true;
-      }
-      unit++;
-      left--;
-      more = true;
-      if (left == 0 && p.tail_count && lane == 0) ticket = atomicAdd(tail_ctr, 1u);
-    } else if (p.tail_count) {
-      const unsigned int t = __shfl_sync(0xffffffffu, ticket, 0);
-      if (t < (unsigned int)p.tail_count) {
-        const int2 e = p.tail[t];
-        x = e.x;
-        y = e.y;
-        unit = p.tail_begin + (int)t;
-        more = true;
-        if (lane == 0) ticket = atomicAdd(tail_ctr, 1u);
-      }
-    }
+    // take the next unit and stage it
+    unit = u_begin + (int)__shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(s_next, 1u) : 0u, 0);
+    const bool more = unit < u_end;
     if (more) {
+      e = p.units[unit];
+      x = e.x;
+      y = e.y;
       if (x != xc) {
         X = p.blocks[x];
         ybeg = min(p.boff[X.c + 1], nb);
-        if (next_block) y = ybeg;
         if (lane < X.size) {  // warm L1 with plane 0 of the next block's rows
           const uint32_t *row = A + (int64_t)(X.base + lane) * ldw;
           prefetch_l1(row);
@@ -500,8 +435,9 @@ __device__ __forceinline__ void sweep_range(const SweepArgs &p, const WarpRange 
 // The CTA's pass counters, summed over its warps and added to the graph's
 // running pass totals with one atomic per counter (thread 0).  Ends with the
 // CTA synchronised.
+template <int WARPS>
 __device__ __forceinline__ void add_cta_counters(PassCounters pc, DevState *st) {
-  __shared__ unsigned long long s_pc[kSweepWarps][3];
+  __shared__ unsigned long long s_pc[WARPS][3];
   for (int o = 16; o > 0; o >>= 1) {
     pc.tests += __shfl_down_sync(0xffffffffu, pc.tests, o);
     pc.de += __shfl_down_sync(0xffffffffu, pc.de, o);
@@ -516,7 +452,7 @@ __device__ __forceinline__ void add_cta_counters(PassCounters pc, DevState *st) 
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t = 0, de = 0, dv = 0;
-    for (int w = 0; w < kSweepWarps; w++) {
+    for (int w = 0; w < WARPS; w++) {
       t += s_pc[w][0];
       de += s_pc[w][1];
       dv += s_pc[w][2];
@@ -529,9 +465,11 @@ __device__ __forceinline__ void add_cta_counters(PassCounters pc, DevState *st) 
 
 // One Jacobi pass per launch (the CUDA-graph loop and the host-driven loop).
 template <int KMAX, int FORM>
-__global__ void __launch_bounds__(kSweepWarps * 32, kMinCtas<KMAX, FORM>)
+__global__ void __launch_bounds__(cta_warps(KMAX, FORM) * 32, 1)
     bitset_sweep_kernel(SweepArgs p) {
+  constexpr int W = cta_warps(KMAX, FORM);
   extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ unsigned int s_next;
   const int wib = threadIdx.x >> 5;
   constexpr int kRow = FORM == kFormTwo ? 2 * KMAX : KMAX;  // staged row stride
   uint32_t *buf0 = smem + wib * warp_smem_words<KMAX, FORM>();
@@ -539,14 +477,16 @@ __global__ void __launch_bounds__(kSweepWarps * 32, kMinCtas<KMAX, FORM>)
   uint32_t *bufh = buf1 + 32 * kRow;  // half-word rows (half-word form only)
   __shared__ int32_t s_rounds[KMAX];
   for (int c = threadIdx.x; c < p.k; c += blockDim.x) s_rounds[c] = p.rounds[c];
+  if (threadIdx.x == 0) s_next = 0;
   __syncthreads();
   DevState *st = p.st;
   const int cur = *((volatile int32_t *)&st->cur);
   const int64_t sweep_no = *((volatile int64_t *)&st->sweeps);
   const bool full = *((volatile int32_t *)&st->full_write) != 0;
   PassCounters pc;
-  sweep_range<KMAX, FORM>(p, p.ranges[blockIdx.x * kSweepWarps + wib], cur, sweep_no, full, buf0, buf1, bufh, s_rounds, pc);
-  add_cta_counters(pc, st);
+  sweep_cta<KMAX, FORM>(p, p.cta_begin[blockIdx.x], p.cta_begin[blockIdx.x + 1], &s_next, cur, sweep_no, full, buf0,
+                        buf1, bufh, s_rounds, pc);
+  add_cta_counters<W>(pc, st);
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned int t = atomicAdd(&st->ticket, 1u);
@@ -574,10 +514,12 @@ constexpr uint32_t kBarrierSpinLimit = 1u << 25;
 // barrier wait is bounded: one that runs out records KZ_ERR_TIMEOUT and all
 // CTAs leave.
 template <int KMAX, int FORM>
-__global__ void __launch_bounds__(kSweepWarps * 32, kMinCtas<KMAX, FORM>)
+__global__ void __launch_bounds__(cta_warps(KMAX, FORM) * 32, 1)
     bitset_persistent_kernel(SweepArgs p) {
+  constexpr int W = cta_warps(KMAX, FORM);
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long s_word;
+  __shared__ unsigned int s_next;
   const int wib = threadIdx.x >> 5;
   constexpr int kRow = FORM == kFormTwo ? 2 * KMAX : KMAX;  // staged row stride
   uint32_t *buf0 = smem + wib * warp_smem_words<KMAX, FORM>();
@@ -592,11 +534,13 @@ __global__ void __launch_bounds__(kSweepWarps * 32, kMinCtas<KMAX, FORM>)
   int cur = *((volatile int32_t *)&st->cur);
   int64_t sweep_no = *((volatile int64_t *)&st->sweeps);
   bool full = *((volatile int32_t *)&st->full_write) != 0;
+  const int u_begin = p.cta_begin[blockIdx.x], u_end = p.cta_begin[blockIdx.x + 1];
   for (;;) {
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
     PassCounters pc;
-    sweep_range<KMAX, FORM>(p, p.ranges[blockIdx.x * kSweepWarps + wib], cur, sweep_no, full, buf0, buf1, bufh,
-                            s_rounds, pc);
-    add_cta_counters(pc, st);
+    sweep_cta<KMAX, FORM>(p, u_begin, u_end, &s_next, cur, sweep_no, full, buf0, buf1, bufh, s_rounds, pc);
+    add_cta_counters<W>(pc, st);
     if (threadIdx.x == 0) {
       __threadfence();
       const unsigned long long w0 = *((volatile unsigned long long *)&st->pass_word);
@@ -658,7 +602,6 @@ __global__ void begin_run_kernel(DevState *st, int64_t max_sweeps, int64_t passe
   st->max_sweeps = max_sweeps;
   st->pass_dv = st->pass_de = st->pass_tests = 0;
   st->ticket = 0;
-  st->tail_next = 0;
 }
 
 __global__ void reset_state_kernel(DevState *st) {
@@ -668,7 +611,6 @@ __global__ void reset_state_kernel(DevState *st) {
   st->sweeps = st->passes = st->tests = 0;
   st->pass_dv = st->pass_de = st->pass_tests = 0;
   st->ticket = 0;
-  st->tail_next = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -808,7 +750,7 @@ static kz_status kernel_fit(SweepFn fn, int kmax, int form, size_t &smem, int &p
   const int half_stride_words = (kmax / 2 + 3) / 4 * 4;
   const size_t warp_words = form == kFormTwo ? 2 * 32 * 2 * (size_t)kmax
                                               : 2 * 32 * (size_t)kmax + (form == kFormHalf ? 32 * half_stride_words : 0);
-  smem = (size_t)kSweepWarps * 4 * warp_words;
+  smem = (size_t)cta_warps(kmax, form) * 4 * warp_words;
   int dev = 0;
   KZ_CUDA_TRY(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lk(mu);
@@ -822,14 +764,14 @@ static kz_status kernel_fit(SweepFn fn, int kmax, int form, size_t &smem, int &p
   KZ_CUDA_TRY(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   per_sm = 0;
   KZ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn,
-                                                            kSweepWarps * 32, smem));
+                                                            cta_warps(kmax, form) * 32, smem));
   fitted[key] = per_sm;
   return KZ_OK;
 }
 
-// The grid of both sweep kernels of one form: every CTA resident at once
-// (the persistent kernel's grid barrier needs that), and no more warps than
-// units.
+// The grid of both sweep kernels of one form: one CTA per SM (every CTA
+// resident at once, as the persistent kernel's grid barrier needs), and no
+// more warps than units.
 static kz_status sweep_grid_size(kz_graph g, int form, int &grid) {
   int kmax = 0, kmax2 = 0, per_a = 0, per_b = 0;
   size_t smem = 0;
@@ -837,40 +779,42 @@ static kz_status sweep_grid_size(kz_graph g, int form, int &grid) {
   if (!fa || !fb) return KZ_ERR_ARG;
   KZ_TRY(kernel_fit(fa, kmax, form, smem, per_a));
   KZ_TRY(kernel_fit(fb, kmax2, form, smem, per_b));
-  const int per_sm = std::max(1, std::min(per_a, per_b));
-  const int64_t want = (std::max<int64_t>(g->n_units, 1) + kSweepWarps - 1) / kSweepWarps;
-  grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)per_sm * sm_count()));
+  if (std::min(per_a, per_b) < 1) return KZ_ERR_UNSUPPORTED;
+  const int w = cta_warps(kmax, form);
+  const int64_t want = (std::max<int64_t>(g->n_units, 1) + w - 1) / w;
+  grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count()));
   return KZ_OK;
 }
 
-// Builds the grid, static ranges and tail of one form, once per graph.
+// Builds the grid and the CTAs' unit ranges of one form, once per graph (the
+// unit list itself is shared by the forms).
 static kz_status ensure_plan(kz_graph g, int form, cudaStream_t s) {
   SweepPlan &pl = g->plan[form];
   if (pl.grid > 0) return KZ_OK;
   int grid = 0;
   KZ_TRY(sweep_grid_size(g, form, grid));
-  std::vector<WarpRange> ranges;
-  std::vector<int2> tail;
-  int64_t units = 0, tail_begin = 0;
-  build_ranges(g, grid * kSweepWarps, form == kFormHalf ? kStaticShareHalf : kStaticShareFull, ranges, tail, units,
-               tail_begin);
-  if (units != g->n_units) return KZ_ERR_INTERNAL;
-  KZ_TRY(graph_alloc(g, &pl.d_ranges, ranges.size(), s));
-  KZ_CUDA_TRY(cudaMemcpyAsync(pl.d_ranges, ranges.data(), sizeof(WarpRange) * ranges.size(),
+  std::vector<int2> units;
+  std::vector<int32_t> cta_begin;
+  build_units(g, grid, units, cta_begin);
+  if ((int64_t)units.size() != g->n_units) return KZ_ERR_INTERNAL;
+  if (!g->d_units) {
+    KZ_TRY(graph_alloc(g, &g->d_units, std::max<size_t>(units.size(), 1), s));
+    if (!units.empty())
+      KZ_CUDA_TRY(cudaMemcpyAsync(g->d_units, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice, s));
+  }
+  KZ_TRY(graph_alloc(g, &pl.d_cta_begin, cta_begin.size(), s));
+  KZ_CUDA_TRY(cudaMemcpyAsync(pl.d_cta_begin, cta_begin.data(), sizeof(int32_t) * cta_begin.size(),
                               cudaMemcpyHostToDevice, s));
-  KZ_TRY(graph_alloc(g, &pl.d_tail, std::max<size_t>(tail.size(), 1), s));
-  if (!tail.empty())
-    KZ_CUDA_TRY(cudaMemcpyAsync(pl.d_tail, tail.data(), sizeof(int2) * tail.size(), cudaMemcpyHostToDevice, s));
-  pl.tail_begin = (int32_t)tail_begin;
-  pl.tail_count = (int32_t)tail.size();
   pl.grid = grid;
   return KZ_OK;
 }
 
-static kz_status launch_config(kz_graph g, SweepFn fn, int kmax, int form, int &grid, size_t &smem) {
+static kz_status launch_config(kz_graph g, SweepFn fn, int kmax, int form, int &grid, size_t &smem,
+                               int &threads) {
   int per_sm = 0;
   KZ_TRY(kernel_fit(fn, kmax, form, smem, per_sm));
   grid = g->plan[form].grid;
+  threads = cta_warps(kmax, form) * 32;
   if (grid <= 0 || grid > std::max(per_sm, 1) * sm_count()) return KZ_ERR_INTERNAL;
   return KZ_OK;
 }
@@ -879,7 +823,8 @@ static SweepArgs make_args(kz_graph g, int form) {
   const SweepPlan &pl = g->plan[form];
   SweepArgs a;
   a.blocks = g->d_blocks;
-  a.ranges = pl.d_ranges;
+  a.units = g->d_units;
+  a.cta_begin = pl.d_cta_begin;
   a.nb = (int32_t)g->blocks.size();
   a.k = g->k;
   a.ldw = g->ldw;
@@ -887,9 +832,6 @@ static SweepArgs make_args(kz_graph g, int form) {
   a.boff = g->d_boff;
   a.changed = g->d_changed;
   a.fast_half = g->fast_half ? 1 : 0;
-  a.tail = pl.d_tail;
-  a.tail_begin = pl.tail_begin;
-  a.tail_count = pl.tail_count;
   a.A0 = g->A[0];
   a.A1 = g->A[1];
   a.V0 = g->V[0];
@@ -909,9 +851,9 @@ static kz_status build_loop_graph(kz_graph g, int64_t max_sweeps, int form) {
   int kmax = 0;
   SweepFn fn = pick_sweep(g->k, form, kmax);
   if (!fn) return KZ_ERR_ARG;
-  int grid = 0;
+  int grid = 0, threads = 0;
   size_t smem = 0;
-  KZ_TRY(launch_config(g, fn, kmax, form, grid, smem));
+  KZ_TRY(launch_config(g, fn, kmax, form, grid, smem, threads));
   cudaGraph_t graph = nullptr;
   KZ_CUDA_TRY(cudaGraphCreate(&graph, 0));
   cudaGraphConditionalHandle handle;
@@ -961,7 +903,7 @@ static kz_status build_loop_graph(kz_graph g, int64_t max_sweeps, int form) {
   memset((void *)&kp, 0, sizeof(kp));
   kp.func = (void *)fn;
   kp.gridDim = dim3(grid);
-  kp.blockDim = dim3(kSweepWarps * 32);
+  kp.blockDim = dim3(threads);
   kp.sharedMemBytes = (unsigned)smem;
   kp.kernelParams = kargs;
   cudaGraphNode_t knode;
@@ -1006,12 +948,12 @@ kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
     int kmax = 0;
     SweepFn fn = pick_persistent(g->k, form, kmax);
     if (!fn) return KZ_ERR_ARG;
-    int grid = 0;
+    int grid = 0, threads = 0;
     size_t smem = 0;
-    KZ_TRY(launch_config(g, fn, kmax, form, grid, smem));
+    KZ_TRY(launch_config(g, fn, kmax, form, grid, smem, threads));
     SweepArgs args = make_args(g, form);
     void *kargs[] = {&args};
-    KZ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(kSweepWarps * 32), kargs, smem, s));
+    KZ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(threads), kargs, smem, s));
     return KZ_OK;
   }
   if (g->n > 0 && opt.use_graph == 2) {
@@ -1034,12 +976,12 @@ kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
   int kmax = 0;
   SweepFn fn = pick_sweep(g->k, form, kmax);
   if (!fn) return KZ_ERR_ARG;
-  int grid = 0;
+  int grid = 0, threads = 0;
   size_t smem = 0;
-  KZ_TRY(launch_config(g, fn, kmax, form, grid, smem));
+  KZ_TRY(launch_config(g, fn, kmax, form, grid, smem, threads));
   SweepArgs args = make_args(g, form);
   for (;;) {
-    fn<<<grid, kSweepWarps * 32, smem, s>>>(args);
+    fn<<<grid, threads, smem, s>>>(args);
     KZ_CUDA_TRY(cudaGetLastError());
     int32_t cont = 0;
     KZ_CUDA_TRY(cudaMemcpyAsync(&cont, &g->st->cont, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -1063,11 +1005,11 @@ kz_status bitset_one_pass(kz_graph g, cudaStream_t s, int *cont) {
   int kmax = 0;
   SweepFn fn = pick_sweep(g->k, g->form, kmax);
   if (!fn) return KZ_ERR_ARG;
-  int grid = 0;
+  int grid = 0, threads = 0;
   size_t smem = 0;
-  KZ_TRY(launch_config(g, fn, kmax, g->form, grid, smem));
+  KZ_TRY(launch_config(g, fn, kmax, g->form, grid, smem, threads));
   SweepArgs args = make_args(g, g->form);
-  fn<<<grid, kSweepWarps * 32, smem, s>>>(args);
+  fn<<<grid, threads, smem, s>>>(args);
   KZ_CUDA_TRY(cudaGetLastError());
   int32_t c = 0;
   KZ_CUDA_TRY(cudaMemcpyAsync(&c, &g->st->cont, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -1086,14 +1028,14 @@ kz_status bitset_barrier_timeout_probe(kz_graph g, uint32_t spin_limit, cudaStre
   int kmax = 0;
   SweepFn fn = pick_persistent(g->k, g->form, kmax);
   if (!fn) return KZ_ERR_ARG;
-  int grid = 0;
+  int grid = 0, threads = 0;
   size_t smem = 0;
-  KZ_TRY(launch_config(g, fn, kmax, g->form, grid, smem));
+  KZ_TRY(launch_config(g, fn, kmax, g->form, grid, smem, threads));
   SweepArgs args = make_args(g, g->form);
   args.bar_extra = 1;
   args.spin_limit = spin_limit;
   void *kargs[] = {&args};
-  KZ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(kSweepWarps * 32), kargs, smem, s));
+  KZ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(threads), kargs, smem, s));
   return KZ_OK;
 }
 

@@ -49,19 +49,6 @@ struct WorkItem {
   int32_t vflag;
 };
 
-// A warp's share of one pass of the single-graph sweep kernels: `count`
-// consecutive units starting at unit number `unit` = (x, y).  Units run over
-// x in order, and for each x over the blocks y of higher classes (a block x
-// of the last class has one unit with y = number of blocks, which only
-// evaluates the vertex rule).  The host cuts the unit sequence into equal-cost
-// ranges, one per warp.
-struct WarpRange {
-  int32_t x;
-  int32_t y;
-  int32_t unit;
-  int32_t count;
-};
-
 // Device-resident loop state of one graph.  Written by the sweep kernels'
 // last warp; read by the host only after a synchronisation.
 struct DevState {
@@ -77,7 +64,7 @@ struct DevState {
   unsigned long long pass_de;
   unsigned long long pass_tests;
   unsigned int ticket;            // warps finished in the running pass
-  unsigned int tail_next;          // next tail unit of the running pass (sweep kernels)
+  unsigned int pad1;
   unsigned int bar_count;         // grid barrier of the persistent sweep kernel
   unsigned int bar_gen;
   int32_t bar_abort;              // a bounded barrier wait ran out
@@ -127,10 +114,8 @@ struct CtaGraph;
 // Grid and work split of the multi-CTA sweep kernels for one plane-0 form
 // (built when the form is first used).
 struct SweepPlan {
-  int32_t grid = 0;              // CTAs, all resident at once (0: not built)
-  WarpRange *d_ranges = nullptr; // one static range per warp
-  int2 *d_tail = nullptr;        // (x, y) of the tail units, taken one at a time
-  int32_t tail_begin = 0, tail_count = 0;
+  int32_t grid = 0;                 // CTAs, one per SM at most (0: not built)
+  int32_t *d_cta_begin = nullptr;   // first unit of each CTA's range, grid + 1
 };
 }  // namespace kz
 typedef kz::CtaGraph *CtaGraphPtr;
@@ -174,6 +159,7 @@ struct kz_graph_s {
   kz::BlockDesc *d_blocks = nullptr;
   kz::SweepPlan plan[3];              // work of the sweep kernels per form (full, half-word, two-plane)
   uint8_t *d_changed = nullptr;       // per unit: low byte of the sweep that last changed it
+  int2 *d_units = nullptr;            // (x, y) of every unit, in pass order
   int64_t n_units = 0;
   // true when the two row buffers differ only in the words of units whose
   // change tag names the current sweep (false after any other path or a

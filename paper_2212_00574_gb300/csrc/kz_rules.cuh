@@ -486,7 +486,6 @@ __device__ __forceinline__ int finish_pass(DevState *st, unsigned long long dv, 
   st->passes = passes + 1;
   st->tests = total + (int64_t)tests;
   st->full_write = 0;
-  st->tail_next = 0;
   if (limited) st->status = KZ_ERR_LIMIT;
   if (cont) {
     if (sweeps < kTraceCap) {
