@@ -103,6 +103,7 @@ void release(kz_graph g) {
   // the graph's last work must be finished before its memory is handed back
   cudaStreamSynchronize(s);
   if (g->loop_exec) cudaGraphExecDestroy(g->loop_exec);
+  if (g->run_exec) cudaGraphExecDestroy(g->run_exec);
   learned_release(g);
   tensor_release(g);
   for (auto &a : g->allocs) dev_free(a.p, a.bytes, s);

@@ -202,6 +202,11 @@ struct kz_graph_s {
 
   // executable CUDA graph of the device-side sweep loop (built lazily)
   cudaGraphExec_t loop_exec = nullptr;
+  // executable CUDA graph of one persistent run: run-start kernel, then the
+  // cooperative sweep kernel (built lazily; one launch per kz_kernelize)
+  cudaGraphExec_t run_exec = nullptr;
+  int64_t run_max_sweeps = 0;
+  int32_t run_form = -1;
   int loop_grid = 0;
   int64_t loop_max_sweeps = 0;
   int32_t loop_form = 0;
