@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--path", choices=["auto", "bitset", "small", "sparse", "tensor"], default="auto")
+    ap.add_argument("--schedule", choices=["plain", "support"], default="plain",
+                    help="plain Jacobi sweeps, or the same sweeps with incremental support counts (CSR state)")
     ap.add_argument("--plane0", choices=["auto", "full", "half", "two"], default="auto",
                     help="first test of the bitset sweep kernels (full words or half words per class)")
     ap.add_argument("--loop", choices=["device", "graph", "host"], default="device",
@@ -263,7 +265,8 @@ def run_ours(args, world, rank, local, pg):
         h_edges = pin_edges.numpy()
         h = kz.kz_load_graph(g.n, g.k, h_col, h_edges, stream=stream)
     opts = kz.kz_default_options(path=args.path, use_graph={"device": 1, "graph": 2, "host": 0}[args.loop],
-                                 plane0={"auto": 0, "full": 1, "half": 2, "two": 3}[args.plane0])
+                                 plane0={"auto": 0, "full": 1, "half": 2, "two": 3}[args.plane0],
+                                 schedule=args.schedule)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def step(i, ev0=None, ev1=None):
@@ -390,7 +393,7 @@ def run_ours(args, world, rank, local, pg):
                        "path": {v: k for k, v in kz.PATHS.items()}.get(st["path"], str(st["path"])),
                        "pass_loop": {"device": "one cooperative persistent launch", "graph": "CUDA-graph while node",
                                      "host": "host-driven"}[args.loop],
-                       "passes": passes, "sweeps": st["sweeps"],
+                       "passes": passes, "sweeps": st["sweeps"], "schedule": args.schedule,
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); per-step CUDA events "
                              "around kz_kernelize only",
                        "parallelism": "replicas" if world > 1 else "single"},

@@ -82,7 +82,13 @@ typedef enum {
  * the result: the greatest fixpoint of monotone deletion rules is unique. */
 typedef enum {
     KZ_SCHED_PLAIN = 0,   /* Jacobi sweeps over every live element */
-    KZ_SCHED_LEARNED = 1  /* MLP-ranked worklist, then a full certifying sweep */
+    KZ_SCHED_LEARNED = 1, /* MLP-ranked worklist, then a full certifying sweep */
+    KZ_SCHED_SUPPORT = 2  /* the same Jacobi sweeps on the CSR state (graphs loaded from an edge
+                             list; path AUTO or SPARSE), with per-class common-neighbour counts
+                             kept up to date as triangles break: a sweep re-tests only elements
+                             whose counts fell.  Sweeps and per-sweep deletions equal PLAIN's;
+                             edge_tests counts the tests made.  Needs about 4 m k bytes
+                             (KZ_ERR_UNSUPPORTED above 6 GiB) */
 } kz_schedule;
 
 /* First test of a pair in the BITSET path's sweep kernels (kz_options.plane0).

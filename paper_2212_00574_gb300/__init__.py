@@ -37,7 +37,7 @@ globals().update({v: k for k, v in STATUS_NAMES.items()})
 
 KZ_DEDUP = 0x1
 PATHS = {"auto": 0, "bitset": 1, "small": 2, "sparse": 3, "tensor": 4}
-SCHEDULES = {"plain": 0, "learned": 1}
+SCHEDULES = {"plain": 0, "learned": 1, "support": 2}
 PLANE0 = {"auto": 0, "full": 1, "half": 2, "two": 3}
 BATCH = {"concurrent": 0, "sequential": 1, "fused": 2}
 

@@ -106,6 +106,7 @@ void release(kz_graph g) {
   if (g->run_exec) cudaGraphExecDestroy(g->run_exec);
   learned_release(g);
   tensor_release(g);
+  support_release(g);
   for (auto &a : g->allocs) dev_free(a.p, a.bytes, s);
   g->allocs.clear();
   cudaStreamSynchronize(s);
@@ -245,7 +246,8 @@ static kz_status read_options(const kz_options *opt, kz_options &o) {
     kz_default_options(&o);
   }
   if (o.path < KZ_PATH_AUTO || o.path > KZ_PATH_TENSOR) return KZ_ERR_ARG;
-  if (o.schedule != KZ_SCHED_PLAIN && o.schedule != KZ_SCHED_LEARNED) return KZ_ERR_ARG;
+  if (o.schedule != KZ_SCHED_PLAIN && o.schedule != KZ_SCHED_LEARNED && o.schedule != KZ_SCHED_SUPPORT)
+    return KZ_ERR_ARG;
   if (o.plane0 < KZ_PLANE0_AUTO || o.plane0 > KZ_PLANE0_TWO) return KZ_ERR_ARG;
   if (o.batch < KZ_BATCH_CONCURRENT || o.batch > KZ_BATCH_FUSED) return KZ_ERR_ARG;
   return KZ_OK;
@@ -295,6 +297,16 @@ kz_status kz_kernelize(kz_graph g, const kz_options *opt, void *stream) {
     KZ_TRY(learned_kernelize(g, o, g->stream));
     g->kernelized = true;
     g->path_ran = KZ_PATH_BITSET;
+    return KZ_OK;
+  }
+  if (o.schedule == KZ_SCHED_SUPPORT) {
+    // incremental support counts on the CSR state
+    if (!g->has_csr) return KZ_ERR_UNSUPPORTED;
+    if (o.path != KZ_PATH_AUTO && o.path != KZ_PATH_SPARSE) return KZ_ERR_UNSUPPORTED;
+    KZ_TRY(state_to_sparse(g, g->stream));
+    KZ_TRY(sparse_kernelize_support(g, o, g->stream));
+    g->kernelized = true;
+    g->path_ran = KZ_PATH_SPARSE;
     return KZ_OK;
   }
   const int path = o.path == KZ_PATH_AUTO ? auto_path(g) : o.path;

@@ -199,6 +199,7 @@ struct kz_graph_s {
   float learned_threshold = 0.5f;
   void *learned_bufs = nullptr;
   void *tensor_bufs = nullptr;  // tensor-core path scratch
+  void *support_bufs = nullptr; // per-class support counts (CSR path, support schedule)
 
   // executable CUDA graph of the device-side sweep loop (built lazily)
   cudaGraphExec_t loop_exec = nullptr;
@@ -264,6 +265,11 @@ kz_status sparse_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s);
 kz_status sparse_fetch(kz_graph g, uint8_t *vertex_alive, int32_t *edges_out, int64_t cap, int64_t *m_live);
 kz_status sparse_vertex_alive(kz_graph g, uint8_t *host_alive, int64_t *n_live);
 kz_status sparse_v_sweep(kz_graph g, int32_t *host);
+// Oriented CSR of the live edges of the current CSR state.
+kz_status sparse_orient_live(kz_graph g, cudaStream_t s);
+// The CSR path with incremental per-class support counts (kz_support.cu).
+kz_status sparse_kernelize_support(kz_graph g, const kz_options &opt, cudaStream_t s);
+void support_release(kz_graph g);
 // Move the live state between the two representations.
 kz_status state_to_sparse(kz_graph g, cudaStream_t s);
 kz_status state_to_bitset(kz_graph g, cudaStream_t s);

@@ -440,6 +440,31 @@ kz_status sparse_reset(kz_graph g, cudaStream_t s) {
   return KZ_OK;
 }
 
+// Oriented CSR of the live edges of the current state (sp_orow, sp_oadj,
+// sp_oeid, sp_osrc; its size in sp_totals[1]); the compacted live rows go to
+// the other row buffer, which serves as scratch here.
+kz_status sparse_orient_live(kz_graph g, cudaStream_t s) {
+  const int c = g->sp_cur, nx = c ^ 1;
+  SparseArgs a;
+  a.n = g->n;
+  a.k = g->k;
+  a.col = g->sp_col;
+  a.rank = g->sp_rank;
+  a.row = g->sp_row[c];
+  a.adj = g->sp_adj[c];
+  a.eid = g->sp_eid[c];
+  a.elive = g->sp_elive[c];
+  a.vlive = g->sp_vlive[c];
+  a.m = g->m;
+  const int grid = 8 * sms_here(), threads = 256;
+  sparse_count_kernel<<<grid, threads, 0, s>>>(a, g->sp_cnt_live, g->sp_cnt_or);
+  KZ_TRY(exclusive_scan(g->sp_cnt_live, g->n, g->sp_row[nx], g->sp_sums, g->sp_totals, s));
+  KZ_TRY(exclusive_scan(g->sp_cnt_or, g->n, g->sp_orow, g->sp_sums, g->sp_totals + 1, s));
+  sparse_fill_kernel<<<grid, threads, 0, s>>>(a, g->sp_row[nx], g->sp_adj[nx], g->sp_eid[nx], g->sp_orow,
+                                              g->sp_oadj, g->sp_oeid, g->sp_osrc);
+  return cuda_status(cudaGetLastError());
+}
+
 kz_status sparse_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
   const int64_t max_sweeps = opt.max_sweeps > 0 ? opt.max_sweeps : (int64_t)g->n + g->m + 1;
   sparse_begin_kernel<<<1, 1, 0, s>>>(g->st, max_sweeps, g->n == 0 ? 1 : 0);

@@ -500,3 +500,68 @@ def test_forced_plane0_forms(plane0):
                             (1100, 29, 0.35, 9), (1500, 6, 0.3, 10)):
         g = synth.tiny_random(seed, n, k, p, planted=True)
         assert_parity(g, gpu_run(g, path="bitset", plane0=plane0))
+
+
+# ---------------------------------------------------------------------------
+# CSR path with incremental support counts (schedule SUPPORT)
+# ---------------------------------------------------------------------------
+
+def assert_support_parity(g, res, max_sweeps=0):
+    """Same Jacobi sweeps as the oracle, fewer or equal tests."""
+    edges = g.get_edges()
+    orc = oracle.fixpoint(g.colour, edges, g.k, max_sweeps=max_sweeps, raise_on_limit=False)
+    st = res["stats"]
+    assert np.array_equal(res["alive"], orc["vlive"]), "surviving vertices differ"
+    assert np.array_equal(res["edges"], edges[orc["elive"].astype(bool)]), "surviving edges differ"
+    assert st["sweeps"] == orc["sweeps"]
+    assert np.array_equal(res["dv"], orc["dv"]) and np.array_equal(res["de"], orc["de"])
+    assert np.array_equal(res["v_sweep"], orc["v_sweep"])
+    if orc["status"] == 0:  # under a sweep limit the refused pass is counted differently
+        assert st["passes"] == orc["passes"]
+        assert 0 < st["edge_tests"] <= orc["tests"] or orc["tests"] == 0
+    return orc
+
+
+def test_support_schedule_cascades():
+    seen = 0
+    for seed in range(12):
+        g = synth.tiny_random(700 + seed, 400, 6, 0.06 + 0.01 * (seed % 5), planted=bool(seed % 2))
+        orc = assert_support_parity(g, gpu_run(g, schedule="support"))
+        seen = max(seen, orc["sweeps"])
+    assert seen >= 3
+    for case in _tiny_cases()[:30]:
+        (i, n, k, p, planted) = case
+        g = synth.tiny_random(i, n, k, p, planted=planted)
+        assert_support_parity(g, gpu_run(g, schedule="support"))
+
+
+def test_support_schedule_c3_reduced_and_dense():
+    g = synth.workload("c3", 0.02)
+    orc = assert_support_parity(g, gpu_run(g, schedule="support"))
+    assert orc["sweeps"] >= 2
+    for seed, (n, k, nd, pd, ps) in enumerate(((1200, 12, 10, 0.95, 0.05), (700, 20, 18, 0.9, 0.1))):
+        g = _two_density_graph(seed, n, k, nd, pd, ps)
+        assert_support_parity(g, gpu_run(g, schedule="support"))
+
+
+def test_support_schedule_limit_rerun_and_switch():
+    g = synth.tiny_random(5, 2500, 8, 0.07, planted=True)
+    edges = g.get_edges()
+    orc = oracle.fixpoint(g.colour, edges, g.k)
+    r = gpu_run(g, schedule="support", max_sweeps=1)
+    assert r["stats"]["status"] == kz.KZ_ERR_LIMIT
+    assert_support_parity(g, r, max_sweeps=1)
+    with kz.KernelGraph.from_synth(g, dense=False) as kg:
+        for s in range(1, orc["sweeps"] + 2):   # one sweep per call, continued on the handle
+            kg.kernelize(schedule="support", max_sweeps=1)
+            alive, got, st = kg.fetch(allow=(kz.KZ_OK, kz.KZ_ERR_LIMIT))
+            want = oracle.fixpoint(g.colour, edges, g.k, max_sweeps=s, raise_on_limit=False)
+            assert np.array_equal(alive, want["vlive"]) and np.array_equal(got, edges[want["elive"].astype(bool)])
+        kg.reset()
+        kg.kernelize(path="bitset", max_sweeps=1)      # another path part-way, then the support schedule
+        kg.kernelize(schedule="support")
+        alive, got, st = kg.fetch()
+        assert np.array_equal(alive, orc["vlive"]) and np.array_equal(got, edges[orc["elive"].astype(bool)])
+    with kz.KernelGraph.from_synth(g, dense=True) as kg:   # no CSR state: refused
+        with pytest.raises(kz.KzError):
+            kg.kernelize(schedule="support")
