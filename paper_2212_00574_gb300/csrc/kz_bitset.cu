@@ -432,11 +432,12 @@ __device__ __forceinline__ void sweep_cta(const SweepArgs &p, int u_begin, int u
   __syncwarp();
 }
 
-// The CTA's pass counters, summed over its warps and added to the graph's
-// running pass totals with one atomic per counter (thread 0).  Ends with the
-// CTA synchronised.
+// The CTA's pass counters, summed over its warps and added to the running
+// pass totals cnt[0..2] = (tests, deleted edges, deleted vertices) with one
+// atomic per counter (thread 0, which also gets whether the CTA deleted
+// anything).  Ends with the CTA synchronised.
 template <int WARPS>
-__device__ __forceinline__ void add_cta_counters(PassCounters pc, DevState *st) {
+__device__ __forceinline__ bool add_cta_counters(PassCounters pc, unsigned long long *cnt) {
   __shared__ unsigned long long s_pc[WARPS][3];
   for (int o = 16; o > 0; o >>= 1) {
     pc.tests += __shfl_down_sync(0xffffffffu, pc.tests, o);
@@ -457,10 +458,12 @@ __device__ __forceinline__ void add_cta_counters(PassCounters pc, DevState *st) 
       de += s_pc[w][1];
       dv += s_pc[w][2];
     }
-    if (t) atomicAdd(&st->pass_tests, t);
-    if (de) atomicAdd(&st->pass_de, de);
-    if (dv) atomicAdd(&st->pass_dv, dv);
+    if (t) atomicAdd(&cnt[0], t);
+    if (de) atomicAdd(&cnt[1], de);
+    if (dv) atomicAdd(&cnt[2], dv);
+    return de + dv > 0;
   }
+  return false;
 }
 
 // One Jacobi pass per launch (the CUDA-graph loop and the host-driven loop).
@@ -486,19 +489,18 @@ __global__ void __launch_bounds__(cta_warps(KMAX, FORM) * 32, 1)
   PassCounters pc;
   sweep_cta<KMAX, FORM>(p, p.cta_begin[blockIdx.x], p.cta_begin[blockIdx.x + 1], &s_next, cur, sweep_no, full, buf0,
                         buf1, bufh, s_rounds, pc);
-  add_cta_counters<W>(pc, st);
+  add_cta_counters<W>(pc, st->ppass[0]);
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned int t = atomicAdd(&st->ticket, 1u);
     if (t == gridDim.x - 1u) {  // the last CTA closes the pass
       __threadfence();
-      const unsigned long long dv = atomicAdd(&st->pass_dv, 0ull);
-      const unsigned long long de = atomicAdd(&st->pass_de, 0ull);
-      const unsigned long long tests = atomicAdd(&st->pass_tests, 0ull);
+      unsigned long long *c = st->ppass[0];
+      const unsigned long long tests = atomicAdd(&c[0], 0ull);
+      const unsigned long long de = atomicAdd(&c[1], 0ull);
+      const unsigned long long dv = atomicAdd(&c[2], 0ull);
       const int cont = finish_pass(st, dv, de, tests);
-      st->pass_dv = 0;
-      st->pass_de = 0;
-      st->pass_tests = 0;
+      c[0] = c[1] = c[2] = 0;
       st->ticket = 0;
       __threadfence();
       if (p.use_cond) cudaGraphSetConditional(p.cond, cont ? 1u : 0u);
@@ -534,31 +536,38 @@ __global__ void __launch_bounds__(cta_warps(KMAX, FORM) * 32, 1)
   int cur = *((volatile int32_t *)&st->cur);
   int64_t sweep_no = *((volatile int64_t *)&st->sweeps);
   bool full = *((volatile int32_t *)&st->full_write) != 0;
+  const int64_t max_sweeps = *((volatile int64_t *)&st->max_sweeps);
   const int u_begin = p.cta_begin[blockIdx.x], u_end = p.cta_begin[blockIdx.x + 1];
-  for (;;) {
+  for (int pass = 0;; pass++) {
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
     PassCounters pc;
     sweep_cta<KMAX, FORM>(p, u_begin, u_end, &s_next, cur, sweep_no, full, buf0, buf1, bufh, s_rounds, pc);
-    add_cta_counters<W>(pc, st);
+    // counters by pass parity: the closing CTA reads this pass's after the
+    // release, while the next pass adds to the other set
+    unsigned long long *cnt = st->ppass[pass & 1];
+    const bool deleted = add_cta_counters<W>(pc, cnt);
     if (threadIdx.x == 0) {
       __threadfence();
       const unsigned long long w0 = *((volatile unsigned long long *)&st->pass_word);
       unsigned long long w = w0;
       bool abort = false;
-      if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1u + p.bar_extra) {
-        __threadfence();
-        const unsigned long long dv = atomicAdd(&st->pass_dv, 0ull);
-        const unsigned long long de = atomicAdd(&st->pass_de, 0ull);
-        const unsigned long long tests = atomicAdd(&st->pass_tests, 0ull);
-        const int cont = finish_pass(st, dv, de, tests);
-        st->pass_dv = 0;
-        st->pass_de = 0;
-        st->pass_tests = 0;
+      // arrival count in the low 20 bits, CTAs that deleted something above
+      const unsigned int old = atomicAdd(&st->bar_count, 1u | (deleted ? 1u << 20 : 0u));
+      if ((old & 0xfffffu) == gridDim.x - 1u + p.bar_extra) {
+        // the pass closes: decide and release first, book-keep after
+        const bool productive = deleted || (old >> 20) != 0u;
+        const int cont = productive && sweep_no < max_sweeps ? 1 : 0;
         st->bar_count = 0;
         w = pass_word(pass_word_gen(w0) + 1u, cont, cont ? cur ^ 1 : cur, cont ? sweep_no + 1 : sweep_no);
         __threadfence();
         atomicExch(&st->pass_word, w);
+        __threadfence();
+        const unsigned long long tests = atomicAdd(&cnt[0], 0ull);
+        const unsigned long long de = atomicAdd(&cnt[1], 0ull);
+        const unsigned long long dv = atomicAdd(&cnt[2], 0ull);
+        finish_pass(st, dv, de, tests);  // the same decision, from the same counts
+        cnt[0] = cnt[1] = cnt[2] = 0;
       } else {
         uint32_t spins = 0;
         for (;;) {
@@ -601,6 +610,7 @@ __global__ void begin_run_kernel(DevState *st, int64_t max_sweeps, int64_t passe
   st->tests = 0;
   st->max_sweeps = max_sweeps;
   st->pass_dv = st->pass_de = st->pass_tests = 0;
+  for (int i = 0; i < 2; i++) st->ppass[i][0] = st->ppass[i][1] = st->ppass[i][2] = 0;
   st->ticket = 0;
 }
 
@@ -610,6 +620,7 @@ __global__ void reset_state_kernel(DevState *st) {
   st->cont = 0;
   st->sweeps = st->passes = st->tests = 0;
   st->pass_dv = st->pass_de = st->pass_tests = 0;
+  for (int i = 0; i < 2; i++) st->ppass[i][0] = st->ppass[i][1] = st->ppass[i][2] = 0;
   st->ticket = 0;
 }
 

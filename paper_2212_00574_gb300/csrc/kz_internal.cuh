@@ -70,6 +70,7 @@ struct DevState {
   int32_t bar_abort;              // a bounded barrier wait ran out
   int32_t pad2;
   unsigned long long pass_word;   // persistent sweep kernel: barrier generation and next-pass state
+  unsigned long long ppass[2][3]; // persistent sweep kernel: pass counters (tests, de, dv) by pass parity
   int64_t trace_dv[kTraceCap];
   int64_t trace_de[kTraceCap];
 };
