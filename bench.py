@@ -32,6 +32,8 @@ WORKLOAD_DESC = {
     "c5": "random k-partite n=32768 k=24 p=0.85, planted 24-clique (dense 0/1 input)",
     "c3": "Chung-Lu n=200000 k=12, Zipf(1.2) class sizes, power-law degrees (exponent 2.3, mean 60), "
           "~6M edges, 5 planted 12-cliques (edge-list input)",
+    "c5c": "random k-partite n=32768 k=24 p=0.12, planted 24-clique: the C5 size in the cascade regime "
+           "(dense 0/1 input)",
     "c4": "batch of 1024 random k-partite graphs, n log-uniform [64,4096], k U{6..32}, p U[0.3,0.95], "
           "planted k-clique on even indices, one kz_kernelize_batch call (graphs spread over streams)",
 }
@@ -58,8 +60,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--path", choices=["auto", "bitset", "small", "sparse", "tensor"], default="auto")
-    ap.add_argument("--schedule", choices=["plain", "support"], default="plain",
-                    help="plain Jacobi sweeps, or the same sweeps with incremental support counts (CSR state)")
+    ap.add_argument("--schedule", choices=["plain", "support", "learned"], default="plain",
+                    help="plain Jacobi sweeps; the same sweeps with incremental support counts (CSR state); "
+                         "or the learned schedule (an MLP trained first, on plain-method traces of "
+                         "C4-style cascading graphs, by the library's own kernels), timed against plain")
     ap.add_argument("--plane0", choices=["auto", "full", "half", "two"], default="auto",
                     help="first test of the bitset sweep kernels (full words or half words per class)")
     ap.add_argument("--loop", choices=["device", "graph", "host"], default="device",
@@ -483,6 +487,91 @@ def run_batch(args, world, rank, local, pg):
     return 0
 
 
+def run_learned(args, world, rank, local, pg):
+    """Learned schedule against plain sweeps on one graph: the network is
+    trained first (plain-method traces of C4-style cascading graphs with other
+    seeds, the library's forward/backward/Adam kernels), then both schedules
+    run to the fixpoint from the same loaded graph, the results compared bit
+    for bit, and each timed with CUDA events around kz_kernelize."""
+    import torch
+
+    import paper_2212_00574_gb300 as kz
+    from paper_2212_00574_gb300 import learned, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    kz.use_torch_allocator()
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    X, y = learned.collect(learned.cascade_specs(24, synth.SEED_BASE + 900 + rank), per_sweep_cap=3000)
+    model, losses = learned.train(X, y, steps=300, batch=4096, lr=3e-3)
+    train_s = time.perf_counter() - t0
+    g = make_workload(args.workload)
+    bits = g.get_bits()
+    h = kz.kz_load_graph_dense(g.n, g.k, g.colour, bits, stream=stream)
+    kz.kz_attach_model(h, model, 0.5)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    res = {}
+    for label, opts in (("plain", kz.kz_default_options(path="bitset")),
+                        ("learned", kz.kz_default_options(path="bitset", schedule="learned"))):
+        def step(i, ev0=None, ev1=None):
+            kz.kz_reset(h, stream)
+            flush.fill_(i & 0xFF)
+            if ev0 is not None:
+                ev0.record(stream)
+            kz.kz_kernelize(h, opts, stream)
+            if ev1 is not None:
+                ev1.record(stream)
+
+        for i in range(args.warmup):
+            step(i)
+        torch.cuda.synchronize(dev)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        barrier(pg)
+        torch.cuda.synchronize(dev)
+        clocks.start()
+        for i in range(args.steps):
+            step(i, *evs[i])
+        torch.cuda.synchronize(dev)
+        clk = clocks.stop()
+        barrier(pg)
+        ms = [a.elapsed_time(b) for a, b in evs]
+        st = kz.kz_fetch_stats(h)
+        alive, out_bits, _ = kz.kz_fetch_kernel_dense(h, g.n)
+        res[label] = dict(ms=sum(ms) / len(ms), tests=st["edge_tests"], sweeps=st["sweeps"], passes=st["passes"],
+                          alive=alive.copy(), bits=out_bits.copy(), clocks=clk, dev_s=sum(ms) / 1e3)
+    kz.kz_free_graph(h)
+    kz.kz_model_free(model)
+    same = bool(np.array_equal(res["plain"]["alive"], res["learned"]["alive"])
+                and np.array_equal(res["plain"]["bits"], res["learned"]["bits"]))
+    lr = res["learned"]
+    slowest = reduce_max(pg, lr["dev_s"])
+    value = reduce_sum(pg, float(lr["tests"]) * args.steps) / slowest
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": lr["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC[args.workload], "n": g.n, "k": g.k, "m": g.m,
+                       "schedule": "learned (threshold 0.5)", "path": "bitset",
+                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "time_to_fixpoint_us": {"learned": 1e3 * lr["ms"], "plain": 1e3 * res["plain"]["ms"]},
+            "learned_vs_plain": {"speedup_time": res["plain"]["ms"] / lr["ms"],
+                                 "tests": {"learned": lr["tests"], "plain": res["plain"]["tests"]},
+                                 "sweeps": {"learned": lr["sweeps"], "plain": res["plain"]["sweeps"]},
+                                 "bit_identical": same},
+            "training": {"records": int(len(y)), "positive_share": float(np.mean(y)), "loss_first": losses[0],
+                         "loss_last": losses[-1], "seconds": train_s,
+                         "graphs": "24 C4-style cascading graphs (n 128..1500, p 0.15..0.45), other seeds"},
+            "clocks": lr["clocks"],
+        }
+        print(json.dumps(line), flush=True)
+    return 0 if same else 1
+
+
 def main():
     args = parse()
     world, rank, local, pg = dist_init()
@@ -491,6 +580,8 @@ def main():
             return run_reference(args, world, rank, pg)
         if args.workload == "c4":
             return run_batch(args, world, rank, local, pg)
+        if args.schedule == "learned":
+            return run_learned(args, world, rank, local, pg)
         return run_ours(args, world, rank, local, pg)
     finally:
         if pg is not None:

@@ -303,6 +303,7 @@ WORKLOADS = {
     "c3": "chung-lu n=200000 k=12 zipf(1.2) mean degree 60, 5 planted 12-cliques",
     "c4": "batch of 1024 kpartite graphs, n log-uniform [64,4096], k U{6..32}, p U[0.3,0.95]",
     "c5": "kpartite n=32768 k=24 p=0.85, planted 24-clique",
+    "c5c": "kpartite n=32768 k=24 p=0.12, planted 24-clique (the C5 size in the cascade regime)",
 }
 
 
@@ -321,4 +322,6 @@ def workload(name: str, scale: float = 1.0):
         return batch(max(2, int(1024 * scale)), seed)
     if name == "c5":
         return kpartite(max(24, int(32768 * scale)), 24, 0.85, seed)
+    if name == "c5c":
+        return kpartite(max(24, int(32768 * scale)), 24, 0.12, seed + 10)
     raise KeyError(name)
