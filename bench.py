@@ -45,7 +45,6 @@ L2_FLUSH_BYTES = 256 << 20
 # the commands are in profiles/.  An entry is removed when its kernel changes.
 MEASURED_TRAFFIC = {
     ("c2", "bitset_persistent_kernel"): 2335744,
-    ("c2", "tensor_edge_kernel"): 19928064,
 }
 
 
@@ -58,6 +57,8 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC), default="c2")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU work budget of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink the workload (n x scale; for small profiler captures, not for bench lines)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--path", choices=["auto", "bitset", "small", "sparse", "tensor"], default="auto")
     ap.add_argument("--schedule", choices=["plain", "support", "learned"], default="plain",
@@ -177,9 +178,14 @@ class ClockSampler:
 # workloads
 # ---------------------------------------------------------------------------
 
-def make_workload(name):
+def wdesc(args):
+    d = WORKLOAD_DESC[args.workload]
+    return d if args.scale == 1.0 else f"{d}, scaled to n x {args.scale:g} (profiling case)"
+
+
+def make_workload(name, scale=1.0):
     from paper_2212_00574_gb300 import synth
-    return synth.workload(name)
+    return synth.workload(name, scale)
 
 
 def cpu_baseline(g, budget_s: float, session=None) -> dict:
@@ -215,7 +221,7 @@ def run_reference(args, world, rank, pg):
     if rank != 0:
         return 0
     import oracle
-    g = make_workload(args.workload)
+    g = make_workload(args.workload, args.scale)
     sess = oracle.Session(g.colour, g.get_edges(), g.k)
     budget = min(max(60.0 / max(args.steps + args.warmup, 1), 0.01), 2.0)
     per_step = []
@@ -230,7 +236,7 @@ def run_reference(args, world, rank, pg):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * g.m / value, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC[args.workload], "n": g.n, "k": g.k, "m": g.m,
+        "config": {"workload": wdesc(args), "n": g.n, "k": g.k, "m": g.m,
                    "l2": "n/a (CPU)", "parallelism": "replicas"},
         "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
                          "sample": per_step[0]["sample"] + " per step; ms_per_step extrapolates "
@@ -253,7 +259,7 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     kz.use_torch_allocator()
-    g = make_workload(args.workload)
+    g = make_workload(args.workload, args.scale)
     stream = torch.cuda.current_stream(dev)
     dense = args.workload != "c3"
     pin_col = torch.from_numpy(g.colour).pin_memory()
@@ -338,6 +344,25 @@ def run_ours(args, world, rank, local, pg):
                         "written per launch from one ncu capture of this kernel on this workload (null where "
                         "none was taken for the current kernel)"}
 
+    if kernel == "tensor_edge_kernel":
+        # the tensor form's work is fixed by the shapes: per upper-triangle
+        # 128 x 128 tile and per K-step (32 vertices of one class), one
+        # M = N = 128, K = 32 fp8 MMA (2 * 128 * 128 * 32 flops); peak = the
+        # measured bf16 dense peak x 2 (the nominal fp8 : bf16 ratio)
+        sizes = np.bincount(np.asarray(g.colour), minlength=k)
+        ksteps = int(sum((int(c) + 31) // 32 for c in sizes))
+        t_side = (g.n + 127) // 128
+        flops = 2.0 * 128 * 128 * 32 * ksteps * t_side * (t_side + 1) / 2
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        fp8_peak = 2.0 * peaks["bf16_tflops"] * 1e12
+        roofline = {"bound": "tensor", "achieved": flops / launch_s / 1e12, "peak": fp8_peak / 1e12,
+                    "unit": "TFLOP/s", "frac": flops / launch_s / fp8_peak,
+                    "traffic": MEASURED_TRAFFIC.get((args.workload, kernel)), "kernel": kernel,
+                    "flops_per_launch": flops,
+                    "note": "flops = 2*128*128*32 per (upper-triangle tile, K-step); peak = measured bf16 burst "
+                            "x 2 (nominal fp8:bf16), of measured; launch time = CUDA events around kz_kernelize "
+                            "/ passes (includes the expand and commit kernels of each pass)"}
+
     # end-to-end through the C ABI: host buffers in, host buffers out
     e2e = None
     if args.e2e_steps > 0 and not dense:
@@ -393,7 +418,7 @@ def run_ours(args, world, rank, local, pg):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC[args.workload], "n": g.n, "k": g.k, "m": g.m,
+            "config": {"workload": wdesc(args), "n": g.n, "k": g.k, "m": g.m,
                        "path": {v: k for k, v in kz.PATHS.items()}.get(st["path"], str(st["path"])),
                        "pass_loop": {"device": "one cooperative persistent launch", "graph": "CUDA-graph while node",
                                      "host": "host-driven"}[args.loop],
@@ -506,7 +531,7 @@ def run_learned(args, world, rank, local, pg):
     X, y = learned.collect(learned.cascade_specs(24, synth.SEED_BASE + 900 + rank), per_sweep_cap=3000)
     model, losses = learned.train(X, y, steps=300, batch=4096, lr=3e-3)
     train_s = time.perf_counter() - t0
-    g = make_workload(args.workload)
+    g = make_workload(args.workload, args.scale)
     bits = g.get_bits()
     h = kz.kz_load_graph_dense(g.n, g.k, g.colour, bits, stream=stream)
     kz.kz_attach_model(h, model, 0.5)
@@ -554,7 +579,7 @@ def run_learned(args, world, rank, local, pg):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": lr["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC[args.workload], "n": g.n, "k": g.k, "m": g.m,
+            "config": {"workload": wdesc(args), "n": g.n, "k": g.k, "m": g.m,
                        "schedule": "learned (threshold 0.5)", "path": "bitset",
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": "replicas" if world > 1 else "single"},

@@ -244,6 +244,9 @@ kz_status bitset_begin_run(kz_graph g, int64_t max_sweeps, cudaStream_t s);
 // Tensor-core edge rule (kz_tensor.cu).
 kz_status tensor_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s);
 void tensor_release(kz_graph g);
+// The driver's cuTensorMapEncodeTiled, found through the runtime's entry-point
+// query (null when the driver does not provide it).
+void *tensor_map_encoder();
 
 // Learned schedule (kz_learned.cu).
 kz_status learned_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s);

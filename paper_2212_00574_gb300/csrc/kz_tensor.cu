@@ -6,24 +6,41 @@
 // col(v) always give 0: no neighbour of u has u's colour).  An edge fails when
 // fewer than k-2 classes do.
 //
-// Layout: the live bitset rows are expanded into a byte matrix M (rows in the
-// relabelled order, padded to a multiple of 128) with one 32-byte K-step per
-// 32-bit block word: byte 32*j + b of row x is E4M3 1.0 (0x38) when bit b of
-// block word j of row x is set, else 0.  Class c is the run of K-steps of its
-// blocks, so S_c is a K-loop over those steps only.
+// Operand layout: the live bitset rows are expanded into an E4M3 0/1 byte
+// matrix with one 32-byte K-step per 32-bit block word (class c is the run of
+// K-steps of its blocks, so S_c is a K-loop over those steps only).  The
+// matrix is stored half-step-major: M[h][x][0..15] holds bits 16(h%2) ..
+// 16(h%2)+15 of block word h/2 of row x (0x38 = E4M3 1.0 for a set bit), so
+// the 128 rows of a tile form one contiguous 2048-byte run per half-step.
+// One TMA box (8 half-steps x 2048 bytes, read as 8-byte elements so that
+// the box's inner extent is the whole contiguous run) then lands in shared
+// memory as four consecutive canonical no-swizzle K-major MMA operands:
+// 8-row x 16-byte core matrices 128 bytes apart along M/N and 2048 bytes
+// apart along K, one K-step every 4096 bytes.  Large boxes matter: the TMA
+// probe measures 35 bytes per clock and SM for 4 KB boxes against 66 for
+// 16 KB boxes with the same bytes in flight.
 //
-// Kernel: one CTA (4 warps) per upper-triangle tile (I, J) of 128 x 128
-// pairs.  For each class: the K-steps of rows I and J are copied into shared
-// memory in the canonical no-swizzle K-major layout (8-row x 16-byte core
-// matrices), one thread issues tcgen05.mma.kind::f8f6f4 (M = N = 128, K = 32
-// per step, fp32 accumulation in TMEM, exact for 0/1 products), and the four
-// warps read the accumulator back with tcgen05.ld and count, per pair, the
-// classes with a non-zero entry (8-bit counters packed four to a register).
-// After the last class the live edges of the tile below k-2 are marked in a
-// deletion bitmap; a row kernel then applies the vertex rule and the edge
-// deletions to produce the next state.  Waits on the MMA mbarrier are
-// bounded: a wait that runs out records KZ_ERR_TIMEOUT and the CTA returns
-// after freeing its tensor memory.
+// Kernel (two CTAs per SM, persistent over upper-triangle 128 x 128 tiles;
+// the MMA probe measures one CTA's M = N = 128 stream at half the tensor
+// pipe's rate, two CTAs at the full rate):
+//   warp 0      TMA producer: fills a ring of pipeline stages (four K-steps
+//               of both tiles each, one box per tile) as soon as the MMAs
+//               free them;
+//   warp 1      MMA issuer: one thread issues tcgen05.mma.kind::f8f6f4
+//               (M = N = 128, K = 32, fp32 accumulation in TMEM, exact for
+//               0/1 products) over a class's K-steps, alternating between
+//               two TMEM accumulators so that the next class runs while the
+//               previous one is read;
+//   warps 2-9   epilogue: tcgen05.ld of the class's counts, one 8-bit
+//               counter per pair of classes with a non-zero count; after the
+//               tile's last class, live edges below k-2 are marked in a
+//               deletion bitmap.
+// A row kernel then applies the vertex rule and the edge deletions.  Every
+// mbarrier wait is bounded (wall clock); a wait that runs out records
+// KZ_ERR_TIMEOUT, the other roles stop at their next wait, the producer and
+// the MMA issuer wait (bounded) for their copies and MMAs in flight, and the
+// CTA frees its tensor memory before it returns.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder comes from the runtime's entry-point query)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -37,25 +54,39 @@
 namespace kz {
 namespace tensor {
 
-constexpr int kTile = 128;          // rows per tile side (MMA M = N = 128)
-constexpr int kStep = 32;           // bytes (E4M3 elements) per K-step
-constexpr int kThreads = 128;       // 4 warps: one TMEM lane quarter each
-constexpr int kMaxStepsPerStage = 16;  // K-steps staged at once (class runs are looped in chunks)
-constexpr uint32_t kSpinLimit = 1u << 26;
+constexpr int kTile = 128;                       // rows per tile side (MMA M = N = 128)
+constexpr int kStep = 32;                        // bytes (E4M3 elements) per K-step
+constexpr int kStepBytes = kTile * kStep;        // one operand, one K-step: 4096 bytes
+constexpr int kStageSteps = 4;                   // K-steps per pipeline stage (class runs are chunked)
+constexpr int kStages = 3;                       // pipeline depth (two CTAs per SM share the rest)
+constexpr int kCtasPerSm = 2;                    // one CTA's M = N = 128 MMA stream fills half the tensor pipe
+constexpr int kOperandBytes = kStageSteps * kStepBytes;   // 16 KB
+constexpr int kStageBytes = 2 * kOperandBytes;            // A and B tiles
+constexpr int kEpiWarps = 8;                     // two per TMEM lane quarter, 64 columns each
+constexpr int kThreads = (2 + kEpiWarps) * 32;
+constexpr uint32_t kAccCols = 128;               // fp32 columns per accumulator
+constexpr uint32_t kTmemCols = 2 * kAccCols;     // double-buffered accumulator
+constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 1024;  // + alignment slack
+constexpr uint64_t kWaitNs = 4000000000ull;      // 4 s per wait before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Shared-memory matrix descriptor: K-major, no swizzle.  A K-step of 128 rows
-// x 32 bytes is 16 groups of 8 rows; each group holds two 8x16-byte core
-// matrices (K halves) 128 bytes apart (leading byte offset), groups are 256
-// bytes apart (stride byte offset).
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Shared-memory matrix descriptor for the K-major, no-swizzle operand one TMA
+// box produces: core matrices (8 rows x 16 bytes) 2048 bytes apart along K
+// (leading byte offset) and 128 bytes apart along M/N (stride byte offset).
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);        // start address
-  d |= (uint64_t)(128u >> 4) << 16;                 // leading byte offset (K direction)
-  d |= (uint64_t)(256u >> 4) << 32;                 // stride byte offset (8-row groups)
+  d |= (uint64_t)(2048u >> 4) << 16;                // leading byte offset (K direction)
+  d |= (uint64_t)(128u >> 4) << 32;                 // stride byte offset (8-row groups)
   d |= (uint64_t)1 << 46;                           // descriptor version
   // base offset 0, relative LBO mode, no swizzle (bits 61-63 = 0)
   return d;
@@ -82,9 +113,23 @@ __device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t a, uint64_t b, 
       : "r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// Arrive on `mbar` once every tcgen05 operation this thread issued before has completed.
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// Arrive and announce `bytes` of asynchronous copies that complete this phase.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
@@ -99,7 +144,59 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
   return ok != 0;
 }
 
-// 32 consecutive fp32 columns of this thread's TMEM lane.
+// One TMA box of the byte matrix: half-steps half0 .. half0 + 2 kStageSteps - 1
+// (kStageSteps K-steps) of the 128 rows starting at row0 (x counts 8-byte
+// elements: 2 per row).  Half-steps past the end of the matrix read as zero;
+// those of the next class are loaded but not used.
+__device__ __forceinline__ void tma_load_step(uint32_t dst, const CUtensorMap *map, uint32_t mbar, int32_t row0,
+                                              int32_t half0) {
+  const int32_t x = row0 * 2;
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar), "r"(x), "r"(half0)
+      : "memory");
+}
+
+// Whole-warp wait for the completion of the phase of parity `parity`.  Every
+// lane polls; the decision to give up is lane 0's, so the warp stays
+// converged.  Returns false when another role has given up, or after kWaitNs
+// (then records KZ_ERR_TIMEOUT and raises the CTA's abort flag).
+__device__ __noinline__ bool warp_wait(uint32_t mbar, uint32_t parity, volatile int *abort_flag, int32_t *status) {
+  const uint64_t t0 = globaltimer();
+  for (uint32_t i = 0;; i++) {
+    const bool ok = mbar_try_wait(mbar, parity);
+    if (__all_sync(0xffffffffu, ok)) return true;
+    if ((i & 15u) == 15u) {
+      int stop = 0;
+      if ((threadIdx.x & 31) == 0) {
+        if (*abort_flag) {
+          stop = 1;
+        } else if (globaltimer() - t0 > kWaitNs || i > (1u << 30)) {
+          *abort_flag = 1;
+          if (status) atomicCAS(status, 0, (int32_t)KZ_ERR_TIMEOUT);
+          stop = 1;
+        }
+      }
+      if (__shfl_sync(0xffffffffu, stop, 0)) return false;
+    }
+  }
+}
+
+// Single-thread bounded wait used when draining work in flight on the way
+// out (ignores the abort flag: copies and MMAs already issued must land
+// before the CTA's shared and tensor memory go away).
+__device__ __noinline__ void drain_wait(uint32_t mbar, uint32_t parity, int32_t *status) {
+  const uint64_t t0 = globaltimer();
+  for (uint32_t i = 0; !mbar_try_wait(mbar, parity); i++) {
+    if ((i & 15u) == 15u && (globaltimer() - t0 > kWaitNs || i > (1u << 30))) {
+      if (status) atomicCAS(status, 0, (int32_t)KZ_ERR_TIMEOUT);
+      return;
+    }
+  }
+}
+
+// 32 consecutive fp32 columns of this thread's TMEM lane (no wait).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -111,17 +208,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
         "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 struct TensorArgs {
-  const uint8_t *M;        // byte matrix [n_pad][ksteps * 32]
-  int32_t n, n_pad, ksteps;
+  int32_t n, k;
   const int32_t *cls_step; // k + 1: first K-step of each class
   const uint32_t *A;       // current rows (adjacency bits)
-  int32_t ldw, k;
-  const int32_t *col;      // relabelled colour
-  const int32_t *coff;     // k + 1
+  int32_t ldw;
+  const int32_t *vinfo;    // n_pad: (word << 5 | bit) of vertex x in any row, -1 past n
   uint32_t *Edel;          // deletion bitmap, rows x ldw (zeroed)
   const int2 *tiles;       // (I, J) tile pairs, I <= J
   int32_t n_tiles;
@@ -129,176 +226,243 @@ struct TensorArgs {
   int32_t *status;
 };
 
-// Copy K-steps [s0, s0 + ns) of the 128 rows starting at `row0` into the
-// canonical layout: step s occupies 4096 bytes; inside it, row r, byte b sits
-// at (r / 8) * 256 + (b / 16) * 128 + (r % 8) * 16 + (b % 16).
-__device__ __forceinline__ void stage_rows(const TensorArgs &a, int row0, int s0, int ns, uint8_t *dst) {
-  const int64_t ld = (int64_t)a.ksteps * kStep;
-  // one 16-byte chunk per thread-iteration: (step, row, half)
-  const int chunks = ns * kTile * 2;
-  for (int q = threadIdx.x; q < chunks; q += kThreads) {
-    const int s = q / (kTile * 2);
-    const int rem = q - s * kTile * 2;
-    const int r = rem >> 1, h = rem & 1;
-    const uint4 v = *reinterpret_cast<const uint4 *>(a.M + (int64_t)(row0 + r) * ld + (int64_t)(s0 + s) * kStep + h * 16);
-    *reinterpret_cast<uint4 *>(dst + s * 4096 + (r >> 3) * 256 + h * 128 + (r & 7) * 16) = v;
-  }
+// Accumulate the non-zero flags of 32 fp32 counts into 8-bit counters: a
+// count is a non-negative float, so its bit pattern is non-zero exactly when
+// the count is.
+__device__ __forceinline__ void count_nonzero(const uint32_t (&r)[32], uint32_t *cnt) {
+#pragma unroll
+  for (int j = 0; j < 32; j++) cnt[j >> 2] += min(r[j], 1u) << ((j & 3) * 8);
 }
 
-__global__ void __launch_bounds__(kThreads, 1) tensor_edge_kernel(TensorArgs a) {
-  extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t *sA = smem;                                   // kMaxStepsPerStage x 4096
-  uint8_t *sB = smem + kMaxStepsPerStage * 4096;        // kMaxStepsPerStage x 4096
-  __shared__ __align__(8) uint64_t mbar;
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) tensor_edge_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                  TensorArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2 * kStages + 5];
   __shared__ uint32_t tmem_base;
-  __shared__ int abort_flag;
+  __shared__ int abort_flag_s;
+  volatile int *abort_flag = &abort_flag_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t bar0 = smem_u32(bars);
+  // barrier addresses: full[s], empty[s], acc_full[b], acc_empty[b], drain
+  const uint32_t full0 = bar0, empty0 = bar0 + 8 * kStages, accf0 = bar0 + 16 * kStages;
+  const uint32_t acce0 = accf0 + 16, drain = accf0 + 32;
 
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(128u));
+                 "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    for (int s = 0; s < kStages; s++) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, kEpiWarps);
+    }
+    mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    abort_flag = 0;
+    abort_flag_s = 0;
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  tc_fence_before();
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  tc_fence_after();
   const uint32_t tmem = tmem_base;
-  const uint32_t mb = smem_u32(&mbar);
-  const uint32_t idesc = make_idesc();
-  uint32_t phase = 0;
-  unsigned long long my_fail = 0, my_tests = 0;
 
-  for (int t = blockIdx.x; t < a.n_tiles && !abort_flag; t += gridDim.x) {
-    const int I = a.tiles[t].x, J = a.tiles[t].y;
-    const int u = I * kTile + tid;  // this thread's TMEM lane = row u of the tile
-    uint32_t cnt[32];               // 128 column counters, 8 bits each
-#pragma unroll
-    for (int i = 0; i < 32; i++) cnt[i] = 0;
-    for (int c = 0; c < a.k && !abort_flag; c++) {
-      const int sb = a.cls_step[c], se = a.cls_step[c + 1];
-      if (se <= sb) continue;
-      for (int s0 = sb; s0 < se && !abort_flag; s0 += kMaxStepsPerStage) {
-        const int ns = min(kMaxStepsPerStage, se - s0);
-        stage_rows(a, I * kTile, s0, ns, sA);
-        stage_rows(a, J * kTile, s0, ns, sB);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
-          for (int s = 0; s < ns; s++) {
-            const uint64_t da = make_desc(smem_u32(sA + s * 4096));
-            const uint64_t db = make_desc(smem_u32(sB + s * 4096));
-            mma_f8(tmem, da, db, idesc, (s0 > sb || s > 0) ? 1u : 0u);
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    int stage = 0;
+    uint32_t ph = 0;
+    uint32_t filled = 0, fill_parity = 0;  // per stage: issued at least once / parity of its last fill
+    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+      const int I = a.tiles[t].x, J = a.tiles[t].y;
+      const bool diag = I == J;
+      for (int c = 0; c < a.k; c++) {
+        const int sb = a.cls_step[c], se = a.cls_step[c + 1];
+        for (int s0 = sb; s0 < se; s0 += kStageSteps) {
+          const int ns = min(kStageSteps, se - s0);
+          if (!warp_wait(empty0 + 8 * stage, ph ^ 1u, abort_flag, a.status)) goto producer_done;
+          if (lane == 0) {
+            const uint32_t fb = full0 + 8 * stage;
+            mbar_expect_tx(fb, (uint32_t)(kOperandBytes * (diag ? 1 : 2)));
+            const uint32_t sA = sbase + stage * kStageBytes, sB = sA + kOperandBytes;
+            tma_load_step(sA, &tmap, fb, I * kTile, 2 * s0);
+            if (!diag) tma_load_step(sB, &tmap, fb, J * kTile, 2 * s0);
           }
-          mma_commit(mb);
-        }
-        // every thread waits for the MMAs of this stage (bounded)
-        uint32_t spins = 0;
-        while (!mbar_try_wait(mb, phase)) {
-          if (++spins > kSpinLimit) {
-            atomicExch(&abort_flag, 1);
-            if (a.status) atomicCAS(a.status, 0, (int32_t)KZ_ERR_TIMEOUT);
-            break;
+          __syncwarp();
+          filled |= 1u << stage;
+          fill_parity = (fill_parity & ~(1u << stage)) | (ph << stage);
+          if (++stage == kStages) {
+            stage = 0;
+            ph ^= 1u;
           }
         }
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        __syncthreads();  // shared operands free again
       }
-      if (abort_flag) break;
-      // class c done: count the non-zero entries of this thread's row
+    }
+  producer_done:
+    // every fill issued must land before the shared memory is released
+    if (lane == 0)
+      for (int s = 0; s < kStages; s++)
+        if ((filled >> s) & 1u) drain_wait(full0 + 8 * s, (fill_parity >> s) & 1u, a.status);
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    const uint32_t idesc = make_idesc();
+    int stage = 0, abuf = 0;
+    uint32_t ph = 0, empty_ph = 0;  // bit b: parity of accumulator b's next release
+    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+      const int I = a.tiles[t].x, J = a.tiles[t].y;
+      const bool diag = I == J;
+      for (int c = 0; c < a.k; c++) {
+        const int sb = a.cls_step[c], se = a.cls_step[c + 1];
+        if (se <= sb) continue;
+        // the epilogue must have read this accumulator's previous class
+        if (!warp_wait(acce0 + 8 * abuf, ((empty_ph >> abuf) & 1u) ^ 1u, abort_flag, a.status)) goto mma_done;
+        tc_fence_after();
+        for (int s0 = sb; s0 < se; s0 += kStageSteps) {
+          const int ns = min(kStageSteps, se - s0);
+          if (!warp_wait(full0 + 8 * stage, ph, abort_flag, a.status)) goto mma_done;
+          tc_fence_after();
+          if (lane == 0) {
+            const uint32_t sA = sbase + stage * kStageBytes, sB = diag ? sA : sA + kOperandBytes;
+            for (int j = 0; j < ns; j++)
+              mma_f8(tmem + (uint32_t)abuf * kAccCols, make_desc(sA + j * kStepBytes), make_desc(sB + j * kStepBytes),
+                     idesc, (s0 > sb || j > 0) ? 1u : 0u);
+            mma_commit(empty0 + 8 * stage);  // stage free once these MMAs have read it
+          }
+          __syncwarp();
+          if (++stage == kStages) {
+            stage = 0;
+            ph ^= 1u;
+          }
+        }
+        if (lane == 0) mma_commit(accf0 + 8 * abuf);  // class complete in this accumulator
+        __syncwarp();
+        empty_ph ^= 1u << abuf;
+        abuf ^= 1;
+      }
+    }
+  mma_done:
+    // every MMA issued must finish before the tensor memory is released
+    if (lane == 0) {
+      mma_commit(drain);
+      drain_wait(drain, 0u, a.status);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;              // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;    // column half of the tile
+    const int row = q * 32 + lane;
+    const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+    int abuf = 0;
+    uint32_t full_ph = 0;  // bit b: parity of accumulator b's next class
+    unsigned long long my_fail = 0, my_tests = 0;
+    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+      const int I = a.tiles[t].x, J = a.tiles[t].y;
+      uint32_t cnt[16];  // 64 column counters, 8 bits each
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * 32), r);
+      for (int i = 0; i < 16; i++) cnt[i] = 0;
+      for (int c = 0; c < a.k; c++) {
+        const int sb = a.cls_step[c], se = a.cls_step[c + 1];
+        if (se <= sb) continue;
+        if (!warp_wait(accf0 + 8 * abuf, (full_ph >> abuf) & 1u, abort_flag, a.status)) goto epilogue_done;
+        tc_fence_after();
+        uint32_t r0[32], r1[32];
+        const uint32_t col0 = (uint32_t)abuf * kAccCols + (uint32_t)(half * 64);
+        tmem_ld32(tmem + lane_addr + col0, r0);
+        tmem_ld32(tmem + lane_addr + col0 + 32, r1);
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acce0 + 8 * abuf);  // accumulator free for the class after next
+        full_ph ^= 1u << abuf;
+        abuf ^= 1;
+        count_nonzero(r0, cnt);
+        count_nonzero(r1, cnt + 8);
+      }
+      // columns whose pair covers fewer than k-2 classes
+      uint64_t low = 0;
 #pragma unroll
-        for (int j = 0; j < 32; j++) {
-          const uint32_t nz = __uint_as_float(r[j]) > 0.f ? 1u : 0u;
-          cnt[q * 8 + (j >> 2)] += nz << ((j & 3) * 8);
+      for (int j = 0; j < 64; j++)
+        low |= (uint64_t)((int)((cnt[j >> 2] >> ((j & 3) * 8)) & 0xFFu) < a.k - 2) << j;
+      // live edges (u, v) of this thread's row and column half, u < v: the
+      // 64 adjacency bits are gathered with independent loads (the position
+      // of every column vertex in a row comes from one table), then the tests
+      // and failures are whole-mask operations
+      const int u = I * kTile + row;
+      const int base = J * kTile + half * 64;
+      if (u < a.n) {
+        const uint32_t *rowu = a.A + (int64_t)u * a.ldw;
+        const int4 *vi4 = reinterpret_cast<const int4 *>(a.vinfo + base);
+        uint64_t adj = 0;
+#pragma unroll
+        for (int q4 = 0; q4 < 16; q4++) {
+          const int4 w4 = vi4[q4];
+          const int w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+          for (int e = 0; e < 4; e++)
+            if (w[e] >= 0) adj |= (uint64_t)((rowu[w[e] >> 5] >> (w[e] & 31)) & 1u) << (4 * q4 + e);
+        }
+        const uint64_t upper = u < base ? ~0ull : (u - base >= 63 ? 0ull : ~0ull << (u - base + 1));
+        const uint64_t live = adj & upper;
+        my_tests += (unsigned long long)__popcll(live);
+        uint64_t fail = live & low;
+        if (fail) {
+          const int wu = a.vinfo[u];
+          my_fail += (unsigned long long)__popcll(fail);
+          while (fail) {
+            const int j = __ffsll((long long)fail) - 1;
+            fail &= fail - 1;
+            const int v = base + j;
+            const int wv = a.vinfo[v];
+            atomicOr(&a.Edel[(int64_t)u * a.ldw + (wv >> 5)], 1u << (wv & 31));
+            atomicOr(&a.Edel[(int64_t)v * a.ldw + (wu >> 5)], 1u << (wu & 31));
+          }
         }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();  // accumulator read before the next class overwrites it
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-    if (abort_flag) break;
-    // live edges of the tile row u: (u, v) with v in tile J, u < v
-    if (u < a.n) {
-      const int cu = a.col[u];
-      const uint32_t *row = a.A + (int64_t)u * a.ldw;
-      for (int j = 0; j < kTile; j++) {
-        const int v = J * kTile + j;
-        if (v >= a.n || v <= u) continue;
-        const int cv = a.col[v];
-        if (cv == cu) continue;
-        const int iv = v - a.coff[cv];
-        const int wv = (iv >> 5) * a.k + cv;
-        if (!((row[wv] >> (iv & 31)) & 1u)) continue;
-        my_tests++;
-        const int cover = (int)((cnt[j >> 2] >> ((j & 3) * 8)) & 0xFFu);
-        if (cover < a.k - 2) {
-          my_fail++;
-          const int iu = u - a.coff[cu];
-          atomicOr(&a.Edel[(int64_t)u * a.ldw + wv], 1u << (iv & 31));
-          atomicOr(&a.Edel[(int64_t)v * a.ldw + (iu >> 5) * a.k + cu], 1u << (iu & 31));
-        }
-      }
+  epilogue_done:
+    for (int o = 16; o > 0; o >>= 1) {
+      my_fail += __shfl_down_sync(0xffffffffu, my_fail, o);
+      my_tests += __shfl_down_sync(0xffffffffu, my_tests, o);
+    }
+    if (lane == 0) {
+      if (my_fail) atomicAdd(&a.counts[0], my_fail);
+      if (my_tests) atomicAdd(&a.counts[1], my_tests);
     }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    my_fail += __shfl_down_sync(0xffffffffu, my_fail, o);
-    my_tests += __shfl_down_sync(0xffffffffu, my_tests, o);
-  }
-  if (lane == 0) {
-    if (my_fail) atomicAdd(&a.counts[0], my_fail);
-    if (my_tests) atomicAdd(&a.counts[1], my_tests);
-  }
-  if (abort_flag && tid == 0) {
-    // a wait ran out: give the MMAs in flight one more bounded wait before the
-    // tensor memory they write is released
-    uint32_t spins = 0;
-    while (!mbar_try_wait(mb, phase) && ++spins < kSpinLimit) {
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  tc_fence_before();
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u));
+  tc_fence_after();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-// Byte matrix from the current rows: block word j of row x -> bytes
-// 32j .. 32j+31 (0x38 = E4M3 1.0 for a set bit).  Rows are laid out by
-// K-step order: word (c, r) -> step cls_step[c] + r.
-__global__ void expand_kernel(const uint32_t *__restrict__ A, int32_t n, int32_t n_pad, int32_t ldw, int32_t k,
-                              int32_t R, const int32_t *__restrict__ rounds, const int32_t *__restrict__ cls_step,
-                              int32_t ksteps, uint8_t *__restrict__ M) {
-  const int64_t ld = (int64_t)ksteps * kStep;
+// Byte matrix from the current rows, half-step-major (see the top of this
+// file): thread t writes both halves of K-step s = t / n_pad of row
+// x = t % n_pad, so a warp's stores are contiguous.  step_word[s] is the
+// word (r * k + c) of the row that K-step s expands.
+__global__ void expand_kernel(const uint32_t *__restrict__ A, int32_t n, int32_t n_pad, int32_t ldw,
+                              const int32_t *__restrict__ step_word, int32_t ksteps, uint8_t *__restrict__ M) {
   const int64_t total = (int64_t)n_pad * ksteps;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t x = (int32_t)(t / ksteps);
-    const int32_t s = (int32_t)(t - (int64_t)x * ksteps);
-    // class of step s
-    int c = 0;
-    while (c + 1 <= k && cls_step[c + 1] <= s) c++;
-    const int r = s - cls_step[c];
-    const uint32_t word = (x < n && r < rounds[c]) ? A[(int64_t)x * ldw + r * k + c] : 0u;
+    const int32_t s = (int32_t)(t / n_pad);
+    const int32_t x = (int32_t)(t - (int64_t)s * n_pad);
+    const uint32_t word = x < n ? __ldg(A + (int64_t)x * ldw + step_word[s]) : 0u;
     uint32_t out[8];
 #pragma unroll
     for (int q = 0; q < 8; q++) {
-      uint32_t v = 0;
-#pragma unroll
-      for (int b = 0; b < 4; b++) v |= ((word >> (q * 4 + b)) & 1u) ? (0x38u << (8 * b)) : 0u;
-      out[q] = v;
+      // bits 4q .. 4q+3 to bytes: bit j of the nibble lands on bit 8j of the product
+      const uint32_t nib = (word >> (4 * q)) & 0xFu;
+      out[q] = ((nib * 0x00204081u) & 0x01010101u) * 0x38u;
     }
-    uint4 *dst = reinterpret_cast<uint4 *>(M + (int64_t)x * ld + (int64_t)s * kStep);
-    dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
-    dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
+    uint4 *lo = reinterpret_cast<uint4 *>(M + ((int64_t)(2 * s) * n_pad + x) * 16);
+    uint4 *hi = reinterpret_cast<uint4 *>(M + ((int64_t)(2 * s + 1) * n_pad + x) * 16);
+    *lo = make_uint4(out[0], out[1], out[2], out[3]);
+    *hi = make_uint4(out[4], out[5], out[6], out[7]);
   }
 }
 
@@ -359,16 +523,41 @@ static int sms_t() {
   return std::max(sms, 1);
 }
 
+// The driver's tensor-map encoder, found once through the runtime (no link
+// against the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+void *tensor_map_encoder() {
+  static void *fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = p;
+  }
+  return fn;
+}
+
+static EncodeTiledFn encode_tiled() { return reinterpret_cast<EncodeTiledFn>(tensor_map_encoder()); }
+
 // Per-graph buffers of the tensor path (allocated on first use).
 struct TensorBufs {
   uint8_t *M = nullptr;
   int32_t n_pad = 0, ksteps = 0;
   int32_t *cls_step = nullptr;
+  int32_t *step_word = nullptr;
   int32_t *col = nullptr;
+  int32_t *vinfo = nullptr;
   uint32_t *Edel = nullptr;
   int2 *tiles = nullptr;
   int32_t n_tiles = 0;
   unsigned long long *counts = nullptr;
+  CUtensorMap tmap;
 };
 
 static kz_status tensor_prepare(kz_graph g, TensorBufs &b, cudaStream_t s) {
@@ -376,27 +565,64 @@ static kz_status tensor_prepare(kz_graph g, TensorBufs &b, cudaStream_t s) {
   std::vector<int32_t> cs((size_t)g->k + 1, 0);
   for (int c = 0; c < g->k; c++) cs[c + 1] = cs[c] + g->rounds[c];
   b.ksteps = std::max(cs[g->k], 1);
+  std::vector<int32_t> sw((size_t)b.ksteps, 0);
+  for (int c = 0; c < g->k; c++)
+    for (int r = 0; r < g->rounds[c]; r++) sw[cs[c] + r] = r * g->k + c;
   const size_t mbytes = (size_t)b.n_pad * b.ksteps * kStep;
   KZ_TRY(graph_alloc(g, &b.M, mbytes, s));
+  if (reinterpret_cast<uintptr_t>(b.M) % 16 != 0) return KZ_ERR_CUDA;  // TMA needs a 16-byte aligned base
   KZ_TRY(graph_alloc(g, &b.cls_step, (size_t)g->k + 1, s));
   KZ_CUDA_TRY(cudaMemcpyAsync(b.cls_step, cs.data(), sizeof(int32_t) * (g->k + 1), cudaMemcpyHostToDevice, s));
+  KZ_TRY(graph_alloc(g, &b.step_word, sw.size(), s));
+  KZ_CUDA_TRY(cudaMemcpyAsync(b.step_word, sw.data(), sizeof(int32_t) * sw.size(), cudaMemcpyHostToDevice, s));
   std::vector<int32_t> col_new((size_t)std::max(g->n, 1));
   for (int c = 0; c < g->k; c++)
     for (int x = g->coff[c]; x < g->coff[c + 1]; x++) col_new[x] = c;
   KZ_TRY(graph_alloc(g, &b.col, col_new.size(), s));
   KZ_CUDA_TRY(cudaMemcpyAsync(b.col, col_new.data(), sizeof(int32_t) * col_new.size(), cudaMemcpyHostToDevice, s));
+  std::vector<int32_t> vinfo((size_t)b.n_pad, -1);
+  for (int c = 0; c < g->k; c++)
+    for (int x = g->coff[c]; x < g->coff[c + 1]; x++) {
+      const int ix = x - g->coff[c];
+      vinfo[x] = (((ix >> 5) * g->k + c) << 5) | (ix & 31);
+    }
+  KZ_TRY(graph_alloc(g, &b.vinfo, vinfo.size(), s));
+  KZ_CUDA_TRY(cudaMemcpyAsync(b.vinfo, vinfo.data(), sizeof(int32_t) * vinfo.size(), cudaMemcpyHostToDevice, s));
   KZ_TRY(graph_alloc(g, &b.Edel, (size_t)g->n * g->ldw, s));
   KZ_CUDA_TRY(cudaMemsetAsync(b.Edel, 0, (size_t)g->n * g->ldw * 4, s));
+  // Upper-triangle tiles in super-blocks of S x S tiles (S^2 about the number
+  // of SMs).  CTA b takes tiles b, b + grid, ..., so the tiles in flight at
+  // one time lie in about one super-block: about 2S distinct row tiles, whose
+  // K-steps are read from HBM once and then shared through L2 by the CTAs
+  // that stream the same K-steps at about the same time.
   const int T = b.n_pad / kTile;
+  int S = 1;
+  while ((S + 1) * (S + 1) <= kCtasPerSm * sms_t()) S++;
   std::vector<int2> tiles;
-  for (int i = 0; i < T; i++)
-    for (int j = i; j < T; j++) tiles.push_back(make_int2(i, j));
+  for (int P = 0; P < T; P += S)
+    for (int Q = P; Q < T; Q += S)
+      for (int i = P; i < std::min(P + S, T); i++)
+        for (int j = std::max(i, Q); j < std::min(Q + S, T); j++) tiles.push_back(make_int2(i, j));
   b.n_tiles = (int32_t)tiles.size();
   KZ_TRY(graph_alloc(g, &b.tiles, std::max<size_t>(tiles.size(), 1), s));
   if (!tiles.empty())
     KZ_CUDA_TRY(cudaMemcpyAsync(b.tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, s));
   KZ_TRY(graph_alloc(g, &b.counts, 4, s));
   KZ_CUDA_TRY(cudaMemsetAsync(b.counts, 0, 32, s));
+  // M as a 2-D tensor of 8-byte elements {2 n_pad per half-step plane,
+  // 2 ksteps planes}; one box {256, 2 kStageSteps} is one pipeline stage of
+  // 128 rows (16 KB: large boxes keep the TMA unit's per-copy cost small).
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return KZ_ERR_UNSUPPORTED;
+  const cuuint64_t dims[2] = {(cuuint64_t)2 * b.n_pad, (cuuint64_t)2 * b.ksteps};
+  const cuuint64_t strides[1] = {(cuuint64_t)b.n_pad * 16};
+  const cuuint32_t box[2] = {2 * kTile, 2 * kStageSteps};
+  const cuuint32_t estr[2] = {1, 1};
+  std::memset(&b.tmap, 0, sizeof(b.tmap));
+  if (enc(&b.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, b.M, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+      CUDA_SUCCESS)
+    return KZ_ERR_CUDA;
   KZ_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors die here
   return KZ_OK;
 }
@@ -416,12 +642,13 @@ kz_status tensor_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
   const int64_t max_sweeps = opt.max_sweeps > 0 ? opt.max_sweeps : (int64_t)g->n + g->m + 1;
   KZ_TRY(bitset_begin_run(g, max_sweeps, s));
   if (g->n == 0) return KZ_OK;
-  const size_t smem = (size_t)2 * kMaxStepsPerStage * 4096;
-  static bool configured = false;
-  if (!configured) {
+  int dev = 0;
+  KZ_CUDA_TRY(cudaGetDevice(&dev));
+  static bool configured[64] = {};
+  if (dev < 64 && !configured[dev]) {
     KZ_CUDA_TRY(cudaFuncSetAttribute((const void *)tensor_edge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-    configured = true;
+                                     (int)kSmemBytes));
+    configured[dev] = true;
   }
   const int sms = sms_t();
   for (;;) {
@@ -430,26 +657,21 @@ kz_status tensor_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
     KZ_CUDA_TRY(cudaStreamSynchronize(s));
     const uint32_t *A = g->A[cur & 1];
     uint32_t *An = g->A[(cur & 1) ^ 1];
-    expand_kernel<<<8 * sms, 256, 0, s>>>(A, g->n, b.n_pad, g->ldw, g->k, g->R, g->d_rounds, b.cls_step, b.ksteps,
-                                          b.M);
+    expand_kernel<<<8 * sms, 256, 0, s>>>(A, g->n, b.n_pad, g->ldw, b.step_word, b.ksteps, b.M);
     TensorArgs a;
-    a.M = b.M;
     a.n = g->n;
-    a.n_pad = b.n_pad;
-    a.ksteps = b.ksteps;
+    a.k = g->k;
     a.cls_step = b.cls_step;
     a.A = A;
     a.ldw = g->ldw;
-    a.k = g->k;
-    a.col = b.col;
-    a.coff = g->d_coff;
+    a.vinfo = b.vinfo;
     a.Edel = b.Edel;
     a.tiles = b.tiles;
     a.n_tiles = b.n_tiles;
     a.counts = b.counts;
     a.status = &g->st->status;
-    const int grid = std::max(1, std::min(b.n_tiles, sms));
-    tensor_edge_kernel<<<grid, kThreads, smem, s>>>(a);
+    const int grid = std::max(1, std::min(b.n_tiles, kCtasPerSm * sms));
+    tensor_edge_kernel<<<grid, kThreads, kSmemBytes, s>>>(b.tmap, a);
     tensor_commit_kernel<<<8 * sms, 256, 0, s>>>(A, An, b.Edel, g->V[cur & 1], g->V[(cur & 1) ^ 1], g->n, g->ldw,
                                                  g->k, g->R, b.col, g->d_coff, g->d_rounds, g->d_blocks,
                                                  (int32_t)g->blocks.size(), g->v_sweep, g->st, b.counts);

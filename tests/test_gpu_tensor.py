@@ -45,3 +45,19 @@ def test_tensor_matches_bitset_on_batch_members():
         b = gpu_run(g, path="bitset", dense=True)
         assert np.array_equal(a["alive"], b["alive"]) and np.array_equal(a["edges"], b["edges"])
         assert a["stats"]["sweeps"] == b["stats"]["sweeps"]
+
+
+@pytest.mark.parametrize("seed,n,k,p", [(84, 2300, 8, 0.1), (86, 2300, 4, 0.04), (81, 2300, 8, 0.3)])
+def test_tensor_more_tiles_than_ctas(seed, n, k, p):
+    # 18 x 18 tiles (171 upper-triangle tiles: more than one per SM), classes
+    # of up to 18 K-steps (several pipeline stages per class), cascades over
+    # several sweeps, and a graph where nothing is deleted
+    g = synth.tiny_random(seed, n, k, p, planted=True)
+    assert_parity(g, gpu_run(g, path="tensor"))
+
+
+@pytest.mark.parametrize("layout", [0, 1, 2])
+def test_mma_probe_runs(layout):
+    import paper_2212_00574_gb300 as kz
+    flops, ms = kz.kz_probe_mma_throughput(layout, 128, 1)
+    assert flops > 0 and ms > 0
