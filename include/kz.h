@@ -71,7 +71,9 @@ typedef enum {
 
 /* Which kernels evaluate the rules (kz_options.path). */
 typedef enum {
-    KZ_PATH_AUTO = 0,   /* chosen by the library's cost model */
+    KZ_PATH_AUTO = 0,   /* SPARSE for a graph loaded as an edge list without bitset rows; SMALL up to 64
+                           vertices; otherwise BITSET or TENSOR from a table of measured times to fixpoint
+                           over n, k and edge density (TENSOR for larger, sparser graphs) */
     KZ_PATH_BITSET = 1, /* per-colour bitset rows in HBM, warp-per-block-pair sweep kernel */
     KZ_PATH_SMALL = 2,  /* whole fixpoint inside one CTA, graph held in shared memory */
     KZ_PATH_SPARSE = 3, /* CSR adjacency, per-edge colour masks from triangle enumeration */

@@ -259,9 +259,36 @@ static kz_status read_options(const kz_options *opt, kz_options &o) {
 // all launch and barrier); anything larger is spread over the GPU.
 constexpr int kSmallAutoMaxN = 64;
 
+// Bitset sweep or tensor-core form for a graph held as bitset rows, from a
+// table measured on GB300 (time to fixpoint of both paths on seeded
+// k-partite graphs with a planted clique, n in {2048, 4096, 8192, 16384},
+// k in {12, 24}, density in {0.05, 0.1, 0.2, 0.3, 0.45}): 1 where the tensor
+// form was faster.  A graph falls in the bin of the nearest measured point.
+// The bitset sweep settles most pairs from the first word of each class when
+// common neighbours are plentiful (dense graphs); the tensor form does the
+// same work whatever the density, so it wins where pairs need many words or
+// sweeps (sparser graphs, larger n).
+constexpr int kTensorTable[4][2][5] = {
+    // density bins: < 0.075, < 0.15, < 0.25, < 0.375, >= 0.375
+    {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}},  // n < 3072 (k < 18, k >= 18)
+    {{0, 1, 1, 0, 0}, {0, 0, 1, 0, 0}},  // n < 6144
+    {{1, 1, 1, 0, 0}, {0, 1, 1, 0, 0}},  // n < 12288
+    {{1, 1, 0, 0, 0}, {1, 1, 1, 0, 0}},  // larger
+};
+
+static bool tensor_preferred(kz_graph g) {
+  if (g->k > 64 || g->k < 3) return false;
+  const int nb = g->n < 3072 ? 0 : g->n < 6144 ? 1 : g->n < 12288 ? 2 : 3;
+  const int kb = g->k < 18 ? 0 : 1;
+  const double d = g->density;
+  const int db = d < 0.075 ? 0 : d < 0.15 ? 1 : d < 0.25 ? 2 : d < 0.375 ? 3 : 4;
+  return kTensorTable[nb][kb][db] != 0;
+}
+
 static int auto_path(kz_graph g) {
   if (!g->has_bitset) return KZ_PATH_SPARSE;
-  return g->n <= kSmallAutoMaxN && cta_fits_shared(g) ? KZ_PATH_SMALL : KZ_PATH_BITSET;
+  if (g->n <= kSmallAutoMaxN && cta_fits_shared(g)) return KZ_PATH_SMALL;
+  return tensor_preferred(g) ? KZ_PATH_TENSOR : KZ_PATH_BITSET;
 }
 
 static kz_status run_one(kz_graph g, const kz_options &o, int path) {

@@ -711,6 +711,7 @@ kz_status bitset_finish_load(kz_graph g, cudaStream_t s) {
       tot += sz;
     }
     const double density = cross > 0 ? (double)g->m / cross : 0.0;
+    g->density = density;
     g->fast_half = density >= kFastHalfDensity;
     g->form = density >= kHalfDensity ? kFormHalf
               : (density < kTwoPlaneDensity && g->R >= 2 && g->k <= 32) ? kFormTwo

@@ -166,6 +166,7 @@ struct kz_graph_s {
   // change tag names the current sweep (false after any other path or a
   // conversion wrote the rows; the next bitset pass then writes every word)
   bool ab_synced = false;
+  double density = 0;                // edges / pairs of vertices in different classes, at load
   int32_t form = 0;                   // the sweep kernels' first test chosen by density
   bool fast_half = false;             // half-word form: fold whole blocks first (very dense graphs)
   kz::DevState *st = nullptr;

@@ -16,21 +16,22 @@
 // the box's inner extent is the whole contiguous run) then lands in shared
 // memory as four consecutive canonical no-swizzle K-major MMA operands:
 // 8-row x 16-byte core matrices 128 bytes apart along M/N and 2048 bytes
-// apart along K, one K-step every 4096 bytes.  Large boxes matter: the TMA
-// probe measures 35 bytes per clock and SM for 4 KB boxes against 66 for
-// 16 KB boxes with the same bytes in flight.
+// apart along K, one K-step every 4096 bytes.  The B operand's box spans two
+// such tiles, so its 256 rows lie at one uniform stride (K halves 4096 bytes
+// apart).  Large boxes matter: the TMA probe measures 35 bytes per clock and
+// SM for 4 KB boxes against 66 for 16 KB boxes with the same bytes in flight.
 //
-// Kernel (two CTAs per SM, persistent over upper-triangle 128 x 128 tiles;
-// the MMA probe measures one CTA's M = N = 128 stream at half the tensor
-// pipe's rate, two CTAs at the full rate):
+// Kernel (one CTA per SM, persistent over tiles of 128 A rows x 256 B rows;
+// the MMA probe measures one CTA's M = 128, N = 256 stream at the full fp8
+// rate, an N = 128 stream at half of it):
 //   warp 0      TMA producer: fills a ring of pipeline stages (four K-steps
-//               of both tiles each, one box per tile) as soon as the MMAs
-//               free them;
+//               of both operands, one box each; a class's last partial stage
+//               one box per K-step) as soon as the MMAs free them;
 //   warp 1      MMA issuer: one thread issues tcgen05.mma.kind::f8f6f4
-//               (M = N = 128, K = 32, fp32 accumulation in TMEM, exact for
-//               0/1 products) over a class's K-steps, alternating between
-//               two TMEM accumulators so that the next class runs while the
-//               previous one is read;
+//               (M = 128, N = 256, K = 32, fp32 accumulation in TMEM, exact
+//               for 0/1 products) over a class's K-steps, alternating
+//               between two TMEM accumulators (all 512 columns) so that the
+//               next class runs while the previous one is read;
 //   warps 2-9   epilogue: tcgen05.ld of the class's counts, one 8-bit
 //               counter per pair of classes with a non-zero count; after the
 //               tile's last class, live edges below k-2 are marked in a
@@ -54,18 +55,19 @@
 namespace kz {
 namespace tensor {
 
-constexpr int kTile = 128;                       // rows per tile side (MMA M = N = 128)
+constexpr int kTile = 128;                       // A rows per tile (MMA M)
+constexpr int kTileN = 256;                      // B rows per tile (MMA N)
 constexpr int kStep = 32;                        // bytes (E4M3 elements) per K-step
-constexpr int kStepBytes = kTile * kStep;        // one operand, one K-step: 4096 bytes
+constexpr int kStepA = kTile * kStep;            // A operand, one K-step: 4 KB
+constexpr int kStepB = kTileN * kStep;           // B operand, one K-step: 8 KB
 constexpr int kStageSteps = 4;                   // K-steps per pipeline stage (class runs are chunked)
-constexpr int kStages = 3;                       // pipeline depth (two CTAs per SM share the rest)
-constexpr int kCtasPerSm = 2;                    // one CTA's M = N = 128 MMA stream fills half the tensor pipe
-constexpr int kOperandBytes = kStageSteps * kStepBytes;   // 16 KB
-constexpr int kStageBytes = 2 * kOperandBytes;            // A and B tiles
-constexpr int kEpiWarps = 8;                     // two per TMEM lane quarter, 64 columns each
+constexpr int kStages = 4;                       // pipeline depth
+constexpr int kABytes = kStageSteps * kStepA;    // 16 KB
+constexpr int kStageBytes = kStageSteps * (kStepA + kStepB);  // 48 KB
+constexpr int kEpiWarps = 8;                     // two per TMEM lane quarter, 128 columns each
 constexpr int kThreads = (2 + kEpiWarps) * 32;
-constexpr uint32_t kAccCols = 128;               // fp32 columns per accumulator
-constexpr uint32_t kTmemCols = 2 * kAccCols;     // double-buffered accumulator
+constexpr uint32_t kAccCols = kTileN;            // fp32 columns per accumulator
+constexpr uint32_t kTmemCols = 2 * kAccCols;     // double-buffered accumulator: all 512 columns
 constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 1024;  // + alignment slack
 constexpr uint64_t kWaitNs = 4000000000ull;      // 4 s per wait before giving up
 
@@ -79,13 +81,15 @@ __device__ __forceinline__ uint64_t globaltimer() {
   return t;
 }
 
-// Shared-memory matrix descriptor for the K-major, no-swizzle operand one TMA
-// box produces: core matrices (8 rows x 16 bytes) 2048 bytes apart along K
-// (leading byte offset) and 128 bytes apart along M/N (stride byte offset).
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor of one K-step of a K-major, no-swizzle
+// operand as the TMA boxes lay it out: core matrices (8 rows x 16 bytes) 128
+// bytes apart along M/N (stride byte offset) and rows x 16 bytes apart along
+// K (leading byte offset: the second 16-byte half of the K-step follows all
+// rows of the first).
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t rows) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);        // start address
-  d |= (uint64_t)(2048u >> 4) << 16;                // leading byte offset (K direction)
+  d |= (uint64_t)((rows * 16u) >> 4) << 16;         // leading byte offset (K direction)
   d |= (uint64_t)(128u >> 4) << 32;                 // stride byte offset (8-row groups)
   d |= (uint64_t)1 << 46;                           // descriptor version
   // base offset 0, relative LBO mode, no swizzle (bits 61-63 = 0)
@@ -93,14 +97,14 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
 }
 
 // Instruction descriptor: dense, D = f32, A = B = E4M3, both K-major,
-// N = 128, M = 128.
+// N = 256, M = 128.
 __device__ __forceinline__ uint32_t make_idesc() {
   uint32_t d = 0;
-  d |= 1u << 4;              // D format f32
-  d |= 0u << 7;              // A format E4M3
-  d |= 0u << 10;             // B format E4M3
-  d |= (128u >> 3) << 17;    // N >> 3
-  d |= (128u >> 4) << 24;    // M >> 4
+  d |= 1u << 4;                        // D format f32
+  d |= 0u << 7;                        // A format E4M3
+  d |= 0u << 10;                       // B format E4M3
+  d |= ((uint32_t)kTileN >> 3) << 17;  // N >> 3
+  d |= ((uint32_t)kTile >> 4) << 24;   // M >> 4
   return d;
 }
 
@@ -132,6 +136,19 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
 }
 
+// try_wait with a suspend-time hint: a waiting thread sleeps in hardware until
+// the phase completes (or 1 ms passes) instead of polling shared memory.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000000;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -144,17 +161,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
   return ok != 0;
 }
 
-// One TMA box of the byte matrix: half-steps half0 .. half0 + 2 kStageSteps - 1
-// (kStageSteps K-steps) of the 128 rows starting at row0 (x counts 8-byte
-// elements: 2 per row).  Half-steps past the end of the matrix read as zero;
-// those of the next class are loaded but not used.
-__device__ __forceinline__ void tma_load_step(uint32_t dst, const CUtensorMap *map, uint32_t mbar, int32_t row0,
-                                              int32_t half0) {
+// TMA loads of the byte matrix (x counts 8-byte elements: 2 per row).
+// A operand: 2-D map {2 n_pad, 2 ksteps}; box of 128 rows and 2 or 8
+// half-steps (one K-step or a whole stage).  Half-steps past the end of the
+// matrix read as zero; those of the next class are loaded but not used.
+__device__ __forceinline__ void tma_load_a(uint32_t dst, const CUtensorMap *map, uint32_t mbar, int32_t row0,
+                                           int32_t half0) {
   const int32_t x = row0 * 2;
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
           dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar), "r"(x), "r"(half0)
+      : "memory");
+}
+// B operand: 3-D map {256 elements (one 128-row tile), n_pad / 128 tiles,
+// 2 ksteps}; box of 2 tiles (256 rows, contiguous in shared memory) and 2 or
+// 8 half-steps.
+__device__ __forceinline__ void tma_load_b(uint32_t dst, const CUtensorMap *map, uint32_t mbar, int32_t tile0,
+                                           int32_t half0) {
+  const int32_t x = 0;
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar), "r"(x), "r"(tile0), "r"(half0)
       : "memory");
 }
 
@@ -165,7 +194,7 @@ __device__ __forceinline__ void tma_load_step(uint32_t dst, const CUtensorMap *m
 __device__ __noinline__ bool warp_wait(uint32_t mbar, uint32_t parity, volatile int *abort_flag, int32_t *status) {
   const uint64_t t0 = globaltimer();
   for (uint32_t i = 0;; i++) {
-    const bool ok = mbar_try_wait(mbar, parity);
+    const bool ok = mbar_try_wait_hint(mbar, parity);
     if (__all_sync(0xffffffffu, ok)) return true;
     if ((i & 15u) == 15u) {
       int stop = 0;
@@ -220,7 +249,7 @@ struct TensorArgs {
   int32_t ldw;
   const int32_t *vinfo;    // n_pad: (word << 5 | bit) of vertex x in any row, -1 past n
   uint32_t *Edel;          // deletion bitmap, rows x ldw (zeroed)
-  const int2 *tiles;       // (I, J) tile pairs, I <= J
+  const int2 *tiles;       // (I, J): A rows 128 I .., B rows 256 J .., 2 J + 1 >= I
   int32_t n_tiles;
   unsigned long long *counts;  // [0] failing edges [1] live edges tested
   int32_t *status;
@@ -234,7 +263,12 @@ __device__ __forceinline__ void count_nonzero(const uint32_t (&r)[32], uint32_t 
   for (int j = 0; j < 32; j++) cnt[j >> 2] += min(r[j], 1u) << ((j & 3) * 8);
 }
 
-__global__ void __launch_bounds__(kThreads, kCtasPerSm) tensor_edge_kernel(const __grid_constant__ CUtensorMap tmap,
+// The tensor maps of the byte matrix: a whole stage or one K-step, per operand.
+struct TensorMaps {
+  CUtensorMap a_stage, a_step, b_stage, b_step;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) tensor_edge_kernel(const __grid_constant__ TensorMaps maps,
                                                                   TensorArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bars[2 * kStages + 5];
@@ -279,7 +313,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) tensor_edge_kernel(const
     uint32_t filled = 0, fill_parity = 0;  // per stage: issued at least once / parity of its last fill
     for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
       const int I = a.tiles[t].x, J = a.tiles[t].y;
-      const bool diag = I == J;
       for (int c = 0; c < a.k; c++) {
         const int sb = a.cls_step[c], se = a.cls_step[c + 1];
         for (int s0 = sb; s0 < se; s0 += kStageSteps) {
@@ -287,10 +320,18 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) tensor_edge_kernel(const
           if (!warp_wait(empty0 + 8 * stage, ph ^ 1u, abort_flag, a.status)) goto producer_done;
           if (lane == 0) {
             const uint32_t fb = full0 + 8 * stage;
-            mbar_expect_tx(fb, (uint32_t)(kOperandBytes * (diag ? 1 : 2)));
-            const uint32_t sA = sbase + stage * kStageBytes, sB = sA + kOperandBytes;
-            tma_load_step(sA, &tmap, fb, I * kTile, 2 * s0);
-            if (!diag) tma_load_step(sB, &tmap, fb, J * kTile, 2 * s0);
+            const uint32_t sA = sbase + stage * kStageBytes, sB = sA + kABytes;
+            if (ns == kStageSteps) {
+              mbar_expect_tx(fb, (uint32_t)kStageBytes);
+              tma_load_a(sA, &maps.a_stage, fb, I * kTile, 2 * s0);
+              tma_load_b(sB, &maps.b_stage, fb, 2 * J, 2 * s0);
+            } else {  // a class's last, partial stage: one box per K-step
+              mbar_expect_tx(fb, (uint32_t)(ns * (kStepA + kStepB)));
+              for (int j = 0; j < ns; j++) {
+                tma_load_a(sA + j * kStepA, &maps.a_step, fb, I * kTile, 2 * (s0 + j));
+                tma_load_b(sB + j * kStepB, &maps.b_step, fb, 2 * J, 2 * (s0 + j));
+              }
+            }
           }
           __syncwarp();
           filled |= 1u << stage;
@@ -314,8 +355,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) tensor_edge_kernel(const
     int stage = 0, abuf = 0;
     uint32_t ph = 0, empty_ph = 0;  // bit b: parity of accumulator b's next release
     for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
-      const int I = a.tiles[t].x, J = a.tiles[t].y;
-      const bool diag = I == J;
       for (int c = 0; c < a.k; c++) {
         const int sb = a.cls_step[c], se = a.cls_step[c + 1];
         if (se <= sb) continue;
@@ -327,10 +366,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) tensor_edge_kernel(const
           if (!warp_wait(full0 + 8 * stage, ph, abort_flag, a.status)) goto mma_done;
           tc_fence_after();
           if (lane == 0) {
-            const uint32_t sA = sbase + stage * kStageBytes, sB = diag ? sA : sA + kOperandBytes;
+            const uint32_t sA = sbase + stage * kStageBytes, sB = sA + kABytes;
             for (int j = 0; j < ns; j++)
-              mma_f8(tmem + (uint32_t)abuf * kAccCols, make_desc(sA + j * kStepBytes), make_desc(sB + j * kStepBytes),
-                     idesc, (s0 > sb || j > 0) ? 1u : 0u);
+              mma_f8(tmem + (uint32_t)abuf * kAccCols, make_desc(sA + j * kStepA, kTile),
+                     make_desc(sB + j * kStepB, kTileN), idesc, (s0 > sb || j > 0) ? 1u : 0u);
             mma_commit(empty0 + 8 * stage);  // stage free once these MMAs have read it
           }
           __syncwarp();
@@ -355,7 +394,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) tensor_edge_kernel(const
   } else {
     // ---------------- epilogue ----------------
     const int q = warp & 3;              // TMEM lane quarter this warp may access
-    const int half = (warp - 2) >> 2;    // column half of the tile
+    const int half = (warp - 2) >> 2;    // 128-column half of the tile
     const int row = q * 32 + lane;
     const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
     int abuf = 0;
@@ -363,56 +402,62 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) tensor_edge_kernel(const
     unsigned long long my_fail = 0, my_tests = 0;
     for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
       const int I = a.tiles[t].x, J = a.tiles[t].y;
-      uint32_t cnt[16];  // 64 column counters, 8 bits each
+      uint32_t cnt[32];  // 128 column counters, 8 bits each
 #pragma unroll
-      for (int i = 0; i < 16; i++) cnt[i] = 0;
+      for (int i = 0; i < 32; i++) cnt[i] = 0;
       for (int c = 0; c < a.k; c++) {
         const int sb = a.cls_step[c], se = a.cls_step[c + 1];
         if (se <= sb) continue;
         if (!warp_wait(accf0 + 8 * abuf, (full_ph >> abuf) & 1u, abort_flag, a.status)) goto epilogue_done;
         tc_fence_after();
+        const uint32_t col0 = (uint32_t)abuf * kAccCols + (uint32_t)(half * 128);
         uint32_t r0[32], r1[32];
-        const uint32_t col0 = (uint32_t)abuf * kAccCols + (uint32_t)(half * 64);
         tmem_ld32(tmem + lane_addr + col0, r0);
         tmem_ld32(tmem + lane_addr + col0 + 32, r1);
+        tmem_wait_ld();
+        count_nonzero(r0, cnt);
+        count_nonzero(r1, cnt + 8);
+        tmem_ld32(tmem + lane_addr + col0 + 64, r0);
+        tmem_ld32(tmem + lane_addr + col0 + 96, r1);
         tmem_wait_ld();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acce0 + 8 * abuf);  // accumulator free for the class after next
         full_ph ^= 1u << abuf;
         abuf ^= 1;
-        count_nonzero(r0, cnt);
-        count_nonzero(r1, cnt + 8);
+        count_nonzero(r0, cnt + 16);
+        count_nonzero(r1, cnt + 24);
       }
-      // columns whose pair covers fewer than k-2 classes
-      uint64_t low = 0;
-#pragma unroll
-      for (int j = 0; j < 64; j++)
-        low |= (uint64_t)((int)((cnt[j >> 2] >> ((j & 3) * 8)) & 0xFFu) < a.k - 2) << j;
-      // live edges (u, v) of this thread's row and column half, u < v: the
-      // 64 adjacency bits are gathered with independent loads (the position
-      // of every column vertex in a row comes from one table), then the tests
-      // and failures are whole-mask operations
+      // live edges (u, v) of this thread's row and column half, u < v, in two
+      // groups of 64 columns: the adjacency bits are gathered with independent
+      // loads (the position of every column vertex in a row comes from one
+      // table), then the tests and failures are whole-mask operations
       const int u = I * kTile + row;
-      const int base = J * kTile + half * 64;
       if (u < a.n) {
         const uint32_t *rowu = a.A + (int64_t)u * a.ldw;
-        const int4 *vi4 = reinterpret_cast<const int4 *>(a.vinfo + base);
-        uint64_t adj = 0;
+        const int wu = a.vinfo[u];
 #pragma unroll
-        for (int q4 = 0; q4 < 16; q4++) {
-          const int4 w4 = vi4[q4];
-          const int w[4] = {w4.x, w4.y, w4.z, w4.w};
+        for (int g = 0; g < 2; g++) {
+          // columns whose pair covers fewer than k-2 classes
+          uint64_t low = 0;
 #pragma unroll
-          for (int e = 0; e < 4; e++)
-            if (w[e] >= 0) adj |= (uint64_t)((rowu[w[e] >> 5] >> (w[e] & 31)) & 1u) << (4 * q4 + e);
-        }
-        const uint64_t upper = u < base ? ~0ull : (u - base >= 63 ? 0ull : ~0ull << (u - base + 1));
-        const uint64_t live = adj & upper;
-        my_tests += (unsigned long long)__popcll(live);
-        uint64_t fail = live & low;
-        if (fail) {
-          const int wu = a.vinfo[u];
+          for (int j = 0; j < 64; j++)
+            low |= (uint64_t)((int)((cnt[16 * g + (j >> 2)] >> ((j & 3) * 8)) & 0xFFu) < a.k - 2) << j;
+          const int base = J * kTileN + half * 128 + g * 64;
+          const int4 *vi4 = reinterpret_cast<const int4 *>(a.vinfo + base);
+          uint64_t adj = 0;
+#pragma unroll
+          for (int q4 = 0; q4 < 16; q4++) {
+            const int4 w4 = vi4[q4];
+            const int w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+              if (w[e] >= 0) adj |= (uint64_t)((rowu[w[e] >> 5] >> (w[e] & 31)) & 1u) << (4 * q4 + e);
+          }
+          const uint64_t upper = u < base ? ~0ull : (u - base >= 63 ? 0ull : ~0ull << (u - base + 1));
+          const uint64_t live = adj & upper;
+          my_tests += (unsigned long long)__popcll(live);
+          uint64_t fail = live & low;
           my_fail += (unsigned long long)__popcll(fail);
           while (fail) {
             const int j = __ffsll((long long)fail) - 1;
@@ -557,11 +602,11 @@ struct TensorBufs {
   int2 *tiles = nullptr;
   int32_t n_tiles = 0;
   unsigned long long *counts = nullptr;
-  CUtensorMap tmap;
+  TensorMaps maps;
 };
 
 static kz_status tensor_prepare(kz_graph g, TensorBufs &b, cudaStream_t s) {
-  b.n_pad = (g->n + kTile - 1) / kTile * kTile;
+  b.n_pad = (g->n + kTileN - 1) / kTileN * kTileN;
   std::vector<int32_t> cs((size_t)g->k + 1, 0);
   for (int c = 0; c < g->k; c++) cs[c + 1] = cs[c] + g->rounds[c];
   b.ksteps = std::max(cs[g->k], 1);
@@ -590,39 +635,54 @@ static kz_status tensor_prepare(kz_graph g, TensorBufs &b, cudaStream_t s) {
   KZ_CUDA_TRY(cudaMemcpyAsync(b.vinfo, vinfo.data(), sizeof(int32_t) * vinfo.size(), cudaMemcpyHostToDevice, s));
   KZ_TRY(graph_alloc(g, &b.Edel, (size_t)g->n * g->ldw, s));
   KZ_CUDA_TRY(cudaMemsetAsync(b.Edel, 0, (size_t)g->n * g->ldw * 4, s));
-  // Upper-triangle tiles in super-blocks of S x S tiles (S^2 about the number
-  // of SMs).  CTA b takes tiles b, b + grid, ..., so the tiles in flight at
-  // one time lie in about one super-block: about 2S distinct row tiles, whose
-  // K-steps are read from HBM once and then shared through L2 by the CTAs
-  // that stream the same K-steps at about the same time.
-  const int T = b.n_pad / kTile;
+  // Tiles (I, J): A rows 128 I .. 128 I + 127 against B rows 256 J ..
+  // 256 J + 255, for every J that holds a column above row 128 I (2 J + 1 >=
+  // I).  They run in super-blocks of 2S x S tiles (2 S^2 about the number of
+  // SMs): CTA b takes tiles b, b + grid, ..., so the tiles in flight at one
+  // time lie in about one super-block, whose rows' K-steps are read from HBM
+  // once and then shared through L2 by the CTAs that stream the same K-steps
+  // at about the same time.
+  const int TI = b.n_pad / kTile, TJ = b.n_pad / kTileN;
   int S = 1;
-  while ((S + 1) * (S + 1) <= kCtasPerSm * sms_t()) S++;
+  while (2 * (S + 1) * (S + 1) <= sms_t()) S++;
   std::vector<int2> tiles;
-  for (int P = 0; P < T; P += S)
-    for (int Q = P; Q < T; Q += S)
-      for (int i = P; i < std::min(P + S, T); i++)
-        for (int j = std::max(i, Q); j < std::min(Q + S, T); j++) tiles.push_back(make_int2(i, j));
+  for (int P = 0; P < TI; P += 2 * S)
+    for (int Q = P / 2 / S * S; Q < TJ; Q += S)
+      for (int i = P; i < std::min(P + 2 * S, TI); i++)
+        for (int j = std::max(i / 2, Q); j < std::min(Q + S, TJ); j++) tiles.push_back(make_int2(i, j));
   b.n_tiles = (int32_t)tiles.size();
   KZ_TRY(graph_alloc(g, &b.tiles, std::max<size_t>(tiles.size(), 1), s));
   if (!tiles.empty())
     KZ_CUDA_TRY(cudaMemcpyAsync(b.tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, s));
   KZ_TRY(graph_alloc(g, &b.counts, 4, s));
   KZ_CUDA_TRY(cudaMemsetAsync(b.counts, 0, 32, s));
-  // M as a 2-D tensor of 8-byte elements {2 n_pad per half-step plane,
-  // 2 ksteps planes}; one box {256, 2 kStageSteps} is one pipeline stage of
-  // 128 rows (16 KB: large boxes keep the TMA unit's per-copy cost small).
+  // M as 8-byte elements.  A operand: 2-D {2 n_pad per half-step plane,
+  // 2 ksteps planes}, boxes of 128 rows.  B operand: 3-D {256 elements (a
+  // 128-row tile), n_pad / 128 tiles, 2 ksteps planes}, boxes of two tiles,
+  // so 256 rows land contiguously.  Stage boxes hold 8 half-steps (large
+  // boxes keep the TMA unit's per-copy cost small), step boxes 2.
   EncodeTiledFn enc = encode_tiled();
   if (!enc) return KZ_ERR_UNSUPPORTED;
-  const cuuint64_t dims[2] = {(cuuint64_t)2 * b.n_pad, (cuuint64_t)2 * b.ksteps};
-  const cuuint64_t strides[1] = {(cuuint64_t)b.n_pad * 16};
-  const cuuint32_t box[2] = {2 * kTile, 2 * kStageSteps};
-  const cuuint32_t estr[2] = {1, 1};
-  std::memset(&b.tmap, 0, sizeof(b.tmap));
-  if (enc(&b.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, b.M, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
-      CUDA_SUCCESS)
-    return KZ_ERR_CUDA;
+  std::memset(&b.maps, 0, sizeof(b.maps));
+  const cuuint64_t dims_a[2] = {(cuuint64_t)2 * b.n_pad, (cuuint64_t)2 * b.ksteps};
+  const cuuint64_t strides_a[1] = {(cuuint64_t)b.n_pad * 16};
+  const cuuint64_t dims_b[3] = {(cuuint64_t)2 * kTile, (cuuint64_t)b.n_pad / kTile, (cuuint64_t)2 * b.ksteps};
+  const cuuint64_t strides_b[2] = {(cuuint64_t)2 * kTile * 8, (cuuint64_t)b.n_pad * 16};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  for (int w = 0; w < 2; w++) {
+    const cuuint32_t halves = w == 0 ? 2 * kStageSteps : 2;
+    const cuuint32_t box_a[2] = {2 * kTile, halves};
+    const cuuint32_t box_b[3] = {2 * kTile, kTileN / kTile, halves};
+    CUtensorMap *ma = w == 0 ? &b.maps.a_stage : &b.maps.a_step;
+    CUtensorMap *mb = w == 0 ? &b.maps.b_stage : &b.maps.b_step;
+    if (enc(ma, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, b.M, dims_a, strides_a, box_a, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS ||
+        enc(mb, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, b.M, dims_b, strides_b, box_b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS)
+      return KZ_ERR_CUDA;
+  }
   KZ_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors die here
   return KZ_OK;
 }
@@ -670,8 +730,8 @@ kz_status tensor_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
     a.n_tiles = b.n_tiles;
     a.counts = b.counts;
     a.status = &g->st->status;
-    const int grid = std::max(1, std::min(b.n_tiles, kCtasPerSm * sms));
-    tensor_edge_kernel<<<grid, kThreads, kSmemBytes, s>>>(b.tmap, a);
+    const int grid = std::max(1, std::min(b.n_tiles, sms));
+    tensor_edge_kernel<<<grid, kThreads, kSmemBytes, s>>>(b.maps, a);
     tensor_commit_kernel<<<8 * sms, 256, 0, s>>>(A, An, b.Edel, g->V[cur & 1], g->V[(cur & 1) ^ 1], g->n, g->ldw,
                                                  g->k, g->R, b.col, g->d_coff, g->d_rounds, g->d_blocks,
                                                  (int32_t)g->blocks.size(), g->v_sweep, g->st, b.counts);

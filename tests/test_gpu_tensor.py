@@ -61,3 +61,17 @@ def test_mma_probe_runs(layout):
     import paper_2212_00574_gb300 as kz
     flops, ms = kz.kz_probe_mma_throughput(layout, 128, 1)
     assert flops > 0 and ms > 0
+
+
+def test_auto_picks_tensor_for_a_larger_sparser_graph():
+    # n = 4500, k = 12, density about 0.12 falls in a bin where the tensor
+    # form measured faster; a dense graph of the same size stays on the bitset
+    # sweep.  The result is the same whichever path runs.
+    g = synth.kpartite(4500, 12, 0.12, 77, planted=True)
+    a = gpu_run(g, path="auto", dense=True)
+    b = gpu_run(g, path="bitset", dense=True)
+    assert a["stats"]["path"] == 4
+    assert np.array_equal(a["alive"], b["alive"]) and np.array_equal(a["edges"], b["edges"])
+    assert a["stats"]["sweeps"] == b["stats"]["sweeps"]
+    g2 = synth.kpartite(4500, 12, 0.6, 78, planted=True)
+    assert gpu_run(g2, path="auto", dense=True)["stats"]["path"] == 1
