@@ -124,7 +124,14 @@ typedef struct {
                              2 a CUDA-graph while node (one launch per pass), 0 host-driven loop */
     int32_t plane0;       /* kz_plane0 (BITSET path only) */
     int32_t batch;        /* kz_batch_mode (kz_kernelize_batch only) */
-    int32_t reserved[7];  /* must be zero */
+    int32_t clique_k;     /* clique size q sought, 1 <= q <= k; 0 means q = k.  The rules delete a
+                             vertex whose live neighbours cover fewer than q-1 classes and an edge whose
+                             live common neighbours cover fewer than q-2 (thesis Section 4.2, Remarks:
+                             a q-clique survives whenever the colouring is legal, whatever k >= q).
+                             q < k runs on the BITSET, SMALL, SPARSE and TENSOR paths with the plain
+                             schedule; the LEARNED and SUPPORT schedules and the FUSED batch return
+                             KZ_ERR_UNSUPPORTED for it */
+    int32_t reserved[6];  /* must be zero */
 } kz_options;
 
 /* Fill *opt with the defaults (AUTO path, PLAIN schedule, no sweep limit,
@@ -141,7 +148,8 @@ typedef struct {
     int32_t path;          /* kz_path that ran */
     int32_t status;        /* kz_status recorded on the device by the last kz_kernelize */
     int32_t k;             /* colours */
-    int32_t reserved[5];
+    int32_t clique_k;      /* clique size q the last kz_kernelize used */
+    int32_t reserved[4];
 } kz_stats;
 
 /* Optional device allocator (for example a caching allocator owned by the

@@ -74,6 +74,8 @@ def _bind(path: str):
     i32, i64 = C.c_int32, C.c_int64
     lib.kzo_fixpoint.restype = C.c_int
     lib.kzo_fixpoint.argtypes = [i32, i32, P, i64, P, i64, P, P, P, P, P, P, i64, P, P]
+    lib.kzo_fixpoint_q.restype = C.c_int
+    lib.kzo_fixpoint_q.argtypes = [i32, i32, i32, P, i64, P, i64, P, P, P, P, P, P, i64, P, P]
     lib.kzo_indices.restype = C.c_int
     lib.kzo_indices.argtypes = [i32, i32, P, i64, P, P, P, P, i64, P, P, i64, P]
     lib.kzo_dense_indices.restype = C.c_int
@@ -119,8 +121,12 @@ def _ptr(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
 
 
-def fixpoint(colour, edges, k: int, max_sweeps: int = 0, raise_on_limit: bool = True, _lib=None) -> dict:
+def fixpoint(colour, edges, k: int, max_sweeps: int = 0, raise_on_limit: bool = True, _lib=None,
+             clique_k: int | None = None) -> dict:
     """Jacobi fixpoint of the vertex and edge colour-index rules.
+
+    ``clique_k`` is the clique size q sought (default k): a vertex fails below
+    colour index q-1 and an edge below q-2 (Section 4.2, Remarks).
 
     Returns a dict with ``vlive`` (uint8[n]), ``elive`` (uint8[m], input edge
     order), ``v_sweep`` / ``e_rule_sweep`` (int32, 1-based productive sweep
@@ -141,7 +147,8 @@ def fixpoint(colour, edges, k: int, max_sweeps: int = 0, raise_on_limit: bool = 
     de = np.zeros(cap, np.int64)
     sweeps = C.c_int64(0)
     tests = C.c_int64(0)
-    rc = lib.kzo_fixpoint(n, int(k), _ptr(colour), m, _ptr(edges), int(max_sweeps),
+    q = int(k if clique_k is None else clique_k)
+    rc = lib.kzo_fixpoint_q(n, int(k), q, _ptr(colour), m, _ptr(edges), int(max_sweeps),
                           _ptr(vlive), _ptr(elive), _ptr(v_sweep), _ptr(e_rule),
                           _ptr(dv), _ptr(de), cap, C.addressof(sweeps), C.addressof(tests))
     if rc not in (0, -7) or (rc == -7 and raise_on_limit):

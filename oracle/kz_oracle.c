@@ -223,14 +223,22 @@ static int32_t edge_index(const adj_t *g, const uint8_t *elive, scratch_t *s,
  *
  * Returns KZO_OK, KZO_ERR_LIMIT (stopped after max_sweeps productive sweeps
  * with deletions still pending), or an input error.
+ *
+ * kzo_fixpoint_q takes the clique size q sought (1 <= q <= k) as its own
+ * argument: a vertex fails below colour index q-1, an edge below q-2.  The
+ * Section 4.2 Remarks derive both thresholds from the clique size alone: a
+ * vertex of a q-clique sees q-1 other clique members, all coloured
+ * differently under a legal colouring, and an edge of it sees q-2 common
+ * neighbours in the clique.  kzo_fixpoint is the thesis's case q = k.
  */
-int kzo_fixpoint(int32_t n, int32_t k, const int32_t *colour, int64_t m,
-                 const int32_t *edges, int64_t max_sweeps,
-                 uint8_t *vlive_out, uint8_t *elive_out,
-                 int32_t *v_sweep, int32_t *e_rule_sweep,
-                 int64_t *dv, int64_t *de, int64_t cap,
-                 int64_t *sweeps_out, int64_t *tests_out)
+int kzo_fixpoint_q(int32_t n, int32_t k, int32_t q, const int32_t *colour, int64_t m,
+                   const int32_t *edges, int64_t max_sweeps,
+                   uint8_t *vlive_out, uint8_t *elive_out,
+                   int32_t *v_sweep, int32_t *e_rule_sweep,
+                   int64_t *dv, int64_t *de, int64_t cap,
+                   int64_t *sweeps_out, int64_t *tests_out)
 {
+    if (q < 1 || q > k) return KZO_ERR_ARG;
     int rc = validate(n, k, colour, m, edges);
     if (rc != KZO_OK) return rc;
     adj_t g;
@@ -261,7 +269,7 @@ int kzo_fixpoint(int32_t n, int32_t k, const int32_t *colour, int64_t m,
         int64_t nv = 0, ne = 0;
         for (int32_t v = 0; v < n; v++) {
             fail_v[v] = 0;
-            if (vlive[v] && vertex_index(&g, elive, &s, v) < k - 1) {
+            if (vlive[v] && vertex_index(&g, elive, &s, v) < q - 1) {
                 fail_v[v] = 1;
                 nv++;
             }
@@ -270,7 +278,7 @@ int kzo_fixpoint(int32_t n, int32_t k, const int32_t *colour, int64_t m,
             fail_e[e] = 0;
             if (!elive[e]) continue;
             tests++;
-            if (edge_index(&g, elive, &s, edges[2 * e], edges[2 * e + 1]) < k - 2) {
+            if (edge_index(&g, elive, &s, edges[2 * e], edges[2 * e + 1]) < q - 2) {
                 fail_e[e] = 1;
                 ne++;
             }
@@ -307,6 +315,17 @@ done:
     scratch_free(&s);
     adj_free(&g);
     return rc;
+}
+
+int kzo_fixpoint(int32_t n, int32_t k, const int32_t *colour, int64_t m,
+                 const int32_t *edges, int64_t max_sweeps,
+                 uint8_t *vlive_out, uint8_t *elive_out,
+                 int32_t *v_sweep, int32_t *e_rule_sweep,
+                 int64_t *dv, int64_t *de, int64_t cap,
+                 int64_t *sweeps_out, int64_t *tests_out)
+{
+    return kzo_fixpoint_q(n, k, k, colour, m, edges, max_sweeps, vlive_out, elive_out, v_sweep,
+                          e_rule_sweep, dv, de, cap, sweeps_out, tests_out);
 }
 
 /*

@@ -240,7 +240,7 @@ kz_status kz_load_graph_dense(int32_t n, int32_t k, const int32_t *colour,
 static kz_status read_options(const kz_options *opt, kz_options &o) {
   if (opt) {
     o = *opt;
-    for (int i = 0; i < 7; i++)
+    for (int i = 0; i < 6; i++)
       if (o.reserved[i]) return KZ_ERR_ARG;
   } else {
     kz_default_options(&o);
@@ -250,6 +250,16 @@ static kz_status read_options(const kz_options *opt, kz_options &o) {
     return KZ_ERR_ARG;
   if (o.plane0 < KZ_PLANE0_AUTO || o.plane0 > KZ_PLANE0_TWO) return KZ_ERR_ARG;
   if (o.batch < KZ_BATCH_CONCURRENT || o.batch > KZ_BATCH_FUSED) return KZ_ERR_ARG;
+  if (o.clique_k < 0) return KZ_ERR_ARG;
+  return KZ_OK;
+}
+
+// The clique size q of this run, as slack = k - q (0: the thesis's rules).
+static kz_status set_clique(kz_graph g, const kz_options &o) {
+  const int q = o.clique_k ? o.clique_k : g->k;
+  if (q < 1 || q > g->k) return KZ_ERR_ARG;
+  g->slack = g->k - q;
+  if (g->slack != 0 && o.schedule != KZ_SCHED_PLAIN) return KZ_ERR_UNSUPPORTED;
   return KZ_OK;
 }
 
@@ -314,6 +324,7 @@ kz_status kz_kernelize(kz_graph g, const kz_options *opt, void *stream) {
   if (!g) return KZ_ERR_ARG;
   kz_options o;
   KZ_TRY(read_options(opt, o));
+  KZ_TRY(set_clique(g, o));
   g->stream = (cudaStream_t)stream;
   if (o.schedule == KZ_SCHED_LEARNED) {
     // learned worklist rounds on the bitset rows, certified by plain sweeps
@@ -466,11 +477,17 @@ kz_status kz_kernelize_batch(kz_graph *graphs, int32_t count, const kz_options *
     for (int32_t i = 0; i < count; i++) KZ_TRY(kz_kernelize(graphs[i], &o, stream));
     return KZ_OK;
   }
+  bool any_slack = false;
+  for (int32_t i = 0; i < count; i++) {
+    KZ_TRY(set_clique(graphs[i], o));
+    any_slack |= graphs[i]->slack != 0;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   for (int32_t i = 0; i < count; i++) graphs[i]->stream = s;
   if (count == 0) return KZ_OK;
   if (o.batch == KZ_BATCH_FUSED) {
     if (o.path == KZ_PATH_BITSET || o.path == KZ_PATH_SPARSE || o.path == KZ_PATH_TENSOR) return KZ_ERR_ARG;
+    if (any_slack) return KZ_ERR_UNSUPPORTED;
     return batch_fused(graphs, count, o, s);
   }
   if (o.batch == KZ_BATCH_SEQUENTIAL) {
@@ -505,6 +522,7 @@ kz_status kz_fetch_stats(kz_graph g, kz_stats *stats) {
     stats->path = g->path_ran;
     stats->status = hs.status;
     stats->k = g->k;
+    stats->clique_k = g->k - g->slack;
     KZ_TRY(owner_vertex_alive(g, nullptr, &stats->n_live));
     stats->m_live = -1;  // filled by the fetch calls that count edges
   }
@@ -678,6 +696,7 @@ kz_status kz_probe_barrier_timeout(kz_graph g, uint32_t spin_limit, void *stream
   if (!g || spin_limit == 0) return KZ_ERR_ARG;
   if (!g->has_bitset) return KZ_ERR_UNSUPPORTED;
   g->stream = (cudaStream_t)stream;
+  g->slack = 0;
   KZ_TRY(state_to_bitset(g, g->stream));
   KZ_TRY(bitset_barrier_timeout_probe(g, spin_limit, g->stream));
   g->kernelized = true;

@@ -231,6 +231,7 @@ struct SweepArgs {
   int32_t *v_sweep;       // relabelled ids, may be null
   uint8_t *changed;       // per unit: low byte of the sweep that last changed its words
   int32_t fast_half;      // half-word form: try the whole-block fold first (very dense graphs)
+  int32_t slack;          // colours minus the clique size sought (0: the thesis's rules)
   DevState *st;
   cudaGraphConditionalHandle cond;
   int32_t use_cond;
@@ -288,7 +289,7 @@ __device__ __forceinline__ void sweep_cta(const SweepArgs &p, int u_begin, int u
   uint32_t *__restrict__ Vn = cur ? p.V0 : p.V1;
   constexpr bool HALF = FORM == kFormHalf;
   constexpr bool TWO = FORM == kFormTwo;
-  const int k = p.k, ldw = p.ldw, nb = p.nb;
+  const int k = p.k, ldw = p.ldw, nb = p.nb, slack = p.slack;
   const int kq4 = TWO ? (2 * k + 3) >> 2 : (k + 3) >> 2;  // 16-byte chunks staged per row
   const uint8_t tag_now = (uint8_t)(sweep_no & 0xff);
   const uint8_t tag_next = (uint8_t)((sweep_no + 1) & 0xff);
@@ -380,8 +381,8 @@ __device__ __forceinline__ void sweep_cta(const SweepArgs &p, int u_begin, int u
     if (vflag) {
       const bool live = valid && ((vword >> lane) & 1u);
       int cnt = vcnt;
-      if (live && cnt < k - 1) cnt += vertex_cover_beyond_plane0(rowu, k, rounds, vmiss);
-      const bool fail = live && cnt < k - 1;
+      if (live && cnt < k - 1 - slack) cnt += vertex_cover_beyond_plane0(rowu, k, rounds, vmiss);
+      const bool fail = live && cnt < k - 1 - slack;
       const uint32_t failmask = __ballot_sync(0xffffffffu, fail);
       if (lane == 0) {
         Vn[Xc.r * k + cu] = vword & ~failmask;
@@ -404,16 +405,16 @@ __device__ __forceinline__ void sweep_cta(const SweepArgs &p, int u_begin, int u
         __syncwarp();
         open = half_unsettled<KMAX, KH>(F, P, bufh, adjw, p.fast_half != 0);
         // the recount starts from the full staged plane 0
-        if (open) del = recount_unsettled(rowu, sv, KMAX, ybase, ldw, open, k, cu, cv, rounds);
+        if (open) del = recount_unsettled(rowu, sv, KMAX, ybase, ldw, open, k, cu, cv, rounds, slack);
       } else if constexpr (TWO) {
         spread_plane1<KMAX>(sv, Yc.size, k, lane);
         __syncwarp();
         open = two_unsettled<KMAX>(F, F1, P, sv, adjw, k);
         // the recount starts from plane 0 of the staged rows, then reads the rows
-        if (open) del = recount_unsettled(rowu, sv, 2 * KMAX, ybase, ldw, open, k, cu, cv, rounds);
+        if (open) del = recount_unsettled(rowu, sv, 2 * KMAX, ybase, ldw, open, k, cu, cv, rounds, slack);
       } else {
         open = plane0_unsettled<KMAX>(F, P, sv, adjw, k);
-        if (open) del = recount_unsettled(rowu, sv, KMAX, ybase, ldw, open, k, cu, cv, rounds);
+        if (open) del = recount_unsettled(rowu, sv, KMAX, ybase, ldw, open, k, cu, cv, rounds, slack);
       }
       const bool anydel = __any_sync(0xffffffffu, del != 0u);
       if (anydel || full || chg == tag_now) {
@@ -844,6 +845,7 @@ static SweepArgs make_args(kz_graph g, int form) {
   a.boff = g->d_boff;
   a.changed = g->d_changed;
   a.fast_half = g->fast_half ? 1 : 0;
+  a.slack = g->slack;
   a.A0 = g->A[0];
   a.A1 = g->A[1];
   a.V0 = g->V[0];
@@ -932,6 +934,7 @@ static kz_status build_loop_graph(kz_graph g, int64_t max_sweeps, int form) {
   g->loop_grid = grid;
   g->loop_max_sweeps = max_sweeps;
   g->loop_form = form;
+  g->loop_slack = g->slack;
   return KZ_OK;
 }
 
@@ -984,6 +987,7 @@ static kz_status build_run_graph(kz_graph g, int64_t max_sweeps, int form) {
   g->run_exec = exec;
   g->run_max_sweeps = max_sweeps;
   g->run_form = form;
+  g->run_slack = g->slack;
   return KZ_OK;
 }
 
@@ -1011,7 +1015,7 @@ kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
     // graph (measured 2 us less on C2); a small one launches them directly
     // (a graph launch was slower there).
     if (g->plan[form].grid >= sm_count()) {
-      if (g->run_exec && (g->run_max_sweeps != max_sweeps || g->run_form != form)) {
+      if (g->run_exec && (g->run_max_sweeps != max_sweeps || g->run_form != form || g->run_slack != g->slack)) {
         cudaGraphExecDestroy(g->run_exec);
         g->run_exec = nullptr;
       }
@@ -1034,7 +1038,7 @@ kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
   }
   if (g->n > 0 && opt.use_graph == 2) {
     // one graph launch: run-start kernel, then the while node of sweep passes
-    if (g->loop_exec && (g->loop_max_sweeps != max_sweeps || g->loop_form != form)) {
+    if (g->loop_exec && (g->loop_max_sweeps != max_sweeps || g->loop_form != form || g->loop_slack != g->slack)) {
       cudaGraphExecDestroy(g->loop_exec);
       g->loop_exec = nullptr;
     }

@@ -30,6 +30,7 @@ struct CtaArgs {
   int32_t count;
   unsigned int *queue;    // next queue slot; null: CTA b takes order[b] only
   int32_t smem_words;     // dynamic shared memory available, in words
+  int32_t slack;          // colours minus the clique size sought, every graph (0: the thesis's rules)
   int64_t max_sweeps;     // option value; <= 0 means n + m + 1 per graph
 };
 
@@ -52,7 +53,7 @@ struct CtaRun {
 };
 
 template <int KMAX, bool SHARED>
-__device__ void cta_fixpoint(const CtaGraph &G, int64_t max_sweeps, uint32_t *smem, unsigned long long *s_cnt,
+__device__ void cta_fixpoint(const CtaGraph &G, int64_t max_sweeps, int slack, uint32_t *smem, unsigned long long *s_cnt,
                              int *s_flag, int32_t *s_rounds, CtaRun *run) {
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -118,8 +119,8 @@ __device__ void cta_fixpoint(const CtaGraph &G, int64_t max_sweeps, uint32_t *sm
       const bool live = valid_u && ((vword >> lane) & 1u);
       const uint64_t miss0 = plane0_vertex_missing<KMAX>(Fu, k, X.c);
       int cnt = (k - 1) - __popcll(miss0);
-      if (live && cnt < k - 1) cnt += vertex_cover_beyond_plane0(rowu, k, s_rounds, miss0);
-      const bool fail = live && cnt < k - 1;
+      if (live && cnt < k - 1 - slack) cnt += vertex_cover_beyond_plane0(rowu, k, s_rounds, miss0);
+      const bool fail = live && cnt < k - 1 - slack;
       const uint32_t failmask = __ballot_sync(0xffffffffu, fail);
       if (lane == 0) {
         Vn[wx] = vword & ~failmask;
@@ -161,7 +162,7 @@ __device__ void cta_fixpoint(const CtaGraph &G, int64_t max_sweeps, uint32_t *sm
         my_tests += __popc(adjw);
         const uint32_t *Ybase = Ac + (size_t)Y.base * ldw;
         const uint32_t del = edge_rule_block<KMAX>(
-            Fu, P, rowu, adjw, k, s_rounds, X.c, Y.c,
+            Fu, P, rowu, adjw, k, slack, s_rounds, X.c, Y.c,
             [&](int b) { return Ybase + (size_t)b * ldw; },
             [&](int b) { return Ybase + (size_t)b * ldw; });
         if (valid_u) An[(size_t)u * ldw + wy] = adjw & ~del;
@@ -251,9 +252,9 @@ __global__ void __launch_bounds__(kCtaThreads, 1) cta_fixpoint_kernel(CtaArgs a)
     const CtaGraph G = a.graphs[a.order[g]];
     if (G.k > KMAX) continue;  // never scheduled: the host groups graphs by KMAX
     if (G.smem_words > 0 && G.smem_words <= a.smem_words)
-      cta_fixpoint<KMAX, true>(G, a.max_sweeps, smem, s_cnt, &s_flag, s_rounds, &s_run);
+      cta_fixpoint<KMAX, true>(G, a.max_sweeps, a.slack, smem, s_cnt, &s_flag, s_rounds, &s_run);
     else
-      cta_fixpoint<KMAX, false>(G, a.max_sweeps, smem, s_cnt, &s_flag, s_rounds, &s_run);
+      cta_fixpoint<KMAX, false>(G, a.max_sweeps, a.slack, smem, s_cnt, &s_flag, s_rounds, &s_run);
   }
 }
 
@@ -394,6 +395,7 @@ kz_status cta_kernelize(kz_graph *gs, int count, const kz_options &opt, cudaStre
     a.count = (int32_t)idx.size();
     a.queue = d_queue + 4 * group;  // each group its own 16-byte counter
     a.smem_words = smem_bytes / 4;
+    a.slack = 0;  // the fused batch runs the thesis's rules only
     a.max_sweeps = opt.max_sweeps;
     const int grid = std::max(1, std::min<int>((int)idx.size(), sms));
     // order slice must be on the device before the launch
@@ -438,6 +440,7 @@ kz_status cta_kernelize_one(kz_graph g, const kz_options &opt, cudaStream_t s) {
   a.count = 1;
   a.queue = nullptr;
   a.smem_words = smem_bytes / 4;
+  a.slack = g->slack;
   a.max_sweeps = opt.max_sweeps;
   fn<<<1, kCtaThreads, smem_bytes, s>>>(a);
   return cuda_status(cudaGetLastError());
@@ -687,9 +690,9 @@ __global__ void __launch_bounds__(kCtaThreads, 1) fixpoint_kernel(int64_t max_sw
   if (s->h.status) return;
   const CtaGraph G = s->h.desc;
   if (G.smem_words > 0 && G.smem_words <= smem_words)
-    cta_fixpoint<32, true>(G, max_sweeps, smem, s_cnt, &s_flag, s_rounds, &s_run);
+    cta_fixpoint<32, true>(G, max_sweeps, 0, smem, s_cnt, &s_flag, s_rounds, &s_run);
   else
-    cta_fixpoint<32, false>(G, max_sweeps, smem, s_cnt, &s_flag, s_rounds, &s_run);
+    cta_fixpoint<32, false>(G, max_sweeps, 0, smem, s_cnt, &s_flag, s_rounds, &s_run);
 }
 
 __global__ void zero_out_kernel(uint64_t *__restrict__ out, int64_t words) {

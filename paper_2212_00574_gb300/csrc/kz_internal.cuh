@@ -167,6 +167,7 @@ struct kz_graph_s {
   // conversion wrote the rows; the next bitset pass then writes every word)
   bool ab_synced = false;
   double density = 0;                // edges / pairs of vertices in different classes, at load
+  int32_t slack = 0;                  // k minus the clique size of the current kz_kernelize (0: q = k)
   int32_t form = 0;                   // the sweep kernels' first test chosen by density
   bool fast_half = false;             // half-word form: fold whole blocks first (very dense graphs)
   kz::DevState *st = nullptr;
@@ -210,9 +211,11 @@ struct kz_graph_s {
   cudaGraphExec_t run_exec = nullptr;
   int64_t run_max_sweeps = 0;
   int32_t run_form = -1;
+  int32_t run_slack = 0;
   int loop_grid = 0;
   int64_t loop_max_sweeps = 0;
   int32_t loop_form = 0;
+  int32_t loop_slack = 0;
 
   // every device allocation, for kz_free_graph
   struct Alloc { void *p; size_t bytes; };

@@ -870,6 +870,7 @@ kz_status kz_collect_trace(kz_graph g, int64_t per_sweep_cap, uint64_t seed, flo
                            int64_t *count) {
   if (!g || per_sweep_cap < 0 || cap < 0 || (cap > 0 && (!X || !y)) || !count) return KZ_ERR_ARG;
   if (!g->has_bitset) return KZ_ERR_UNSUPPORTED;
+  g->slack = 0;  // traces follow the thesis's rules (q = k)
   KZ_TRY(state_to_bitset(g, g->stream));
   g->ab_synced = false;
   KZ_TRY(learned_collect(g, per_sweep_cap, seed, X, y, cap, count));

@@ -3,9 +3,13 @@
 // sweep kernel and the whole-fixpoint-in-one-CTA kernel.
 //
 // Vertex rule: a live vertex u fails when the classes other than col(u) that
-// hold a live neighbour number fewer than k-1.
+// hold a live neighbour number fewer than q-1.
 // Edge rule: a live edge {u,v} fails when the classes other than col(u),
-// col(v) that hold a live common neighbour number fewer than k-2.
+// col(v) that hold a live common neighbour number fewer than q-2.
+// q is the clique size sought, at most the number of colours k; the thesis
+// states the rules for q = k.  With slack = k - q the rules read "more than
+// slack needed classes uncovered", so the all-covered tests below settle a
+// pair for every q and only the recounts take slack.
 //
 // A warp works on a block X (lane = member u) against a block Y of a higher
 // class.  Plane 0 of row u (the first 32 members of every class) sits in
@@ -146,7 +150,12 @@ __device__ __forceinline__ uint64_t plane0_missing(const uint32_t (&Fu)[KMAX], c
 // `miss` must show a common neighbour in some later plane.  Returns true
 // when the edge fails (some needed class has none in any plane).
 __device__ __forceinline__ bool edge_fails_beyond_plane0(const uint32_t *ru, const uint32_t *rv, int k,
-                                                         const int32_t *__restrict__ rounds, uint64_t miss) {
+                                                         const int32_t *__restrict__ rounds, uint64_t miss,
+                                                         int slack) {
+  // the edge fails when more than `slack` needed classes hold no common
+  // neighbour (slack = colours - clique size: 0 for the thesis's rule)
+  if (__popcll(miss) <= slack) return false;
+  int missing = 0;
   while (miss) {
     const int c = __ffsll((long long)miss) - 1;
     miss &= miss - 1;
@@ -158,7 +167,7 @@ __device__ __forceinline__ bool edge_fails_beyond_plane0(const uint32_t *ru, con
         break;
       }
     }
-    if (!found) return true;
+    if (!found && ++missing > slack) return true;
   }
   return false;
 }
@@ -172,7 +181,7 @@ __device__ __forceinline__ bool edge_fails_beyond_plane0(const uint32_t *ru, con
 // only; the lanes' recounts run side by side, so their loads overlap.
 template <int KMAX, class FvRow, class FullRow>
 __device__ __forceinline__ uint32_t edge_rule_block(const uint32_t (&Fu)[KMAX], const uint32_t (&P)[KMAX],
-                                                    const uint32_t *ru, uint32_t adjw, int k,
+                                                    const uint32_t *ru, uint32_t adjw, int k, int slack,
                                                     const int32_t *__restrict__ rounds, int cu, int cv,
                                                     FvRow fv_row, FullRow row_v) {
   (void)cu;
@@ -186,7 +195,7 @@ __device__ __forceinline__ uint32_t edge_rule_block(const uint32_t (&Fu)[KMAX], 
     const bool covered = plane0_covered<KMAX>(Fu, P, fv, k);
     if (((adjw >> b) & 1u) && !covered) {
       const uint64_t miss = plane0_missing<KMAX>(Fu, P, fv, k);
-      if (edge_fails_beyond_plane0(ru, row_v(b), k, rounds, miss)) del |= 1u << b;
+      if (edge_fails_beyond_plane0(ru, row_v(b), k, rounds, miss, slack)) del |= 1u << b;
     }
   }
   return del;
@@ -425,7 +434,8 @@ __device__ __forceinline__ uint32_t two_unsettled(const uint32_t (&F0)[KMAX], co
 // only, so the hot loop's register arrays stay in registers.
 static __device__ __noinline__ uint32_t recount_unsettled(const uint32_t *ru, const uint32_t *sv, int kmax_stride,
                                                          const uint32_t *ybase, int ldw, uint32_t open, int k,
-                                                         int cu, int cv, const int32_t *__restrict__ rounds) {
+                                                         int cu, int cv, const int32_t *__restrict__ rounds,
+                                                         int slack) {
   uint32_t del = 0;
   while (open) {
     const int b = __ffs(open) - 1;
@@ -434,7 +444,7 @@ static __device__ __noinline__ uint32_t recount_unsettled(const uint32_t *ru, co
     uint64_t miss = 0;
     for (int c = 0; c < k; c++)
       if (c != cu && c != cv && (ru[c] & fv[c]) == 0u) miss |= 1ull << c;
-    if (edge_fails_beyond_plane0(ru, ybase + (int64_t)b * ldw, k, rounds, miss)) del |= 1u << b;
+    if (edge_fails_beyond_plane0(ru, ybase + (int64_t)b * ldw, k, rounds, miss, slack)) del |= 1u << b;
   }
   return del;
 }

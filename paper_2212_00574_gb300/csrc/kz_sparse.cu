@@ -127,6 +127,7 @@ static kz_status exclusive_scan(const int32_t *in, int64_t n, int64_t *out, int6
 struct SparseArgs {
   int32_t n;
   int32_t k;
+  int32_t q;                // clique size sought (k for the thesis's rules)
   const int32_t *col;       // colour of each vertex
   const int32_t *rank;      // orientation rank
   const int64_t *row;       // live CSR of this pass (n + 1)
@@ -263,7 +264,7 @@ __global__ void sparse_rule_kernel(SparseArgs a, const int32_t *__restrict__ eu,
     uint8_t live = a.elive[e];
     if (live) {
       tests++;
-      if (__popcll(mask[e]) < a.k - 2) {
+      if (__popcll(mask[e]) < a.q - 2) {
         live = 0;
         de++;
       }
@@ -279,7 +280,7 @@ __global__ void sparse_rule_kernel(SparseArgs a, const int32_t *__restrict__ eu,
       for (int64_t i = a.row[u] + lane; i < a.row[u + 1]; i += 32) cm |= 1ull << a.col[a.adj[i]];
     for (int o = 16; o > 0; o >>= 1) cm |= __shfl_xor_sync(0xffffffffu, cm, o);
     if (lane == 0) {
-      const bool fail = lv && __popcll(cm & ~(1ull << a.col[u])) < a.k - 1;
+      const bool fail = lv && __popcll(cm & ~(1ull << a.col[u])) < a.q - 1;
       vlive_n[u] = (lv && !fail) ? 1 : 0;
       if (fail) {
         dv++;
@@ -448,6 +449,7 @@ kz_status sparse_orient_live(kz_graph g, cudaStream_t s) {
   SparseArgs a;
   a.n = g->n;
   a.k = g->k;
+  a.q = g->k - g->slack;
   a.col = g->sp_col;
   a.rank = g->sp_rank;
   a.row = g->sp_row[c];
@@ -477,6 +479,7 @@ kz_status sparse_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
     SparseArgs a;
     a.n = g->n;
     a.k = g->k;
+  a.q = g->k - g->slack;
     a.col = g->sp_col;
     a.rank = g->sp_rank;
     a.row = g->sp_row[c];

@@ -141,7 +141,7 @@ __device__ __forceinline__ void sweep_item(const GraphView &p, const WorkItem it
       const uint32_t open = plane0_unsettled<KMAX>(Fu, P, sv, adjw, k);
       uint32_t del = 0;
       if (open)
-        del = recount_unsettled(rowu, sv, KMAX, A + (int64_t)Y.base * ldw, ldw, open, k, cu, cv, p.rounds);
+        del = recount_unsettled(rowu, sv, KMAX, A + (int64_t)Y.base * ldw, ldw, open, k, cu, cv, p.rounds, 0);
       const int wy = Y.r * k + cv;
       if (valid_u) An[(int64_t)u * ldw + wy] = adjw & ~del;
       pc.de += __popc(del);

@@ -4,7 +4,7 @@
 // neighbours of every vertex pair inside class c.  The edge rule asks, per
 // live edge {u,v}, how many classes have S_c(u,v) > 0 (classes col(u) and
 // col(v) always give 0: no neighbour of u has u's colour).  An edge fails when
-// fewer than k-2 classes do.
+// fewer than q-2 classes do (q: the clique size sought, k in the thesis).
 //
 // Operand layout: the live bitset rows are expanded into an E4M3 0/1 byte
 // matrix with one 32-byte K-step per 32-bit block word (class c is the run of
@@ -34,7 +34,7 @@
 //               next class runs while the previous one is read;
 //   warps 2-9   epilogue: tcgen05.ld of the class's counts, one 8-bit
 //               counter per pair of classes with a non-zero count; after the
-//               tile's last class, live edges below k-2 are marked in a
+//               tile's last class, live edges below q-2 are marked in a
 //               deletion bitmap.
 // A row kernel then applies the vertex rule and the edge deletions.  Every
 // mbarrier wait is bounded (wall clock); a wait that runs out records
@@ -244,6 +244,7 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 
 struct TensorArgs {
   int32_t n, k;
+  int32_t q;               // clique size sought (k for the thesis's rules)
   const int32_t *cls_step; // k + 1: first K-step of each class
   const uint32_t *A;       // current rows (adjacency bits)
   int32_t ldw;
@@ -438,11 +439,11 @@ __global__ void __launch_bounds__(kThreads, 1) tensor_edge_kernel(const __grid_c
         const int wu = a.vinfo[u];
 #pragma unroll
         for (int g = 0; g < 2; g++) {
-          // columns whose pair covers fewer than k-2 classes
+          // columns whose pair covers fewer than q-2 classes
           uint64_t low = 0;
 #pragma unroll
           for (int j = 0; j < 64; j++)
-            low |= (uint64_t)((int)((cnt[16 * g + (j >> 2)] >> ((j & 3) * 8)) & 0xFFu) < a.k - 2) << j;
+            low |= (uint64_t)((int)((cnt[16 * g + (j >> 2)] >> ((j & 3) * 8)) & 0xFFu) < a.q - 2) << j;
           const int base = J * kTileN + half * 128 + g * 64;
           const int4 *vi4 = reinterpret_cast<const int4 *>(a.vinfo + base);
           uint64_t adj = 0;
@@ -515,7 +516,8 @@ __global__ void expand_kernel(const uint32_t *__restrict__ A, int32_t n, int32_t
 // current rows minus the deletion bitmap; next live words; pass counters.
 __global__ void tensor_commit_kernel(const uint32_t *__restrict__ A, uint32_t *__restrict__ An,
                                      uint32_t *__restrict__ Edel, const uint32_t *__restrict__ V,
-                                     uint32_t *__restrict__ Vn, int32_t n, int32_t ldw, int32_t k, int32_t R,
+                                     uint32_t *__restrict__ Vn, int32_t n, int32_t ldw, int32_t k, int32_t q,
+                                     int32_t R,
                                      const int32_t *__restrict__ col, const int32_t *__restrict__ coff,
                                      const int32_t *__restrict__ rounds, const BlockDesc *__restrict__ blocks,
                                      int32_t nb, int32_t *__restrict__ v_sweep, DevState *st,
@@ -540,7 +542,7 @@ __global__ void tensor_commit_kernel(const uint32_t *__restrict__ A, uint32_t *_
     const int u = X.base + lane;
     const bool live = valid && ((vword >> lane) & 1u);
     int cnt = live ? exact_vertex_cover_row(A + (int64_t)u * ldw, k, rounds, X.c) : 0;
-    const bool fail = live && cnt < k - 1;
+    const bool fail = live && cnt < q - 1;
     const uint32_t failmask = __ballot_sync(0xffffffffu, fail);
     if (lane == 0) {
       Vn[wx] = vword & ~failmask;
@@ -721,6 +723,7 @@ kz_status tensor_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
     TensorArgs a;
     a.n = g->n;
     a.k = g->k;
+    a.q = g->k - g->slack;
     a.cls_step = b.cls_step;
     a.A = A;
     a.ldw = g->ldw;
@@ -733,7 +736,7 @@ kz_status tensor_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
     const int grid = std::max(1, std::min(b.n_tiles, sms));
     tensor_edge_kernel<<<grid, kThreads, kSmemBytes, s>>>(b.maps, a);
     tensor_commit_kernel<<<8 * sms, 256, 0, s>>>(A, An, b.Edel, g->V[cur & 1], g->V[(cur & 1) ^ 1], g->n, g->ldw,
-                                                 g->k, g->R, b.col, g->d_coff, g->d_rounds, g->d_blocks,
+                                                 g->k, g->k - g->slack, g->R, b.col, g->d_coff, g->d_rounds, g->d_blocks,
                                                  (int32_t)g->blocks.size(), g->v_sweep, g->st, b.counts);
     tensor_finish_kernel<<<1, 1, 0, s>>>(g->st, b.counts);
     KZ_CUDA_TRY(cudaGetLastError());

@@ -237,6 +237,60 @@ def pin_validation(orc):
     return None
 
 
+def pin_brute_force_q(orc, cases=30, seed0=3000):
+    """Clique size q below the colour count k (thresholds q-1 and q-2, Section
+    4.2 Remarks): exact greatest fixpoint by enumerating edge subsets."""
+    rng = np.random.default_rng(seed0)
+    done = tries = 0
+    while done < cases and tries < 20 * cases:
+        tries += 1
+        n = int(rng.integers(3, 9))
+        k = int(rng.integers(3, 7))
+        q = int(rng.integers(1, k))
+        p = float(rng.uniform(0.3, 0.9))
+        colour, edges = _graph(seed0 + tries, n, k, p, planted=bool(rng.integers(0, 2)) and n >= k)
+        if len(edges) > 14:
+            continue
+        done += 1
+        vb, eb = refs.brute_force_gfp(n, k, colour, edges, q=q)
+        r = orc.fixpoint(colour, edges, k, clique_k=q)
+        if not (np.array_equal(r["vlive"].astype(bool), vb) and np.array_equal(r["elive"].astype(bool), eb)):
+            return f"brute force mismatch n={n} k={k} q={q} m={len(edges)} seed={seed0 + tries}"
+    return None
+
+
+def pin_q_cliques_and_order(orc, cases=12):
+    """Clique size q < k: every q-clique (any q colours) survives; random
+    Gauss-Seidel and random-subset schedules reach the same survivors; and
+    the kernel only grows as q falls (each threshold is lower)."""
+    rng = np.random.default_rng(4321)
+    for s in range(cases):
+        n = int(rng.integers(10, 36))
+        k = int(rng.integers(4, 8))
+        p = float(rng.uniform(0.25, 0.7))
+        colour, edges = _graph(13000 + s, n, k, p, planted=(s % 2 == 0))
+        eid = {tuple(e): i for i, e in enumerate(edges.tolist())}
+        prev = None
+        for q in range(k, 0, -1):
+            r = orc.fixpoint(colour, edges, k, clique_k=q)
+            vl, el = r["vlive"].astype(bool), r["elive"].astype(bool)
+            if prev is not None and not (np.all(vl >= prev[0]) and np.all(el >= prev[1])):
+                return f"kernel shrank as q fell to {q} (case {s})"
+            prev = (vl, el)
+            if q >= 3:
+                for cl in refs.q_cliques(n, q, colour, edges):
+                    if not all(vl[v] for v in cl) or not all(
+                            el[eid[(cl[i], cl[j])]] for i in range(q) for j in range(i + 1, q)):
+                        return f"{q}-clique lost with k={k} (case {s})"
+            if q in (k - 1, 2 + (k - 1) // 2):
+                for mode in ("shuffled", "subset"):
+                    cv, ce = refs.chaotic_fixpoint(n, k, colour, edges, rng, mode, q=q)
+                    if not (np.array_equal(cv, vl) and np.array_equal(ce, el)):
+                        return f"order dependence at q={q} ({mode}, case {s})"
+    return None
+
+
 ALL_PINS = [pin_fig8, pin_brute_force, pin_k3_triangles, pin_k2, pin_k1, pin_complete_kpartite,
             pin_empty_class, pin_planted_isolated, pin_clique_survival, pin_order_independence,
-            pin_certificate, pin_incident_edges_fail, pin_validation]
+            pin_certificate, pin_incident_edges_fail, pin_validation, pin_brute_force_q,
+            pin_q_cliques_and_order]

@@ -57,21 +57,23 @@ def load_fig8():
 # brute-force greatest closed subgraph
 # ----------------------------------------------------------------------------
 
-def brute_force_gfp(n, k, colour, edges):
+def brute_force_gfp(n, k, colour, edges, q=None):
     """Union of all closed subgraphs, by enumerating every edge subset.
 
-    H = (V_H, E_H) is closed when every vertex of V_H has an H-neighbour of
-    every colour other than its own, and every edge {u,v} of E_H has, for
-    every colour other than col(u), col(v), a vertex w with {u,w} and {v,w}
-    in E_H.  For k >= 2 a vertex of a closed H needs an incident H-edge, so
-    V_H is the set of endpoints of E_H; for k = 1 there are no conditions.
+    H = (V_H, E_H) is closed when every vertex of V_H has H-neighbours in at
+    least q-1 colours other than its own, and every edge {u,v} of E_H has,
+    in at least q-2 colours other than col(u), col(v), a vertex w with {u,w}
+    and {v,w} in E_H (q = k: every such colour).  For q >= 2 a vertex of a
+    closed H needs an incident H-edge, so V_H is the set of endpoints of E_H;
+    for q = 1 there are no conditions.
     Returns (vertex_mask bool[n], edge_mask bool[m]).
     """
+    q = k if q is None else q
     colour = [int(c) for c in colour]
     edges = [tuple(map(int, e)) for e in edges]
     m = len(edges)
     assert m <= 18, "brute force is exponential in m"
-    if k == 1:
+    if q <= 1:
         return np.ones(n, bool), np.ones(m, bool)
     eidx = {}
     for i, (u, v) in enumerate(edges):
@@ -103,21 +105,17 @@ def brute_force_gfp(n, k, colour, edges):
             if S >> i & 1:
                 verts.update(edges[i])
         for v in verts:
-            for c in range(k):
-                if c != colour[v] and not (S & inc[v][c]):
-                    ok = False
-                    break
-            if not ok:
+            covered = sum(1 for c in range(k) if c != colour[v] and (S & inc[v][c]))
+            if covered < q - 1:
+                ok = False
                 break
         if ok:
             for i in range(m):
                 if not (S >> i & 1):
                     continue
-                for masks in wit[i]:
-                    if not any((S & pm) == pm for pm in masks):
-                        ok = False
-                        break
-                if not ok:
+                covered = sum(1 for masks in wit[i] if any((S & pm) == pm for pm in masks))
+                if covered < q - 2:
+                    ok = False
                     break
         if ok:
             union |= S
@@ -174,6 +172,29 @@ def k_cliques(n, k, colour, edges):
     return out
 
 
+def q_cliques(n, q, colour, edges):
+    """All cliques of exactly q vertices (sorted tuples), by extending each
+    vertex with higher-numbered common neighbours; independent of colours."""
+    adj = [set() for _ in range(n)]
+    for u, v in edges:
+        adj[int(u)].add(int(v))
+        adj[int(v)].add(int(u))
+    out = []
+
+    def rec(chosen, cand):
+        if len(chosen) == q:
+            out.append(tuple(chosen))
+            return
+        for v in sorted(cand):
+            if not chosen or v > chosen[-1]:
+                rec(chosen + [v], cand & adj[v])
+
+    if q <= 0:
+        return [()]
+    rec([], set(range(n)))
+    return out
+
+
 # ----------------------------------------------------------------------------
 # random-order deletion
 # ----------------------------------------------------------------------------
@@ -187,18 +208,22 @@ def _live_adj(n, edges, elive):
     return adj
 
 
-def _misses_colour_v(v, colour, k, adj):
+def _misses_colour_v(v, colour, k, adj, q=None):
     seen = {colour[w] for w in adj[v]}
+    if q is not None:
+        return len(seen) < q - 1
     return any(c not in seen for c in range(k) if c != colour[v])
 
 
-def _misses_colour_e(u, v, colour, k, adj):
+def _misses_colour_e(u, v, colour, k, adj, q=None):
     common = set(adj[u]) & set(adj[v])
     seen = {colour[w] for w in common}
+    if q is not None:
+        return len(seen) < q - 2
     return any(c not in seen for c in range(k) if c not in (colour[u], colour[v]))
 
 
-def chaotic_fixpoint(n, k, colour, edges, rng, mode="shuffled"):
+def chaotic_fixpoint(n, k, colour, edges, rng, mode="shuffled", q=None):
     """Delete failing elements in a random order until nothing fails.
 
     A vertex fails when some colour other than its own has no live neighbour;
@@ -206,7 +231,9 @@ def chaotic_fixpoint(n, k, colour, edges, rng, mode="shuffled"):
     common neighbour (these are the Section 4.2 conditions, phrased as
     "misses a colour").  ``shuffled``: Gauss-Seidel over a random order,
     deleting at once.  ``subset``: each round tests a random subset on the
-    round's snapshot and deletes the failures together.
+    round's snapshot and deletes the failures together.  With ``q`` (the
+    clique size sought) an element fails below q-1 (vertex) or q-2 (edge)
+    covered colours instead.
     """
     colour = [int(c) for c in colour]
     edges = [tuple(map(int, e)) for e in edges]
@@ -229,21 +256,21 @@ def chaotic_fixpoint(n, k, colour, edges, rng, mode="shuffled"):
             for j in order:
                 kind, x = items[j]
                 if kind == "v":
-                    if vlive[x] and _misses_colour_v(x, colour, k, adj):
+                    if vlive[x] and _misses_colour_v(x, colour, k, adj, q):
                         kill_vertex(x, adj)
                         changed = True
                 else:
                     if elive[x]:
                         u, v = edges[x]
-                        if _misses_colour_e(u, v, colour, k, adj):
+                        if _misses_colour_e(u, v, colour, k, adj, q):
                             elive[x] = False
                             del adj[u][v]
                             del adj[v][u]
                             changed = True
         else:
             take = [items[j] for j in order if rng.random() < 0.5]
-            fv = [x for kind, x in take if kind == "v" and _misses_colour_v(x, colour, k, adj)]
-            fe = [x for kind, x in take if kind == "e" and _misses_colour_e(*edges[x], colour, k, adj)]
+            fv = [x for kind, x in take if kind == "v" and _misses_colour_v(x, colour, k, adj, q)]
+            fe = [x for kind, x in take if kind == "e" and _misses_colour_e(*edges[x], colour, k, adj, q)]
             for x in fe:
                 if elive[x]:
                     u, v = edges[x]
@@ -256,8 +283,8 @@ def chaotic_fixpoint(n, k, colour, edges, rng, mode="shuffled"):
             if not changed:
                 # certify with a full pass before stopping
                 adj = _live_adj(n, edges, elive)
-                changed = any(vlive[v] and _misses_colour_v(v, colour, k, adj) for v in range(n)) or \
-                    any(elive[i] and _misses_colour_e(*edges[i], colour, k, adj) for i in range(len(edges)))
+                changed = any(vlive[v] and _misses_colour_v(v, colour, k, adj, q) for v in range(n)) or \
+                    any(elive[i] and _misses_colour_e(*edges[i], colour, k, adj, q) for i in range(len(edges)))
         if not changed:
             return vlive, elive
 

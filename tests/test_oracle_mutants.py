@@ -9,10 +9,13 @@ import oracle
 from tests import pins
 
 MUTANTS = {
-    # vertex rule threshold off by one (index < k-2 instead of < k-1)
-    "vertex_threshold": ("vertex_index(&g, elive, &s, v) < k - 1", "vertex_index(&g, elive, &s, v) < k - 2"),
+    # vertex rule threshold off by one (index < q-2 instead of < q-1)
+    "vertex_threshold": ("vertex_index(&g, elive, &s, v) < q - 1", "vertex_index(&g, elive, &s, v) < q - 2"),
     # edge rule threshold off by one
-    "edge_threshold": ("edges[2 * e + 1]) < k - 2)", "edges[2 * e + 1]) < k - 3)"),
+    "edge_threshold": ("edges[2 * e + 1]) < q - 2)", "edges[2 * e + 1]) < q - 3)"),
+    # the clique size ignored: thresholds from the colour count
+    "vertex_threshold_from_k": ("vertex_index(&g, elive, &s, v) < q - 1", "vertex_index(&g, elive, &s, v) < k - 1"),
+    "edge_threshold_from_k": ("edges[2 * e + 1]) < q - 2)", "edges[2 * e + 1]) < k - 2)"),
     # common neighbour test dropped: counts every neighbour of v
     "no_common_check": ("        if (s->nbr_mark[w] != s->stamp) continue;\n", ""),
     # (Not listed: keeping the edges of a deleted vertex live.  That edit is
@@ -25,8 +28,8 @@ MUTANTS = {
     # the sweep index recorded one too late
     "sweep_off_by_one": ("if (v_sweep) v_sweep[v] = (int32_t)sweeps;", "if (v_sweep) v_sweep[v] = (int32_t)sweeps + 1;"),
     # Gauss-Seidel instead of Jacobi: vertices leave before the edge rule runs
-    "not_jacobi": ("            if (vlive[v] && vertex_index(&g, elive, &s, v) < k - 1) {\n                fail_v[v] = 1;",
-                   "            if (vlive[v] && vertex_index(&g, elive, &s, v) < k - 1) {\n                fail_v[v] = 1;\n                for (int64_t i = g.off[v]; i < g.off[v + 1]; i++) elive[g.eid[i]] = 0;"),
+    "not_jacobi": ("            if (vlive[v] && vertex_index(&g, elive, &s, v) < q - 1) {\n                fail_v[v] = 1;",
+                   "            if (vlive[v] && vertex_index(&g, elive, &s, v) < q - 1) {\n                fail_v[v] = 1;\n                for (int64_t i = g.off[v]; i < g.off[v + 1]; i++) elive[g.eid[i]] = 0;"),
 }
 
 
