@@ -250,6 +250,43 @@ kz_status kz_fetch_trace(kz_graph g, int64_t *dv, int64_t *de, int64_t cap, int3
 /* Restore the live state to the graph as loaded (asynchronous). */
 kz_status kz_reset(kz_graph g, void *stream);
 
+/*
+ * Clique search on the current kernel (synchronous; host branch and bound).
+ * Looks for a clique of q vertices (0 <= q <= k) in the kernel that the last
+ * kz_kernelize left; the kernel for clique size q holds every q-clique of the
+ * graph (thesis Section 4.2, Remarks), so the answer is the graph's.  The
+ * search is exact: colour-ordered branch and bound (at most one vertex per
+ * class under the legal colouring), branching on the class with the fewest
+ * candidates, pruned when fewer classes with candidates remain than vertices
+ * are still needed.
+ *   node_limit  search nodes allowed; <= 0 means no limit
+ *   clique_out  host int32[q]: the clique's caller ids in ascending order
+ *               (written when one is found)
+ *   found       1 when a q-clique was found, 0 when there is none
+ * Returns KZ_ERR_NOT_READY before any kz_kernelize, KZ_ERR_LIMIT when the
+ * node limit ran out before the search ended (found = 0, unknown), KZ_ERR_ARG
+ * for q outside [0, k], KZ_ERR_UNSUPPORTED when the kernel's adjacency
+ * bitsets would exceed 8 GB of host memory.
+ */
+kz_status kz_find_clique(kz_graph g, int32_t q, int64_t node_limit, int32_t *clique_out, int32_t *found);
+
+/*
+ * Maximum clique through kernelization (synchronous): for q = k, k-1, ..., 1
+ * the graph is reset, kernelized for clique size q (opt with clique_k = q;
+ * opt may be NULL for the defaults) and searched with kz_find_clique; the
+ * first q with a clique is the clique number (the thesis, Section 4: the
+ * k-clique test run for decreasing k answers the maximum clique problem; a
+ * legal k-colouring bounds it by k).  On return the handle holds the kernel
+ * for *q_out.
+ *   q_out       the clique number (0 for an empty graph)
+ *   clique_out  host int32[k]: one maximum clique, caller ids ascending
+ *               (its first *q_out entries)
+ * Returns KZ_ERR_LIMIT when a search ran out of nodes (*q_out is the size
+ * being searched then), or the first error of kz_reset / kz_kernelize.
+ */
+kz_status kz_max_clique(kz_graph g, const kz_options *opt, int64_t node_limit, int32_t *q_out, int32_t *clique_out,
+                        void *stream);
+
 /* Release the handle and its device memory (waits for its stream).  NULL is
  * ignored. */
 void kz_free_graph(kz_graph g);

@@ -107,6 +107,8 @@ def _lib():
                 "kz_version": (i32, []),
                 "kz_probe_int_throughput": (C.c_int, [i32, P, P, P]),
                 "kz_probe_mma_throughput": (C.c_int, [i32, i32, i32, P, P, P]),
+                "kz_find_clique": (C.c_int, [P, i32, i64, P, P]),
+                "kz_max_clique": (C.c_int, [P, P, i64, P, P, P]),
                 "kz_probe_tma_throughput": (C.c_int, [i32, i32, P, P, P]),
                 "kz_probe_barrier_timeout": (C.c_int, [P, u32, P]),
                 "kz_kernelize_dense_noalloc": (C.c_int, [i32, i32, P, P, i64, i64, P, P, P, P]),
@@ -346,6 +348,25 @@ def kz_kernelize_dense_noalloc(n: int, k: int, colour_ptr: int, adj_bits_ptr: in
 def kz_probe_barrier_timeout(g: int, spin_limit: int = 1 << 14, stream=None):
     _check(_lib().kz_probe_barrier_timeout(C.c_void_p(g), int(spin_limit), _stream(stream)),
            "kz_probe_barrier_timeout")
+
+
+def kz_find_clique(g: int, q: int, node_limit: int = 0):
+    """(found, clique) on the current kernel: clique is int32[q] caller ids,
+    ascending (empty when none was found)."""
+    out = np.zeros(max(int(q), 1), np.int32)
+    found = C.c_int32(0)
+    _check(_lib().kz_find_clique(C.c_void_p(g), int(q), int(node_limit), _ptr(out), C.byref(found)),
+           "kz_find_clique")
+    return bool(found.value), (out[:q].copy() if found.value else np.zeros(0, np.int32))
+
+
+def kz_max_clique(g: int, k: int, options: kz_options | None = None, node_limit: int = 0, stream=None):
+    """(clique number, one maximum clique as ascending caller ids)."""
+    out = np.zeros(max(int(k), 1), np.int32)
+    q = C.c_int32(0)
+    _check(_lib().kz_max_clique(C.c_void_p(g), None if options is None else C.byref(options), int(node_limit),
+                                C.byref(q), _ptr(out), _stream(stream)), "kz_max_clique")
+    return int(q.value), out[:q.value].copy()
 
 
 def kz_probe_mma_throughput(layout: int, n: int = 128, ctas_per_sm: int = 1, stream=None):
