@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC), default="c2")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU work budget of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clique-k", type=int, default=0,
+                    help="clique size q sought (0: q = k); q < k lowers both rule thresholds")
+    ap.add_argument("--max-clique", action="store_true",
+                    help="time the maximum-clique driver (kernelize for q = k, k-1, ... and search each kernel)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (n x scale; for small profiler captures, not for bench lines)")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -279,7 +283,7 @@ def run_ours(args, world, rank, local, pg):
         h = kz.kz_load_graph(g.n, g.k, h_col, h_edges, stream=stream)
     opts = kz.kz_default_options(path=args.path, use_graph={"device": 1, "graph": 2, "host": 0}[args.loop],
                                  plane0={"auto": 0, "full": 1, "half": 2, "two": 3}[args.plane0],
-                                 schedule=args.schedule)
+                                 schedule=args.schedule, clique_k=args.clique_k)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def step(i, ev0=None, ev1=None):
@@ -429,6 +433,7 @@ def run_ours(args, world, rank, local, pg):
                        "pass_loop": {"device": "one cooperative persistent launch", "graph": "CUDA-graph while node",
                                      "host": "host-driven"}[args.loop],
                        "passes": passes, "sweeps": st["sweeps"], "schedule": args.schedule,
+                       "clique_k": st["clique_k"],
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); per-step CUDA events "
                              "around kz_kernelize only",
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -515,6 +520,45 @@ def run_batch(args, world, rank, local, pg):
             "clocks": b["clocks"],
         }
         print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_max_clique(args, world, rank, local, pg):
+    """The maximum-clique driver end to end on one graph: for q = k, k-1, ...
+    reset, kernelize for clique size q on the GPU, search the kernel (host
+    branch and bound), stop at the first q with a clique.  Timed on the wall
+    clock (the search runs on the host), after warm-up runs."""
+    import paper_2212_00574_gb300 as kz
+    dev = torch.device("cuda", local)
+    kz.use_torch_allocator()
+    stream = torch.cuda.current_stream(dev)
+    g = make_workload(args.workload, args.scale)
+    dense = g.bits is not None
+    if dense:
+        h = kz.kz_load_graph_dense(g.n, g.k, g.colour, g.get_bits(), stream=stream)
+    else:
+        h = kz.kz_load_graph(g.n, g.k, g.colour, g.get_edges(), stream=stream)
+    opts = kz.kz_default_options(path=args.path)
+    times = []
+    q = 0
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        q, clique = kz.kz_max_clique(h, g.k, opts, stream=stream)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    st = kz.kz_fetch_stats(h)
+    kz.kz_free_graph(h)
+    if rank == 0:
+        ms = 1e3 * statistics.median(times)
+        print(json.dumps({"metric": "maximum-clique time (kernelize for q = k, k-1, ... and search)",
+                          "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "u32", "data": "synthetic",
+                          "config": {"workload": wdesc(args), "n": g.n, "k": g.k, "path": st["path"],
+                                     "clique_number": q, "kernel_vertices": st["n_live"],
+                                     "kernel_edges": st["m_live"], "parallelism": "single"}}), flush=True)
     return 0
 
 
@@ -613,6 +657,8 @@ def main():
             return run_batch(args, world, rank, local, pg)
         if args.schedule == "learned":
             return run_learned(args, world, rank, local, pg)
+        if args.max_clique:
+            return run_max_clique(args, world, rank, local, pg)
         return run_ours(args, world, rank, local, pg)
     finally:
         if pg is not None:

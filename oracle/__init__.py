@@ -74,6 +74,8 @@ def _bind(path: str):
     i32, i64 = C.c_int32, C.c_int64
     lib.kzo_fixpoint.restype = C.c_int
     lib.kzo_fixpoint.argtypes = [i32, i32, P, i64, P, i64, P, P, P, P, P, P, i64, P, P]
+    lib.kzo_fixpoint_dominance.restype = C.c_int
+    lib.kzo_fixpoint_dominance.argtypes = [i32, i32, i32, P, i64, P, P, P, P, P]
     lib.kzo_fixpoint_q.restype = C.c_int
     lib.kzo_fixpoint_q.argtypes = [i32, i32, i32, P, i64, P, i64, P, P, P, P, P, P, i64, P, P]
     lib.kzo_indices.restype = C.c_int
@@ -110,6 +112,9 @@ class Oracle:
     def fixpoint(self, *a, **kw):
         return fixpoint(*a, _lib=self.lib(), **kw)
 
+    def fixpoint_dominance(self, *a, **kw):
+        return fixpoint_dominance(*a, _lib=self.lib(), **kw)
+
     def indices(self, *a, **kw):
         return indices(*a, _lib=self.lib(), **kw)
 
@@ -119,6 +124,26 @@ class Oracle:
 
 def _ptr(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def fixpoint_dominance(colour, edges, k: int, clique_k: int | None = None, _lib=None) -> dict:
+    """Colour-index fixpoint, then rounds of vertex dominance (Definition
+    4.3.1), each followed by the colour-index fixpoint again, until a round
+    deletes nothing.  Returns ``vlive``, ``elive``, ``rounds`` (dominance
+    rounds that deleted something) and ``dominated`` (vertices they deleted)."""
+    lib = _lib or _load()
+    colour = np.ascontiguousarray(colour, dtype=np.int32)
+    edges = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    n, m = len(colour), len(edges)
+    vlive = np.zeros(n, np.uint8)
+    elive = np.zeros(m, np.uint8)
+    rounds, dominated = C.c_int64(0), C.c_int64(0)
+    q = int(k if clique_k is None else clique_k)
+    rc = lib.kzo_fixpoint_dominance(n, int(k), q, _ptr(colour), m, _ptr(edges), _ptr(vlive), _ptr(elive),
+                                    C.addressof(rounds), C.addressof(dominated))
+    if rc != 0:
+        raise OracleError(rc)
+    return dict(vlive=vlive, elive=elive, rounds=int(rounds.value), dominated=int(dominated.value))
 
 
 def fixpoint(colour, edges, k: int, max_sweeps: int = 0, raise_on_limit: bool = True, _lib=None,

@@ -329,6 +329,121 @@ int kzo_fixpoint(int32_t n, int32_t k, const int32_t *colour, int64_t m,
 }
 
 /*
+ * Colour-index fixpoint followed by rounds of vertex dominance (thesis
+ * Section 4.3, Definition 4.3.1), each round followed by the colour-index
+ * fixpoint again, until a dominance round deletes nothing.
+ *
+ * Vertex b dominates vertex a when a and b are distinct, not adjacent, and
+ * N(a) is a subset of N(b) (live neighbours).  The Remarks of Definition
+ * 4.3.1 allow deleting a dominated vertex: a clique through a becomes one
+ * through b when a is swapped for b, so the clique number is kept (some
+ * cliques may go, which is why this pass is opt-in).  Reading for the
+ * parallel (Jacobi) round: every vertex dominated on the round's snapshot is
+ * deleted together, except that of two vertices with equal neighbourhoods
+ * only the one with the smaller key (colour, id) goes.  The dominators then
+ * form a strict order, whose maximal elements survive and dominate every
+ * deleted vertex of their chain, so the clique number is still kept.
+ *
+ * The colour-index phases are kzo_fixpoint_q's Jacobi sweeps for clique
+ * size q.  Outputs: vlive[n], elive[m], the dominance rounds that deleted
+ * something, and the vertices they deleted.
+ */
+int kzo_fixpoint_dominance(int32_t n, int32_t k, int32_t q, const int32_t *colour, int64_t m,
+                           const int32_t *edges, uint8_t *vlive_out, uint8_t *elive_out,
+                           int64_t *rounds_out, int64_t *dominated_out)
+{
+    if (q < 1 || q > k) return KZO_ERR_ARG;
+    int rc = validate(n, k, colour, m, edges);
+    if (rc != KZO_OK) return rc;
+    adj_t g;
+    rc = adj_build(&g, n, k, colour, m, edges);
+    if (rc != KZO_OK) return rc;
+    scratch_t s;
+    if (scratch_init(&s, n, k) != KZO_OK) {
+        adj_free(&g);
+        return KZO_ERR_OOM;
+    }
+    uint8_t *vlive = (uint8_t *)malloc((size_t)n + 1);
+    uint8_t *elive = (uint8_t *)malloc((size_t)m + 1);
+    uint8_t *fail_v = (uint8_t *)malloc((size_t)n + 1);
+    uint8_t *fail_e = (uint8_t *)malloc((size_t)m + 1);
+    int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    int64_t rounds = 0, dominated = 0;
+    if (!vlive || !elive || !fail_v || !fail_e || !deg) {
+        rc = KZO_ERR_OOM;
+        goto done;
+    }
+    memset(vlive, 1, (size_t)n);
+    memset(elive, 1, (size_t)m);
+    for (;;) {
+        /* colour-index Jacobi sweeps from the current state */
+        for (;;) {
+            int64_t nv = 0, ne = 0;
+            for (int32_t v = 0; v < n; v++) {
+                fail_v[v] = vlive[v] && vertex_index(&g, elive, &s, v) < q - 1;
+                nv += fail_v[v];
+            }
+            for (int64_t e = 0; e < m; e++) {
+                fail_e[e] = elive[e] && edge_index(&g, elive, &s, edges[2 * e], edges[2 * e + 1]) < q - 2;
+                ne += fail_e[e];
+            }
+            if (nv == 0 && ne == 0) break;
+            for (int32_t v = 0; v < n; v++)
+                if (fail_v[v]) vlive[v] = 0;
+            for (int64_t e = 0; e < m; e++)
+                if (elive[e] && (fail_e[e] || fail_v[edges[2 * e]] || fail_v[edges[2 * e + 1]])) elive[e] = 0;
+        }
+        /* one dominance round on the snapshot */
+        for (int32_t v = 0; v < n; v++) {
+            deg[v] = 0;
+            for (int64_t i = g.off[v]; i < g.off[v + 1]; i++) deg[v] += elive[g.eid[i]];
+        }
+        int64_t nd = 0;
+        for (int32_t a = 0; a < n; a++) {
+            fail_v[a] = 0;
+            if (!vlive[a]) continue;
+            for (int32_t b = 0; b < n && !fail_v[a]; b++) {
+                if (b == a || !vlive[b] || deg[b] < deg[a]) continue;
+                /* mark the live neighbours of b; a must not be one of them */
+                s.stamp++;
+                for (int64_t i = g.off[b]; i < g.off[b + 1]; i++)
+                    if (elive[g.eid[i]]) s.nbr_mark[g.nbr[i]] = s.stamp;
+                if (s.nbr_mark[a] == s.stamp) continue;
+                int subset = 1;
+                for (int64_t i = g.off[a]; i < g.off[a + 1] && subset; i++)
+                    if (elive[g.eid[i]] && s.nbr_mark[g.nbr[i]] != s.stamp) subset = 0;
+                if (!subset) continue;
+                /* equal neighbourhoods: only the smaller key (colour, id) goes */
+                if (deg[a] == deg[b] &&
+                    (colour[b] < colour[a] || (colour[b] == colour[a] && b < a))) continue;
+                fail_v[a] = 1;
+            }
+            nd += fail_v[a];
+        }
+        if (nd == 0) break;
+        rounds++;
+        dominated += nd;
+        for (int32_t v = 0; v < n; v++)
+            if (fail_v[v]) vlive[v] = 0;
+        for (int64_t e = 0; e < m; e++)
+            if (elive[e] && (fail_v[edges[2 * e]] || fail_v[edges[2 * e + 1]])) elive[e] = 0;
+    }
+    if (vlive_out) memcpy(vlive_out, vlive, (size_t)n);
+    if (elive_out) memcpy(elive_out, elive, (size_t)m);
+    if (rounds_out) *rounds_out = rounds;
+    if (dominated_out) *dominated_out = dominated;
+done:
+    free(vlive);
+    free(elive);
+    free(fail_v);
+    free(fail_e);
+    free(deg);
+    scratch_free(&s);
+    adj_free(&g);
+    return rc;
+}
+
+/*
  * Colour indices of chosen elements on a given live state (vlive, elive).
  * The state must be consistent: a live edge has live endpoints.  Used for
  * the Figure 8 worked example and for sampled checks on large graphs.

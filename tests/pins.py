@@ -290,7 +290,76 @@ def pin_q_cliques_and_order(orc, cases=12):
     return None
 
 
+def _live_nbrs(n, edges, vlive, elive):
+    nb = [set() for _ in range(n)]
+    for i, (u, v) in enumerate(np.asarray(edges).tolist()):
+        if elive[i]:
+            nb[u].add(v)
+            nb[v].add(u)
+    return nb
+
+
+def pin_dominance_examples(orc):
+    """Definition 4.3.1 on hand-made graphs.  (1) Twins: a path a-c-b with a,
+    b of colour 0 and c of colour 1 (k = 2): N(a) = N(b) = {c}; of two
+    vertices with equal neighbourhoods only the smaller key (colour, id)
+    goes, so a (id 0) is deleted and b, c and their edge stay.  (2) Strict
+    subsets: k = 3, a and b of colour 0, c and d of colour 1, e of colour 2,
+    edges a-c, a-e, c-e, b-c, b-d, b-e, d-e.  N(a) = {c, e} lies inside
+    N(b) = {c, d, e} and N(d) = {b, e} inside N(c) = {a, b, e}, so a and d
+    go in one round; the triangle b-c-e remains, and nothing in it is
+    dominated (its vertices are pairwise adjacent)."""
+    r = orc.fixpoint_dominance(np.array([0, 0, 1], np.int32), np.array([[0, 2], [1, 2]], np.int32), 2)
+    if r["vlive"].tolist() != [0, 1, 1] or r["elive"].tolist() != [0, 1] or r["rounds"] != 1:
+        return f"twins: {r['vlive'].tolist()} {r['elive'].tolist()} rounds {r['rounds']}"
+    colour = np.array([0, 0, 1, 1, 2], np.int32)
+    edges = np.array([[0, 2], [0, 4], [2, 4], [1, 2], [1, 3], [1, 4], [3, 4]], np.int32)
+    r = orc.fixpoint_dominance(colour, edges, 3)
+    if r["vlive"].tolist() != [0, 1, 1, 0, 1] or r["elive"].tolist() != [0, 0, 1, 1, 0, 1, 0] or \
+            r["dominated"] != 2 or r["rounds"] != 1:
+        return f"strict subset: {r['vlive'].tolist()} {r['elive'].tolist()} dominated {r['dominated']}"
+    # (3) No edges, q = 2: the vertex rule removes every vertex (it needs one
+    # neighbour) before dominance could keep the largest of the equal twins.
+    r = orc.fixpoint_dominance(np.array([0, 1, 2], np.int32), np.zeros((0, 2), np.int32), 3, clique_k=2)
+    if r["vlive"].tolist() != [0, 0, 0] or r["rounds"] != 0:
+        return f"edgeless q=2: {r['vlive'].tolist()} rounds {r['rounds']}"
+    return None
+
+
+def pin_dominance_keeps_cliques(orc, cases=16):
+    """Vertex dominance keeps the clique number: a q-clique exists in the
+    graph exactly when one exists in the result (checked by exhaustive
+    enumeration), and the result is closed: no live vertex is dominated (two
+    with equal neighbourhoods are allowed only when neither would go) and no
+    element fails a colour-index rule."""
+    rng = np.random.default_rng(909)
+    for s in range(cases):
+        n = int(rng.integers(8, 28))
+        k = int(rng.integers(3, 6))
+        p = float(rng.uniform(0.35, 0.85))
+        colour, edges = _graph(15000 + s, n, k, p, planted=(s % 2 == 0))
+        for q in (k, k - 1):
+            r = orc.fixpoint_dominance(colour, edges, k, clique_k=q)
+            vl, el = r["vlive"].astype(bool), r["elive"].astype(bool)
+            had = bool(refs.q_cliques(n, q, colour, edges))
+            kept = bool(refs.q_cliques(n, q, colour, edges[el])) if el.any() else False
+            if had != kept:
+                return f"q-clique existence changed (q={q}, case {s}): before {had}, after {kept}"
+            nb = _live_nbrs(n, edges, vl, el)
+            for i, (u, v) in enumerate(np.asarray(edges).tolist()):
+                if el[i] and len({int(colour[w]) for w in nb[u] & nb[v]}) < q - 2:
+                    return f"live edge fails the edge rule (case {s})"
+            for a in np.flatnonzero(vl).tolist():
+                if len({int(colour[w]) for w in nb[a]}) < q - 1:
+                    return f"live vertex fails the vertex rule (case {s})"
+                for b in np.flatnonzero(vl).tolist():
+                    if b != a and nb[a] <= nb[b] and b not in nb[a]:
+                        if nb[a] != nb[b] or (int(colour[b]), b) > (int(colour[a]), a):
+                            return f"vertex {a} still dominated by {b} (case {s})"
+    return None
+
+
 ALL_PINS = [pin_fig8, pin_brute_force, pin_k3_triangles, pin_k2, pin_k1, pin_complete_kpartite,
             pin_empty_class, pin_planted_isolated, pin_clique_survival, pin_order_independence,
             pin_certificate, pin_incident_edges_fail, pin_validation, pin_brute_force_q,
-            pin_q_cliques_and_order]
+            pin_q_cliques_and_order, pin_dominance_examples, pin_dominance_keeps_cliques]

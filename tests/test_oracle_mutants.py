@@ -10,11 +10,15 @@ from tests import pins
 
 MUTANTS = {
     # vertex rule threshold off by one (index < q-2 instead of < q-1)
-    "vertex_threshold": ("vertex_index(&g, elive, &s, v) < q - 1", "vertex_index(&g, elive, &s, v) < q - 2"),
+    "vertex_threshold": ("(vlive[v] && vertex_index(&g, elive, &s, v) < q - 1) {", "(vlive[v] && vertex_index(&g, elive, &s, v) < q - 2) {"),
     # edge rule threshold off by one
     "edge_threshold": ("edges[2 * e + 1]) < q - 2)", "edges[2 * e + 1]) < q - 3)"),
     # the clique size ignored: thresholds from the colour count
-    "vertex_threshold_from_k": ("vertex_index(&g, elive, &s, v) < q - 1", "vertex_index(&g, elive, &s, v) < k - 1"),
+    "vertex_threshold_from_k": ("(vlive[v] && vertex_index(&g, elive, &s, v) < q - 1) {", "(vlive[v] && vertex_index(&g, elive, &s, v) < k - 1) {"),
+    # the same thresholds in the dominance procedure's colour-index phases
+    "dominance_vertex_threshold": ("fail_v[v] = vlive[v] && vertex_index(&g, elive, &s, v) < q - 1;",
+                                   "fail_v[v] = vlive[v] && vertex_index(&g, elive, &s, v) < q - 2;"),
+    "dominance_edge_threshold": ("edges[2 * e], edges[2 * e + 1]) < q - 2;", "edges[2 * e], edges[2 * e + 1]) < q - 3;"),
     "edge_threshold_from_k": ("edges[2 * e + 1]) < q - 2)", "edges[2 * e + 1]) < k - 2)"),
     # common neighbour test dropped: counts every neighbour of v
     "no_common_check": ("        if (s->nbr_mark[w] != s->stamp) continue;\n", ""),
@@ -25,6 +29,10 @@ MUTANTS = {
     # a dead edge still counts as a witness in the edge index
     "dead_witness_edge": ("    for (int64_t i = g->off[v]; i < g->off[v + 1]; i++) {\n        if (!elive[g->eid[i]]) continue;\n        int32_t w = g->nbr[i];",
                           "    for (int64_t i = g->off[v]; i < g->off[v + 1]; i++) {\n        int32_t w = g->nbr[i];"),
+    # dominance: both of two vertices with equal neighbourhoods deleted
+    "dominance_no_tie_break": ("                if (deg[a] == deg[b] &&\n", "                if (0 && deg[a] == deg[b] &&\n"),
+    # dominance: the dominator deleted instead of the dominated vertex
+    "dominance_reversed": ("if (b == a || !vlive[b] || deg[b] < deg[a]) continue;", "if (b == a || !vlive[b] || deg[b] > deg[a]) continue;"),
     # the sweep index recorded one too late
     "sweep_off_by_one": ("if (v_sweep) v_sweep[v] = (int32_t)sweeps;", "if (v_sweep) v_sweep[v] = (int32_t)sweeps + 1;"),
     # Gauss-Seidel instead of Jacobi: vertices leave before the edge rule runs
