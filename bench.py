@@ -528,6 +528,7 @@ def run_max_clique(args, world, rank, local, pg):
     reset, kernelize for clique size q on the GPU, search the kernel (host
     branch and bound), stop at the first q with a clique.  Timed on the wall
     clock (the search runs on the host), after warm-up runs."""
+    import torch
     import paper_2212_00574_gb300 as kz
     dev = torch.device("cuda", local)
     kz.use_torch_allocator()

@@ -131,7 +131,14 @@ typedef struct {
                              q < k runs on the BITSET, SMALL, SPARSE and TENSOR paths with the plain
                              schedule; the LEARNED and SUPPORT schedules and the FUSED batch return
                              KZ_ERR_UNSUPPORTED for it */
-    int32_t reserved[6];  /* must be zero */
+    int32_t dominance;    /* 1: after the colour-index fixpoint, rounds of vertex dominance (thesis
+                             Section 4.3, Definition 4.3.1), each followed by the fixpoint again, until
+                             a round deletes nothing; 0 (default): off.  Opt-in because dominance keeps
+                             the clique number but may delete some maximum cliques.  Needs bitset rows
+                             (paths BITSET, SMALL, TENSOR) and the plain schedule, else
+                             KZ_ERR_UNSUPPORTED; kz_kernelize_batch refuses it.  The statistics and
+                             the trace then cover the last colour-index run */
+    int32_t reserved[5];  /* must be zero */
 } kz_options;
 
 /* Fill *opt with the defaults (AUTO path, PLAIN schedule, no sweep limit,
@@ -149,7 +156,9 @@ typedef struct {
     int32_t status;        /* kz_status recorded on the device by the last kz_kernelize */
     int32_t k;             /* colours */
     int32_t clique_k;      /* clique size q the last kz_kernelize used */
-    int32_t reserved[4];
+    int32_t dominance_rounds;  /* dominance rounds of the last kz_kernelize that deleted something */
+    int32_t dominated;     /* vertices those rounds deleted */
+    int32_t reserved[2];
 } kz_stats;
 
 /* Optional device allocator (for example a caching allocator owned by the

@@ -53,14 +53,14 @@ class KzError(RuntimeError):
 class kz_options(C.Structure):
     _fields_ = [("path", C.c_int32), ("schedule", C.c_int32), ("max_sweeps", C.c_int64),
                 ("use_graph", C.c_int32), ("plane0", C.c_int32), ("batch", C.c_int32),
-                ("clique_k", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("clique_k", C.c_int32), ("dominance", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class kz_stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("n_live", C.c_int64), ("m_live", C.c_int64),
                 ("sweeps", C.c_int64), ("passes", C.c_int64), ("edge_tests", C.c_int64),
                 ("path", C.c_int32), ("status", C.c_int32), ("k", C.c_int32), ("clique_k", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("dominance_rounds", C.c_int32), ("dominated", C.c_int32), ("reserved", C.c_int32 * 2)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

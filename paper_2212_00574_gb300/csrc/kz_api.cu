@@ -106,6 +106,7 @@ void release(kz_graph g) {
   if (g->run_exec) cudaGraphExecDestroy(g->run_exec);
   learned_release(g);
   tensor_release(g);
+  dominance_release(g);
   support_release(g);
   for (auto &a : g->allocs) dev_free(a.p, a.bytes, s);
   g->allocs.clear();
@@ -240,7 +241,7 @@ kz_status kz_load_graph_dense(int32_t n, int32_t k, const int32_t *colour,
 static kz_status read_options(const kz_options *opt, kz_options &o) {
   if (opt) {
     o = *opt;
-    for (int i = 0; i < 6; i++)
+    for (int i = 0; i < 5; i++)
       if (o.reserved[i]) return KZ_ERR_ARG;
   } else {
     kz_default_options(&o);
@@ -251,6 +252,7 @@ static kz_status read_options(const kz_options *opt, kz_options &o) {
   if (o.plane0 < KZ_PLANE0_AUTO || o.plane0 > KZ_PLANE0_TWO) return KZ_ERR_ARG;
   if (o.batch < KZ_BATCH_CONCURRENT || o.batch > KZ_BATCH_FUSED) return KZ_ERR_ARG;
   if (o.clique_k < 0) return KZ_ERR_ARG;
+  if (o.dominance < 0 || o.dominance > 1) return KZ_ERR_ARG;
   return KZ_OK;
 }
 
@@ -326,6 +328,9 @@ kz_status kz_kernelize(kz_graph g, const kz_options *opt, void *stream) {
   KZ_TRY(read_options(opt, o));
   KZ_TRY(set_clique(g, o));
   g->stream = (cudaStream_t)stream;
+  g->dom_rounds = 0;
+  g->dom_removed = 0;
+  if (o.dominance && (o.schedule != KZ_SCHED_PLAIN || !g->has_bitset)) return KZ_ERR_UNSUPPORTED;
   if (o.schedule == KZ_SCHED_LEARNED) {
     // learned worklist rounds on the bitset rows, certified by plain sweeps
     if (!g->has_bitset || !g->model) return KZ_ERR_UNSUPPORTED;
@@ -348,7 +353,22 @@ kz_status kz_kernelize(kz_graph g, const kz_options *opt, void *stream) {
     return KZ_OK;
   }
   const int path = o.path == KZ_PATH_AUTO ? auto_path(g) : o.path;
-  return run_one(g, o, path);
+  if (o.dominance && path == KZ_PATH_SPARSE) return KZ_ERR_UNSUPPORTED;
+  KZ_TRY(run_one(g, o, path));
+  if (!o.dominance) return KZ_OK;
+  // rounds of vertex dominance, each followed by the colour-index fixpoint
+  for (;;) {
+    int32_t status = 0;
+    KZ_CUDA_TRY(cudaMemcpyAsync(&status, &g->st->status, 4, cudaMemcpyDeviceToHost, g->stream));
+    KZ_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (status != KZ_OK) return KZ_OK;  // a sweep limit or timeout ends the run; fetch reports it
+    int64_t removed = 0;
+    KZ_TRY(dominance_round(g, &removed, g->stream));
+    if (removed == 0) return KZ_OK;
+    g->dom_rounds++;
+    g->dom_removed += removed;
+    KZ_TRY(run_one(g, o, path));
+  }
 }
 
 }  // extern "C"
@@ -473,6 +493,7 @@ kz_status kz_kernelize_batch(kz_graph *graphs, int32_t count, const kz_options *
     if (!graphs[i]) return KZ_ERR_ARG;
   kz_options o;
   KZ_TRY(read_options(opt, o));
+  if (o.dominance) return KZ_ERR_UNSUPPORTED;
   if (o.schedule != KZ_SCHED_PLAIN) {
     for (int32_t i = 0; i < count; i++) KZ_TRY(kz_kernelize(graphs[i], &o, stream));
     return KZ_OK;
@@ -523,6 +544,8 @@ kz_status kz_fetch_stats(kz_graph g, kz_stats *stats) {
     stats->status = hs.status;
     stats->k = g->k;
     stats->clique_k = g->k - g->slack;
+    stats->dominance_rounds = g->dom_rounds;
+    stats->dominated = (int32_t)g->dom_removed;
     KZ_TRY(owner_vertex_alive(g, nullptr, &stats->n_live));
     stats->m_live = -1;  // filled by the fetch calls that count edges
   }

@@ -203,6 +203,9 @@ struct kz_graph_s {
   void *learned_bufs = nullptr;
   void *tensor_bufs = nullptr;  // tensor-core path scratch
   void *support_bufs = nullptr; // per-class support counts (CSR path, support schedule)
+  void *dominance_bufs = nullptr;  // vertex dominance rounds
+  int32_t dom_rounds = 0;          // dominance rounds of the last kz_kernelize that deleted something
+  int64_t dom_removed = 0;         // vertices they deleted
 
   // executable CUDA graph of the device-side sweep loop (built lazily)
   cudaGraphExec_t loop_exec = nullptr;
@@ -251,6 +254,10 @@ void tensor_release(kz_graph g);
 // The driver's cuTensorMapEncodeTiled, found through the runtime's entry-point
 // query (null when the driver does not provide it).
 void *tensor_map_encoder();
+// One round of vertex dominance (Definition 4.3.1) on the current bitset rows;
+// synchronous, returns the vertices deleted.
+kz_status dominance_round(kz_graph g, int64_t *removed, cudaStream_t s);
+void dominance_release(kz_graph g);
 
 // Learned schedule (kz_learned.cu).
 kz_status learned_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s);

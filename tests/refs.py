@@ -195,6 +195,27 @@ def q_cliques(n, q, colour, edges):
     return out
 
 
+def has_q_clique(n, q, colour, edges):
+    """Whether a clique of q vertices exists: depth-first extension that stops
+    at the first one (dense graphs hold far too many to list)."""
+    adj = [set() for _ in range(n)]
+    for u, v in edges:
+        adj[int(u)].add(int(v))
+        adj[int(v)].add(int(u))
+
+    def rec(size, cand):
+        if size == q:
+            return True
+        if size + len(cand) < q:
+            return False
+        for v in sorted(cand):
+            if rec(size + 1, {w for w in cand & adj[v] if w > v}):
+                return True
+        return False
+
+    return q <= 0 or rec(0, set(range(n)))
+
+
 # ----------------------------------------------------------------------------
 # random-order deletion
 # ----------------------------------------------------------------------------
