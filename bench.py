@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clique-k", type=int, default=0,
                     help="clique size q sought (0: q = k); q < k lowers both rule thresholds")
+    ap.add_argument("--tensor-precision", choices=["fp8", "bf16"], default="fp8",
+                    help="tensor path operands: E4M3 (kind::f8f6f4) or BF16 (kind::f16)")
+    ap.add_argument("--dominance", action="store_true",
+                    help="vertex dominance rounds (Definition 4.3.1) after the colour-index fixpoint")
     ap.add_argument("--max-clique", action="store_true",
                     help="time the maximum-clique driver (kernelize for q = k, k-1, ... and search each kernel)")
     ap.add_argument("--scale", type=float, default=1.0,
@@ -283,7 +287,9 @@ def run_ours(args, world, rank, local, pg):
         h = kz.kz_load_graph(g.n, g.k, h_col, h_edges, stream=stream)
     opts = kz.kz_default_options(path=args.path, use_graph={"device": 1, "graph": 2, "host": 0}[args.loop],
                                  plane0={"auto": 0, "full": 1, "half": 2, "two": 3}[args.plane0],
-                                 schedule=args.schedule, clique_k=args.clique_k)
+                                 schedule=args.schedule, clique_k=args.clique_k,
+                                 dominance=1 if args.dominance else 0,
+                                 tensor_precision=1 if args.tensor_precision == "bf16" else 0)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def step(i, ev0=None, ev1=None):
@@ -361,7 +367,7 @@ def run_ours(args, world, rank, local, pg):
         t_side = (g.n + 127) // 128
         flops = 2.0 * 128 * 128 * 32 * ksteps * t_side * (t_side + 1) / 2
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        fp8_peak = 2.0 * peaks["bf16_tflops"] * 1e12
+        fp8_peak = (1.0 if args.tensor_precision == "bf16" else 2.0) * peaks["bf16_tflops"] * 1e12
         roofline = {"bound": "tensor", "achieved": flops / launch_s / 1e12, "peak": fp8_peak / 1e12,
                     "unit": "TFLOP/s", "frac": flops / launch_s / fp8_peak,
                     "traffic": MEASURED_TRAFFIC.get((args.workload, kernel)), "kernel": kernel,
@@ -433,7 +439,8 @@ def run_ours(args, world, rank, local, pg):
                        "pass_loop": {"device": "one cooperative persistent launch", "graph": "CUDA-graph while node",
                                      "host": "host-driven"}[args.loop],
                        "passes": passes, "sweeps": st["sweeps"], "schedule": args.schedule,
-                       "clique_k": st["clique_k"],
+                       "clique_k": st["clique_k"], "dominance_rounds": st["dominance_rounds"],
+                       "dominated": st["dominated"],
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); per-step CUDA events "
                              "around kz_kernelize only",
                        "parallelism": "replicas" if world > 1 else "single"},

@@ -138,7 +138,10 @@ typedef struct {
                              (paths BITSET, SMALL, TENSOR) and the plain schedule, else
                              KZ_ERR_UNSUPPORTED; kz_kernelize_batch refuses it.  The statistics and
                              the trace then cover the last colour-index run */
-    int32_t reserved[5];  /* must be zero */
+    int32_t tensor_precision;  /* TENSOR path operands: 0 (default) E4M3 0/1 through
+                                  tcgen05.mma kind::f8f6f4; 1 BF16 0/1 through kind::f16 (twice
+                                  the operand bytes and MMAs; the same exact counts) */
+    int32_t reserved[4];  /* must be zero */
 } kz_options;
 
 /* Fill *opt with the defaults (AUTO path, PLAIN schedule, no sweep limit,

@@ -53,7 +53,8 @@ class KzError(RuntimeError):
 class kz_options(C.Structure):
     _fields_ = [("path", C.c_int32), ("schedule", C.c_int32), ("max_sweeps", C.c_int64),
                 ("use_graph", C.c_int32), ("plane0", C.c_int32), ("batch", C.c_int32),
-                ("clique_k", C.c_int32), ("dominance", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("clique_k", C.c_int32), ("dominance", C.c_int32), ("tensor_precision", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
 
 
 class kz_stats(C.Structure):

@@ -241,7 +241,7 @@ kz_status kz_load_graph_dense(int32_t n, int32_t k, const int32_t *colour,
 static kz_status read_options(const kz_options *opt, kz_options &o) {
   if (opt) {
     o = *opt;
-    for (int i = 0; i < 5; i++)
+    for (int i = 0; i < 4; i++)
       if (o.reserved[i]) return KZ_ERR_ARG;
   } else {
     kz_default_options(&o);
@@ -253,6 +253,7 @@ static kz_status read_options(const kz_options *opt, kz_options &o) {
   if (o.batch < KZ_BATCH_CONCURRENT || o.batch > KZ_BATCH_FUSED) return KZ_ERR_ARG;
   if (o.clique_k < 0) return KZ_ERR_ARG;
   if (o.dominance < 0 || o.dominance > 1) return KZ_ERR_ARG;
+  if (o.tensor_precision < 0 || o.tensor_precision > 1) return KZ_ERR_ARG;
   return KZ_OK;
 }
 

@@ -12,6 +12,10 @@
 // matrix is stored half-step-major: M[h][x][0..15] holds bits 16(h%2) ..
 // 16(h%2)+15 of block word h/2 of row x (0x38 = E4M3 1.0 for a set bit), so
 // the 128 rows of a tile form one contiguous 2048-byte run per half-step.
+// A BF16 variant (kind::f16, 0x3F80 = 1.0) spends two bytes per vertex: one
+// MMA step then covers 16 vertices (half a block word) in the same 32 bytes
+// per row, so the layout, boxes and descriptors are the same and a class
+// takes twice the steps.
 // One TMA box (8 half-steps x 2048 bytes, read as 8-byte elements so that
 // the box's inner extent is the whole contiguous run) then lands in shared
 // memory as four consecutive canonical no-swizzle K-major MMA operands:
@@ -96,13 +100,16 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t rows) {
   return d;
 }
 
-// Instruction descriptor: dense, D = f32, A = B = E4M3, both K-major,
-// N = 256, M = 128.
+// Instruction descriptor: dense, D = f32, both operands K-major, N = 256,
+// M = 128; A = B = E4M3 (kind::f8f6f4, format code 0) or A = B = BF16
+// (kind::f16, format code 1).
+template <bool BF16>
 __device__ __forceinline__ uint32_t make_idesc() {
+  const uint32_t fmt = BF16 ? 1u : 0u;
   uint32_t d = 0;
   d |= 1u << 4;                        // D format f32
-  d |= 0u << 7;                        // A format E4M3
-  d |= 0u << 10;                       // B format E4M3
+  d |= fmt << 7;                       // A format
+  d |= fmt << 10;                      // B format
   d |= ((uint32_t)kTileN >> 3) << 17;  // N >> 3
   d |= ((uint32_t)kTile >> 4) << 24;   // M >> 4
   return d;
@@ -113,6 +120,17 @@ __device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t a, uint64_t b, 
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n"
+      :
+      : "r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// The same MMA on BF16 0/1 operands: K = 16 elements, the same 32 bytes per
+// operand row as one E4M3 K-step.
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
       :
       : "r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
@@ -269,6 +287,7 @@ struct TensorMaps {
   CUtensorMap a_stage, a_step, b_stage, b_step;
 };
 
+template <bool BF16>
 __global__ void __launch_bounds__(kThreads, 1) tensor_edge_kernel(const __grid_constant__ TensorMaps maps,
                                                                   TensorArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -352,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1) tensor_edge_kernel(const __grid_c
     __syncwarp();
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
-    const uint32_t idesc = make_idesc();
+    const uint32_t idesc = make_idesc<BF16>();
     int stage = 0, abuf = 0;
     uint32_t ph = 0, empty_ph = 0;  // bit b: parity of accumulator b's next release
     for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
@@ -368,9 +387,12 @@ __global__ void __launch_bounds__(kThreads, 1) tensor_edge_kernel(const __grid_c
           tc_fence_after();
           if (lane == 0) {
             const uint32_t sA = sbase + stage * kStageBytes, sB = sA + kABytes;
-            for (int j = 0; j < ns; j++)
-              mma_f8(tmem + (uint32_t)abuf * kAccCols, make_desc(sA + j * kStepA, kTile),
-                     make_desc(sB + j * kStepB, kTileN), idesc, (s0 > sb || j > 0) ? 1u : 0u);
+            for (int j = 0; j < ns; j++) {
+              const uint64_t da = make_desc(sA + j * kStepA, kTile), db = make_desc(sB + j * kStepB, kTileN);
+              const uint32_t acc = (s0 > sb || j > 0) ? 1u : 0u;
+              if constexpr (BF16) mma_bf16(tmem + (uint32_t)abuf * kAccCols, da, db, idesc, acc);
+              else mma_f8(tmem + (uint32_t)abuf * kAccCols, da, db, idesc, acc);
+            }
             mma_commit(empty0 + 8 * stage);  // stage free once these MMAs have read it
           }
           __syncwarp();
@@ -487,23 +509,35 @@ __global__ void __launch_bounds__(kThreads, 1) tensor_edge_kernel(const __grid_c
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-// Byte matrix from the current rows, half-step-major (see the top of this
-// file): thread t writes both halves of K-step s = t / n_pad of row
-// x = t % n_pad, so a warp's stores are contiguous.  step_word[s] is the
-// word (r * k + c) of the row that K-step s expands.
+// Operand matrix from the current rows, half-step-major (see the top of this
+// file): thread t writes both 16-byte halves of MMA step s = t / n_pad of row
+// x = t % n_pad, so a warp's stores are contiguous.  E4M3: one step is a
+// whole 32-bit block word, step_word[s] = its index r * k + c in the row,
+// one byte per vertex (0x38 = 1.0).  BF16: one step is half a block word,
+// step_word[s] = 2 (r * k + c) + half, two bytes per vertex (0x3F80 = 1.0).
+template <bool BF16>
 __global__ void expand_kernel(const uint32_t *__restrict__ A, int32_t n, int32_t n_pad, int32_t ldw,
                               const int32_t *__restrict__ step_word, int32_t ksteps, uint8_t *__restrict__ M) {
   const int64_t total = (int64_t)n_pad * ksteps;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int32_t s = (int32_t)(t / n_pad);
     const int32_t x = (int32_t)(t - (int64_t)s * n_pad);
-    const uint32_t word = x < n ? __ldg(A + (int64_t)x * ldw + step_word[s]) : 0u;
+    const int32_t sw = step_word[s];
+    const int32_t wi = BF16 ? (sw >> 1) : sw;
+    const uint32_t word = x < n ? __ldg(A + (int64_t)x * ldw + wi) : 0u;
     uint32_t out[8];
+    if constexpr (BF16) {
+      const uint32_t bits = (sw & 1) ? (word >> 16) : (word & 0xFFFFu);
 #pragma unroll
-    for (int q = 0; q < 8; q++) {
-      // bits 4q .. 4q+3 to bytes: bit j of the nibble lands on bit 8j of the product
-      const uint32_t nib = (word >> (4 * q)) & 0xFu;
-      out[q] = ((nib * 0x00204081u) & 0x01010101u) * 0x38u;
+      for (int q = 0; q < 8; q++)
+        out[q] = (((bits >> (2 * q)) & 1u) ? 0x3F80u : 0u) | (((bits >> (2 * q + 1)) & 1u) ? 0x3F800000u : 0u);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        // bits 4q .. 4q+3 to bytes: bit j of the nibble lands on bit 8j of the product
+        const uint32_t nib = (word >> (4 * q)) & 0xFu;
+        out[q] = ((nib * 0x00204081u) & 0x01010101u) * 0x38u;
+      }
     }
     uint4 *lo = reinterpret_cast<uint4 *>(M + ((int64_t)(2 * s) * n_pad + x) * 16);
     uint4 *hi = reinterpret_cast<uint4 *>(M + ((int64_t)(2 * s + 1) * n_pad + x) * 16);
@@ -607,14 +641,23 @@ struct TensorBufs {
   TensorMaps maps;
 };
 
-static kz_status tensor_prepare(kz_graph g, TensorBufs &b, cudaStream_t s) {
+// Buffers per operand precision (0 E4M3, 1 BF16), built on first use.
+struct TensorState {
+  TensorBufs *by[2] = {nullptr, nullptr};
+};
+
+static kz_status tensor_prepare(kz_graph g, TensorBufs &b, bool bf16, cudaStream_t s) {
   b.n_pad = (g->n + kTileN - 1) / kTileN * kTileN;
+  // MMA steps per class: one per block word (E4M3), two (BF16: 16 vertices
+  // of two bytes fill the 32 bytes per row of one MMA)
+  const int per = bf16 ? 2 : 1;
   std::vector<int32_t> cs((size_t)g->k + 1, 0);
-  for (int c = 0; c < g->k; c++) cs[c + 1] = cs[c] + g->rounds[c];
+  for (int c = 0; c < g->k; c++) cs[c + 1] = cs[c] + per * g->rounds[c];
   b.ksteps = std::max(cs[g->k], 1);
   std::vector<int32_t> sw((size_t)b.ksteps, 0);
   for (int c = 0; c < g->k; c++)
-    for (int r = 0; r < g->rounds[c]; r++) sw[cs[c] + r] = r * g->k + c;
+    for (int r = 0; r < g->rounds[c]; r++)
+      for (int h = 0; h < per; h++) sw[cs[c] + per * r + h] = bf16 ? 2 * (r * g->k + c) + h : r * g->k + c;
   const size_t mbytes = (size_t)b.n_pad * b.ksteps * kStep;
   KZ_TRY(graph_alloc(g, &b.M, mbytes, s));
   if (reinterpret_cast<uintptr_t>(b.M) % 16 != 0) return KZ_ERR_CUDA;  // TMA needs a 16-byte aligned base
@@ -691,26 +734,29 @@ static kz_status tensor_prepare(kz_graph g, TensorBufs &b, cudaStream_t s) {
 
 kz_status tensor_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
   if (g->k > 64) return KZ_ERR_UNSUPPORTED;
-  if (!g->tensor_bufs) {
-    TensorBufs *b = new TensorBufs();
-    kz_status st = tensor_prepare(g, *b, s);
+  const bool bf16 = opt.tensor_precision == 1;
+  if (!g->tensor_bufs) g->tensor_bufs = new TensorState();
+  TensorState &ts = *static_cast<TensorState *>(g->tensor_bufs);
+  if (!ts.by[bf16]) {
+    TensorBufs *nb = new TensorBufs();
+    kz_status st = tensor_prepare(g, *nb, bf16, s);
     if (st != KZ_OK) {
-      delete b;
+      delete nb;
       return st;
     }
-    g->tensor_bufs = b;
+    ts.by[bf16] = nb;
   }
-  TensorBufs &b = *static_cast<TensorBufs *>(g->tensor_bufs);
+  TensorBufs &b = *ts.by[bf16];
   const int64_t max_sweeps = opt.max_sweeps > 0 ? opt.max_sweeps : (int64_t)g->n + g->m + 1;
   KZ_TRY(bitset_begin_run(g, max_sweeps, s));
   if (g->n == 0) return KZ_OK;
   int dev = 0;
   KZ_CUDA_TRY(cudaGetDevice(&dev));
-  static bool configured[64] = {};
-  if (dev < 64 && !configured[dev]) {
-    KZ_CUDA_TRY(cudaFuncSetAttribute((const void *)tensor_edge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kSmemBytes));
-    configured[dev] = true;
+  static bool configured[64][2] = {};
+  if (dev < 64 && !configured[dev][bf16]) {
+    const void *fn = bf16 ? (const void *)tensor_edge_kernel<true> : (const void *)tensor_edge_kernel<false>;
+    KZ_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+    configured[dev][bf16] = true;
   }
   const int sms = sms_t();
   for (;;) {
@@ -719,7 +765,8 @@ kz_status tensor_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
     KZ_CUDA_TRY(cudaStreamSynchronize(s));
     const uint32_t *A = g->A[cur & 1];
     uint32_t *An = g->A[(cur & 1) ^ 1];
-    expand_kernel<<<8 * sms, 256, 0, s>>>(A, g->n, b.n_pad, g->ldw, b.step_word, b.ksteps, b.M);
+    if (bf16) expand_kernel<true><<<8 * sms, 256, 0, s>>>(A, g->n, b.n_pad, g->ldw, b.step_word, b.ksteps, b.M);
+    else expand_kernel<false><<<8 * sms, 256, 0, s>>>(A, g->n, b.n_pad, g->ldw, b.step_word, b.ksteps, b.M);
     TensorArgs a;
     a.n = g->n;
     a.k = g->k;
@@ -734,7 +781,8 @@ kz_status tensor_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
     a.counts = b.counts;
     a.status = &g->st->status;
     const int grid = std::max(1, std::min(b.n_tiles, sms));
-    tensor_edge_kernel<<<grid, kThreads, kSmemBytes, s>>>(b.maps, a);
+    if (bf16) tensor_edge_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(b.maps, a);
+    else tensor_edge_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(b.maps, a);
     tensor_commit_kernel<<<8 * sms, 256, 0, s>>>(A, An, b.Edel, g->V[cur & 1], g->V[(cur & 1) ^ 1], g->n, g->ldw,
                                                  g->k, g->k - g->slack, g->R, b.col, g->d_coff, g->d_rounds, g->d_blocks,
                                                  (int32_t)g->blocks.size(), g->v_sweep, g->st, b.counts);
@@ -750,7 +798,12 @@ kz_status tensor_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
 }
 
 void tensor_release(kz_graph g) {
-  delete static_cast<TensorBufs *>(g->tensor_bufs);
+  TensorState *ts = static_cast<TensorState *>(g->tensor_bufs);
+  if (ts) {
+    delete ts->by[0];
+    delete ts->by[1];
+  }
+  delete ts;
   g->tensor_bufs = nullptr;
 }
 

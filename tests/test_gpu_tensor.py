@@ -3,6 +3,7 @@ the C ABI (GPU only).  Bit-exact: survivors, sweeps, per-sweep counts."""
 import numpy as np
 import pytest
 
+import paper_2212_00574_gb300 as kz
 from paper_2212_00574_gb300 import synth
 from tests import refs
 from tests.test_gpu_parity import _graph, _tiny_cases, assert_parity, gpu_run
@@ -75,3 +76,24 @@ def test_auto_picks_tensor_for_a_larger_sparser_graph():
     assert a["stats"]["sweeps"] == b["stats"]["sweeps"]
     g2 = synth.kpartite(4500, 12, 0.6, 78, planted=True)
     assert gpu_run(g2, path="auto", dense=True)["stats"]["path"] == 1
+
+
+@pytest.mark.parametrize("case", _tiny_cases()[1::4], ids=lambda c: f"s{c[0]}-n{c[1]}-k{c[2]}")
+def test_tensor_bf16_tiny(case):
+    # BF16 0/1 operands through kind::f16: the same exact counts
+    seed, n, k, p, planted = case
+    g = synth.tiny_random(5000 + seed, n, k, p, planted=planted and n >= k)
+    assert_parity(g, gpu_run(g, path="tensor", tensor_precision=1))
+
+
+@pytest.mark.parametrize("seed,n,k,p", [(84, 2300, 8, 0.1), (86, 2300, 4, 0.04)])
+def test_tensor_bf16_more_tiles_than_ctas(seed, n, k, p):
+    g = synth.tiny_random(seed, n, k, p, planted=True)
+    a = gpu_run(g, path="tensor", tensor_precision=1)
+    assert_parity(g, a)
+    # switching precision on one handle keeps both buffer sets apart
+    with kz.KernelGraph.from_synth(g) as kg:
+        for prec in (0, 1, 0):
+            kg.reset().kernelize(path="tensor", tensor_precision=prec)
+            alive, edges, st = kg.fetch()
+            assert np.array_equal(alive, a["alive"]) and np.array_equal(edges, a["edges"])
