@@ -145,12 +145,24 @@ kz_status load_common(int32_t n, int32_t k, const int32_t *colour, void *stream,
   if (st == KZ_OK && want_bitset) {
     st = graph_alloc(g, &g->d_perm, (size_t)std::max(n, 1), g->stream);
     if (st == KZ_OK) st = graph_alloc(g, &g->d_inv, (size_t)std::max(n, 1), g->stream);
+    if (st == KZ_OK) st = graph_alloc(g, &g->d_cpos, (size_t)std::max(n, 1), g->stream);
     if (st == KZ_OK && n > 0)
       st = cuda_status(cudaMemcpyAsync(g->d_perm, g->perm.data(), sizeof(int32_t) * n,
                                        cudaMemcpyHostToDevice, g->stream));
     if (st == KZ_OK && n > 0)
       st = cuda_status(cudaMemcpyAsync(g->d_inv, g->inv.data(), sizeof(int32_t) * n,
                                        cudaMemcpyHostToDevice, g->stream));
+    if (st == KZ_OK && n > 0) {
+      // position of every caller vertex inside a row of the block-plane layout
+      std::vector<int32_t> cpos((size_t)n);
+      for (int c = 0; c < k; c++)
+        for (int x = g->coff[c]; x < g->coff[c + 1]; x++) {
+          const int ix = x - g->coff[c];
+          cpos[g->perm[x]] = ((((ix >> 5) * k) + c) << 5) | (ix & 31);
+        }
+      st = cuda_status(cudaMemcpyAsync(g->d_cpos, cpos.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice,
+                                       g->stream));
+    }
     if (st == KZ_OK) st = pack(g);
     if (st == KZ_OK) st = bitset_finish_load(g, g->stream);
     if (st == KZ_OK) g->has_bitset = true;
@@ -225,15 +237,11 @@ kz_status kz_load_graph_dense(int32_t n, int32_t k, const int32_t *colour,
     const size_t bytes = (size_t)n * row_words * 8;
     if (bytes == 0) return bitset_pack_edges(g, nullptr, 0, true, g->stream);
     uint64_t *d_bits = (uint64_t *)dev_alloc(bytes, g->stream);
-    int32_t *d_col = (int32_t *)dev_alloc((size_t)n * 4, g->stream);
-    kz_status st = (d_bits && d_col) ? KZ_OK : KZ_ERR_OOM;
+    kz_status st = d_bits ? KZ_OK : KZ_ERR_OOM;
     if (st == KZ_OK)
       st = cuda_status(cudaMemcpyAsync(d_bits, adj_bits, bytes, cudaMemcpyHostToDevice, g->stream));
-    if (st == KZ_OK)
-      st = cuda_status(cudaMemcpyAsync(d_col, colour, (size_t)n * 4, cudaMemcpyHostToDevice, g->stream));
-    if (st == KZ_OK) st = bitset_pack_dense(g, d_bits, row_words, d_col, g->stream);
+    if (st == KZ_OK) st = bitset_pack_dense(g, d_bits, row_words, nullptr, g->stream);
     if (d_bits) dev_free(d_bits, bytes, g->stream);
-    if (d_col) dev_free(d_col, (size_t)n * 4, g->stream);
     return st;
   }, no_csr, false);
 }
@@ -558,8 +566,8 @@ kz_status kz_fetch_kernel_dense(kz_graph g, uint8_t *vertex_alive, uint64_t *adj
   if (!g) return KZ_ERR_ARG;
   if (!g->kernelized) return KZ_ERR_NOT_READY;
   if (row_words < (int64_t)((g->n + 63) / 64) || (g->n > 0 && !adj_bits)) return KZ_ERR_ARG;
-  KZ_CUDA_TRY(cudaStreamSynchronize(g->stream));
   if (g->owner == KZ_PATH_SPARSE) {
+    KZ_CUDA_TRY(cudaStreamSynchronize(g->stream));
     std::vector<int32_t> e;
     int64_t ml = 0;
     KZ_TRY(sparse_fetch(g, vertex_alive, nullptr, 0, &ml));
@@ -581,26 +589,50 @@ kz_status kz_fetch_kernel_dense(kz_graph g, uint8_t *vertex_alive, uint64_t *adj
     if (stats) *stats = tmp;
     return dev_status;
   }
+  // everything on the stream, one wait at the end: the caller-ordered rows
+  // and vertex flags (gathered on the device), the bit count, the run record
   const size_t bytes = (size_t)g->n * row_words * 8;
+  const size_t aux = 16 + (size_t)g->n;
   uint64_t *d_out = (uint64_t *)dev_alloc(std::max<size_t>(bytes, 16), g->stream);
-  unsigned long long *d_cnt = (unsigned long long *)dev_alloc(16, g->stream);
-  kz_status st = (d_out && d_cnt) ? KZ_OK : KZ_ERR_OOM;
+  uint8_t *d_aux = (uint8_t *)dev_alloc(aux, g->stream);
+  kz_status st = (d_out && d_aux) ? KZ_OK : KZ_ERR_OOM;
   unsigned long long cnt = 0;
-  if (st == KZ_OK) st = bitset_unpack_dense(g, d_out, row_words, d_cnt, g->stream);
+  std::vector<uint8_t> alive((size_t)std::max(g->n, 1));
+  DevState hs;
+  unsigned long long *d_cnt = reinterpret_cast<unsigned long long *>(d_aux);
+  if (st == KZ_OK) st = bitset_unpack_gather(g, d_out, row_words, d_aux + 16, d_cnt, g->stream);
   if (st == KZ_OK && bytes)
     st = cuda_status(cudaMemcpyAsync(adj_bits, d_out, bytes, cudaMemcpyDeviceToHost, g->stream));
+  if (st == KZ_OK && g->n)
+    st = cuda_status(cudaMemcpyAsync(alive.data(), d_aux + 16, (size_t)g->n, cudaMemcpyDeviceToHost, g->stream));
   if (st == KZ_OK)
     st = cuda_status(cudaMemcpyAsync(&cnt, d_cnt, 8, cudaMemcpyDeviceToHost, g->stream));
+  if (st == KZ_OK)
+    st = cuda_status(cudaMemcpyAsync(&hs, g->st, offsetof(DevState, trace_dv), cudaMemcpyDeviceToHost, g->stream));
   if (st == KZ_OK) st = cuda_status(cudaStreamSynchronize(g->stream));
   if (d_out) dev_free(d_out, bytes, g->stream);
-  if (d_cnt) dev_free(d_cnt, 16, g->stream);
+  if (d_aux) dev_free(d_aux, aux, g->stream);
   if (st != KZ_OK) return st;
-  kz_stats tmp;
-  kz_status dev_status = kz_fetch_stats(g, &tmp);
-  if (vertex_alive) KZ_TRY(owner_vertex_alive(g, vertex_alive, nullptr));
-  tmp.m_live = (int64_t)(cnt / 2);
-  if (stats) *stats = tmp;
-  return dev_status;
+  int64_t n_live = 0;
+  for (int32_t v = 0; v < g->n; v++) n_live += alive[v];
+  if (vertex_alive && g->n) memcpy(vertex_alive, alive.data(), (size_t)g->n);
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->n = g->n;
+    stats->m = g->m;
+    stats->sweeps = hs.sweeps;
+    stats->passes = hs.passes;
+    stats->edge_tests = hs.tests;
+    stats->path = g->path_ran;
+    stats->status = hs.status;
+    stats->k = g->k;
+    stats->clique_k = g->k - g->slack;
+    stats->dominance_rounds = g->dom_rounds;
+    stats->dominated = (int32_t)g->dom_removed;
+    stats->n_live = n_live;
+    stats->m_live = (int64_t)(cnt / 2);
+  }
+  return (kz_status)hs.status;
 }
 
 kz_status kz_fetch_kernel(kz_graph g, uint8_t *vertex_alive, int32_t *edges_out, int64_t cap,

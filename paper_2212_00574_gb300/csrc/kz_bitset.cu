@@ -162,46 +162,39 @@ __global__ void pack_edges_kernel(PackArgs a, const int32_t *__restrict__ edges,
 }
 
 // Dense caller-id bit matrix: only bits j > i are read.
-__global__ void pack_dense_kernel(PackArgs a, const uint64_t *__restrict__ bits, int64_t row_words,
-                                  int32_t n, const int32_t *__restrict__ colour_caller) {
+// Gather form of the dense packer: one thread per word (x, w) of the pristine
+// rows.  Block word w = r * k + c of relabelled row x holds, for member
+// y = coff[c] + 32 r + b of block (c, r), the caller's bit between i = perm[x]
+// and j = perm[y], read from the strict upper triangle (row min(i, j), column
+// max(i, j)).  Every word is written once, without atomics; a bit between two
+// vertices of one class is an illegal colouring.
+__global__ void pack_dense_gather_kernel(PackArgs a, const uint64_t *__restrict__ bits, int64_t row_words,
+                                         int32_t n, const int32_t *__restrict__ perm) {
   unsigned long long mine = 0;
-  const int64_t total = (int64_t)n * row_words;
+  const int64_t total = (int64_t)n * a.ldw;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t i = (int32_t)(t / row_words);
-    const int64_t w = t - (int64_t)i * row_words;
-    uint64_t word = bits[t];
-    const int64_t j0 = w * 64;
-    if (j0 + 63 <= i || j0 >= n) continue;
-    // keep bits j with i < j < n
-    if (j0 <= i) {
-      const int sh = i - (int)j0 + 1;  // 1..64
-      word = sh >= 64 ? 0 : (word >> sh) << sh;
-    }
-    if (j0 + 64 > n) {
-      const int keep = n - (int)j0;  // 1..63
-      word &= (keep >= 64) ? ~0ull : ((1ull << keep) - 1);
-    }
-    if (!word) continue;
-    const int32_t ci = colour_caller[i];
-    const int32_t x = a.inv[i];
-    const int32_t ix = x - a.coff[ci];
-    const uint32_t bx = 1u << (ix & 31);
-    while (word) {
-      const int b = __ffsll((long long)word) - 1;
-      word &= word - 1;
-      const int32_t j = (int32_t)j0 + b;
-      const int32_t cj = colour_caller[j];
-      if (cj == ci) {
-        atomicCAS(a.error, 0, (int32_t)KZ_ERR_ILLEGAL_COLOURING);
-        continue;
+    const int32_t x = (int32_t)(t / a.ldw);
+    const int32_t w = (int32_t)(t - (int64_t)x * a.ldw);
+    const int32_t c = w % a.k, r = w / a.k;
+    uint32_t out = 0;
+    {
+      const int32_t base = a.coff[c] + 32 * r, end = min(a.coff[c + 1], base + 32);
+      const int32_t i = perm[x];
+      for (int32_t y = base; y < end; y++) {
+        const int32_t j = perm[y];
+        if (j == i) continue;
+        const int32_t lo = min(i, j), hi = max(i, j);
+        const uint32_t bit = (uint32_t)(bits[(int64_t)lo * row_words + (hi >> 6)] >> (hi & 63)) & 1u;
+        out |= bit << (y - base);
+        mine += bit & (uint32_t)(i < j);
       }
-      const int32_t y = a.inv[j];
-      const int32_t iy = y - a.coff[cj];
-      atomicOr(&a.A[(int64_t)x * a.ldw + (iy >> 5) * a.k + cj], 1u << (iy & 31));
-      atomicOr(&a.A[(int64_t)y * a.ldw + (ix >> 5) * a.k + ci], bx);
-      mine++;
+      if (out && c == a.col[x]) {
+        atomicCAS(a.error, 0, (int32_t)KZ_ERR_ILLEGAL_COLOURING);
+        out = 0;
+      }
     }
+    a.A[t] = out;
   }
   for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
   if ((threadIdx.x & 31) == 0 && mine) atomicAdd(a.edge_count, mine);
@@ -1123,53 +1116,54 @@ kz_status bitset_barrier_timeout_probe(kz_graph g, uint32_t spin_limit, cudaStre
 // unpacking to caller ids
 // ---------------------------------------------------------------------------
 
-__global__ void unpack_dense_kernel(const uint32_t *__restrict__ A, int32_t n, int32_t ldw, int32_t k,
-                                    int32_t rk, const int32_t *__restrict__ coff,
-                                    const int32_t *__restrict__ perm, uint64_t *out,
-                                    int64_t row_words, unsigned long long *edge_count) {
+// Gather form of the unpacker: one thread per caller word (ox, ow); bit b is
+// the relabelled bit between ox and oy = 64 ow + b, read from row inv[ox] at
+// oy's position.  The thread of word 0 also writes ox's vertex flag.
+__global__ void unpack_gather_kernel(const uint32_t *__restrict__ A0, const uint32_t *__restrict__ A1,
+                                     const uint32_t *__restrict__ V0, const uint32_t *__restrict__ V1,
+                                     const int32_t *__restrict__ cur, int32_t n, int32_t ldw,
+                                     const int32_t *__restrict__ inv, const int32_t *__restrict__ cpos,
+                                     uint64_t *__restrict__ out, int64_t row_words, uint8_t *__restrict__ alive,
+                                     unsigned long long *__restrict__ edge_count) {
+  const bool one = (*cur & 1) != 0;
+  const uint32_t *A = one ? A1 : A0;
+  const uint32_t *V = one ? V1 : V0;
   unsigned long long mine = 0;
-  const int64_t total = (int64_t)n * rk;
+  const int64_t total = (int64_t)n * row_words;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t x = (int32_t)(t / rk);
-    const int32_t w = (int32_t)(t - (int64_t)x * rk);
-    uint32_t word = A[(int64_t)x * ldw + w];
-    if (!word) continue;
-    const int32_t c = w % k, r = w / k;
-    const int32_t ox = perm[x];
-    mine += __popc(word);
-    while (word) {
-      const int b = __ffs(word) - 1;
-      word &= word - 1;
-      const int32_t y = coff[c] + 32 * r + b;
-      const int32_t oy = perm[y];
-      atomicOr(reinterpret_cast<unsigned long long *>(&out[(int64_t)ox * row_words + (oy >> 6)]),
-               1ull << (oy & 63));
+    const int32_t ox = (int32_t)(t / row_words);
+    const int64_t ow = t - (int64_t)ox * row_words;
+    const uint32_t *row = A + (int64_t)inv[ox] * ldw;
+    uint64_t word = 0;
+    const int32_t oy0 = (int32_t)(ow * 64);
+    const int32_t cnt = min(64, n - oy0);
+    for (int32_t b = 0; b < cnt; b++) {
+      const int32_t p = cpos[oy0 + b];
+      word |= (uint64_t)((row[p >> 5] >> (p & 31)) & 1u) << b;
+    }
+    out[t] = word;
+    mine += __popcll(word);
+    if (ow == 0) {
+      const int32_t p = cpos[ox];
+      alive[ox] = (uint8_t)((V[p >> 5] >> (p & 31)) & 1u);
     }
   }
   for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
   if ((threadIdx.x & 31) == 0 && mine) atomicAdd(edge_count, mine);
 }
 
-kz_status bitset_unpack_dense(kz_graph g, uint64_t *d_out, int64_t row_words,
-                              unsigned long long *d_edge_count, cudaStream_t s) {
-  KZ_CUDA_TRY(cudaMemsetAsync(d_out, 0, (size_t)g->n * row_words * 8, s));
+kz_status bitset_unpack_gather(kz_graph g, uint64_t *d_out, int64_t row_words, uint8_t *d_alive,
+                               unsigned long long *d_edge_count, cudaStream_t s) {
   KZ_CUDA_TRY(cudaMemsetAsync(d_edge_count, 0, sizeof(unsigned long long), s));
   if (g->n == 0) return KZ_OK;
-  // the current buffer index lives on the device; read it (the stream is
-  // synchronous with the caller here)
-  int32_t cur = 0;
-  KZ_CUDA_TRY(cudaMemcpyAsync(&cur, &g->st->cur, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  KZ_CUDA_TRY(cudaStreamSynchronize(s));
-  const int32_t rk = g->R * g->k;
-  const int64_t total = (int64_t)g->n * rk;
+  const int64_t total = (int64_t)g->n * row_words;
   const int threads = 256;
   const int grid = (int)std::min<int64_t>((total + threads - 1) / threads, 32 * sm_count());
-  unpack_dense_kernel<<<std::max(grid, 1), threads, 0, s>>>(g->A[cur & 1], g->n, g->ldw, g->k, rk,
-                                                           g->d_coff, g->d_perm, d_out, row_words,
-                                                           d_edge_count);
-  KZ_CUDA_TRY(cudaGetLastError());
-  return KZ_OK;
+  unpack_gather_kernel<<<std::max(grid, 1), threads, 0, s>>>(g->A[0], g->A[1], g->V[0], g->V[1], &g->st->cur, g->n,
+                                                            g->ldw, g->d_inv, g->d_cpos, d_out, row_words, d_alive,
+                                                            d_edge_count);
+  return cuda_status(cudaGetLastError());
 }
 
 kz_status bitset_vertex_alive(kz_graph g, uint8_t *host_alive, int64_t *n_live) {
@@ -1269,7 +1263,10 @@ kz_status bitset_pack_dense(kz_graph g, const uint64_t *d_bits, int64_t row_word
   if (st == KZ_OK && total > 0) {
     const int threads = 256;
     const int grid = (int)std::min<int64_t>((total + threads - 1) / threads, 64 * sm_count());
-    pack_dense_kernel<<<grid, threads, 0, s>>>(a, d_bits, row_words, g->n, d_colour_caller);
+    (void)d_colour_caller;  // the gather form reads colours from the relabelled layout
+    const int64_t words = (int64_t)g->n * g->ldw;
+    const int grid2 = (int)std::min<int64_t>((words + threads - 1) / threads, 64 * sm_count());
+    pack_dense_gather_kernel<<<std::max(grid2, 1), threads, 0, s>>>(a, d_bits, row_words, g->n, g->d_perm);
     st = cuda_status(cudaGetLastError());
   }
   kz_status st2 = tmp.empty() ? KZ_OK : pack_finish(g, s, a, tmp);

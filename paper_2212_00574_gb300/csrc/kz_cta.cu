@@ -309,9 +309,8 @@ kz_status cta_upload_descriptor(kz_graph g, cudaStream_t s) {
   KZ_TRY(graph_alloc(g, &g->d_zero, 4, s));
   KZ_CUDA_TRY(cudaMemsetAsync(g->d_zero, 0, 16, s));
   CtaGraph h = describe(g, 0);
+  // a copy from pageable memory has left the local by the time the call returns
   KZ_CUDA_TRY(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s));
-  // the host struct is a local: wait for the copy
-  KZ_CUDA_TRY(cudaStreamSynchronize(s));
   return KZ_OK;
 }
 

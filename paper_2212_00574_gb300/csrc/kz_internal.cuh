@@ -178,6 +178,7 @@ struct kz_graph_s {
   bool has_csr = false;
   int32_t owner = KZ_PATH_BITSET;
   int32_t *d_inv = nullptr;    // caller id -> relabelled id (bitset layout)
+  int32_t *d_cpos = nullptr;   // caller id -> (word << 5) | bit of its relabelled vertex inside any row
 
   // CSR path (caller ids)
   int64_t *sp_row0 = nullptr;  // n + 1, all edges
@@ -236,8 +237,11 @@ kz_status bitset_pack_dense(kz_graph g, const uint64_t *d_bits, int64_t row_word
 kz_status bitset_finish_load(kz_graph g, cudaStream_t s);
 kz_status bitset_reset(kz_graph g, cudaStream_t s);
 kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s);
-kz_status bitset_unpack_dense(kz_graph g, uint64_t *d_out, int64_t row_words,
-                              unsigned long long *d_edge_count, cudaStream_t s);
+// Caller-ordered dense rows, vertex flags (bytes) and the count of set bits
+// (twice the edges) of the current state, all on the device; the current
+// buffer index is read on the device, so nothing synchronises.
+kz_status bitset_unpack_gather(kz_graph g, uint64_t *d_out, int64_t row_words, uint8_t *d_alive,
+                               unsigned long long *d_edge_count, cudaStream_t s);
 kz_status bitset_vertex_alive(kz_graph g, uint8_t *host_alive, int64_t *n_live);
 
 // One plain multi-CTA sweep pass (no loop graph); *cont = 1 when it deleted
