@@ -224,6 +224,9 @@ struct kz_graph_s {
   // every device allocation, for kz_free_graph
   struct Alloc { void *p; size_t bytes; };
   std::vector<Alloc> allocs;
+  // small allocations are carved from chunks (one allocator call per chunk)
+  uint8_t *arena = nullptr;
+  size_t arena_size = 0, arena_used = 0, arena_next = 256 << 10;
 };
 
 namespace kz {
@@ -297,16 +300,40 @@ kz_status state_to_bitset(kz_graph g, cudaStream_t s);
 kz_status batch_kernelize(kz_graph *gs, int count, const kz_options &opt, cudaStream_t s);
 
 // Allocation bookkeeping on the handle.
+// Device memory owned by the graph (freed with it).  Requests below 1 MiB
+// are carved, 256-byte aligned, from chunks of at least 256 KiB (each chunk
+// twice the last), so loading a graph makes few allocator calls; larger ones
+// get their own allocation.
 template <class T>
 kz_status graph_alloc(kz_graph g, T **out, size_t count, cudaStream_t s) {
   size_t bytes = count * sizeof(T);
   if (bytes == 0) bytes = 16;
-  void *p = dev_alloc(bytes, s);
-  if (!p) {
-    *out = nullptr;
-    return KZ_ERR_OOM;
+  bytes = (bytes + 255) & ~(size_t)255;
+  void *p = nullptr;
+  if (bytes < ((size_t)1 << 20)) {
+    if (!g->arena || g->arena_used + bytes > g->arena_size) {
+      const size_t chunk = g->arena_next > bytes ? g->arena_next : bytes;
+      void *c = dev_alloc(chunk, s);
+      if (!c) {
+        *out = nullptr;
+        return KZ_ERR_OOM;
+      }
+      g->allocs.push_back({c, chunk});
+      g->arena = static_cast<uint8_t *>(c);
+      g->arena_size = chunk;
+      g->arena_used = 0;
+      g->arena_next = chunk * 2;
+    }
+    p = g->arena + g->arena_used;
+    g->arena_used += bytes;
+  } else {
+    p = dev_alloc(bytes, s);
+    if (!p) {
+      *out = nullptr;
+      return KZ_ERR_OOM;
+    }
+    g->allocs.push_back({p, bytes});
   }
-  g->allocs.push_back({p, bytes});
   *out = static_cast<T *>(p);
   return KZ_OK;
 }
