@@ -88,3 +88,31 @@ def test_no_cpu_fallback():
     with pytest.raises(kz.KzError) as ei:
         kz.kz_load_graph(2, 2, [0, 1], [[0, 1]])
     assert ei.value.status == kz.KZ_ERR_CUDA
+
+
+def _header_struct_fields(name):
+    import re
+    src = open(kz.HEADER).read()
+    end = re.search(r"\}\s*" + name + ";", src).start()
+    body = src[src.rindex("typedef struct {", 0, end) + len("typedef struct {"):end]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    return re.findall(r"\b(\w+)(?:\[\d+\])?\s*;", body)
+
+
+@pytest.mark.parametrize("name,cls", [("kz_options", kz.kz_options), ("kz_stats", kz.kz_stats)])
+def test_struct_fields_follow_header(name, cls):
+    # the binding's field order is the header's (offsets follow from it)
+    assert [f for f, _ in cls._fields_] == _header_struct_fields(name)
+
+
+def test_new_entry_points_validate_on_host(lib):
+    found = ctypes.c_int32(0)
+    q = ctypes.c_int32(0)
+    out = (ctypes.c_int32 * 4)()
+    assert lib.kz_find_clique(None, 3, 0, out, ctypes.byref(found)) == kz.KZ_ERR_ARG
+    assert lib.kz_max_clique(None, None, 0, ctypes.byref(q), out, None) == kz.KZ_ERR_ARG
+    d1, d2 = ctypes.c_double(), ctypes.c_double()
+    assert lib.kz_probe_mma_throughput(3, 128, 1, ctypes.byref(d1), ctypes.byref(d2), None) == kz.KZ_ERR_ARG
+    assert lib.kz_probe_mma_throughput(0, 64, 1, ctypes.byref(d1), ctypes.byref(d2), None) == kz.KZ_ERR_ARG
+    assert lib.kz_probe_tma_throughput(4, 1, ctypes.byref(d1), ctypes.byref(d2), None) == kz.KZ_ERR_ARG
+    assert lib.kz_probe_tma_throughput(0, 3, ctypes.byref(d1), ctypes.byref(d2), None) == kz.KZ_ERR_ARG
