@@ -96,7 +96,11 @@ def _header_struct_fields(name):
     end = re.search(r"\}\s*" + name + ";", src).start()
     body = src[src.rindex("typedef struct {", 0, end) + len("typedef struct {"):end]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
-    return re.findall(r"\b(\w+)(?:\[\d+\])?\s*;", body)
+    names = []
+    for decl in body.split(";"):  # "int64_t n, m" declares two fields
+        if decl.strip():
+            names += [re.sub(r"\[.*?\]", "", part).split()[-1] for part in decl.split(",")]
+    return names
 
 
 @pytest.mark.parametrize("name,cls", [("kz_options", kz.kz_options), ("kz_stats", kz.kz_stats)])
