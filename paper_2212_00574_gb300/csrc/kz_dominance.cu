@@ -13,11 +13,11 @@
 // Kernels, all on the current ping-pong buffer:
 //   position_kernel   word and bit of every vertex inside a row (once);
 //   degree_kernel     live degree of every vertex (-1: deleted);
-//   dominated_kernel  one warp per vertex a scans the live vertices b with
-//                     deg(b) >= deg(a) that a's row does not hold, and tests
-//                     N(a) & ~N(b) == 0 word-parallel across the lanes; a
-//                     dominated a sets its bit in a deletion mask laid out
-//                     like the vertex live words;
+//   dominated_kernel  one warp per vertex a: the lanes filter 32 candidates
+//                     b at a time (live, deg(b) >= deg(a), not in a's row),
+//                     then the warp tests N(a) & ~N(b) == 0 word-parallel
+//                     for each survivor; a dominated a sets its bit in a
+//                     deletion mask laid out like the vertex live words;
 //   apply_kernel      clears the deleted vertices' rows, their bits in every
 //                     row, and their live bits.
 #include <cuda_runtime.h>
@@ -75,20 +75,31 @@ __global__ void dominated_kernel(const uint32_t *__restrict__ A, int32_t n, int3
     if (da < 0) continue;
     const uint32_t *ra = A + a * ldw;
     bool dominated = false;
-    for (int64_t b = 0; b < n && !dominated; b++) {
-      const int db = deg[b];
-      if (b == a || db < da) continue;  // a deleted b has deg -1 <= da
-      const int pb = pos[b];
-      if ((ra[pb >> 5] >> (pb & 31)) & 1u) continue;  // adjacent: b is in N(a), never in N(b)
-      if (db == da && b < a) continue;  // equal neighbourhoods: only the smaller id goes
-      const uint32_t *rb = A + b * ldw;
-      bool outside = false;
-      for (int w0 = 0; w0 < ldw && !outside; w0 += 32) {
-        const int w = w0 + lane;
-        const bool miss = w < ldw && (ra[w] & ~rb[w]) != 0u;
-        outside = __any_sync(0xffffffffu, miss);
+    // the lanes filter 32 candidates at a time; the warp then tests the
+    // survivors' rows one by one
+    for (int64_t b0 = 0; b0 < n && !dominated; b0 += 32) {
+      const int64_t b = b0 + lane;
+      bool cand = false;
+      if (b < n && b != a) {
+        const int db = deg[b];
+        const int pb = pos[b];
+        cand = db >= da                                 // a deleted b has deg -1 <= da
+               && !((ra[pb >> 5] >> (pb & 31)) & 1u)    // adjacent: b is in N(a), never in N(b)
+               && !(db == da && b < a);                 // equal neighbourhoods: only the smaller id goes
       }
-      dominated = !outside;
+      uint32_t todo = __ballot_sync(0xffffffffu, cand);
+      while (todo && !dominated) {
+        const int64_t bb = b0 + __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint32_t *rb = A + bb * ldw;
+        bool outside = false;
+        for (int w0 = 0; w0 < ldw && !outside; w0 += 32) {
+          const int w = w0 + lane;
+          const bool miss = w < ldw && (ra[w] & ~rb[w]) != 0u;
+          outside = __any_sync(0xffffffffu, miss);
+        }
+        dominated = !outside;
+      }
     }
     if (dominated && lane == 0) {
       const int pa = pos[a];
