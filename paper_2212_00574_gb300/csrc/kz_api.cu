@@ -240,7 +240,7 @@ kz_status kz_load_graph_dense(int32_t n, int32_t k, const int32_t *colour,
     kz_status st = d_bits ? KZ_OK : KZ_ERR_OOM;
     if (st == KZ_OK)
       st = cuda_status(cudaMemcpyAsync(d_bits, adj_bits, bytes, cudaMemcpyHostToDevice, g->stream));
-    if (st == KZ_OK) st = bitset_pack_dense(g, d_bits, row_words, nullptr, g->stream);
+    if (st == KZ_OK) st = bitset_pack_dense(g, d_bits, row_words, g->stream);
     if (d_bits) dev_free(d_bits, bytes, g->stream);
     return st;
   }, no_csr, false);

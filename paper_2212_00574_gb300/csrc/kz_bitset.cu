@@ -1254,19 +1254,15 @@ kz_status bitset_pack_edges(kz_graph g, const int32_t *d_edges, int64_t m, bool 
   return st != KZ_OK ? st : st2;
 }
 
-kz_status bitset_pack_dense(kz_graph g, const uint64_t *d_bits, int64_t row_words,
-                            const int32_t *d_colour_caller, cudaStream_t s) {
+kz_status bitset_pack_dense(kz_graph g, const uint64_t *d_bits, int64_t row_words, cudaStream_t s) {
   PackArgs a;
   std::vector<void *> tmp;
   kz_status st = pack_setup(g, s, a, tmp);
-  const int64_t total = (int64_t)g->n * row_words;
-  if (st == KZ_OK && total > 0) {
+  const int64_t words = (int64_t)g->n * g->ldw;
+  if (st == KZ_OK && words > 0) {
     const int threads = 256;
-    const int grid = (int)std::min<int64_t>((total + threads - 1) / threads, 64 * sm_count());
-    (void)d_colour_caller;  // the gather form reads colours from the relabelled layout
-    const int64_t words = (int64_t)g->n * g->ldw;
-    const int grid2 = (int)std::min<int64_t>((words + threads - 1) / threads, 64 * sm_count());
-    pack_dense_gather_kernel<<<std::max(grid2, 1), threads, 0, s>>>(a, d_bits, row_words, g->n, g->d_perm);
+    const int grid = (int)std::min<int64_t>((words + threads - 1) / threads, 64 * sm_count());
+    pack_dense_gather_kernel<<<std::max(grid, 1), threads, 0, s>>>(a, d_bits, row_words, g->n, g->d_perm);
     st = cuda_status(cudaGetLastError());
   }
   kz_status st2 = tmp.empty() ? KZ_OK : pack_finish(g, s, a, tmp);

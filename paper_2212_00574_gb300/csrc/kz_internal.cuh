@@ -235,8 +235,7 @@ namespace kz {
 kz_status bitset_build_layout(kz_graph g);
 kz_status bitset_pack_edges(kz_graph g, const int32_t *d_edges, int64_t m, bool dedup,
                             cudaStream_t s);
-kz_status bitset_pack_dense(kz_graph g, const uint64_t *d_bits, int64_t row_words,
-                            const int32_t *d_colour_caller, cudaStream_t s);
+kz_status bitset_pack_dense(kz_graph g, const uint64_t *d_bits, int64_t row_words, cudaStream_t s);
 kz_status bitset_finish_load(kz_graph g, cudaStream_t s);
 kz_status bitset_reset(kz_graph g, cudaStream_t s);
 kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s);
