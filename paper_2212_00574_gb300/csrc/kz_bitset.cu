@@ -1193,17 +1193,17 @@ static kz_status pack_setup(kz_graph g, cudaStream_t s, PackArgs &a, std::vector
   std::vector<int32_t> col_new((size_t)g->n);
   for (int c = 0; c < g->k; c++)
     for (int x = g->coff[c]; x < g->coff[c + 1]; x++) col_new[x] = c;
+  // small tables of the packers: carved from the graph's chunks (one
+  // allocator call at most), released with the graph
   int32_t *d_inv = nullptr, *d_col = nullptr, *d_coff = nullptr, *d_err = nullptr;
   unsigned long long *d_cnt = nullptr;
   const size_t nn = (size_t)std::max(g->n, 1);
-  d_inv = (int32_t *)dev_alloc(nn * 4, s);
-  d_col = (int32_t *)dev_alloc(nn * 4, s);
-  d_coff = (int32_t *)dev_alloc(((size_t)g->k + 1) * 4, s);
-  d_err = (int32_t *)dev_alloc(16, s);
-  d_cnt = (unsigned long long *)dev_alloc(16, s);
-  tmp = {d_inv, d_col, d_coff, d_err, d_cnt};
-  for (void *q : tmp)
-    if (!q) return KZ_ERR_OOM;
+  KZ_TRY(graph_alloc(g, &d_inv, nn, s));
+  KZ_TRY(graph_alloc(g, &d_col, nn, s));
+  KZ_TRY(graph_alloc(g, &d_coff, (size_t)g->k + 1, s));
+  KZ_TRY(graph_alloc(g, &d_err, 4, s));
+  KZ_TRY(graph_alloc(g, &d_cnt, 2, s));
+  tmp.clear();
   if (g->n) {
     KZ_CUDA_TRY(cudaMemcpyAsync(d_inv, g->inv.data(), (size_t)g->n * 4, cudaMemcpyHostToDevice, s));
     KZ_CUDA_TRY(cudaMemcpyAsync(d_col, col_new.data(), (size_t)g->n * 4, cudaMemcpyHostToDevice, s));
@@ -1228,8 +1228,6 @@ static kz_status pack_finish(kz_graph g, cudaStream_t s, PackArgs &a, std::vecto
   cudaError_t e1 = cudaMemcpyAsync(&err, a.error, 4, cudaMemcpyDeviceToHost, s);
   cudaError_t e2 = cudaMemcpyAsync(&cnt, a.edge_count, 8, cudaMemcpyDeviceToHost, s);
   cudaError_t e3 = cudaStreamSynchronize(s);
-  for (void *q : tmp)
-    if (q) dev_free(q, 0, s);
   tmp.clear();
   if (e1 != cudaSuccess) return cuda_status(e1);
   if (e2 != cudaSuccess) return cuda_status(e2);
@@ -1250,7 +1248,7 @@ kz_status bitset_pack_edges(kz_graph g, const int32_t *d_edges, int64_t m, bool 
     pack_edges_kernel<<<grid, threads, 0, s>>>(a, d_edges, m, dedup ? 1 : 0);
     st = cuda_status(cudaGetLastError());
   }
-  kz_status st2 = tmp.empty() ? KZ_OK : pack_finish(g, s, a, tmp);
+  kz_status st2 = st == KZ_OK ? pack_finish(g, s, a, tmp) : KZ_OK;
   return st != KZ_OK ? st : st2;
 }
 
@@ -1265,7 +1263,7 @@ kz_status bitset_pack_dense(kz_graph g, const uint64_t *d_bits, int64_t row_word
     pack_dense_gather_kernel<<<std::max(grid, 1), threads, 0, s>>>(a, d_bits, row_words, g->n, g->d_perm);
     st = cuda_status(cudaGetLastError());
   }
-  kz_status st2 = tmp.empty() ? KZ_OK : pack_finish(g, s, a, tmp);
+  kz_status st2 = st == KZ_OK ? pack_finish(g, s, a, tmp) : KZ_OK;
   return st != KZ_OK ? st : st2;
 }
 
