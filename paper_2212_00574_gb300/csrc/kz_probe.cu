@@ -28,7 +28,6 @@ __device__ __forceinline__ uint32_t umin_asm(uint32_t a, uint32_t b) {
 template <int KIND>
 __global__ void int_probe_kernel(uint32_t seed, uint32_t *out) {
   uint32_t x[kChains];
-#pragma unroll
   uint32_t m[kChains];
 #pragma unroll
   for (int i = 0; i < kChains; i++) {
