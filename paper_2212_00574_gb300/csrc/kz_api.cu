@@ -281,10 +281,12 @@ static kz_status set_clique(kz_graph g, const kz_options &o) {
 constexpr int kSmallAutoMaxN = 64;
 
 // Bitset sweep or tensor-core form for a graph held as bitset rows, from a
-// table measured on GB300 (time to fixpoint of both paths on seeded
-// k-partite graphs with a planted clique, n in {2048, 4096, 8192, 16384},
-// k in {12, 24}, density in {0.05, 0.1, 0.2, 0.3, 0.45}): 1 where the tensor
-// form was faster.  A graph falls in the bin of the nearest measured point.
+// table measured on GB300 by the autotuner (paper_2212_00574_gb300/autotune.py:
+// time to fixpoint of both paths on seeded k-partite graphs with a planted
+// clique, n in {2048, 4096, 8192, 16384}, k in {12, 24}, density in {0.05,
+// 0.1, 0.2, 0.3, 0.45}; its measurements are in autotune_grid.json beside
+// it): 1 where the tensor form was faster.  A graph falls in the bin of the
+// nearest measured point.
 // The bitset sweep settles most pairs from the first word of each class when
 // common neighbours are plentiful (dense graphs); the tensor form does the
 // same work whatever the density, so it wins where pairs need many words or
