@@ -31,3 +31,12 @@ def test_cells_and_rendering():
     t = autotune.table_from([dict(n=8192, k=24, p=0.2, bitset_us=10, tensor_us=5)])
     assert t[2][1][2] == 1 and sum(map(sum, (r for per in t for r in per))) == 1
     assert "kTensorTable[4][2][5]" in autotune.render_c(t)
+
+
+def test_bin_edges_match_the_library():
+    src = open(os.path.join(ROOT, "paper_2212_00574_gb300", "csrc", "kz_api.cu")).read()
+    body = src[src.index("static bool tensor_preferred"):src.index("static int auto_path")]
+    nb = [int(x) for x in re.findall(r"g->n < (\d+)", body)]
+    kb = [int(x) for x in re.findall(r"g->k < (\d+) \?", body)]
+    db = [float(x) for x in re.findall(r"d < ([0-9.]+)", body)]
+    assert tuple(nb) == autotune.N_EDGES and kb == [autotune.K_EDGE] and tuple(db) == autotune.D_EDGES
