@@ -16,7 +16,7 @@
 // MMA step then covers 16 vertices (half a block word) in the same 32 bytes
 // per row, so the layout, boxes and descriptors are the same and a class
 // takes twice the steps.
-// One TMA box (8 half-steps x 2048 bytes, read as 8-byte elements so that
+// One A-operand TMA box (8 half-steps x 2048 bytes, read as 8-byte elements so that
 // the box's inner extent is the whole contiguous run) then lands in shared
 // memory as four consecutive canonical no-swizzle K-major MMA operands:
 // 8-row x 16-byte core matrices 128 bytes apart along M/N and 2048 bytes
@@ -32,8 +32,9 @@
 //               of both operands, one box each; a class's last partial stage
 //               one box per K-step) as soon as the MMAs free them;
 //   warp 1      MMA issuer: one thread issues tcgen05.mma.kind::f8f6f4
-//               (M = 128, N = 256, K = 32, fp32 accumulation in TMEM, exact
-//               for 0/1 products) over a class's K-steps, alternating
+//               (kind::f16 for BF16; M = 128, N = 256, 32 bytes of K per
+//               row, fp32 accumulation in TMEM, exact for 0/1 products)
+//               over a class's K-steps, alternating
 //               between two TMEM accumulators (all 512 columns) so that the
 //               next class runs while the previous one is read;
 //   warps 2-9   epilogue: tcgen05.ld of the class's counts, one 8-bit
