@@ -217,9 +217,13 @@ kz_status kz_load_graph_dense(int32_t n, int32_t k, const int32_t *colour,
 kz_status kz_kernelize(kz_graph g, const kz_options *opt, void *stream);
 
 /*
- * Kernelize `count` graphs with one persistent launch (asynchronous).  Every
- * graph ends exactly as kz_kernelize would leave it.  opt as kz_kernelize;
- * opt->path selects the per-graph path (AUTO lets the autotuner choose).
+ * Kernelize `count` graphs (asynchronous).  Every graph ends exactly as
+ * kz_kernelize would leave it.  opt as kz_kernelize; opt->path selects the
+ * per-graph path (AUTO lets the measured table choose per graph), and
+ * opt->batch how the graphs are scheduled (kz_batch_mode): by default each
+ * graph runs on its own path over the library's internal streams (one or a
+ * few launches per graph); KZ_BATCH_FUSED runs them all in one persistent
+ * launch.  The caller's stream waits for every graph.
  */
 kz_status kz_kernelize_batch(kz_graph *graphs, int32_t count, const kz_options *opt, void *stream);
 
@@ -319,9 +323,13 @@ const char *kz_status_string(kz_status s);
  * Every intermediate (relabelling, bitset rows, ping-pong buffers, loop
  * state) lives in a static device array of about 9 MiB that each GPU loading
  * the library holds until the process exits.  The first call on a device
- * looks up that array's device address (once per device); make that first
- * call outside any stream capture.  The call makes no cudaMalloc, cudaFree or
- * other allocating call, host or device.
+ * does the set-up: it looks up that array's device address (once per
+ * device).  Make that first call before any stream capture, and while about
+ * 9 MiB of device memory is still free: with lazy module loading the CUDA
+ * runtime materialises the array at that first call, so a caller whose pool
+ * will reserve the whole GPU should make one warm-up call before the pool
+ * does.  The call itself makes no cudaMalloc, cudaFree or other allocating
+ * call, host or device.
  *
  * All calls share the one array, which keeps the last call's contents (every
  * call re-initialises what it reads).  Calls that overlap on the GPU (two
@@ -340,7 +348,11 @@ const char *kz_status_string(kz_status s);
  *   stream        stream for every launch; the call waits for it at the end
  * Returns the status (also in counts[3]).  n > KZ_NOALLOC_MAX_N, or colour
  * classes so uneven that the bitset rows exceed KZ_NOALLOC_MAX_WORDS words,
- * give KZ_ERR_UNSUPPORTED.
+ * give KZ_ERR_UNSUPPORTED.  Statuses found on the host (KZ_ERR_ARG, and
+ * KZ_ERR_UNSUPPORTED for n) leave the outputs untouched; statuses found on
+ * the device (KZ_ERR_COLOUR_RANGE, KZ_ERR_ILLEGAL_COLOURING, KZ_ERR_UNSUPPORTED
+ * for uneven classes) leave vertex_alive and adj_out all zero and counts[0..2]
+ * zero.  KZ_ERR_LIMIT leaves the partial kernel, as kz_fetch_kernel does.
  */
 #define KZ_NOALLOC_MAX_N 4096
 #define KZ_NOALLOC_MAX_WORDS (1 << 20)

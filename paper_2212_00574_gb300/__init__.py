@@ -107,10 +107,8 @@ def _lib():
                 "kz_status_string": (C.c_char_p, [C.c_int]),
                 "kz_version": (i32, []),
                 "kz_probe_int_throughput": (C.c_int, [i32, P, P, P]),
-                "kz_probe_mma_throughput": (C.c_int, [i32, i32, i32, P, P, P]),
                 "kz_find_clique": (C.c_int, [P, i32, i64, P, P]),
                 "kz_max_clique": (C.c_int, [P, P, i64, P, P, P]),
-                "kz_probe_tma_throughput": (C.c_int, [i32, i32, P, P, P]),
                 "kz_probe_barrier_timeout": (C.c_int, [P, u32, P]),
                 "kz_kernelize_dense_noalloc": (C.c_int, [i32, i32, P, P, i64, i64, P, P, P, P]),
                 "kz_model_create": (C.c_int, [P, P]),
@@ -368,22 +366,6 @@ def kz_max_clique(g: int, k: int, options: kz_options | None = None, node_limit:
     _check(_lib().kz_max_clique(C.c_void_p(g), None if options is None else C.byref(options), int(node_limit),
                                 C.byref(q), _ptr(out), _stream(stream)), "kz_max_clique")
     return int(q.value), out[:q.value].copy()
-
-
-def kz_probe_mma_throughput(layout: int, n: int = 128, ctas_per_sm: int = 1, stream=None):
-    """(flops per second, kernel ms) of the tcgen05 fp8 MMA probe."""
-    flops, ms = C.c_double(), C.c_double()
-    _check(_lib().kz_probe_mma_throughput(int(layout), int(n), int(ctas_per_sm), C.byref(flops), C.byref(ms),
-                                          _stream(stream)), "kz_probe_mma_throughput")
-    return flops.value, ms.value
-
-
-def kz_probe_tma_throughput(mode: int, ctas_per_sm: int = 1, stream=None):
-    """(bytes per second, kernel ms) of the TMA load probe."""
-    bps, ms = C.c_double(), C.c_double()
-    _check(_lib().kz_probe_tma_throughput(int(mode), int(ctas_per_sm), C.byref(bps), C.byref(ms), _stream(stream)),
-           "kz_probe_tma_throughput")
-    return bps.value, ms.value
 
 
 def kz_probe_int_throughput(kind: int, stream=None):

@@ -498,8 +498,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(kz::noal
 namespace kz {
 namespace noalloc {
 
-__device__ __forceinline__ Scratch *S() { return reinterpret_cast<Scratch *>(g_noalloc_scratch); }
-
 // First index i in [0, len) with a[i] > x (a sorted ascending).
 __device__ __forceinline__ int upper_bound_int(const int32_t *a, int len, int32_t x) {
   int lo = 0, hi = len;
@@ -513,8 +511,7 @@ __device__ __forceinline__ int upper_bound_int(const int32_t *a, int len, int32_
 
 // Layout of the caller's graph: colour classes, blocks, block pairs, the
 // descriptor of the in-CTA kernel.  One CTA.
-__global__ void setup_kernel(int32_t n, int32_t k, const int32_t *__restrict__ colour) {
-  Scratch *s = S();
+__global__ void setup_kernel(Scratch *s, int32_t n, int32_t k, const int32_t *__restrict__ colour) {
   Header &h = s->h;
   __shared__ int cnt[64];
   __shared__ int bad;
@@ -598,8 +595,7 @@ __global__ void setup_kernel(int32_t n, int32_t k, const int32_t *__restrict__ c
 }
 
 // Zeroed rows, live words of every block, zeroed deletion sweeps.
-__global__ void clear_kernel() {
-  Scratch *s = S();
+__global__ void clear_kernel(Scratch *s) {
   if (s->h.status) return;
   const CtaGraph &d = s->h.desc;
   const int64_t words = (int64_t)d.n * d.ldw;
@@ -610,8 +606,7 @@ __global__ void clear_kernel() {
   for (int64_t i = tid; i < d.n; i += stride) s->v_sweep[i] = 0;
 }
 
-__global__ void live_words_kernel() {
-  Scratch *s = S();
+__global__ void live_words_kernel(Scratch *s) {
   if (s->h.status) return;
   const CtaGraph &d = s->h.desc;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < d.nb; b += gridDim.x * blockDim.x) {
@@ -621,9 +616,8 @@ __global__ void live_words_kernel() {
 }
 
 // Caller's dense bit matrix (strict upper triangle) into the block-plane rows.
-__global__ void pack_kernel(const uint64_t *__restrict__ bits, int64_t row_words,
+__global__ void pack_kernel(Scratch *s, const uint64_t *__restrict__ bits, int64_t row_words,
                             const int32_t *__restrict__ colour) {
-  Scratch *s = S();
   Header &h = s->h;
   if (h.status) return;
   const int n = h.desc.n, k = h.desc.k, ldw = h.desc.ldw;
@@ -666,8 +660,7 @@ __global__ void pack_kernel(const uint64_t *__restrict__ bits, int64_t row_words
 }
 
 // Both ping-pong copies start from the packed rows (own-class words zero).
-__global__ void mirror_kernel() {
-  Scratch *s = S();
+__global__ void mirror_kernel(Scratch *s) {
   if (s->h.status) return;
   const CtaGraph &d = s->h.desc;
   const int64_t words = (int64_t)d.n * d.ldw;
@@ -679,13 +672,13 @@ __global__ void mirror_kernel() {
 }
 
 // The in-CTA fixpoint on the scratch descriptor (k <= 32).
-__global__ void __launch_bounds__(kCtaThreads, 1) fixpoint_kernel(int64_t max_sweeps, int32_t smem_words) {
+__global__ void __launch_bounds__(kCtaThreads, 1) fixpoint_kernel(Scratch *s, int64_t max_sweeps,
+                                                                        int32_t smem_words) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long s_cnt[3];
   __shared__ int s_flag;
   __shared__ int32_t s_rounds[32];
   __shared__ CtaRun s_run;
-  Scratch *s = S();
   if (s->h.status) return;
   const CtaGraph G = s->h.desc;
   if (G.smem_words > 0 && G.smem_words <= smem_words)
@@ -701,13 +694,15 @@ __global__ void zero_out_kernel(uint64_t *__restrict__ out, int64_t words) {
 
 // Kernel rows back to caller ids: the symmetric bit matrix, the live
 // vertices, and (sweeps, passes, edge tests, status).
-__global__ void unpack_kernel(uint64_t *__restrict__ out, int64_t row_words, uint8_t *__restrict__ alive,
-                              int64_t *__restrict__ counts) {
-  Scratch *s = S();
+__global__ void unpack_kernel(Scratch *s, int32_t n_in, uint64_t *__restrict__ out, int64_t row_words,
+                              uint8_t *__restrict__ alive, int64_t *__restrict__ counts) {
   const Header &h = s->h;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if (h.status) {
+    // a rejected input leaves defined outputs: no vertex, no edge (the bit
+    // matrix was zeroed before this kernel), zero counts and the status
+    for (int64_t v = tid; v < n_in; v += stride) alive[v] = 0;
     if (tid == 0) {
       counts[0] = counts[1] = counts[2] = 0;
       counts[3] = h.status;
@@ -786,8 +781,8 @@ extern "C" kz_status kz_kernelize_dense_noalloc(int32_t n, int32_t k, const int3
   if (n > 0 && (!colour || !adj_bits || !vertex_alive || !adj_out)) return KZ_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   void *scratch = nullptr;
-  KZ_TRY(noalloc_scratch(&scratch));
-  (void)scratch;  // set-up check: the kernels name the array directly
+  KZ_TRY(noalloc_scratch(&scratch));  // device address of the array on this device
+  Scratch *sp = static_cast<Scratch *>(scratch);
   int dev = 0, sms = 1, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -804,14 +799,14 @@ extern "C" kz_status kz_kernelize_dense_noalloc(int32_t n, int32_t k, const int3
     }
   }
   const int grid = 2 * std::max(sms, 1);
-  setup_kernel<<<1, 1024, 0, s>>>(n, k, colour);
-  clear_kernel<<<grid, 256, 0, s>>>();
-  live_words_kernel<<<1, 256, 0, s>>>();
-  if ((int64_t)n * row_words > 0) pack_kernel<<<grid, 256, 0, s>>>(adj_bits, row_words, colour);
-  mirror_kernel<<<grid, 256, 0, s>>>();
-  fixpoint_kernel<<<1, kz::kCtaThreads, smem_bytes, s>>>(max_sweeps, smem_bytes / 4);
+  setup_kernel<<<1, 1024, 0, s>>>(sp, n, k, colour);
+  clear_kernel<<<grid, 256, 0, s>>>(sp);
+  live_words_kernel<<<1, 256, 0, s>>>(sp);
+  if ((int64_t)n * row_words > 0) pack_kernel<<<grid, 256, 0, s>>>(sp, adj_bits, row_words, colour);
+  mirror_kernel<<<grid, 256, 0, s>>>(sp);
+  fixpoint_kernel<<<1, kz::kCtaThreads, smem_bytes, s>>>(sp, max_sweeps, smem_bytes / 4);
   if ((int64_t)n * row_words > 0) zero_out_kernel<<<grid, 256, 0, s>>>(adj_out, (int64_t)n * row_words);
-  unpack_kernel<<<grid, 256, 0, s>>>(adj_out, row_words, vertex_alive, counts);
+  unpack_kernel<<<grid, 256, 0, s>>>(sp, n, adj_out, row_words, vertex_alive, counts);
   KZ_CUDA_TRY(cudaGetLastError());
   // synchronous: the device status decides the return value
   int64_t status = 0;

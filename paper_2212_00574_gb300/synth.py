@@ -303,15 +303,23 @@ WORKLOADS = {
     "c3": "chung-lu n=200000 k=12 zipf(1.2) mean degree 60, 5 planted 12-cliques",
     "c4": "batch of 1024 kpartite graphs, n log-uniform [64,4096], k U{6..32}, p U[0.3,0.95]",
     "c5": "kpartite n=32768 k=24 p=0.85, planted 24-clique",
-    "c5c": "kpartite n=32768 k=24 p=0.12, planted 24-clique (the C5 size in the cascade regime)",
+    "c5c": "kpartite n=32768 k=24 p=0.12, planted 24-clique (the C5 size where the tensor form wins)",
+    "c5s": "kpartite n=32768 k=24 p=0.07, planted 24-clique (the C5 size in the cascade regime)",
 }
+
+# the seed offset of the workloads that share a config number with another
+_SEED_OFFSET = {"c5c": 10, "c5s": 20}
+
+
+def workload_seed(name: str) -> int:
+    """The fixed seed of a named workload: 221200574 * 10 + i for config i."""
+    return SEED_BASE + int(name[1]) + _SEED_OFFSET.get(name, 0)
 
 
 def workload(name: str, scale: float = 1.0):
     """Build a named workload. ``scale`` < 1 shrinks n (and the batch count)
     for small parity cases while keeping k, p and the structure."""
-    i = int(name[1])
-    seed = SEED_BASE + i
+    seed = workload_seed(name)
     if name == "c1":
         return kpartite(max(10, int(300 * scale)), 10, 0.7, seed)
     if name == "c2":
@@ -323,5 +331,7 @@ def workload(name: str, scale: float = 1.0):
     if name == "c5":
         return kpartite(max(24, int(32768 * scale)), 24, 0.85, seed)
     if name == "c5c":
-        return kpartite(max(24, int(32768 * scale)), 24, 0.12, seed + 10)
+        return kpartite(max(24, int(32768 * scale)), 24, 0.12, seed)
+    if name == "c5s":
+        return kpartite(max(24, int(32768 * scale)), 24, 0.07, seed)
     raise KeyError(name)

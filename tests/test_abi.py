@@ -116,7 +116,5 @@ def test_new_entry_points_validate_on_host(lib):
     assert lib.kz_find_clique(None, 3, 0, out, ctypes.byref(found)) == kz.KZ_ERR_ARG
     assert lib.kz_max_clique(None, None, 0, ctypes.byref(q), out, None) == kz.KZ_ERR_ARG
     d1, d2 = ctypes.c_double(), ctypes.c_double()
-    assert lib.kz_probe_mma_throughput(3, 128, 1, ctypes.byref(d1), ctypes.byref(d2), None) == kz.KZ_ERR_ARG
-    assert lib.kz_probe_mma_throughput(0, 64, 1, ctypes.byref(d1), ctypes.byref(d2), None) == kz.KZ_ERR_ARG
-    assert lib.kz_probe_tma_throughput(4, 1, ctypes.byref(d1), ctypes.byref(d2), None) == kz.KZ_ERR_ARG
-    assert lib.kz_probe_tma_throughput(0, 3, ctypes.byref(d1), ctypes.byref(d2), None) == kz.KZ_ERR_ARG
+    assert lib.kz_probe_int_throughput(5, ctypes.byref(d1), ctypes.byref(d2), None) == kz.KZ_ERR_ARG
+    assert lib.kz_probe_int_throughput(0, None, ctypes.byref(d2), None) == kz.KZ_ERR_ARG

@@ -57,13 +57,6 @@ def test_tensor_more_tiles_than_ctas(seed, n, k, p):
     assert_parity(g, gpu_run(g, path="tensor"))
 
 
-@pytest.mark.parametrize("layout", [0, 1, 2])
-def test_mma_probe_runs(layout):
-    import paper_2212_00574_gb300 as kz
-    flops, ms = kz.kz_probe_mma_throughput(layout, 128, 1)
-    assert flops > 0 and ms > 0
-
-
 def test_auto_picks_tensor_for_a_larger_sparser_graph():
     # n = 4500, k = 12, density about 0.12 falls in a bin where the tensor
     # form measured faster; a dense graph of the same size stays on the bitset

@@ -6,8 +6,9 @@ run inside such an allocator's own callbacks. Or it may be a latency-critical
 loop in which cudaMalloc, which can synchronise the device, is not acceptable.
 The entry point serves those callers from one fixed static scratch array. These
 tests check its output against the ordinary entry points (kz_load_graph_dense +
-kz_kernelize + kz_fetch_kernel_dense). The comparison is exact, since this is
-integer work. They run it on calls in a row, so that nothing left in the shared
+kz_kernelize + kz_fetch_kernel_dense) and against the CPU oracle, so that a
+mistake the two CUDA paths might share is still caught. The comparison is
+exact, since this is integer work. They run it on calls in a row, so that nothing left in the shared
 scratch by one call leaks into the next.
 
 This file is collected last on purpose: when it fails, a run that stops at the
@@ -16,6 +17,7 @@ first failure has already run every other test.
 import numpy as np
 import pytest
 
+import oracle
 import paper_2212_00574_gb300 as kz
 from paper_2212_00574_gb300 import synth
 
@@ -56,6 +58,16 @@ def _check_same(g, max_sweeps=0):
     assert np.array_equal(r["alive"], alive), "vertex survivors differ from the ordinary entry points"
     assert np.array_equal(r["bits"], bits), "edge survivors differ from the ordinary entry points"
     assert list(r["counts"][:3]) == [stats["sweeps"], stats["passes"], stats["edge_tests"]]
+    # the oracle: survivors and productive sweeps (and, without a limit, the
+    # passes and live-edge tests too)
+    edges = g.get_edges()
+    orc = oracle.fixpoint(g.colour, edges, g.k, max_sweeps=max_sweeps, raise_on_limit=False)
+    assert np.array_equal(r["alive"], orc["vlive"]), "vertex survivors differ from the oracle"
+    kept = synth.bits_to_edges(np.ascontiguousarray(r["bits"]), g.n)
+    assert np.array_equal(kept, edges[orc["elive"].astype(bool)]), "edge survivors differ from the oracle"
+    assert int(r["counts"][0]) == orc["sweeps"]
+    if orc["status"] == 0:
+        assert [int(r["counts"][1]), int(r["counts"][2])] == [orc["passes"], orc["tests"]]
     return r
 
 
@@ -92,6 +104,20 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
     colour = np.zeros(4096, np.int32)
     colour[:31] = np.arange(1, 32)
     lop = synth.Graph(n=4096, k=32, colour=colour, edges=np.zeros((0, 2), np.int32))
-    assert _noalloc(lop)["status"] == kz.KZ_ERR_UNSUPPORTED
+    r = _noalloc(lop)
+    assert r["status"] == kz.KZ_ERR_UNSUPPORTED
+    # refused on the device: the outputs are defined (empty kernel, zero counts)
+    assert not r["alive"].any() and not r["bits"].any() and list(r["counts"]) == [0, 0, 0, r["status"]]
+    # a colour outside [0, k) and an edge inside one class: found on the device
+    bad = synth.tiny_random(7006, 60, 4, 0.5)
+    bad.colour = bad.colour.copy()
+    bad.colour[5] = 4
+    r = _noalloc(bad)
+    assert r["status"] == kz.KZ_ERR_COLOUR_RANGE
+    assert not r["alive"].any() and not r["bits"].any() and list(r["counts"]) == [0, 0, 0, r["status"]]
+    mono = synth.Graph(n=3, k=2, colour=np.array([0, 0, 1], np.int32), edges=np.array([[0, 1]], np.int32))
+    r = _noalloc(mono)
+    assert r["status"] == kz.KZ_ERR_ILLEGAL_COLOURING
+    assert not r["alive"].any() and not r["bits"].any()
     # and a correct call right after the refusals
     _check_same(synth.kpartite(200, 8, 0.6, seed=7005))
