@@ -343,14 +343,16 @@ kz_status kz_kernelize(kz_graph g, const kz_options *opt, void *stream) {
   g->dom_removed = 0;
   if (o.dominance && (o.schedule != KZ_SCHED_PLAIN || !g->has_bitset)) return KZ_ERR_UNSUPPORTED;
   if (o.schedule == KZ_SCHED_LEARNED) {
-    // learned worklist rounds on the bitset rows, certified by plain sweeps
+    // learned worklist rounds on the bitset rows, certified by full passes of
+    // the path AUTO would take (the bitset sweep or the tensor form)
     if (!g->has_bitset || !g->model) return KZ_ERR_UNSUPPORTED;
-    if (o.path != KZ_PATH_AUTO && o.path != KZ_PATH_BITSET) return KZ_ERR_UNSUPPORTED;
+    if (o.path != KZ_PATH_AUTO && o.path != KZ_PATH_BITSET && o.path != KZ_PATH_TENSOR) return KZ_ERR_UNSUPPORTED;
+    const int full = o.path == KZ_PATH_AUTO ? (tensor_preferred(g) ? KZ_PATH_TENSOR : KZ_PATH_BITSET) : o.path;
     KZ_TRY(state_to_bitset(g, g->stream));
     g->ab_synced = false;
-    KZ_TRY(learned_kernelize(g, o, g->stream));
+    KZ_TRY(learned_kernelize(g, o, full, g->stream));
     g->kernelized = true;
-    g->path_ran = KZ_PATH_BITSET;
+    g->path_ran = full;
     return KZ_OK;
   }
   if (o.schedule == KZ_SCHED_SUPPORT) {

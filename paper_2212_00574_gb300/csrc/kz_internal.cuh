@@ -256,6 +256,9 @@ kz_status bitset_begin_run(kz_graph g, int64_t max_sweeps, cudaStream_t s);
 
 // Tensor-core edge rule (kz_tensor.cu).
 kz_status tensor_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s);
+// One pass of the tensor form (the run started by bitset_begin_run); *cont = 1
+// when it deleted something and the run may go on.
+kz_status tensor_one_pass(kz_graph g, const kz_options &opt, cudaStream_t s, int *cont);
 void tensor_release(kz_graph g);
 // The driver's cuTensorMapEncodeTiled, found through the runtime's entry-point
 // query (null when the driver does not provide it).
@@ -266,7 +269,7 @@ kz_status dominance_round(kz_graph g, int64_t *removed, cudaStream_t s);
 void dominance_release(kz_graph g);
 
 // Learned schedule (kz_learned.cu).
-kz_status learned_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s);
+kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cudaStream_t s);
 void learned_release(kz_graph g);
 
 // Whole-fixpoint-in-one-CTA kernel (kz_cta.cu).

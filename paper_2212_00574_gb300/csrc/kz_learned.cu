@@ -25,10 +25,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "../../include/kz_learned.h"
 #include "kz_internal.cuh"
+#include "kz_mlp.cuh"
 #include "kz_rules.cuh"
 
 struct kz_model_s {
@@ -42,148 +44,284 @@ struct kz_model_s {
 namespace kz {
 namespace learned {
 
-constexpr int F = KZ_MLP_FEATURES;
-constexpr int H = KZ_MLP_HIDDEN;
-constexpr int P = KZ_MLP_PARAMS;
-// offsets of the weight blocks in the flat array
-constexpr int oW1 = 0, ob1 = oW1 + H * F, oW2 = ob1 + H, ob2 = oW2 + H * H, ow3 = ob2 + H, ob3 = ow3 + H;
-static_assert(ob3 + 1 == P, "weight layout");
+using namespace kz::mlp;
 
 // ---------------------------------------------------------------------------
-// MLP kernels
+// MLP kernels (tensor cores: warp-level bf16 MMAs, see kz_mlp.cuh)
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ float mlp_logit(const float *__restrict__ w, const float *x) {
-  float h1[H];
-#pragma unroll
-  for (int j = 0; j < H; j++) {
-    float a = w[ob1 + j];
-#pragma unroll
-    for (int i = 0; i < F; i++) a = fmaf(w[oW1 + j * F + i], x[i], a);
-    h1[j] = fmaxf(a, 0.f);
-  }
-  float out = w[ob3];
-  for (int j = 0; j < H; j++) {
-    float a = w[ob2 + j];
-#pragma unroll
-    for (int i = 0; i < H; i++) a = fmaf(w[oW2 + j * H + i], h1[i], a);
-    out = fmaf(w[ow3 + j], fmaxf(a, 0.f), out);
-  }
-  return out;
-}
+constexpr int kFwdWarps = 8;
 
-// bf16 weights widened into shared memory once per block; fp32 arithmetic.
-__global__ void mlp_forward_kernel(const __nv_bfloat16 *__restrict__ w16, const float *__restrict__ X, int64_t B,
-                                   float *__restrict__ logits) {
-  __shared__ float w[P];
-  for (int i = threadIdx.x; i < P; i += blockDim.x) w[i] = __bfloat162float(w16[i]);
+// Logits of B feature rows X (fp32 [B][16]), 32 rows per warp step.
+__global__ void __launch_bounds__(32 * kFwdWarps) mlp_forward_kernel(const __nv_bfloat16 *__restrict__ w16,
+                                                                      const float *__restrict__ X, int64_t B,
+                                                                      float *__restrict__ logits) {
+  __shared__ SmemNet net;
+  __shared__ __align__(16) __nv_bfloat16 sx[kFwdWarps][kTileRows * kXLd];
+  load_net(net, w16);
+  uint32_t w1f[8][2];
+  load_w1_frags(w1f, w16);
   __syncthreads();
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < B; s += (int64_t)gridDim.x * blockDim.x) {
-    float x[F];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * kFwdWarps * kTileRows;
+  for (int64_t base = ((int64_t)blockIdx.x * kFwdWarps + warp) * kTileRows; base < B; base += stride) {
+    const int64_t q = base + lane;
+    float f[F];
 #pragma unroll
-    for (int i = 0; i < F; i++) x[i] = X[s * F + i];
-    logits[s] = mlp_logit(w, x);
+    for (int i = 0; i < F; i++) f[i] = q < B ? X[q * F + i] : 0.f;
+    store_row(sx[warp] + lane * kXLd, f);
+    __syncwarp();
+    const float l = tile_logits(net, w1f, sx[warp]);
+    if (q < B) logits[q] = l;
+    __syncwarp();
   }
 }
 
-constexpr int kGradThreads = 64;
+// Mean BCE and its gradient, four warps per CTA, 64 samples per chunk (16 per
+// warp).  Each warp runs the forward pass and the per-sample backward pass of
+// its 16 samples in registers (the layer outputs turn into the next product's
+// A fragments), and leaves the product operands the weight gradients need in
+// shared memory, transposed to [feature or hidden unit][sample]; then every
+// warp forms 16 rows of dW2 = dz2^T h1 and dW1 = dz1^T x over the chunk's
+// samples (K = samples), accumulated in registers across the CTA's chunks.
+constexpr int kGradWarps = 4;
+constexpr int kChunk = 16 * kGradWarps;
+constexpr int kSLd = kChunk + 8;  // row stride of the [unit][sample] tiles
 
-// Mean BCE and its gradient for one chunk of kGradThreads samples per block:
-// per-sample deltas go to shared memory, then the block forms the weight
-// gradients as sums of outer products and adds them to the global gradient.
-__global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(const float *__restrict__ w32,
-                                                                 const float *__restrict__ X,
-                                                                 const float *__restrict__ y, int64_t B,
-                                                                 float *__restrict__ grad, float *__restrict__ loss) {
-  extern __shared__ float sm[];
-  float *w = sm;                          // P
-  float *sx = w + P;                      // [T][F]
-  float *sh1 = sx + kGradThreads * F;     // [T][H]
-  float *sh2 = sh1 + kGradThreads * H;    // [T][H]
-  float *sdz1 = sh2 + kGradThreads * H;   // [T][H]
-  float *sdz2 = sdz1 + kGradThreads * H;  // [T][H]
-  float *sdl = sdz2 + kGradThreads * H;   // [T]
-  const int t = threadIdx.x;
-  for (int i = t; i < P; i += kGradThreads) w[i] = w32[i];
+struct GradSmem {
+  SmemNet net;
+  __nv_bfloat16 W2T[H * kWLd];  // W2 transposed: [i][j]
+  __nv_bfloat16 x[kGradWarps][16 * kXLd];
+  __nv_bfloat16 xT[F * kSLd];
+  __nv_bfloat16 h1T[H * kSLd];
+  __nv_bfloat16 dz2T[H * kSLd];
+  __nv_bfloat16 dz1T[H * kSLd];
+  float gb1[H], gb2[H], gw3[H];
+  float gb3, loss;
+};
+
+__device__ __forceinline__ float quad_sum(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v + __shfl_xor_sync(0xffffffffu, v, 2);
+}
+
+// sum over the eight row groups (lanes with the same t)
+__device__ __forceinline__ float column_sum(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 8);
+  return v + __shfl_xor_sync(0xffffffffu, v, 16);
+}
+
+__global__ void __launch_bounds__(32 * kGradWarps) mlp_grad_kernel(const __nv_bfloat16 *__restrict__ w16,
+                                                                    const float *__restrict__ X,
+                                                                    const float *__restrict__ y, int64_t B,
+                                                                    float *__restrict__ grad,
+                                                                    float *__restrict__ loss) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  GradSmem &S = *reinterpret_cast<GradSmem *>(smraw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  load_net(S.net, w16);
+  for (int e = tid; e < H * H; e += blockDim.x) S.W2T[(e % H) * kWLd + e / H] = w16[oW2 + e];
+  for (int j = tid; j < H; j += blockDim.x) S.gb1[j] = S.gb2[j] = S.gw3[j] = 0.f;
+  if (tid == 0) S.gb3 = S.loss = 0.f;
+  uint32_t w1f[8][2];
+  load_w1_frags(w1f, w16);
   __syncthreads();
-  const int64_t s = blockIdx.x * (int64_t)kGradThreads + t;
-  const bool valid = s < B;
-  float x[F];
+  const SmemNet &net = S.net;
+  const float invB = 1.f / (float)B;
+  float accW2[8][4], accW1[2][4];
 #pragma unroll
-  for (int i = 0; i < F; i++) x[i] = valid ? X[s * F + i] : 0.f;
-  float z1[H], h2[H], z2[H];
+  for (int i = 0; i < 8; i++) accW2[i][0] = accW2[i][1] = accW2[i][2] = accW2[i][3] = 0.f;
 #pragma unroll
-  for (int j = 0; j < H; j++) {
-    float a = w[ob1 + j];
+  for (int i = 0; i < 2; i++) accW1[i][0] = accW1[i][1] = accW1[i][2] = accW1[i][3] = 0.f;
+  const int scol = 16 * warp;  // this warp's sample columns in the transposed tiles
+
+  for (int64_t c0 = (int64_t)blockIdx.x * kChunk; c0 < B; c0 += (int64_t)gridDim.x * kChunk) {
+    const int64_t sbase = c0 + scol;
+    __nv_bfloat16 *sx = S.x[warp];
+    if (lane < 16) {
+      const int64_t q = sbase + lane;
+      float f[F];
 #pragma unroll
-    for (int i = 0; i < F; i++) a = fmaf(w[oW1 + j * F + i], x[i], a);
-    z1[j] = a;
-  }
-  float out = w[ob3];
-  for (int j = 0; j < H; j++) {
-    float a = w[ob2 + j];
+      for (int i = 0; i < F; i++) f[i] = q < B ? X[q * F + i] : 0.f;
+      store_row(sx + lane * kXLd, f);
 #pragma unroll
-    for (int i = 0; i < H; i++) a = fmaf(w[oW2 + j * H + i], fmaxf(z1[i], 0.f), a);
-    z2[j] = a;
-    h2[j] = fmaxf(a, 0.f);
-    out = fmaf(w[ow3 + j], h2[j], out);
-  }
-  const float yy = valid ? y[s] : 0.f;
-  const float sig = 1.f / (1.f + expf(-out));
-  const float dl = valid ? (sig - yy) / (float)B : 0.f;
-  const float term = valid ? (fmaxf(out, 0.f) - out * yy + log1pf(expf(-fabsf(out)))) / (float)B : 0.f;
-  float dz2[H];
-#pragma unroll
-  for (int j = 0; j < H; j++) dz2[j] = z2[j] > 0.f ? dl * w[ow3 + j] : 0.f;
-  for (int i = 0; i < H; i++) {
-    float a = 0.f;
-#pragma unroll
-    for (int j = 0; j < H; j++) a = fmaf(w[oW2 + j * H + i], dz2[j], a);
-    sdz1[t * H + i] = z1[i] > 0.f ? a : 0.f;
-    sh1[t * H + i] = fmaxf(z1[i], 0.f);
-  }
-#pragma unroll
-  for (int j = 0; j < H; j++) {
-    sh2[t * H + j] = h2[j];
-    sdz2[t * H + j] = dz2[j];
-  }
-#pragma unroll
-  for (int i = 0; i < F; i++) sx[t * F + i] = x[i];
-  sdl[t] = dl;
-  // block sum of the loss terms
-  float lt = term;
-  for (int o = 16; o > 0; o >>= 1) lt += __shfl_down_sync(0xffffffffu, lt, o);
-  if ((t & 31) == 0) atomicAdd(loss, lt);
-  __syncthreads();
-  // dW2[j][i] = sum_s dz2[s][j] h1[s][i]
-  for (int e = t; e < H * H; e += kGradThreads) {
-    const int j = e / H, i = e % H;
-    float a = 0.f;
-    for (int q = 0; q < kGradThreads; q++) a = fmaf(sdz2[q * H + j], sh1[q * H + i], a);
-    atomicAdd(&grad[oW2 + e], a);
-  }
-  // dW1[j][i] = sum_s dz1[s][j] x[s][i]
-  for (int e = t; e < H * F; e += kGradThreads) {
-    const int j = e / F, i = e % F;
-    float a = 0.f;
-    for (int q = 0; q < kGradThreads; q++) a = fmaf(sdz1[q * H + j], sx[q * F + i], a);
-    atomicAdd(&grad[oW1 + e], a);
-  }
-  for (int j = t; j < H; j += kGradThreads) {
-    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    for (int q = 0; q < kGradThreads; q++) {
-      a1 += sdz1[q * H + j];
-      a2 += sdz2[q * H + j];
-      a3 = fmaf(sdl[q], sh2[q * H + j], a3);
+      for (int i = 0; i < F; i++) S.xT[i * kSLd + scol + lane] = sx[lane * kXLd + i];
     }
-    atomicAdd(&grad[ob1 + j], a1);
-    atomicAdd(&grad[ob2 + j], a2);
-    atomicAdd(&grad[ow3 + j], a3);
+    __syncwarp();
+    // forward, layer 1: rows g and g + 8 of this warp's 16 samples
+    uint32_t a[4];
+    a[0] = ld_u32(sx + g * kXLd + 2 * t);
+    a[1] = ld_u32(sx + (g + 8) * kXLd + 2 * t);
+    a[2] = ld_u32(sx + g * kXLd + 2 * t + 8);
+    a[3] = ld_u32(sx + (g + 8) * kXLd + 2 * t + 8);
+    uint32_t a2[4][4];
+    uint32_t z1pos = 0;  // bit 4 nt + e: element e of n-tile nt has z1 > 0
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+      float c[2][4];
+#pragma unroll
+      for (int hh = 0; hh < 2; hh++) {
+        const int nt = 2 * s + hh, col = 8 * nt + 2 * t;
+        c[hh][0] = c[hh][2] = net.b1[col];
+        c[hh][1] = c[hh][3] = net.b1[col + 1];
+        mma_bf16_16816(c[hh], a, w1f[nt][0], w1f[nt][1]);
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          if (c[hh][e] > 0.f) z1pos |= 1u << (4 * nt + e);
+          const __nv_bfloat16 hv = __float2bfloat16_rn(fmaxf(c[hh][e], 0.f));
+          S.h1T[(col + (e & 1)) * kSLd + scol + g + 8 * (e >> 1)] = hv;
+        }
+      }
+      a2[s][0] = pack_bf16x2(fmaxf(c[0][0], 0.f), fmaxf(c[0][1], 0.f));
+      a2[s][1] = pack_bf16x2(fmaxf(c[0][2], 0.f), fmaxf(c[0][3], 0.f));
+      a2[s][2] = pack_bf16x2(fmaxf(c[1][0], 0.f), fmaxf(c[1][1], 0.f));
+      a2[s][3] = pack_bf16x2(fmaxf(c[1][2], 0.f), fmaxf(c[1][3], 0.f));
+    }
+    // forward, layer 2
+    float z2[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; nt++) {
+      const int col = 8 * nt + 2 * t;
+      z2[nt][0] = z2[nt][2] = net.b2[col];
+      z2[nt][1] = z2[nt][3] = net.b2[col + 1];
+      const __nv_bfloat16 *wr = net.W2 + (8 * nt + g) * kWLd;
+#pragma unroll
+      for (int s = 0; s < 4; s++) mma_bf16_16816(z2[nt], a2[s], ld_u32(wr + 16 * s + 2 * t), ld_u32(wr + 16 * s + 2 * t + 8));
+    }
+    // output and loss of rows g (index 0) and g + 8 (index 1)
+    float o[2] = {0.f, 0.f};
+#pragma unroll
+    for (int nt = 0; nt < 8; nt++) {
+      const int col = 8 * nt + 2 * t;
+      o[0] = fmaf(net.w3[col], fmaxf(z2[nt][0], 0.f), fmaf(net.w3[col + 1], fmaxf(z2[nt][1], 0.f), o[0]));
+      o[1] = fmaf(net.w3[col], fmaxf(z2[nt][2], 0.f), fmaf(net.w3[col + 1], fmaxf(z2[nt][3], 0.f), o[1]));
+    }
+    float dl[2], lterm = 0.f, dsum = 0.f;
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+      const float logit = quad_sum(o[r]) + net.b3;
+      const int64_t q = sbase + g + 8 * r;
+      const bool valid = q < B;
+      const float yy = valid ? y[q] : 0.f;
+      const float sig = 1.f / (1.f + expf(-logit));
+      dl[r] = valid ? (sig - yy) * invB : 0.f;
+      if (valid && t == 0) {
+        lterm += (fmaxf(logit, 0.f) - logit * yy + log1pf(expf(-fabsf(logit)))) * invB;
+        dsum += dl[r];
+      }
+    }
+    // per-sample backward of layer 3 and 2: dz2 = bf16(dl w3 [z2 > 0])
+    uint32_t adz[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; nt++) {
+      const int col = 8 * nt + 2 * t;
+      float dz[4];
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        const int r = e >> 1, cc = col + (e & 1);
+        dz[e] = __bfloat162float(__float2bfloat16_rn(z2[nt][e] > 0.f ? dl[r] * net.w3[cc] : 0.f));
+        S.dz2T[cc * kSLd + scol + g + 8 * r] = __float2bfloat16_rn(dz[e]);
+      }
+      const float gw_lo = column_sum(dl[0] * fmaxf(z2[nt][0], 0.f) + dl[1] * fmaxf(z2[nt][2], 0.f));
+      const float gw_hi = column_sum(dl[0] * fmaxf(z2[nt][1], 0.f) + dl[1] * fmaxf(z2[nt][3], 0.f));
+      const float gb_lo = column_sum(dz[0] + dz[2]), gb_hi = column_sum(dz[1] + dz[3]);
+      if (g == 0) {
+        atomicAdd(&S.gw3[col], gw_lo);
+        atomicAdd(&S.gw3[col + 1], gw_hi);
+        atomicAdd(&S.gb2[col], gb_lo);
+        atomicAdd(&S.gb2[col + 1], gb_hi);
+      }
+      const int s = nt >> 1, base = (nt & 1) * 2;
+      adz[s][base] = pack_bf16x2(dz[0], dz[1]);
+      adz[s][base + 1] = pack_bf16x2(dz[2], dz[3]);
+    }
+    // dh1 = dz2 W2 (K = hidden units j), then dz1 = bf16(dh1 [z1 > 0])
+#pragma unroll
+    for (int nt = 0; nt < 8; nt++) {
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      const __nv_bfloat16 *wr = S.W2T + (8 * nt + g) * kWLd;
+#pragma unroll
+      for (int s = 0; s < 4; s++) mma_bf16_16816(c, adz[s], ld_u32(wr + 16 * s + 2 * t), ld_u32(wr + 16 * s + 2 * t + 8));
+      const int col = 8 * nt + 2 * t;
+      float dz[4];
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        dz[e] = __bfloat162float(__float2bfloat16_rn(((z1pos >> (4 * nt + e)) & 1u) ? c[e] : 0.f));
+        S.dz1T[(col + (e & 1)) * kSLd + scol + g + 8 * (e >> 1)] = __float2bfloat16_rn(dz[e]);
+      }
+      const float gb_lo = column_sum(dz[0] + dz[2]), gb_hi = column_sum(dz[1] + dz[3]);
+      if (g == 0) {
+        atomicAdd(&S.gb1[col], gb_lo);
+        atomicAdd(&S.gb1[col + 1], gb_hi);
+      }
+    }
+    // warp sums of the loss terms and of dl (one thread per row holds them)
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+      lterm += __shfl_xor_sync(0xffffffffu, lterm, o2);
+      dsum += __shfl_xor_sync(0xffffffffu, dsum, o2);
+    }
+    if (lane == 0) {
+      atomicAdd(&S.loss, lterm);
+      atomicAdd(&S.gb3, dsum);
+    }
+    __syncthreads();
+    // weight gradients over the chunk: warp w forms rows j in [16 w, 16 w + 16)
+#pragma unroll
+    for (int ks = 0; ks < kChunk / 16; ks++) {
+      uint32_t ad2[4], ad1[4];
+      const int r0 = 16 * warp + g, k0 = 16 * ks + 2 * t;
+      ad2[0] = ld_u32(S.dz2T + r0 * kSLd + k0);
+      ad2[1] = ld_u32(S.dz2T + (r0 + 8) * kSLd + k0);
+      ad2[2] = ld_u32(S.dz2T + r0 * kSLd + k0 + 8);
+      ad2[3] = ld_u32(S.dz2T + (r0 + 8) * kSLd + k0 + 8);
+      ad1[0] = ld_u32(S.dz1T + r0 * kSLd + k0);
+      ad1[1] = ld_u32(S.dz1T + (r0 + 8) * kSLd + k0);
+      ad1[2] = ld_u32(S.dz1T + r0 * kSLd + k0 + 8);
+      ad1[3] = ld_u32(S.dz1T + (r0 + 8) * kSLd + k0 + 8);
+#pragma unroll
+      for (int nt = 0; nt < 8; nt++) {
+        const __nv_bfloat16 *hr = S.h1T + (8 * nt + g) * kSLd + k0;
+        mma_bf16_16816(accW2[nt], ad2, ld_u32(hr), ld_u32(hr + 8));
+      }
+#pragma unroll
+      for (int nt = 0; nt < 2; nt++) {
+        const __nv_bfloat16 *xr = S.xT + (8 * nt + g) * kSLd + k0;
+        mma_bf16_16816(accW1[nt], ad1, ld_u32(xr), ld_u32(xr + 8));
+      }
+    }
+    __syncthreads();
   }
-  if (t == 0) {
-    float a = 0.f;
-    for (int q = 0; q < kGradThreads; q++) a += sdl[q];
-    atomicAdd(&grad[ob3], a);
+  // this CTA's sums into the global gradient
+  {
+    const int j0 = 16 * warp + g;
+#pragma unroll
+    for (int nt = 0; nt < 8; nt++) {
+      const int i = 8 * nt + 2 * t;
+      atomicAdd(&grad[oW2 + j0 * H + i], accW2[nt][0]);
+      atomicAdd(&grad[oW2 + j0 * H + i + 1], accW2[nt][1]);
+      atomicAdd(&grad[oW2 + (j0 + 8) * H + i], accW2[nt][2]);
+      atomicAdd(&grad[oW2 + (j0 + 8) * H + i + 1], accW2[nt][3]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 2; nt++) {
+      const int i = 8 * nt + 2 * t;
+      atomicAdd(&grad[oW1 + j0 * F + i], accW1[nt][0]);
+      atomicAdd(&grad[oW1 + j0 * F + i + 1], accW1[nt][1]);
+      atomicAdd(&grad[oW1 + (j0 + 8) * F + i], accW1[nt][2]);
+      atomicAdd(&grad[oW1 + (j0 + 8) * F + i + 1], accW1[nt][3]);
+    }
+  }
+  __syncthreads();
+  for (int j = tid; j < H; j += blockDim.x) {
+    atomicAdd(&grad[ob1 + j], S.gb1[j]);
+    atomicAdd(&grad[ob2 + j], S.gb2[j]);
+    atomicAdd(&grad[ow3 + j], S.gw3[j]);
+  }
+  if (tid == 0) {
+    atomicAdd(&grad[ob3], S.gb3);
+    atomicAdd(loss, S.loss);
   }
 }
 
@@ -350,34 +488,67 @@ __device__ __forceinline__ void pend_bit(const RowView &r, int x, int y, int64_t
   bit = 1u << (ib & 31);
 }
 
-// Scores the frontier: edges above the threshold are tested this round (and
-// leave the pending set); the others join the pending set, to be tested in
-// a later flush unless they die first.
-__global__ void score_kernel(RowView r, Stats s, const __nv_bfloat16 *__restrict__ w16, const int2 *__restrict__ fr,
-                             const unsigned long long *__restrict__ n_fr, float logit_threshold, int round,
-                             float density, float live_frac, int2 *__restrict__ work,
-                             unsigned long long *n_work, uint32_t *__restrict__ pend) {
-  __shared__ float w[P];
-  for (int i = threadIdx.x; i < P; i += blockDim.x) w[i] = __bfloat162float(w16[i]);
+// Scores the frontier on the tensor cores: each warp takes 32 frontier edges
+// at a time, computes their features (one edge per lane) into a bf16 tile in
+// shared memory and runs the network on it (kz_mlp.cuh).  Edges above the
+// threshold are listed for an exact test this round (and leave the pending
+// set); the others join the pending set, to be tested later unless they die
+// first.  The live counts for the density features come from the device
+// (cnt[4] = twice the live edges, cnt[5] = live vertices).
+constexpr int kScoreWarps = 8;
+
+__global__ void __launch_bounds__(32 * kScoreWarps) score_kernel(RowView r, Stats s,
+                                                                  const __nv_bfloat16 *__restrict__ w16,
+                                                                  const int2 *__restrict__ fr,
+                                                                  const unsigned long long *__restrict__ cnt,
+                                                                  float logit_threshold, int round,
+                                                                  int2 *__restrict__ work,
+                                                                  unsigned long long *n_work,
+                                                                  uint32_t *__restrict__ pend) {
+  __shared__ SmemNet net;
+  __shared__ __align__(16) __nv_bfloat16 sx[kScoreWarps][kTileRows * kXLd];
+  const bool all = !(logit_threshold > -INFINITY);
+  if (!all) load_net(net, w16);
+  uint32_t w1f[8][2];
+  if (!all) load_w1_frags(w1f, w16);
   __syncthreads();
-  const int64_t total = (int64_t)*n_fr;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int2 e = fr[q];
-    int64_t pw;
-    uint32_t pb;
-    pend_bit(r, e.x, e.y, pw, pb);
-    bool take = true;
-    if (logit_threshold > -INFINITY) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t total = (int64_t)cnt[0];
+  const double nn = (double)max(r.n, 1);
+  const float density = (float)((double)cnt[4] / (nn * fmax(nn - 1.0, 1.0)));
+  const float live_frac = (float)((double)cnt[5] / nn);
+  const int64_t stride = (int64_t)gridDim.x * kScoreWarps * kTileRows;
+  for (int64_t base = ((int64_t)blockIdx.x * kScoreWarps + warp) * kTileRows; base < total; base += stride) {
+    const int64_t q = base + lane;
+    const bool valid = q < total;
+    const int2 e = valid ? fr[q] : make_int2(0, 0);
+    bool take = valid;
+    if (!all) {
       float f[F];
-      edge_features(r, s, e.x, e.y, round, density, live_frac, f);
-      take = mlp_logit(w, f) > logit_threshold;
+      if (valid) {
+        edge_features(r, s, e.x, e.y, round, density, live_frac, f);
+      } else {
+#pragma unroll
+        for (int i = 0; i < F; i++) f[i] = 0.f;
+      }
+      store_row(sx[warp] + lane * kXLd, f);
+      __syncwarp();
+      const float logit = tile_logits(net, w1f, sx[warp]);
+      take = valid && logit > logit_threshold;
+      __syncwarp();
     }
-    if (take) {
-      work[atomicAdd(n_work, 1ull)] = e;
-      atomicAnd(&pend[pw], ~pb);
-    } else {
-      atomicOr(&pend[pw], pb);
+    if (valid) {
+      int64_t pw;
+      uint32_t pb;
+      pend_bit(r, e.x, e.y, pw, pb);
+      if (take) atomicAnd(&pend[pw], ~pb);
+      else atomicOr(&pend[pw], pb);
     }
+    const uint32_t m = __ballot_sync(0xffffffffu, take);
+    unsigned long long at = 0;
+    if (lane == 0 && m) at = atomicAdd(n_work, (unsigned long long)__popc(m));
+    at = __shfl_sync(0xffffffffu, at, 0);
+    if (take) work[at + __popc(m & ((1u << lane) - 1u))] = e;
   }
 }
 
@@ -405,7 +576,10 @@ __global__ void flush_pending_kernel(RowView r, uint32_t *__restrict__ pend, int
   }
 }
 
-// Exact edge rule for listed edges, one warp per edge, all planes.
+// Exact edge rule for listed edges, one warp per edge.  The lanes read the
+// two rows four words at a time (a row is 16-byte aligned and zero-padded to
+// a multiple of four words) and stop as soon as every class the edge needs
+// has a common neighbour: on a dense graph the first plane settles it.
 __global__ void test_edges_kernel(RowView r, const int2 *__restrict__ work, const unsigned long long *__restrict__ n_work,
                                   int2 *__restrict__ dead, unsigned long long *n_dead) {
   const int lane = threadIdx.x & 31;
@@ -413,17 +587,30 @@ __global__ void test_edges_kernel(RowView r, const int2 *__restrict__ work, cons
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t total = (int64_t)*n_work;
   const int rk = r.R * r.k;
+  const uint64_t every = r.k >= 64 ? ~0ull : ((1ull << r.k) - 1ull);
   for (int64_t q = warp0; q < total; q += warps) {
     const int2 e = work[q];
     const uint32_t *ru = r.A + (int64_t)e.x * r.ldw, *rv = r.A + (int64_t)e.y * r.ldw;
-    uint64_t cov = 0;
-    for (int w = lane; w < rk; w += 32)
-      if (ru[w] & rv[w]) cov |= 1ull << (w % r.k);
-    uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)cov);
-    uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(cov >> 32));
-    const uint64_t all = ((uint64_t)hi << 32) | lo;
-    const uint64_t own = (1ull << r.col[e.x]) | (1ull << r.col[e.y]);
-    if (lane == 0 && __popcll(all & ~own) < r.k - 2) dead[atomicAdd(n_dead, 1ull)] = e;
+    const uint64_t need = every & ~((1ull << r.col[e.x]) | (1ull << r.col[e.y]));
+    uint64_t all = 0;
+    for (int w0 = 0; w0 < rk; w0 += 128) {
+      const int w = w0 + 4 * lane;
+      uint64_t cov = 0;
+      if (w < rk) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(ru + w);
+        const uint4 b = *reinterpret_cast<const uint4 *>(rv + w);
+        const int c = w % r.k;
+        if (a.x & b.x) cov |= 1ull << c;
+        if (a.y & b.y) cov |= 1ull << ((c + 1) % r.k);
+        if (a.z & b.z) cov |= 1ull << ((c + 2) % r.k);
+        if (a.w & b.w) cov |= 1ull << ((c + 3) % r.k);
+      }
+      const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)cov);
+      const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(cov >> 32));
+      all |= ((uint64_t)hi << 32) | lo;
+      if ((all & need) == need) break;
+    }
+    if (lane == 0 && __popcll(all & need) < r.k - 2) dead[atomicAdd(n_dead, 1ull)] = e;
   }
 }
 
@@ -621,8 +808,9 @@ int32_t read_cur(kz_graph g, cudaStream_t s) {
 
 namespace kz {
 
-// Learned schedule on the bitset rows (see the file comment).
-kz_status learned_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
+// Learned schedule (see the file comment).  full_path is the path of the
+// full passes: KZ_PATH_BITSET (the multi-CTA sweep) or KZ_PATH_TENSOR.
+kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cudaStream_t s) {
   if (!g->model) return KZ_ERR_UNSUPPORTED;
   if (!g->learned_bufs) {
     LearnedBufs *b = new LearnedBufs();
@@ -637,70 +825,85 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
   const int64_t max_sweeps = opt.max_sweeps > 0 ? opt.max_sweeps : (int64_t)g->n + g->m + 1;
   const float p = std::min(std::max(g->learned_threshold, 0.f), 0.999999f);
   const float logit_thr = p <= 0.f ? -INFINITY : std::log(p / (1.f - p));
-  const int grid = 8 * sms_now();
+  const int sms = sms_now();
+  const int grid = 8 * sms;
   KZ_TRY(bitset_begin_run(g, max_sweeps, s));
   if (g->n == 0) return KZ_OK;
   const int64_t cap = std::max<int64_t>(g->m, 1);
-  // degrees before the first sweep, so that the first learned round's
-  // frontier is what that sweep changed
+  auto full_pass = [&](int *cont) -> kz_status {
+    if (full_path == KZ_PATH_TENSOR) return tensor_one_pass(g, opt, s, cont);
+    return bitset_one_pass(g, s, cont);
+  };
+  // counters and the run's productive sweeps, read back in one wait
+  unsigned long long h[8];
+  int64_t sweeps = 0;
+  auto read_counts = [&]() -> kz_status {
+    KZ_CUDA_TRY(cudaMemcpyAsync(h, b.cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
+    KZ_CUDA_TRY(cudaMemcpyAsync(&sweeps, &g->st->sweeps, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    KZ_CUDA_TRY(cudaStreamSynchronize(s));
+    return KZ_OK;
+  };
+  // degrees before the first pass, so that the first learned round's frontier
+  // is what that pass changed
   {
     RowView r0 = view_of(g, b, read_cur(g, s));
     KZ_CUDA_TRY(cudaMemsetAsync(b.cnt, 0, sizeof(unsigned long long) * 8, s));
     stats_kernel<<<grid, 256, 0, s>>>(r0, b.s, 1, b.cnt + 3);
     KZ_CUDA_TRY(cudaGetLastError());
   }
+  KZ_CUDA_TRY(cudaMemsetAsync(b.pend, 0, (size_t)g->n * g->ldw * 4, s));
   int round = 1;
   bool need_full = true;
-  KZ_CUDA_TRY(cudaMemsetAsync(b.pend, 0, (size_t)g->n * g->ldw * 4, s));
+  RowView r;
   for (;;) {
     if (need_full) {
-      // a full plain sweep: the first one, and the certifying ones
+      // a full pass: the first one, and the certifying ones
       int cont = 0;
-      KZ_TRY(bitset_one_pass(g, s, &cont));
+      KZ_TRY(full_pass(&cont));
       if (!cont) return KZ_OK;  // nothing deleted (or the sweep limit): certified / stopped
       need_full = false;
+      r = view_of(g, b, read_cur(g, s));
     }
-    const int cur = read_cur(g, s);
-    RowView r = view_of(g, b, cur);
     KZ_CUDA_TRY(cudaMemsetAsync(b.cnt, 0, sizeof(unsigned long long) * 8, s));
     count_live_kernel<<<grid, 256, 0, s>>>(r, b.cnt + 4, b.cnt + 5);
     stats_kernel<<<grid, 256, 0, s>>>(r, b.s, 0, b.cnt + 3);
     frontier_kernel<<<grid, 256, 0, s>>>(r, b.s, b.fr, b.cnt + 0, cap);
-    unsigned long long h[8];
-    KZ_TRY(read_u64(b.cnt, h, 8, s));
-    const double n = std::max(g->n, 1);
-    const float density = (float)((double)h[4] / (n * std::max(n - 1.0, 1.0)));
-    const float live_frac = (float)(h[5] / n);
-    score_kernel<<<grid, 256, 0, s>>>(r, b.s, g->model->w16, b.fr, b.cnt + 0, logit_thr, round, density,
-                                      live_frac, b.work, b.cnt + 1, b.pend);
+    score_kernel<<<2 * sms, 32 * kScoreWarps, 0, s>>>(r, b.s, g->model->w16, b.fr, b.cnt, logit_thr, round, b.work,
+                                                      b.cnt + 1, b.pend);
     test_edges_kernel<<<grid, 256, 0, s>>>(r, b.work, b.cnt + 1, b.dead, b.cnt + 2);
-    KZ_TRY(read_u64(b.cnt, h, 8, s));
+    KZ_CUDA_TRY(cudaGetLastError());
+    KZ_TRY(read_counts());
     unsigned long long dv = h[3], de = h[2];
     if (dv + de == 0) {
-      // the scored edges found nothing: test the pending ones
+      // the scored edges found nothing: the pending ones next, when they are
+      // few; otherwise (or when they hold no failure either) a full pass
       learned_finish_kernel<<<1, 1, 0, s>>>(g->st, b.cnt + 3, b.cnt + 2, b.cnt + 1, nullptr);
       KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 1, 0, sizeof(unsigned long long) * 2, s));
       flush_pending_kernel<<<grid, 256, 0, s>>>(r, b.pend, b.work, b.cnt + 1, cap);
+      KZ_TRY(read_counts());
+      const unsigned long long pending = h[1], live_edges = h[4] / 2;
+      if (pending == 0 || pending * 8 > live_edges) {
+        need_full = true;
+        continue;
+      }
       test_edges_kernel<<<grid, 256, 0, s>>>(r, b.work, b.cnt + 1, b.dead, b.cnt + 2);
-      KZ_TRY(read_u64(b.cnt, h, 8, s));
+      KZ_TRY(read_counts());
       dv = 0;
       de = h[2];
       if (de == 0) {
-        // nothing pending fails either: certify with a full sweep
         learned_finish_kernel<<<1, 1, 0, s>>>(g->st, b.cnt + 3, b.cnt + 2, b.cnt + 1, nullptr);
         need_full = true;
         continue;
       }
       KZ_CUDA_TRY(cudaMemsetAsync(b.s.vfail, 0, (size_t)g->n, s));
+      KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 3, 0, sizeof(unsigned long long), s));
     }
-    DevState hs;
-    KZ_CUDA_TRY(cudaMemcpy(&hs, g->st, offsetof(DevState, trace_dv), cudaMemcpyDeviceToHost));
-    if (hs.sweeps >= max_sweeps) {
+    if (sweeps >= max_sweeps) {
       int32_t lim = KZ_ERR_LIMIT;
-      KZ_CUDA_TRY(cudaMemcpy(&g->st->status, &lim, 4, cudaMemcpyHostToDevice));
+      KZ_CUDA_TRY(cudaMemcpyAsync(&g->st->status, &lim, 4, cudaMemcpyHostToDevice, s));
+      KZ_CUDA_TRY(cudaStreamSynchronize(s));
       return KZ_OK;
     }
-    if (dv == 0) KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 3, 0, sizeof(unsigned long long), s));
     apply_kernel<<<grid, 256, 0, s>>>(r, b.s.vfail, b.dead, b.cnt + 2);
     learned_finish_kernel<<<1, 1, 0, s>>>(g->st, b.cnt + 3, b.cnt + 2, b.cnt + 1, nullptr);
     KZ_CUDA_TRY(cudaGetLastError());
@@ -834,8 +1037,9 @@ void kz_model_free(kz_model m) {
 kz_status kz_mlp_forward(kz_model m, const float *X, int64_t B, float *logits, void *stream) {
   if (!m || B < 0 || (B > 0 && (!X || !logits))) return KZ_ERR_ARG;
   if (B == 0) return KZ_OK;
-  const int grid = (int)std::min<int64_t>((B + 127) / 128, 8 * sms_now());
-  mlp_forward_kernel<<<grid, 128, 0, (cudaStream_t)stream>>>(m->w16, X, B, logits);
+  const int64_t per_block = (int64_t)kFwdWarps * kTileRows;
+  const int grid = (int)std::min<int64_t>((B + per_block - 1) / per_block, 2 * sms_now());
+  mlp_forward_kernel<<<grid, 32 * kFwdWarps, 0, (cudaStream_t)stream>>>(m->w16, X, B, logits);
   return cuda_status(cudaGetLastError());
 }
 
@@ -843,17 +1047,23 @@ kz_status kz_mlp_grad(kz_model m, const float *X, const float *y, int64_t B, flo
                       void *stream) {
   if (!m || B <= 0 || !X || !y || !grad || !loss) return KZ_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t smem = sizeof(float) * (P + kGradThreads * F + 4 * kGradThreads * H + kGradThreads);
-  static bool configured = false;
-  if (!configured) {
-    KZ_CUDA_TRY(cudaFuncSetAttribute((const void *)mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-    configured = true;
+  const size_t smem = sizeof(GradSmem);
+  {
+    static std::mutex mu;
+    static bool configured[64] = {};
+    int dev = 0;
+    KZ_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 64 && !configured[dev]) {
+      KZ_CUDA_TRY(cudaFuncSetAttribute((const void *)mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+      configured[dev] = true;
+    }
   }
   KZ_CUDA_TRY(cudaMemsetAsync(grad, 0, P * 4, s));
   KZ_CUDA_TRY(cudaMemsetAsync(loss, 0, 4, s));
-  const int64_t blocks = (B + kGradThreads - 1) / kGradThreads;
-  mlp_grad_kernel<<<(unsigned)blocks, kGradThreads, smem, s>>>(m->w32, X, y, B, grad, loss);
+  const int64_t blocks = std::min<int64_t>((B + kChunk - 1) / kChunk, 2 * sms_now());
+  mlp_grad_kernel<<<(unsigned)blocks, 32 * kGradWarps, smem, s>>>(m->w16, X, y, B, grad, loss);
   return cuda_status(cudaGetLastError());
 }
 

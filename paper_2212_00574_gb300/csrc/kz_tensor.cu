@@ -733,9 +733,10 @@ static kz_status tensor_prepare(kz_graph g, TensorBufs &b, bool bf16, cudaStream
   return KZ_OK;
 }
 
-kz_status tensor_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
+// The buffers of the tensor form for this graph and precision (built on
+// first use) and the kernels' shared-memory opt-in.
+static kz_status tensor_buffers(kz_graph g, bool bf16, cudaStream_t s, TensorBufs **out) {
   if (g->k > 64) return KZ_ERR_UNSUPPORTED;
-  const bool bf16 = opt.tensor_precision == 1;
   if (!g->tensor_bufs) g->tensor_bufs = new TensorState();
   TensorState &ts = *static_cast<TensorState *>(g->tensor_bufs);
   if (!ts.by[bf16]) {
@@ -747,10 +748,6 @@ kz_status tensor_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
     }
     ts.by[bf16] = nb;
   }
-  TensorBufs &b = *ts.by[bf16];
-  const int64_t max_sweeps = opt.max_sweeps > 0 ? opt.max_sweeps : (int64_t)g->n + g->m + 1;
-  KZ_TRY(bitset_begin_run(g, max_sweeps, s));
-  if (g->n == 0) return KZ_OK;
   int dev = 0;
   KZ_CUDA_TRY(cudaGetDevice(&dev));
   static bool configured[64][2] = {};
@@ -759,41 +756,71 @@ kz_status tensor_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
     KZ_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
     configured[dev][bf16] = true;
   }
+  *out = ts.by[bf16];
+  return KZ_OK;
+}
+
+// One pass of the tensor form on the current rows: expand them into the
+// operand matrix, count every class's common neighbours of every pair on the
+// tensor cores and mark the failing live edges, then apply those deletions
+// and the vertex rule into the other row buffer.  The run's counters must
+// have been started (bitset_begin_run).  *cont receives 1 when the pass
+// deleted something and the run may go on (no sweep limit or error).
+kz_status tensor_one_pass(kz_graph g, const kz_options &opt, cudaStream_t s, int *cont) {
+  *cont = 0;
+  if (g->n == 0) return KZ_OK;
+  const bool bf16 = opt.tensor_precision == 1;
+  TensorBufs *bp = nullptr;
+  KZ_TRY(tensor_buffers(g, bf16, s, &bp));
+  TensorBufs &b = *bp;
   const int sms = sms_t();
+  int32_t cur = 0;
+  KZ_CUDA_TRY(cudaMemcpyAsync(&cur, &g->st->cur, 4, cudaMemcpyDeviceToHost, s));
+  KZ_CUDA_TRY(cudaStreamSynchronize(s));
+  const uint32_t *A = g->A[cur & 1];
+  uint32_t *An = g->A[(cur & 1) ^ 1];
+  if (bf16) expand_kernel<true><<<8 * sms, 256, 0, s>>>(A, g->n, b.n_pad, g->ldw, b.step_word, b.ksteps, b.M);
+  else expand_kernel<false><<<8 * sms, 256, 0, s>>>(A, g->n, b.n_pad, g->ldw, b.step_word, b.ksteps, b.M);
+  TensorArgs a;
+  a.n = g->n;
+  a.k = g->k;
+  a.q = g->k - g->slack;
+  a.cls_step = b.cls_step;
+  a.A = A;
+  a.ldw = g->ldw;
+  a.vinfo = b.vinfo;
+  a.Edel = b.Edel;
+  a.tiles = b.tiles;
+  a.n_tiles = b.n_tiles;
+  a.counts = b.counts;
+  a.status = &g->st->status;
+  const int grid = std::max(1, std::min(b.n_tiles, sms));
+  if (bf16) tensor_edge_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(b.maps, a);
+  else tensor_edge_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(b.maps, a);
+  tensor_commit_kernel<<<8 * sms, 256, 0, s>>>(A, An, b.Edel, g->V[cur & 1], g->V[(cur & 1) ^ 1], g->n, g->ldw,
+                                               g->k, g->k - g->slack, g->R, b.col, g->d_coff, g->d_rounds, g->d_blocks,
+                                               (int32_t)g->blocks.size(), g->v_sweep, g->st, b.counts);
+  tensor_finish_kernel<<<1, 1, 0, s>>>(g->st, b.counts);
+  KZ_CUDA_TRY(cudaGetLastError());
+  int32_t c = 0, status = 0;
+  KZ_CUDA_TRY(cudaMemcpyAsync(&c, &g->st->cont, 4, cudaMemcpyDeviceToHost, s));
+  KZ_CUDA_TRY(cudaMemcpyAsync(&status, &g->st->status, 4, cudaMemcpyDeviceToHost, s));
+  KZ_CUDA_TRY(cudaStreamSynchronize(s));
+  *cont = (c && status == KZ_OK) ? 1 : 0;
+  return KZ_OK;
+}
+
+kz_status tensor_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
+  if (g->k > 64) return KZ_ERR_UNSUPPORTED;
+  TensorBufs *bp = nullptr;
+  KZ_TRY(tensor_buffers(g, opt.tensor_precision == 1, s, &bp));
+  const int64_t max_sweeps = opt.max_sweeps > 0 ? opt.max_sweeps : (int64_t)g->n + g->m + 1;
+  KZ_TRY(bitset_begin_run(g, max_sweeps, s));
+  if (g->n == 0) return KZ_OK;
   for (;;) {
-    int32_t cur = 0;
-    KZ_CUDA_TRY(cudaMemcpyAsync(&cur, &g->st->cur, 4, cudaMemcpyDeviceToHost, s));
-    KZ_CUDA_TRY(cudaStreamSynchronize(s));
-    const uint32_t *A = g->A[cur & 1];
-    uint32_t *An = g->A[(cur & 1) ^ 1];
-    if (bf16) expand_kernel<true><<<8 * sms, 256, 0, s>>>(A, g->n, b.n_pad, g->ldw, b.step_word, b.ksteps, b.M);
-    else expand_kernel<false><<<8 * sms, 256, 0, s>>>(A, g->n, b.n_pad, g->ldw, b.step_word, b.ksteps, b.M);
-    TensorArgs a;
-    a.n = g->n;
-    a.k = g->k;
-    a.q = g->k - g->slack;
-    a.cls_step = b.cls_step;
-    a.A = A;
-    a.ldw = g->ldw;
-    a.vinfo = b.vinfo;
-    a.Edel = b.Edel;
-    a.tiles = b.tiles;
-    a.n_tiles = b.n_tiles;
-    a.counts = b.counts;
-    a.status = &g->st->status;
-    const int grid = std::max(1, std::min(b.n_tiles, sms));
-    if (bf16) tensor_edge_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(b.maps, a);
-    else tensor_edge_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(b.maps, a);
-    tensor_commit_kernel<<<8 * sms, 256, 0, s>>>(A, An, b.Edel, g->V[cur & 1], g->V[(cur & 1) ^ 1], g->n, g->ldw,
-                                                 g->k, g->k - g->slack, g->R, b.col, g->d_coff, g->d_rounds, g->d_blocks,
-                                                 (int32_t)g->blocks.size(), g->v_sweep, g->st, b.counts);
-    tensor_finish_kernel<<<1, 1, 0, s>>>(g->st, b.counts);
-    KZ_CUDA_TRY(cudaGetLastError());
-    int32_t cont = 0, status = 0;
-    KZ_CUDA_TRY(cudaMemcpyAsync(&cont, &g->st->cont, 4, cudaMemcpyDeviceToHost, s));
-    KZ_CUDA_TRY(cudaMemcpyAsync(&status, &g->st->status, 4, cudaMemcpyDeviceToHost, s));
-    KZ_CUDA_TRY(cudaStreamSynchronize(s));
-    if (!cont || status != KZ_OK) break;
+    int cont = 0;
+    KZ_TRY(tensor_one_pass(g, opt, s, &cont));
+    if (!cont) break;
   }
   return KZ_OK;
 }
