@@ -82,8 +82,9 @@ def parse():
                     help="clique size q sought (0: q = k); q < k lowers both rule thresholds")
     ap.add_argument("--tensor-precision", choices=["fp8", "bf16"], default="fp8",
                     help="tensor path operands: E4M3 (kind::f8f6f4) or BF16 (kind::f16)")
-    ap.add_argument("--dominance", action="store_true",
-                    help="vertex dominance rounds (Definition 4.3.1) after the colour-index fixpoint")
+    ap.add_argument("--dominance", choices=["none", "vertex", "edge"], default="none",
+                    help="rounds of vertex (Definition 4.3.1) or edge (Definitions 4.3.2-4.3.3) dominance after "
+                         "the colour-index fixpoint")
     ap.add_argument("--max-clique", action="store_true",
                     help="time the maximum-clique driver (kernelize for q = k, k-1, ... and search each kernel)")
     ap.add_argument("--scale", type=float, default=1.0,
@@ -105,7 +106,7 @@ def default_headline(args) -> bool:
     """The default run: the headline workload with no option changed, so the
     comparisons belong on its line."""
     return (args.workload == "c5" and args.schedule == "plain" and args.path == "auto" and args.scale == 1.0
-            and args.clique_k == 0 and not args.dominance and args.plane0 == "auto" and args.loop == "device"
+            and args.clique_k == 0 and args.dominance == "none" and args.plane0 == "auto" and args.loop == "device"
             and args.tensor_precision == "fp8" and not args.no_compare)
 
 
@@ -530,7 +531,7 @@ def run_ours(args, world, rank, local, pg):
     opts = kz.kz_default_options(path=args.path, use_graph={"device": 1, "graph": 2, "host": 0}[args.loop],
                                  plane0={"auto": 0, "full": 1, "half": 2, "two": 3}[args.plane0],
                                  schedule=args.schedule, clique_k=args.clique_k,
-                                 dominance=1 if args.dominance else 0,
+                                 dominance={"none": 0, "vertex": 1, "edge": 2}[args.dominance],
                                  tensor_precision=1 if args.tensor_precision == "bf16" else 0)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 

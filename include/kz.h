@@ -133,11 +133,16 @@ typedef struct {
                              KZ_ERR_UNSUPPORTED for it */
     int32_t dominance;    /* 1: after the colour-index fixpoint, rounds of vertex dominance (thesis
                              Section 4.3, Definition 4.3.1), each followed by the fixpoint again, until
-                             a round deletes nothing; 0 (default): off.  Opt-in because dominance keeps
-                             the clique number but may delete some maximum cliques.  Needs bitset rows
-                             (paths BITSET, SMALL, TENSOR) and the plain schedule, else
-                             KZ_ERR_UNSUPPORTED; kz_kernelize_batch refuses it.  The statistics and
-                             the trace then cover the last colour-index run */
+                             a round deletes nothing.  2: the same with rounds of edge dominance
+                             (Definitions 4.3.2 and 4.3.3: an edge {x, y} goes when another live edge
+                             {u, v} has every common neighbour of x and y as a common neighbour; in one
+                             round, of dominated edges whose records {x, y, u, v} share a vertex only
+                             the one with the smallest caller-id key goes); needs a clique size of at
+                             least 3.  0 (default): off.  Opt-in because dominance keeps the clique
+                             number but may delete some maximum cliques.  Needs bitset rows (paths
+                             BITSET, SMALL, TENSOR) and the plain schedule, else KZ_ERR_UNSUPPORTED;
+                             kz_kernelize_batch refuses it.  The statistics and the trace then cover
+                             the last colour-index run */
     int32_t tensor_precision;  /* TENSOR path operands: 0 (default) E4M3 0/1 through
                                   tcgen05.mma kind::f8f6f4; 1 BF16 0/1 through kind::f16 (twice
                                   the operand bytes and MMAs; the same exact counts) */
@@ -160,7 +165,7 @@ typedef struct {
     int32_t k;             /* colours */
     int32_t clique_k;      /* clique size q the last kz_kernelize used */
     int32_t dominance_rounds;  /* dominance rounds of the last kz_kernelize that deleted something */
-    int32_t dominated;     /* vertices those rounds deleted */
+    int32_t dominated;     /* vertices (vertex dominance) or edges (edge dominance) those rounds deleted */
     int32_t reserved[2];
 } kz_stats;
 
@@ -226,6 +231,19 @@ kz_status kz_kernelize(kz_graph g, const kz_options *opt, void *stream);
  * launch.  The caller's stream waits for every graph.
  */
 kz_status kz_kernelize_batch(kz_graph *graphs, int32_t count, const kz_options *opt, void *stream);
+
+/*
+ * Tuning of the fused batch (kz_options.batch = KZ_BATCH_FUSED).  Its cost
+ * model gives each graph a group of clamp(cost / unit, 1, max_group) CTAs of
+ * the persistent launch, where a graph's cost is its block pairs times k and
+ * unit is the batch's total cost over group_spread times the resident CTAs;
+ * a graph's pass is split into about items_per_warp work items per warp of
+ * its group.  A value <= 0 restores the default (the values the batch
+ * autotuner measured best on the 1024-graph workload).  Applies to the next
+ * fused batch (a changed setting rebuilds the batch's plan).  Process-wide.
+ * Returns KZ_ERR_ARG for a NaN group_spread.
+ */
+kz_status kz_set_batch_tuning(double group_spread, int32_t items_per_warp, int32_t max_group);
 
 /*
  * Copy the kernel back (synchronous: waits for the graph's last stream).

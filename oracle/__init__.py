@@ -76,6 +76,8 @@ def _bind(path: str):
     lib.kzo_fixpoint.argtypes = [i32, i32, P, i64, P, i64, P, P, P, P, P, P, i64, P, P]
     lib.kzo_fixpoint_dominance.restype = C.c_int
     lib.kzo_fixpoint_dominance.argtypes = [i32, i32, i32, P, i64, P, P, P, P, P]
+    lib.kzo_fixpoint_edge_dominance.restype = C.c_int
+    lib.kzo_fixpoint_edge_dominance.argtypes = [i32, i32, i32, P, i64, P, P, P, P, P]
     lib.kzo_fixpoint_q.restype = C.c_int
     lib.kzo_fixpoint_q.argtypes = [i32, i32, i32, P, i64, P, i64, P, P, P, P, P, P, i64, P, P]
     lib.kzo_indices.restype = C.c_int
@@ -115,6 +117,9 @@ class Oracle:
     def fixpoint_dominance(self, *a, **kw):
         return fixpoint_dominance(*a, _lib=self.lib(), **kw)
 
+    def fixpoint_edge_dominance(self, *a, **kw):
+        return fixpoint_edge_dominance(*a, _lib=self.lib(), **kw)
+
     def indices(self, *a, **kw):
         return indices(*a, _lib=self.lib(), **kw)
 
@@ -144,6 +149,26 @@ def fixpoint_dominance(colour, edges, k: int, clique_k: int | None = None, _lib=
     if rc != 0:
         raise OracleError(rc)
     return dict(vlive=vlive, elive=elive, rounds=int(rounds.value), dominated=int(dominated.value))
+
+
+def fixpoint_edge_dominance(colour, edges, k: int, clique_k: int | None = None, _lib=None) -> dict:
+    """Colour-index fixpoint, then rounds of edge dominance (Definitions 4.3.2
+    and 4.3.3), each followed by the colour-index fixpoint again, until a
+    round deletes nothing.  Returns ``vlive``, ``elive``, ``rounds`` (rounds
+    that deleted something) and ``deleted`` (edges they deleted).  n <= 4096."""
+    lib = _lib or _load()
+    colour = np.ascontiguousarray(colour, dtype=np.int32)
+    edges = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    n, m = len(colour), len(edges)
+    vlive = np.zeros(n, np.uint8)
+    elive = np.zeros(m, np.uint8)
+    rounds, deleted = C.c_int64(0), C.c_int64(0)
+    q = int(k if clique_k is None else clique_k)
+    rc = lib.kzo_fixpoint_edge_dominance(n, int(k), q, _ptr(colour), m, _ptr(edges), _ptr(vlive), _ptr(elive),
+                                         C.addressof(rounds), C.addressof(deleted))
+    if rc != 0:
+        raise OracleError(rc)
+    return dict(vlive=vlive, elive=elive, rounds=int(rounds.value), deleted=int(deleted.value))
 
 
 def fixpoint(colour, edges, k: int, max_sweeps: int = 0, raise_on_limit: bool = True, _lib=None,

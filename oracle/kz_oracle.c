@@ -329,6 +329,34 @@ int kzo_fixpoint(int32_t n, int32_t k, const int32_t *colour, int64_t m,
 }
 
 /*
+ * The colour-index phase of the dominance procedures: kzo_fixpoint_q's
+ * Jacobi sweeps for clique size q, from the current live state (vlive,
+ * elive) until a sweep deletes nothing.  fail_v[n] and fail_e[m] are scratch.
+ */
+static void colour_index_phase(const adj_t *g, scratch_t *s, int32_t q, const int32_t *edges,
+                               uint8_t *vlive, uint8_t *elive, uint8_t *fail_v, uint8_t *fail_e)
+{
+    const int32_t n = g->n;
+    const int64_t m = g->m;
+    for (;;) {
+        int64_t nv = 0, ne = 0;
+        for (int32_t v = 0; v < n; v++) {
+            fail_v[v] = vlive[v] && vertex_index(g, elive, s, v) < q - 1;
+            nv += fail_v[v];
+        }
+        for (int64_t e = 0; e < m; e++) {
+            fail_e[e] = elive[e] && edge_index(g, elive, s, edges[2 * e], edges[2 * e + 1]) < q - 2;
+            ne += fail_e[e];
+        }
+        if (nv == 0 && ne == 0) break;
+        for (int32_t v = 0; v < n; v++)
+            if (fail_v[v]) vlive[v] = 0;
+        for (int64_t e = 0; e < m; e++)
+            if (elive[e] && (fail_e[e] || fail_v[edges[2 * e]] || fail_v[edges[2 * e + 1]])) elive[e] = 0;
+    }
+}
+
+/*
  * Colour-index fixpoint followed by rounds of vertex dominance (thesis
  * Section 4.3, Definition 4.3.1), each round followed by the colour-index
  * fixpoint again, until a dominance round deletes nothing.
@@ -376,23 +404,7 @@ int kzo_fixpoint_dominance(int32_t n, int32_t k, int32_t q, const int32_t *colou
     memset(vlive, 1, (size_t)n);
     memset(elive, 1, (size_t)m);
     for (;;) {
-        /* colour-index Jacobi sweeps from the current state */
-        for (;;) {
-            int64_t nv = 0, ne = 0;
-            for (int32_t v = 0; v < n; v++) {
-                fail_v[v] = vlive[v] && vertex_index(&g, elive, &s, v) < q - 1;
-                nv += fail_v[v];
-            }
-            for (int64_t e = 0; e < m; e++) {
-                fail_e[e] = elive[e] && edge_index(&g, elive, &s, edges[2 * e], edges[2 * e + 1]) < q - 2;
-                ne += fail_e[e];
-            }
-            if (nv == 0 && ne == 0) break;
-            for (int32_t v = 0; v < n; v++)
-                if (fail_v[v]) vlive[v] = 0;
-            for (int64_t e = 0; e < m; e++)
-                if (elive[e] && (fail_e[e] || fail_v[edges[2 * e]] || fail_v[edges[2 * e + 1]])) elive[e] = 0;
-        }
+        colour_index_phase(&g, &s, q, edges, vlive, elive, fail_v, fail_e);
         /* one dominance round on the snapshot */
         for (int32_t v = 0; v < n; v++) {
             deg[v] = 0;
@@ -438,6 +450,166 @@ done:
     free(fail_v);
     free(fail_e);
     free(deg);
+    scratch_free(&s);
+    adj_free(&g);
+    return rc;
+}
+
+/*
+ * Colour-index fixpoint alternating with rounds of edge dominance (thesis
+ * Section 4.3, Definitions 4.3.2 and 4.3.3), until a round deletes nothing.
+ *
+ * Definition 4.3.3: for four distinct vertices, edge f = {u, v} dominates
+ * edge e = {x, y} when u is not adjacent to both x and y, v is not adjacent
+ * to both x and y, and N(x) and N(y) have no common neighbour outside
+ * N(u) and N(v): N(x) ∩ N(y) ⊆ N(u) ∩ N(v).  Definition 4.3.2 is the case of
+ * two edges sharing a vertex: {u, b} dominates {a, u} when
+ * N(a) ∩ N(u) ⊆ N(u) ∩ N(b) and b is not adjacent to a.  (The printed
+ * condition reads "b is not in N(a) ∩ N(b)", which every b meets since no
+ * vertex is its own neighbour; the reading "b is not in N(a)" is the one the
+ * Remarks' swap argument needs.)  Taking "{u, x} is not an edge" as true
+ * when u = x, the conditions of Definition 4.3.3 for f = {y, b} sharing y
+ * with e = {x, y} are exactly those of Definition 4.3.2 with a = x, so one
+ * test covers both: f != e live, u and v each non-adjacent to x or to y, and
+ * the subset condition, on live neighbourhoods.
+ *
+ * The Remarks: a clique through e turns into one through f when x and y are
+ * swapped for u and v (a for b), so deleting a dominated edge keeps the
+ * clique number (some cliques may go: the pass is opt-in).
+ *
+ * Reading for a parallel round: on the round's snapshot every dominated live
+ * edge e takes as witness the dominating edge of smallest key, the key of an
+ * edge {s, t} being (min(s, t), max(s, t)) in caller ids; the record of e is
+ * the set of the vertices of e and of its witness.  An edge is deleted in the
+ * round when its key is the smallest among all records that share a vertex
+ * with its record.  Deleted records are pairwise vertex-disjoint, so deleting
+ * them together equals deleting them one at a time (a deletion changes only
+ * its endpoints' neighbourhoods, which no other deleted record involves), and
+ * the dominated edge of smallest key is always deleted.
+ *
+ * Dense adjacency matrix: n <= 4096 (KZO_ERR_ARG beyond).  Outputs: vlive[n],
+ * elive[m], the dominance rounds that deleted something, the edges they
+ * deleted.
+ */
+static uint64_t edge_key(int32_t s, int32_t t)
+{
+    int32_t lo = s < t ? s : t, hi = s < t ? t : s;
+    return ((uint64_t)(uint32_t)lo << 32) | (uint32_t)hi;
+}
+
+int kzo_fixpoint_edge_dominance(int32_t n, int32_t k, int32_t q, const int32_t *colour, int64_t m,
+                                const int32_t *edges, uint8_t *vlive_out, uint8_t *elive_out,
+                                int64_t *rounds_out, int64_t *deleted_out)
+{
+    if (q < 1 || q > k || n > 4096) return KZO_ERR_ARG;
+    int rc = validate(n, k, colour, m, edges);
+    if (rc != KZO_OK) return rc;
+    adj_t g;
+    rc = adj_build(&g, n, k, colour, m, edges);
+    if (rc != KZO_OK) return rc;
+    scratch_t s;
+    if (scratch_init(&s, n, k) != KZO_OK) {
+        adj_free(&g);
+        return KZO_ERR_OOM;
+    }
+    uint8_t *vlive = (uint8_t *)malloc((size_t)n + 1);
+    uint8_t *elive = (uint8_t *)malloc((size_t)m + 1);
+    uint8_t *fail_v = (uint8_t *)malloc((size_t)n + 1);
+    uint8_t *fail_e = (uint8_t *)malloc((size_t)m + 1);
+    uint8_t *A = (uint8_t *)calloc((size_t)n * (size_t)n + 1, 1);   /* live adjacency */
+    int64_t *witness = (int64_t *)malloc(sizeof(int64_t) * ((size_t)m + 1));
+    uint64_t *claim = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)n + 1));
+    int32_t *common = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    int64_t rounds = 0, deleted = 0;
+    if (!vlive || !elive || !fail_v || !fail_e || !A || !witness || !claim || !common) {
+        rc = KZO_ERR_OOM;
+        goto done;
+    }
+    memset(vlive, 1, (size_t)n);
+    memset(elive, 1, (size_t)m);
+    for (int64_t e = 0; e < m; e++) {
+        int32_t x = edges[2 * e], y = edges[2 * e + 1];
+        A[(size_t)x * n + y] = A[(size_t)y * n + x] = 1;
+    }
+    for (;;) {
+        colour_index_phase(&g, &s, q, edges, vlive, elive, fail_v, fail_e);
+        for (int64_t e = 0; e < m; e++)
+            if (!elive[e]) {
+                int32_t x = edges[2 * e], y = edges[2 * e + 1];
+                A[(size_t)x * n + y] = A[(size_t)y * n + x] = 0;
+            }
+        /* one edge-dominance round on the snapshot: each dominated edge's witness */
+        for (int64_t e = 0; e < m; e++) {
+            witness[e] = -1;
+            if (!elive[e]) continue;
+            int32_t x = edges[2 * e], y = edges[2 * e + 1];
+            /* the common neighbours of x and y */
+            int32_t nx = 0;
+            for (int32_t w = 0; w < n; w++)
+                if (A[(size_t)x * n + w] && A[(size_t)y * n + w]) common[nx++] = w;
+            for (int64_t f = 0; f < m; f++) {
+                if (f == e || !elive[f]) continue;
+                int32_t u = edges[2 * f], v = edges[2 * f + 1];
+                /* u and v each non-adjacent to x or to y ({z, z} is no edge) */
+                int u_ok = (u == x || u == y) || !A[(size_t)u * n + x] || !A[(size_t)u * n + y];
+                int v_ok = (v == x || v == y) || !A[(size_t)v * n + x] || !A[(size_t)v * n + y];
+                if (!u_ok || !v_ok) continue;
+                /* every common neighbour of x and y is a neighbour of u and of v */
+                int subset = 1;
+                for (int32_t i = 0; i < nx && subset; i++)
+                    if (!(A[(size_t)u * n + common[i]] && A[(size_t)v * n + common[i]])) subset = 0;
+                if (!subset) continue;
+                if (witness[e] < 0 ||
+                    edge_key(u, v) < edge_key(edges[2 * witness[e]], edges[2 * witness[e] + 1]))
+                    witness[e] = f;
+            }
+        }
+        /* claims: the smallest key of a record through each vertex */
+        for (int32_t z = 0; z < n; z++) claim[z] = UINT64_MAX;
+        for (int64_t e = 0; e < m; e++) {
+            if (witness[e] < 0) continue;
+            const int32_t rec[4] = {edges[2 * e], edges[2 * e + 1], edges[2 * witness[e]],
+                                    edges[2 * witness[e] + 1]};
+            const uint64_t key = edge_key(edges[2 * e], edges[2 * e + 1]);
+            for (int i = 0; i < 4; i++)
+                if (key < claim[rec[i]]) claim[rec[i]] = key;
+        }
+        int64_t nd = 0;
+        for (int64_t e = 0; e < m; e++) {
+            fail_e[e] = 0;
+            if (witness[e] < 0) continue;
+            const int32_t rec[4] = {edges[2 * e], edges[2 * e + 1], edges[2 * witness[e]],
+                                    edges[2 * witness[e] + 1]};
+            const uint64_t key = edge_key(edges[2 * e], edges[2 * e + 1]);
+            int mine = 1;
+            for (int i = 0; i < 4; i++)
+                if (claim[rec[i]] != key) mine = 0;
+            fail_e[e] = (uint8_t)mine;
+            nd += mine;
+        }
+        if (nd == 0) break;
+        rounds++;
+        deleted += nd;
+        for (int64_t e = 0; e < m; e++)
+            if (fail_e[e]) {
+                int32_t x = edges[2 * e], y = edges[2 * e + 1];
+                elive[e] = 0;
+                A[(size_t)x * n + y] = A[(size_t)y * n + x] = 0;
+            }
+    }
+    if (vlive_out) memcpy(vlive_out, vlive, (size_t)n);
+    if (elive_out) memcpy(elive_out, elive, (size_t)m);
+    if (rounds_out) *rounds_out = rounds;
+    if (deleted_out) *deleted_out = deleted;
+done:
+    free(vlive);
+    free(elive);
+    free(fail_v);
+    free(fail_e);
+    free(A);
+    free(witness);
+    free(claim);
+    free(common);
     scratch_free(&s);
     adj_free(&g);
     return rc;

@@ -260,7 +260,7 @@ static kz_status read_options(const kz_options *opt, kz_options &o) {
   if (o.plane0 < KZ_PLANE0_AUTO || o.plane0 > KZ_PLANE0_TWO) return KZ_ERR_ARG;
   if (o.batch < KZ_BATCH_CONCURRENT || o.batch > KZ_BATCH_FUSED) return KZ_ERR_ARG;
   if (o.clique_k < 0) return KZ_ERR_ARG;
-  if (o.dominance < 0 || o.dominance > 1) return KZ_ERR_ARG;
+  if (o.dominance < 0 || o.dominance > 2) return KZ_ERR_ARG;
   if (o.tensor_precision < 0 || o.tensor_precision > 1) return KZ_ERR_ARG;
   return KZ_OK;
 }
@@ -367,16 +367,20 @@ kz_status kz_kernelize(kz_graph g, const kz_options *opt, void *stream) {
   }
   const int path = o.path == KZ_PATH_AUTO ? auto_path(g) : o.path;
   if (o.dominance && path == KZ_PATH_SPARSE) return KZ_ERR_UNSUPPORTED;
+  // edge dominance relies on every live edge having a common neighbour
+  if (o.dominance == 2 && g->k - g->slack < 3) return KZ_ERR_UNSUPPORTED;
   KZ_TRY(run_one(g, o, path));
   if (!o.dominance) return KZ_OK;
-  // rounds of vertex dominance, each followed by the colour-index fixpoint
+  // rounds of vertex (1) or edge (2) dominance, each followed by the
+  // colour-index fixpoint
   for (;;) {
     int32_t status = 0;
     KZ_CUDA_TRY(cudaMemcpyAsync(&status, &g->st->status, 4, cudaMemcpyDeviceToHost, g->stream));
     KZ_CUDA_TRY(cudaStreamSynchronize(g->stream));
     if (status != KZ_OK) return KZ_OK;  // a sweep limit or timeout ends the run; fetch reports it
     int64_t removed = 0;
-    KZ_TRY(dominance_round(g, &removed, g->stream));
+    if (o.dominance == 2) KZ_TRY(edge_dominance_round(g, &removed, g->stream));
+    else KZ_TRY(dominance_round(g, &removed, g->stream));
     if (removed == 0) return KZ_OK;
     g->dom_rounds++;
     g->dom_removed += removed;

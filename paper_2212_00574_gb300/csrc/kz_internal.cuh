@@ -266,6 +266,9 @@ void *tensor_map_encoder();
 // One round of vertex dominance (Definition 4.3.1) on the current bitset rows;
 // synchronous, returns the vertices deleted.
 kz_status dominance_round(kz_graph g, int64_t *removed, cudaStream_t s);
+// One round of edge dominance (Definitions 4.3.2, 4.3.3) on the current rows;
+// *removed = edges deleted.  Needs a colour-index fixpoint for q >= 3 first.
+kz_status edge_dominance_round(kz_graph g, int64_t *removed, cudaStream_t s);
 void dominance_release(kz_graph g);
 
 // Learned schedule (kz_learned.cu).

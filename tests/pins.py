@@ -359,7 +359,98 @@ def pin_dominance_keeps_cliques(orc, cases=16):
     return None
 
 
+def pin_edge_dominance_examples(orc):
+    """Definitions 4.3.2 and 4.3.3 on hand-made graphs.  (1) Two triangles
+    a-u-w and u-b-w sharing the edge u-w, a and b not adjacent (k = 3; a, b of
+    colour 0, u of 1, w of 2): N(a) ∩ N(u) = {w} = N(u) ∩ N(b), so {u, b}
+    dominates {a, u} and {a, u} dominates {u, b} (Definition 4.3.2).  Their
+    records share vertices, so only the smaller key {a, u} goes; then a-w has
+    no common neighbour left and a none of colour 1, so the colour-index rules
+    remove both, and the triangle u-b-w remains.  (2) Two 4-cliques
+    {x, y, c, d} and {u, v, c, d} sharing c-d, with x, u of colour 0 and y, v
+    of colour 1 (k = 4): N(x) ∩ N(y) = {c, d} = N(u) ∩ N(v), and neither u nor
+    v is adjacent to x or y, so {u, v} and {x, y} dominate each other
+    (Definition 4.3.3) and no other edge is dominated; {x, y} (the smaller
+    key) goes, x and y then see only colours 2 and 3 and leave, and the
+    4-clique {u, v, c, d} remains."""
+    r = orc.fixpoint_edge_dominance(np.array([0, 1, 0, 2], np.int32),
+                                    np.array([[0, 1], [1, 2], [0, 3], [1, 3], [2, 3]], np.int32), 3)
+    if r["vlive"].tolist() != [0, 1, 1, 1] or r["elive"].tolist() != [0, 1, 0, 1, 1] or \
+            r["rounds"] != 1 or r["deleted"] != 1:
+        return f"shared vertex: {r['vlive'].tolist()} {r['elive'].tolist()} rounds {r['rounds']}"
+    colour = np.array([0, 1, 2, 3, 0, 1], np.int32)
+    edges = np.array([[0, 1], [0, 2], [0, 3], [1, 2], [1, 3], [2, 3], [4, 5], [2, 4], [3, 4], [2, 5], [3, 5]],
+                     np.int32)
+    r = orc.fixpoint_edge_dominance(colour, edges, 4)
+    if r["vlive"].tolist() != [0, 0, 1, 1, 1, 1] or r["elive"].tolist() != [0] * 5 + [1] * 6 or \
+            r["rounds"] != 1 or r["deleted"] != 1:
+        return f"disjoint edges: {r['vlive'].tolist()} {r['elive'].tolist()} rounds {r['rounds']}"
+    # (3) A strict subset (k = 3): triangle x-y-c and triangles u-v-c, u-v-c'
+    # (x, u of colour 0; y, v of 1; c, c' of 2; ids x..c' = 0..5).
+    # N(x) ∩ N(y) = {c} lies strictly inside N(u) ∩ N(v) = {c, c'}, so {u, v}
+    # dominates {x, y} but not the other way round; also {u, c} and {u, c'}
+    # dominate each other (N = {v} for both), as do {v, c} and {v, c'}.
+    # Round 1: the record of {x, y} is {x, y, u, v} and holds the smallest key
+    # at all four vertices, while {u, c} loses u to it, so only {x, y} goes;
+    # x and y then see one colour and leave.  Round 2: {u, c} (the smallest
+    # key left) goes, c keeps only v and leaves.  The triangle u-v-c' remains.
+    colour = np.array([0, 1, 2, 0, 1, 2], np.int32)
+    edges = np.array([[0, 1], [0, 2], [1, 2], [3, 4], [2, 3], [2, 4], [3, 5], [4, 5]], np.int32)
+    r = orc.fixpoint_edge_dominance(colour, edges, 3)
+    if r["vlive"].tolist() != [0, 0, 0, 1, 1, 1] or r["elive"].tolist() != [0, 0, 0, 1, 0, 0, 1, 1] or \
+            r["rounds"] != 2 or r["deleted"] != 2:
+        return f"strict subset: {r['vlive'].tolist()} {r['elive'].tolist()} rounds {r['rounds']}"
+    return None
+
+
+def _dominated(nb, e, f):
+    """Edge f dominates edge e (Definitions 4.3.2 and 4.3.3, written out on
+    live neighbourhoods): f != e, each endpoint of f non-adjacent to an
+    endpoint of e (a vertex is not adjacent to itself), and every common
+    neighbour of e's endpoints a neighbour of both of f's."""
+    (x, y), (u, v) = e, f
+    if {x, y} == {u, v}:
+        return False
+    for z in (u, v):
+        if z in nb[x] and z in nb[y]:
+            return False
+    return (nb[x] & nb[y]) <= (nb[u] & nb[v])
+
+
+def pin_edge_dominance_keeps_cliques(orc, cases=14):
+    """Edge dominance keeps the clique number: a q-clique exists in the graph
+    exactly when one exists in the result (exhaustive enumeration), and the
+    result is closed: no live edge is dominated by another live edge and no
+    element fails a colour-index rule."""
+    rng = np.random.default_rng(919)
+    for s in range(cases):
+        n = int(rng.integers(8, 24))
+        k = int(rng.integers(3, 6))
+        p = float(rng.uniform(0.4, 0.9))
+        colour, edges = _graph(16000 + s, n, k, p, planted=(s % 2 == 0))
+        for q in (k, k - 1):
+            r = orc.fixpoint_edge_dominance(colour, edges, k, clique_k=q)
+            vl, el = r["vlive"].astype(bool), r["elive"].astype(bool)
+            had = bool(refs.q_cliques(n, q, colour, edges))
+            kept = bool(refs.q_cliques(n, q, colour, edges[el])) if el.any() else False
+            if had != kept:
+                return f"q-clique existence changed (q={q}, case {s}): before {had}, after {kept}"
+            nb = _live_nbrs(n, edges, vl, el)
+            live = [tuple(e) for e, on in zip(np.asarray(edges).tolist(), el) if on]
+            for e in live:
+                if len({int(colour[w]) for w in nb[e[0]] & nb[e[1]]}) < q - 2:
+                    return f"live edge fails the edge rule (case {s})"
+                for f in live:
+                    if _dominated(nb, e, f):
+                        return f"edge {e} still dominated by {f} (case {s}, q={q})"
+            for a in np.flatnonzero(vl).tolist():
+                if len({int(colour[w]) for w in nb[a]}) < q - 1:
+                    return f"live vertex fails the vertex rule (case {s})"
+    return None
+
+
 ALL_PINS = [pin_fig8, pin_brute_force, pin_k3_triangles, pin_k2, pin_k1, pin_complete_kpartite,
             pin_empty_class, pin_planted_isolated, pin_clique_survival, pin_order_independence,
             pin_certificate, pin_incident_edges_fail, pin_validation, pin_brute_force_q,
-            pin_q_cliques_and_order, pin_dominance_examples, pin_dominance_keeps_cliques]
+            pin_q_cliques_and_order, pin_dominance_examples, pin_dominance_keeps_cliques,
+            pin_edge_dominance_examples, pin_edge_dominance_keeps_cliques]

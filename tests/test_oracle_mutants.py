@@ -16,8 +16,8 @@ MUTANTS = {
     # the clique size ignored: thresholds from the colour count
     "vertex_threshold_from_k": ("(vlive[v] && vertex_index(&g, elive, &s, v) < q - 1) {", "(vlive[v] && vertex_index(&g, elive, &s, v) < k - 1) {"),
     # the same thresholds in the dominance procedure's colour-index phases
-    "dominance_vertex_threshold": ("fail_v[v] = vlive[v] && vertex_index(&g, elive, &s, v) < q - 1;",
-                                   "fail_v[v] = vlive[v] && vertex_index(&g, elive, &s, v) < q - 2;"),
+    "dominance_vertex_threshold": ("fail_v[v] = vlive[v] && vertex_index(g, elive, s, v) < q - 1;",
+                                   "fail_v[v] = vlive[v] && vertex_index(g, elive, s, v) < q - 2;"),
     "dominance_edge_threshold": ("edges[2 * e], edges[2 * e + 1]) < q - 2;", "edges[2 * e], edges[2 * e + 1]) < q - 3;"),
     "edge_threshold_from_k": ("edges[2 * e + 1]) < q - 2)", "edges[2 * e + 1]) < k - 2)"),
     # common neighbour test dropped: counts every neighbour of v
@@ -33,6 +33,13 @@ MUTANTS = {
     "dominance_no_tie_break": ("                if (deg[a] == deg[b] &&\n", "                if (0 && deg[a] == deg[b] &&\n"),
     # dominance: the dominator deleted instead of the dominated vertex
     "dominance_reversed": ("if (b == a || !vlive[b] || deg[b] < deg[a]) continue;", "if (b == a || !vlive[b] || deg[b] > deg[a]) continue;"),
+    # edge dominance: every dominated edge deleted, no vertex-disjoint selection
+    "edge_dominance_no_selection": ("            fail_e[e] = (uint8_t)mine;", "            fail_e[e] = 1;"),
+    # edge dominance: the subset condition reversed
+    "edge_dominance_reversed": ("                for (int32_t i = 0; i < nx && subset; i++)\n                    if (!(A[(size_t)u * n + common[i]] && A[(size_t)v * n + common[i]])) subset = 0;",
+                                "                for (int32_t w = 0; w < n && subset; w++)\n                    if (A[(size_t)u * n + w] && A[(size_t)v * n + w] && !(A[(size_t)x * n + w] && A[(size_t)y * n + w])) subset = 0;"),
+    # edge dominance: an edge counted as its own dominator
+    "edge_dominance_self": ("                if (f == e || !elive[f]) continue;", "                if (!elive[f]) continue;"),
     # the sweep index recorded one too late
     "sweep_off_by_one": ("if (v_sweep) v_sweep[v] = (int32_t)sweeps;", "if (v_sweep) v_sweep[v] = (int32_t)sweeps + 1;"),
     # Gauss-Seidel instead of Jacobi: vertices leave before the edge rule runs
