@@ -107,6 +107,7 @@ def _lib():
                 "kz_status_string": (C.c_char_p, [C.c_int]),
                 "kz_version": (i32, []),
                 "kz_probe_int_throughput": (C.c_int, [i32, P, P, P]),
+                "kz_set_batch_tuning": (C.c_int, [C.c_double, i32, i32]),
                 "kz_find_clique": (C.c_int, [P, i32, i64, P, P]),
                 "kz_max_clique": (C.c_int, [P, P, i64, P, P, P]),
                 "kz_probe_barrier_timeout": (C.c_int, [P, u32, P]),
@@ -262,6 +263,12 @@ def kz_kernelize_batch(graphs, options: kz_options | None = None, stream=None):
     st = _lib().kz_kernelize_batch(arr, len(graphs), None if options is None else C.byref(options),
                                    _stream(stream))
     _check(st, "kz_kernelize_batch")
+
+
+def kz_set_batch_tuning(group_spread: float = 0.0, items_per_warp: int = 0, max_group: int = 0):
+    """Tuning of the fused batch's cost model (0 restores a default)."""
+    _check(_lib().kz_set_batch_tuning(float(group_spread), int(items_per_warp), int(max_group)),
+           "kz_set_batch_tuning")
 
 
 def kz_fetch_stats(g: int, allow=(KZ_OK,)) -> dict:

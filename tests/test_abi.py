@@ -118,3 +118,6 @@ def test_new_entry_points_validate_on_host(lib):
     d1, d2 = ctypes.c_double(), ctypes.c_double()
     assert lib.kz_probe_int_throughput(5, ctypes.byref(d1), ctypes.byref(d2), None) == kz.KZ_ERR_ARG
     assert lib.kz_probe_int_throughput(0, None, ctypes.byref(d2), None) == kz.KZ_ERR_ARG
+    lib.kz_set_batch_tuning.argtypes = [ctypes.c_double, ctypes.c_int32, ctypes.c_int32]
+    assert lib.kz_set_batch_tuning(float("nan"), 0, 0) == kz.KZ_ERR_ARG
+    assert lib.kz_set_batch_tuning(0.0, 0, 0) == kz.KZ_OK   # the defaults

@@ -416,6 +416,50 @@ def test_batch_limit_and_repeat():
             h.close()
 
 
+def test_fused_batch_replays_plans_and_limits():
+    """The fused batch replays its captured launch on repeated calls, builds a
+    new plan when the set of graphs changes, gives large graphs multi-CTA
+    groups and applies a sweep limit per graph; every graph matches the
+    oracle each time."""
+    gs = [synth.kpartite(3000, 12, 0.5, 61, planted=True),                      # a multi-CTA group
+          synth.kpartite(2500, 20, 0.35, 62, planted=False)]
+    gs += [synth.tiny_random(1400 + i, 150 + 60 * i, 5 + (i % 4), 0.1, planted=bool(i % 2)) for i in range(10)]
+    orcs = [oracle.fixpoint(g.colour, g.get_edges(), g.k) for g in gs]
+    handles = [kz.KernelGraph.from_synth(g, dense=True) for g in gs]
+    fused = kz.kz_default_options(batch="fused")
+
+    def check(sub, limit=0):
+        for i in sub:
+            alive, edges, st = handles[i].fetch(allow=(kz.KZ_OK, kz.KZ_ERR_LIMIT))
+            orc = orcs[i] if not limit else oracle.fixpoint(gs[i].colour, gs[i].get_edges(), gs[i].k,
+                                                            max_sweeps=limit, raise_on_limit=False)
+            assert np.array_equal(alive, orc["vlive"]), i
+            assert np.array_equal(edges, gs[i].get_edges()[orc["elive"].astype(bool)]), i
+            assert st["sweeps"] == orc["sweeps"], i
+            if not limit:
+                assert st["passes"] == orc["passes"] and st["edge_tests"] == orc["tests"], i
+
+    try:
+        every = list(range(len(gs)))
+        for _ in range(3):
+            for h in handles:
+                h.reset()
+            kz.kz_kernelize_batch([h.h for h in handles], fused)
+            check(every)
+        sub = every[::2]
+        for i in sub:
+            handles[i].reset()
+        kz.kz_kernelize_batch([handles[i].h for i in sub], fused)
+        check(sub)
+        for h in handles:
+            h.reset()
+        kz.kz_kernelize_batch([h.h for h in handles], kz.kz_default_options(batch="fused", max_sweeps=1))
+        check(every, limit=1)
+    finally:
+        for h in handles:
+            h.close()
+
+
 # ---------------------------------------------------------------------------
 # multi-CTA sweep: equal-cost warp ranges and change-tagged writes
 # ---------------------------------------------------------------------------
