@@ -14,12 +14,16 @@
 //
 // Sweep t:
 //   1. rule: every dirty element (its counts changed in the last update; all
-//      live elements in the first sweep) is tested on the counts of S_t; the
+//      live elements after a recount) is tested on the counts of S_t; the
 //      failing edges are listed;
 //   2. update (only when the sweep is applied): every live triangle of S_t
 //      that loses an edge is visited once, from its deleted edge of smallest
 //      id, and each surviving edge of it loses that witness; each deleted
-//      edge decrements its endpoints' vertex counts;
+//      edge decrements its endpoints' vertex counts.  The rows walked are
+//      the live rows compacted at the last recount (their dead entries are
+//      skipped).  After a sweep that deletes more than a quarter of the live
+//      edges the counts are recounted from scratch on the compacted live
+//      graph instead;
 //   3. apply: the live flags drop the failing elements.
 // Every edge of a failing vertex fails the edge rule in the same sweep (see
 // kz_bitset.cu), so the edge list of step 1 already holds them.  Counts only
@@ -317,8 +321,35 @@ void support_release(kz_graph g) {
   g->support_bufs = nullptr;
 }
 
-// Oriented CSR of the live edges (the plain path's compaction kernels, with
-// the second row buffer as scratch), then the per-class counts.
+// Counts from scratch for the current live state: the plain path's
+// compaction (the live rows, compacted, land in the other row buffer; the
+// oriented CSR of the live edges beside them), then the per-class vertex and
+// edge counts; every live element is marked dirty.  Returns the live edges.
+static kz_status support_recount(kz_graph g, SupportBufs *b, cudaStream_t s, int64_t *live_edges) {
+  const int grid = 8 * sms_of_device(), threads = 256;
+  const int64_t n = g->n, m = g->m;
+  const int k = g->k;
+  const int c = g->sp_cur;
+  uint8_t *elive = g->sp_elive[c], *vlive = g->sp_vlive[c];
+  KZ_CUDA_TRY(cudaMemsetAsync(b->cnt_e, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(m, 1) * k, s));
+  KZ_CUDA_TRY(cudaMemsetAsync(b->cnt_v, 0, sizeof(uint32_t) * (size_t)n * k, s));
+  support_init_kernel<<<grid, threads, 0, s>>>(g->sp_eu, g->sp_ev, g->sp_col, elive, vlive, m, (int32_t)n, k,
+                                               b->cnt_v, b->edirty, b->vdirty);
+  KZ_TRY(sparse_orient_live(g, s));
+  support_triangle_kernel<<<grid, threads, 0, s>>>(g->sp_col, g->sp_orow, g->sp_oadj, g->sp_oeid, g->sp_osrc,
+                                                   g->sp_totals + 1, k, b->cnt_e);
+  KZ_CUDA_TRY(cudaGetLastError());
+  KZ_CUDA_TRY(cudaMemcpyAsync(live_edges, g->sp_totals + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  KZ_CUDA_TRY(cudaStreamSynchronize(s));
+  return KZ_OK;
+}
+
+// A sweep that deletes more than this share of the live edges is followed by
+// a recount from scratch instead of the incremental update: the update
+// visits every triangle a deleted edge closes (atomics on counts shared by
+// hub edges), while a recount enumerates the much smaller surviving graph.
+constexpr int64_t kRecountShareInv = 4;  // one quarter
+
 kz_status sparse_kernelize_support(kz_graph g, const kz_options &opt, cudaStream_t s) {
   if (!g->has_csr) return KZ_ERR_UNSUPPORTED;
   const int64_t max_sweeps = opt.max_sweeps > 0 ? opt.max_sweeps : (int64_t)g->n + g->m + 1;
@@ -332,17 +363,11 @@ kz_status sparse_kernelize_support(kz_graph g, const kz_options &opt, cudaStream
   const int k = g->k;
   const int c = g->sp_cur;
   uint8_t *elive = g->sp_elive[c], *vlive = g->sp_vlive[c];
-
-  // counts of the live graph
-  KZ_CUDA_TRY(cudaMemsetAsync(b->cnt_e, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(m, 1) * k, s));
-  KZ_CUDA_TRY(cudaMemsetAsync(b->cnt_v, 0, sizeof(uint32_t) * (size_t)n * k, s));
   KZ_CUDA_TRY(cudaMemsetAsync(b->dcount, 0, 4, s));
-  support_init_kernel<<<grid, threads, 0, s>>>(g->sp_eu, g->sp_ev, g->sp_col, elive, vlive, m, (int32_t)n, k,
-                                               b->cnt_v, b->edirty, b->vdirty);
-  KZ_TRY(sparse_orient_live(g, s));
-  support_triangle_kernel<<<grid, threads, 0, s>>>(g->sp_col, g->sp_orow, g->sp_oadj, g->sp_oeid, g->sp_osrc,
-                                                   g->sp_totals + 1, k, b->cnt_e);
-  KZ_CUDA_TRY(cudaGetLastError());
+  // counts of the live graph; the compacted live rows (buffer c ^ 1) serve
+  // the incremental updates until the next recount (dead entries skipped)
+  int64_t live_edges = 0;
+  KZ_TRY(support_recount(g, b, s, &live_edges));
   for (;;) {
     support_rule_kernel<<<grid, threads, 0, s>>>(g->sp_eu, g->sp_ev, g->sp_col, elive, vlive, m, (int32_t)n, k,
                                                  b->cnt_e, b->cnt_v, b->edirty, b->vdirty, b->edel, b->vdel,
@@ -350,7 +375,9 @@ kz_status sparse_kernelize_support(kz_graph g, const kz_options &opt, cudaStream
     support_finish_kernel<<<1, 1, 0, s>>>(g->st);
     KZ_CUDA_TRY(cudaGetLastError());
     int32_t cont = 0;
+    unsigned int deleted = 0;
     KZ_CUDA_TRY(cudaMemcpyAsync(&cont, &g->st->cont, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    KZ_CUDA_TRY(cudaMemcpyAsync(&deleted, b->dcount, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
     KZ_CUDA_TRY(cudaStreamSynchronize(s));
     if (!cont) {
       // a sweep that deleted nothing (or was refused by the limit) is not
@@ -358,11 +385,19 @@ kz_status sparse_kernelize_support(kz_graph g, const kz_options &opt, cudaStream
       KZ_CUDA_TRY(cudaMemsetAsync(b->dcount, 0, 4, s));
       break;
     }
-    support_update_kernel<<<grid, threads, 0, s>>>(g->sp_eu, g->sp_ev, g->sp_col, g->sp_row0, g->sp_adj0,
-                                                   g->sp_eid0, elive, b->edel, b->dlist, b->dcount, k, b->cnt_e,
+    if ((int64_t)deleted * kRecountShareInv > live_edges) {
+      support_apply_kernel<<<grid, threads, 0, s>>>(elive, vlive, b->edel, b->vdel, m, (int32_t)n, b->dcount);
+      KZ_CUDA_TRY(cudaGetLastError());
+      KZ_TRY(support_recount(g, b, s, &live_edges));
+      continue;
+    }
+    const int nx = c ^ 1;  // the compacted rows of the last recount
+    support_update_kernel<<<grid, threads, 0, s>>>(g->sp_eu, g->sp_ev, g->sp_col, g->sp_row[nx], g->sp_adj[nx],
+                                                   g->sp_eid[nx], elive, b->edel, b->dlist, b->dcount, k, b->cnt_e,
                                                    b->cnt_v, b->edirty, b->vdirty);
     support_apply_kernel<<<grid, threads, 0, s>>>(elive, vlive, b->edel, b->vdel, m, (int32_t)n, b->dcount);
     KZ_CUDA_TRY(cudaGetLastError());
+    live_edges -= (int64_t)deleted;
   }
   return KZ_OK;
 }
