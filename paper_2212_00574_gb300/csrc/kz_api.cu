@@ -284,9 +284,10 @@ constexpr int kSmallAutoMaxN = 64;
 // table measured on GB300 by the autotuner (paper_2212_00574_gb300/autotune.py:
 // time to fixpoint of both paths on seeded k-partite graphs with a planted
 // clique, n in {2048, 4096, 8192, 16384}, k in {12, 24}, density in {0.05,
-// 0.1, 0.2, 0.3, 0.45}; its measurements are in autotune_grid.json beside
-// it): 1 where the tensor form was faster.  A graph falls in the bin of the
-// nearest measured point.
+// 0.1, 0.2, 0.3, 0.45}, and over the batch workload's range, n in {64, 256,
+// 1024, 2048, 4096}, k in {6, 12, 24, 32}, density in {0.3, 0.45, 0.6, 0.8,
+// 0.95}; its measurements are in autotune_grid.json beside it): 1 where the
+// tensor form was faster over the bin's measured graphs.
 // The bitset sweep settles most pairs from the first word of each class when
 // common neighbours are plentiful (dense graphs); the tensor form does the
 // same work whatever the density, so it wins where pairs need many words or

@@ -240,10 +240,12 @@ static int sm_count_here() {
 // batch's total cost divided by kGroupSpread times the grid (so that, if all
 // graphs ran at once, they would ask for kGroupSpread grids' worth of CTAs),
 // and its items hold about kItemsPerWarp items per warp of the group.
-// kGroupSpread was read off the batch autotuner's measurements over the
-// 1024-graph workload's range (n 64..4096, k 6..32, p 0.3..0.95).
-constexpr int kMaxGroup = 32;
-constexpr double kGroupSpread = 2.0;
+// The three constants are the batch autotuner's fastest setting on the
+// 1024-graph workload (paper_2212_00574_gb300/autotune_batch.json): large
+// groups win, because a graph's passes are latency-bound chains of work items
+// and cascading graphs need many of them.
+constexpr int kMaxGroup = 64;
+constexpr double kGroupSpread = 128.0;
 constexpr int kItemsPerWarp = 4;
 
 struct BatchTuning {

@@ -20,7 +20,7 @@ def _compiled_table():
 
 def test_compiled_table_matches_measurements():
     records = json.load(open(autotune.GRID_FILE))["records"]
-    assert len(records) == 40
+    assert len(records) == 140
     assert autotune.table_from(records) == _compiled_table()
 
 
@@ -40,3 +40,9 @@ def test_bin_edges_match_the_library():
     kb = [int(x) for x in re.findall(r"g->k < (\d+) \?", body)]
     db = [float(x) for x in re.findall(r"d < ([0-9.]+)", body)]
     assert tuple(nb) == autotune.N_EDGES and kb == [autotune.K_EDGE] and tuple(db) == autotune.D_EDGES
+
+
+def test_batch_constants_match_measurements():
+    records = json.load(open(autotune.BATCH_FILE))["records"]
+    src = open(os.path.join(ROOT, "paper_2212_00574_gb300", "csrc", "kz_batch.cu")).read()
+    assert autotune.render_batch_c(autotune.best_batch_tuning(records)) in src
