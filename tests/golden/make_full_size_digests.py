@@ -111,7 +111,10 @@ def _write(name: str, obj) -> None:
     path = os.path.join(OUT, f"{name}.json")
     tmp = path + ".tmp"
     with open(tmp, "w") as f:
-        json.dump(obj, f, indent=1, sort_keys=True)
+        if "graphs" in obj:  # the batch: one record per graph, kept compact
+            json.dump(obj, f, sort_keys=True, separators=(",", ":"))
+        else:
+            json.dump(obj, f, indent=1, sort_keys=True)
         f.write("\n")
     os.replace(tmp, path)
     print(f"wrote {path}", flush=True)
