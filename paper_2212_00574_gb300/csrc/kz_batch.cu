@@ -10,7 +10,8 @@
 // Inside a group a pass is split into work items (block X against a run of
 // higher-class blocks Y) that the group's warps take in turn; the warp that
 // finishes a graph's last item closes the pass; a barrier among the group's
-// CTAs (one CTA: __syncthreads) separates passes.  So a graph's rows stay in
+// CTAs (one CTA: __syncthreads) separates passes, and its last arriver
+// decides for the whole group whether another pass follows.  So a graph's rows stay in
 // L2 across its passes, no CTA waits for graphs it does not work on, and
 // small graphs (one CTA each) never pay a grid-wide barrier.
 //
@@ -82,6 +83,38 @@ __device__ __forceinline__ uint64_t batch_clock() {
   return t;
 }
 
+// Barrier of a group's CTAs (thread 0 of each), bounded by the wall clock.
+// The last to arrive reads whether the graph needs another pass and publishes
+// it in the top bit of the barrier word together with the next generation
+// (low 31 bits); the others wait for the generation to move and read the
+// decision from the word.  Returns the decision (0 also after an abort).
+__device__ __forceinline__ int group_sync(DevState *st, BatchCtl *ctl, int members, uint32_t gen) {
+  constexpr uint32_t kGenMask = 0x7fffffffu;
+  __threadfence();
+  if (atomicAdd(&st->bar_count, 1u) == (unsigned int)members - 1u) {
+    st->bar_count = 0;
+    __threadfence();
+    const int go = *((volatile int32_t *)&st->cont) && !*((volatile int32_t *)&ctl->abort);
+    atomicExch(&st->bar_gen, ((gen + 1u) & kGenMask) | (go ? 0x80000000u : 0u));
+    return go;
+  }
+  const uint64_t t0 = batch_clock();
+  for (;;) {
+    const uint32_t w = *((volatile unsigned int *)&st->bar_gen);
+    if ((w & kGenMask) != (gen & kGenMask)) {
+      __threadfence();
+      return (int)(w >> 31) && !*((volatile int32_t *)&ctl->abort);
+    }
+    if (*((volatile int32_t *)&ctl->abort)) return 0;
+    __nanosleep(128);
+    if (batch_clock() - t0 > kGroupWaitNs) {
+      atomicExch(&ctl->abort, 1);
+      atomicCAS(&st->status, (int32_t)KZ_OK, (int32_t)KZ_ERR_TIMEOUT);
+      return 0;
+    }
+  }
+}
+
 // One work item at class-word width KMAX, kept out of line so that the four
 // widths the kernel dispatches between do not add up their registers.
 template <int KMAX>
@@ -118,10 +151,20 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 3) batch_group_kernel(BatchA
     G.v_sweep = B.v_sweep;
     G.k = B.k;
     G.ldw = B.ldw;
-    uint32_t gen = 0;  // the group barrier's generation this CTA has passed
+    uint32_t gen = 0;  // the group barrier's generations this CTA has passed
     for (;;) {
-      // every member sees the state the last pass left
-      if (threadIdx.x == 0) s_go = *((volatile int32_t *)&st->cont) && !*((volatile int32_t *)&ctl->abort);
+      // Whether the graph needs another pass.  A group decides it at its
+      // barrier: every member arrives (once before the first pass, then after
+      // each pass), and the last to arrive -- after every item of the pass, so
+      // after the pass was closed -- publishes the decision with the new
+      // generation.  A member must not read the graph's state on its own: one
+      // with no items in a pass could read it after the others closed the pass
+      // and leave without arriving.
+      if (threadIdx.x == 0) {
+        if (E.members > 1) s_go = group_sync(st, ctl, E.members, gen);
+        else s_go = *((volatile int32_t *)&st->cont) && !*((volatile int32_t *)&ctl->abort);
+      }
+      gen++;
       __syncthreads();
       if (!s_go) break;
       const int cur = *((volatile int32_t *)&st->cur);
@@ -164,29 +207,6 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 3) batch_group_kernel(BatchA
         }
         __syncwarp();
       }
-      __syncthreads();
-      if (E.members > 1 && threadIdx.x == 0) {
-        // barrier of the group's CTAs (bounded by the wall clock)
-        __threadfence();
-        if (atomicAdd(&st->bar_count, 1u) == (unsigned int)E.members - 1u) {
-          st->bar_count = 0;
-          __threadfence();
-          atomicExch(&st->bar_gen, gen + 1u);
-        } else {
-          const uint64_t t0 = batch_clock();
-          while (*((volatile unsigned int *)&st->bar_gen) == gen) {
-            if (*((volatile int32_t *)&ctl->abort)) break;
-            __nanosleep(128);
-            if (batch_clock() - t0 > kGroupWaitNs) {
-              atomicExch(&ctl->abort, 1);
-              atomicCAS(&st->status, (int32_t)KZ_OK, (int32_t)KZ_ERR_TIMEOUT);
-              break;
-            }
-          }
-        }
-        __threadfence();
-      }
-      gen++;
       __syncthreads();
     }
   }

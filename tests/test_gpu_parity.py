@@ -460,6 +460,31 @@ def test_fused_batch_replays_plans_and_limits():
             h.close()
 
 
+def test_fused_batch_groups_larger_than_their_work():
+    """Groups of many CTAs on graphs with only a few work items per pass: most
+    members of a group then have no item at all and may join late.  The
+    group's continue decision is taken at its barrier, so every member leaves
+    on the same pass; every graph matches the oracle."""
+    gs = [synth.tiny_random(1500 + i, 40 + 17 * i, 4 + (i % 5), 0.15 + 0.05 * (i % 4), planted=bool(i % 2))
+          for i in range(16)]
+    handles = [kz.KernelGraph.from_synth(g, dense=True) for g in gs]
+    try:
+        for spread, ipw, group in ((1e6, 1, 64), (1e6, 16, 456), (0, 0, 0)):
+            kz.kz_set_batch_tuning(spread, ipw, group)
+            for h in handles:
+                h.reset()
+            kz.kz_kernelize_batch([h.h for h in handles], kz.kz_default_options(batch="fused"))
+            for g, h in zip(gs, handles):
+                alive, edges, st = h.fetch()
+                orc = oracle.fixpoint(g.colour, g.get_edges(), g.k)
+                assert np.array_equal(alive, orc["vlive"]) and st["sweeps"] == orc["sweeps"], (spread, g.name)
+                assert np.array_equal(edges, g.get_edges()[orc["elive"].astype(bool)]), (spread, g.name)
+    finally:
+        kz.kz_set_batch_tuning(0, 0, 0)
+        for h in handles:
+            h.close()
+
+
 # ---------------------------------------------------------------------------
 # multi-CTA sweep: equal-cost warp ranges and change-tagged writes
 # ---------------------------------------------------------------------------
