@@ -22,7 +22,12 @@
  *   6,7  relative live-degree change of u, v since the previous round
  *   8    k / 64          9  round index / 32        10  live edge density
  *   11   min(deg u, deg v) / max(deg u, deg v)     12  (deg u + deg v) / (2 n)
- *   13   log2(n) / 16    14  fraction of live vertices        15  1
+ *   13   log2(n) / 16    14  fraction of live vertices
+ *   15   1 - exp(-lambda), lambda = sum over the classes c other than the
+ *        endpoints' of exp(-cnt_u[c] cnt_v[c] / |C_c|), cnt_u[c] the live
+ *        neighbours of u in class c: the chance that a needed class holds no
+ *        common neighbour if the endpoints' neighbours in each class were
+ *        random (a scale-free summary of the per-class degrees)
  */
 #ifndef KZ_LEARNED_H
 #define KZ_LEARNED_H

@@ -93,29 +93,71 @@ kz_status bitset_build_layout(kz_graph g) {
 // stays busy until the CTA's share is done.  A unit costs the members of Y it
 // tests plus a fixed part for staging and bookkeeping; the first unit of each
 // x also evaluates the vertex rule.
-static void build_units(kz_graph g, int ctas, std::vector<int2> &units, std::vector<int32_t> &cta_begin) {
+//
+// The list is laid out block by block: block x's units are (x, y) for every
+// block y of a higher class (one unit (x, nb) when there is none), starting at
+// unit_off[x].  The host computes unit_off and the CTA ranges from per-block
+// sums in O(blocks) (binary searches inside a block's run of units); the
+// list itself is filled on the device (fill_units_kernel).
+static void plan_units(kz_graph g, int ctas, std::vector<int32_t> &unit_off, std::vector<int32_t> &cta_begin) {
   constexpr int64_t kUnitFixed = 8, kVertexCost = 8;
   const int nb = (int)g->blocks.size();
   auto ybegin = [&](int x) { return std::min(g->boff[g->blocks[x].c + 1], nb); };
-  units.clear();
-  std::vector<int64_t> acc;  // running cost after each unit
-  int64_t total = 0;
+  // size_pre[y] = sizes of blocks 0..y-1
+  std::vector<int64_t> size_pre((size_t)nb + 1, 0);
+  for (int y = 0; y < nb; y++) size_pre[y + 1] = size_pre[y] + g->blocks[y].size;
+  // cost of the first i units of block x (y = yb .. yb + i - 1)
+  auto run_cost = [&](int x, int64_t i) -> int64_t {
+    const int yb = ybegin(x);
+    if (i <= 0) return 0;
+    if (yb >= nb) return kUnitFixed + kVertexCost;  // the single unit (x, nb)
+    return size_pre[yb + i] - size_pre[yb] + kUnitFixed * i + kVertexCost;
+  };
+  unit_off.assign((size_t)nb + 1, 0);
+  std::vector<int64_t> cost_off((size_t)nb + 1, 0);
   for (int x = 0; x < nb; x++) {
     const int yb = ybegin(x);
-    const int y_end = yb >= nb ? nb + 1 : nb;
-    for (int y = yb; y < y_end; y++) {
-      total += (y < nb ? g->blocks[y].size : 0) + kUnitFixed + (y == yb ? kVertexCost : 0);
-      units.push_back(make_int2(x, y));
-      acc.push_back(total);
-    }
+    const int64_t cnt = yb >= nb ? 1 : nb - yb;
+    unit_off[x + 1] = unit_off[x] + (int32_t)cnt;
+    cost_off[x + 1] = cost_off[x] + run_cost(x, cnt);
   }
+  const int64_t total = cost_off[nb];
   // CTA c takes the units whose running cost ends in (c, c + 1] * total / ctas
-  cta_begin.assign((size_t)ctas + 1, (int32_t)units.size());
+  cta_begin.assign((size_t)ctas + 1, unit_off[nb]);
   cta_begin[0] = 0;
-  size_t u = 0;
+  int x = 0;
   for (int c = 1; c < ctas; c++) {
-    while (u < units.size() && acc[u] * ctas <= (int64_t)c * total) u++;
-    cta_begin[(size_t)c] = (int32_t)u;
+    // the first unit whose running cost * ctas exceeds c * total
+    while (x < nb && cost_off[x + 1] * ctas <= (int64_t)c * total) x++;
+    if (x >= nb) {
+      cta_begin[(size_t)c] = unit_off[nb];
+      continue;
+    }
+    const int64_t cnt = unit_off[x + 1] - unit_off[x];
+    int64_t lo = 0, hi = cnt;  // units i < lo end at or below the cut
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if ((cost_off[x] + run_cost(x, mid + 1)) * ctas <= (int64_t)c * total) lo = mid + 1;
+      else hi = mid;
+    }
+    cta_begin[(size_t)c] = unit_off[x] + (int32_t)lo;
+  }
+}
+
+// The unit list from the per-block offsets: unit u of block x is (x, y) with
+// y = ybegin(x) + (u - unit_off[x]), or (x, nb) when x has no partner.
+__global__ void fill_units_kernel(int2 *__restrict__ units, const int32_t *__restrict__ unit_off,
+                                  const BlockDesc *__restrict__ blocks, const int32_t *__restrict__ boff, int32_t nb) {
+  const int64_t total = unit_off[nb];
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < total; u += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nb;  // the last x with unit_off[x] <= u
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (unit_off[mid] <= u) lo = mid;
+      else hi = mid;
+    }
+    const int yb = min(boff[blocks[lo].c + 1], nb);
+    units[u] = make_int2(lo, yb >= nb ? nb : yb + (int32_t)(u - unit_off[lo]));
   }
 }
 
@@ -161,43 +203,84 @@ __global__ void pack_edges_kernel(PackArgs a, const int32_t *__restrict__ edges,
   if ((threadIdx.x & 31) == 0 && mine) atomicAdd(a.edge_count, mine);
 }
 
-// Dense caller-id bit matrix: only bits j > i are read.
-// Gather form of the dense packer: one thread per word (x, w) of the pristine
-// rows.  Block word w = r * k + c of relabelled row x holds, for member
-// y = coff[c] + 32 r + b of block (c, r), the caller's bit between i = perm[x]
-// and j = perm[y], read from the strict upper triangle (row min(i, j), column
-// max(i, j)).  Every word is written once, without atomics; a bit between two
-// vertices of one class is an illegal colouring.
-__global__ void pack_dense_gather_kernel(PackArgs a, const uint64_t *__restrict__ bits, int64_t row_words,
-                                         int32_t n, const int32_t *__restrict__ perm) {
+// Row form of the dense packer, first half: one CTA per relabelled row x at
+// a time.  The lanes walk the caller's row i = perm[x] column by column
+// (consecutive columns on consecutive lanes, so the row word is a broadcast
+// and the position table, staged in shared memory when it fits, is read
+// without bank conflicts); every upper-triangle bit j > i is set at j's
+// position in a shared-memory copy of the output row, which is then written
+// out whole.  Every edge lands in the row of its endpoint with the smaller
+// caller id; symmetrize_kernel adds the other half.  An edge inside one class
+// lands in an own-class word: an illegal colouring.
+__global__ void pack_dense_rows_kernel(PackArgs a, const uint64_t *__restrict__ bits, int64_t row_words, int32_t n,
+                                       const int32_t *__restrict__ perm, const int32_t *__restrict__ cpos_g,
+                                       int32_t cpos_in_smem) {
+  extern __shared__ __align__(16) uint32_t psm[];
+  uint32_t *sout = psm;                                           // ldw words
+  int32_t *scpos = reinterpret_cast<int32_t *>(psm + a.ldw);      // n entries (when staged)
+  const int32_t *cpos = cpos_in_smem ? scpos : cpos_g;
+  if (cpos_in_smem)
+    for (int32_t j = threadIdx.x; j < n; j += blockDim.x) scpos[j] = cpos_g[j];
   unsigned long long mine = 0;
-  const int64_t total = (int64_t)n * a.ldw;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t x = (int32_t)(t / a.ldw);
-    const int32_t w = (int32_t)(t - (int64_t)x * a.ldw);
-    const int32_t c = w % a.k, r = w / a.k;
-    uint32_t out = 0;
-    {
-      const int32_t base = a.coff[c] + 32 * r, end = min(a.coff[c + 1], base + 32);
-      const int32_t i = perm[x];
-      for (int32_t y = base; y < end; y++) {
-        const int32_t j = perm[y];
-        if (j == i) continue;
-        const int32_t lo = min(i, j), hi = max(i, j);
-        const uint32_t bit = (uint32_t)(bits[(int64_t)lo * row_words + (hi >> 6)] >> (hi & 63)) & 1u;
-        out |= bit << (y - base);
-        mine += bit & (uint32_t)(i < j);
-      }
-      if (out && c == a.col[x]) {
-        atomicCAS(a.error, 0, (int32_t)KZ_ERR_ILLEGAL_COLOURING);
-        out = 0;
+  for (int32_t x = blockIdx.x; x < n; x += gridDim.x) {
+    for (int32_t w = threadIdx.x; w < a.ldw; w += blockDim.x) sout[w] = 0u;
+    __syncthreads();
+    const int32_t i = perm[x];
+    const uint64_t *row = bits + (int64_t)i * row_words;
+    for (int32_t j = i + 1 + threadIdx.x; j < n; j += blockDim.x) {
+      if ((row[j >> 6] >> (j & 63)) & 1ull) {
+        const int32_t pp = cpos[j];
+        atomicOr(&sout[pp >> 5], 1u << (pp & 31));
+        mine++;
       }
     }
-    a.A[t] = out;
+    __syncthreads();
+    const int32_t own = a.col[x];
+    for (int32_t w = threadIdx.x; w < a.ldw; w += blockDim.x) {
+      uint32_t out = sout[w];
+      if (out && w % a.k == own) {
+        atomicCAS(a.error, 0, (int32_t)KZ_ERR_ILLEGAL_COLOURING);
+        out = 0u;
+      }
+      a.A[(int64_t)x * a.ldw + w] = out;
+    }
+    __syncthreads();
   }
   for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
   if ((threadIdx.x & 31) == 0 && mine) atomicAdd(a.edge_count, mine);
+}
+
+// Second half: every 32 x 32 tile of a block X against a block Y of a higher
+// class becomes the OR of itself and the transpose of the (Y, X) tile, and
+// the (Y, X) tile the transpose of the result.  One warp per tile pair, over
+// all pairs (pair q of block X is partner boff[class(X) + 1] + q - pair0[X]),
+// so that many independent tiles are in flight.
+__global__ void symmetrize_kernel(uint32_t *__restrict__ A, const BlockDesc *__restrict__ blocks,
+                                  const int32_t *__restrict__ boff, const int64_t *__restrict__ pair0, int32_t nb,
+                                  int32_t k, int32_t ldw) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = pair0[nb];
+  for (int64_t q = warp0; q < total; q += warps) {
+    int lo = 0, hi = nb;  // the last X with pair0[X] <= q
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (pair0[mid] <= q) lo = mid;
+      else hi = mid;
+    }
+    const BlockDesc X = blocks[lo];
+    const BlockDesc Y = blocks[boff[X.c + 1] + (int32_t)(q - pair0[lo])];
+    const bool vx = lane < X.size, vy = lane < Y.size;
+    uint32_t *px = A + (int64_t)(X.base + lane) * ldw + Y.r * k + Y.c;
+    uint32_t *py = A + (int64_t)(Y.base + lane) * ldw + X.r * k + X.c;
+    const uint32_t xy = vx ? *px : 0u;  // row X.base + lane, bits over Y's members
+    const uint32_t yx = vy ? *py : 0u;  // row Y.base + lane, bits over X's members
+    const uint32_t nxy = xy | transpose32(yx);
+    const uint32_t nyx = transpose32(nxy);
+    if (vx) *px = nxy;
+    if (vy) *py = nyx;
+  }
 }
 
 __global__ void init_vlive_kernel(uint32_t *V, const BlockDesc *blocks, int nb, int k) {
@@ -695,6 +778,7 @@ kz_status bitset_finish_load(kz_graph g, cudaStream_t s) {
   KZ_TRY(graph_alloc(g, &g->d_rounds, (size_t)g->k, s));
   KZ_CUDA_TRY(cudaMemcpyAsync(g->d_rounds, g->rounds.data(), sizeof(int32_t) * g->k,
                               cudaMemcpyHostToDevice, s));
+  KZ_TRY(cta_prepare(g, s));  // block-pair offsets and class block offsets (the unit list needs them)
   // the half-word plane-0 test pays off when 16 members of a class almost
   // always hold a common neighbour: dense graphs
   {
@@ -727,7 +811,6 @@ kz_status bitset_finish_load(kz_graph g, cudaStream_t s) {
     KZ_TRY(graph_alloc(g, &g->st, 1, s));
     KZ_CUDA_TRY(cudaMemsetAsync(g->st, 0, sizeof(DevState), s));
   }
-  KZ_TRY(cta_prepare(g, s));
   KZ_TRY(cta_upload_descriptor(g, s));
   return bitset_reset(g, s);
 }
@@ -799,14 +882,20 @@ static kz_status ensure_plan(kz_graph g, int form, cudaStream_t s) {
   if (pl.grid > 0) return KZ_OK;
   int grid = 0;
   KZ_TRY(sweep_grid_size(g, form, grid));
-  std::vector<int2> units;
-  std::vector<int32_t> cta_begin;
-  build_units(g, grid, units, cta_begin);
-  if ((int64_t)units.size() != g->n_units) return KZ_ERR_INTERNAL;
+  std::vector<int32_t> unit_off, cta_begin;
+  plan_units(g, grid, unit_off, cta_begin);
+  const int nb = (int)g->blocks.size();
+  if ((int64_t)unit_off[nb] != g->n_units) return KZ_ERR_INTERNAL;
   if (!g->d_units) {
-    KZ_TRY(graph_alloc(g, &g->d_units, std::max<size_t>(units.size(), 1), s));
-    if (!units.empty())
-      KZ_CUDA_TRY(cudaMemcpyAsync(g->d_units, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice, s));
+    KZ_TRY(graph_alloc(g, &g->d_units, std::max<size_t>((size_t)g->n_units, 1), s));
+    if (g->n_units > 0) {
+      int32_t *d_off = nullptr;
+      KZ_TRY(graph_alloc(g, &d_off, (size_t)nb + 1, s));
+      KZ_CUDA_TRY(cudaMemcpyAsync(d_off, unit_off.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice, s));
+      const int ugrid = (int)std::min<int64_t>((g->n_units + 255) / 256, 8 * sm_count());
+      fill_units_kernel<<<std::max(ugrid, 1), 256, 0, s>>>(g->d_units, d_off, g->d_blocks, g->d_boff, nb);
+      KZ_CUDA_TRY(cudaGetLastError());
+    }
   }
   KZ_TRY(graph_alloc(g, &pl.d_cta_begin, cta_begin.size(), s));
   KZ_CUDA_TRY(cudaMemcpyAsync(pl.d_cta_begin, cta_begin.data(), sizeof(int32_t) * cta_begin.size(),
@@ -1116,35 +1205,65 @@ kz_status bitset_barrier_timeout_probe(kz_graph g, uint32_t spin_limit, cudaStre
 // unpacking to caller ids
 // ---------------------------------------------------------------------------
 
-// Gather form of the unpacker: one thread per caller word (ox, ow); bit b is
-// the relabelled bit between ox and oy = 64 ow + b, read from row inv[ox] at
-// oy's position.  The thread of word 0 also writes ox's vertex flag.
-__global__ void unpack_gather_kernel(const uint32_t *__restrict__ A0, const uint32_t *__restrict__ A1,
-                                     const uint32_t *__restrict__ V0, const uint32_t *__restrict__ V1,
-                                     const int32_t *__restrict__ cur, int32_t n, int32_t ldw,
-                                     const int32_t *__restrict__ inv, const int32_t *__restrict__ cpos,
-                                     uint64_t *__restrict__ out, int64_t row_words, uint8_t *__restrict__ alive,
-                                     unsigned long long *__restrict__ edge_count) {
+// Shared memory the row kernels use: the row (ldw words) plus the position
+// table (n entries) when both fit in kStagedSmemBytes.
+constexpr size_t kStagedSmemBytes = 200 * 1024;
+
+static kz_status row_kernel_smem(kz_graph g, const void *fn, size_t *smem, int32_t *staged) {
+  const size_t row = (size_t)g->ldw * 4, table = (size_t)g->n * 4;
+  *staged = row + table <= kStagedSmemBytes ? 1 : 0;
+  *smem = row + (*staged ? table : 0);
+  KZ_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(*smem, 1)));
+  return KZ_OK;
+}
+
+// Row form of the unpacker: one CTA per caller row ox at a time; the
+// relabelled row inv[ox] is staged in shared memory (with the position table
+// when it fits).  Each warp builds 32 caller words (2048 columns) in 64
+// rounds: in a round the lanes take 32 consecutive columns (the position
+// table is read without bank conflicts), look up their bits in the staged
+// row, and a ballot gives half of one word, kept by the lane that writes it.
+// The CTA also writes ox's vertex flag.
+__global__ void unpack_rows_kernel(const uint32_t *__restrict__ A0, const uint32_t *__restrict__ A1,
+                                   const uint32_t *__restrict__ V0, const uint32_t *__restrict__ V1,
+                                   const int32_t *__restrict__ cur, int32_t n, int32_t ldw,
+                                   const int32_t *__restrict__ inv, const int32_t *__restrict__ cpos_g,
+                                   int32_t cpos_in_smem, uint64_t *__restrict__ out, int64_t row_words,
+                                   uint8_t *__restrict__ alive, unsigned long long *__restrict__ edge_count) {
+  extern __shared__ __align__(16) uint32_t usm[];
+  uint32_t *srow = usm;
+  int32_t *scpos = reinterpret_cast<int32_t *>(usm + ldw);
+  const int32_t *cpos = cpos_in_smem ? scpos : cpos_g;
+  if (cpos_in_smem)
+    for (int32_t j = threadIdx.x; j < n; j += blockDim.x) scpos[j] = cpos_g[j];
   const bool one = (*cur & 1) != 0;
   const uint32_t *A = one ? A1 : A0;
   const uint32_t *V = one ? V1 : V0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   unsigned long long mine = 0;
-  const int64_t total = (int64_t)n * row_words;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t ox = (int32_t)(t / row_words);
-    const int64_t ow = t - (int64_t)ox * row_words;
+  for (int32_t ox = blockIdx.x; ox < n; ox += gridDim.x) {
+    __syncthreads();
     const uint32_t *row = A + (int64_t)inv[ox] * ldw;
-    uint64_t word = 0;
-    const int32_t oy0 = (int32_t)(ow * 64);
-    const int32_t cnt = min(64, n - oy0);
-    for (int32_t b = 0; b < cnt; b++) {
-      const int32_t p = cpos[oy0 + b];
-      word |= (uint64_t)((row[p >> 5] >> (p & 31)) & 1u) << b;
+    for (int32_t w = threadIdx.x; w < ldw; w += blockDim.x) srow[w] = row[w];
+    __syncthreads();
+    for (int64_t w0 = (int64_t)warp * 32; w0 < row_words; w0 += (int64_t)nwarps * 32) {
+      uint64_t word = 0;
+      for (int h = 0; h < 64; h++) {
+        const int64_t col = w0 * 64 + 32 * h + lane;
+        bool bit = false;
+        if (col < n) {
+          const int32_t p = cpos[col];
+          bit = (srow[p >> 5] >> (p & 31)) & 1u;
+        }
+        const uint32_t half = __ballot_sync(0xffffffffu, bit);
+        if (lane == (h >> 1)) word |= (uint64_t)half << ((h & 1) * 32);
+      }
+      if (w0 + lane < row_words) {
+        out[(int64_t)ox * row_words + w0 + lane] = word;
+        mine += __popcll(word);
+      }
     }
-    out[t] = word;
-    mine += __popcll(word);
-    if (ow == 0) {
+    if (threadIdx.x == 0) {
       const int32_t p = cpos[ox];
       alive[ox] = (uint8_t)((V[p >> 5] >> (p & 31)) & 1u);
     }
@@ -1157,12 +1276,12 @@ kz_status bitset_unpack_gather(kz_graph g, uint64_t *d_out, int64_t row_words, u
                                unsigned long long *d_edge_count, cudaStream_t s) {
   KZ_CUDA_TRY(cudaMemsetAsync(d_edge_count, 0, sizeof(unsigned long long), s));
   if (g->n == 0) return KZ_OK;
-  const int64_t total = (int64_t)g->n * row_words;
-  const int threads = 256;
-  const int grid = (int)std::min<int64_t>((total + threads - 1) / threads, 32 * sm_count());
-  unpack_gather_kernel<<<std::max(grid, 1), threads, 0, s>>>(g->A[0], g->A[1], g->V[0], g->V[1], &g->st->cur, g->n,
-                                                            g->ldw, g->d_inv, g->d_cpos, d_out, row_words, d_alive,
-                                                            d_edge_count);
+  size_t smem = 0;
+  int32_t staged = 0;
+  KZ_TRY(row_kernel_smem(g, (const void *)unpack_rows_kernel, &smem, &staged));
+  const int grid = std::max(1, std::min(g->n, (staged ? 1 : 4) * sm_count()));
+  unpack_rows_kernel<<<grid, 512, smem, s>>>(g->A[0], g->A[1], g->V[0], g->V[1], &g->st->cur, g->n, g->ldw,
+                                             g->d_inv, g->d_cpos, staged, d_out, row_words, d_alive, d_edge_count);
   return cuda_status(cudaGetLastError());
 }
 
@@ -1258,10 +1377,34 @@ kz_status bitset_pack_dense(kz_graph g, const uint64_t *d_bits, int64_t row_word
   kz_status st = pack_setup(g, s, a, tmp);
   const int64_t words = (int64_t)g->n * g->ldw;
   if (st == KZ_OK && words > 0) {
-    const int threads = 256;
-    const int grid = (int)std::min<int64_t>((words + threads - 1) / threads, 64 * sm_count());
-    pack_dense_gather_kernel<<<std::max(grid, 1), threads, 0, s>>>(a, d_bits, row_words, g->n, g->d_perm);
-    st = cuda_status(cudaGetLastError());
+    // the upper triangle row by row, then the transposed half tile by tile
+    size_t smem = 0;
+    int32_t staged = 0;
+    st = row_kernel_smem(g, (const void *)pack_dense_rows_kernel, &smem, &staged);
+    const int nb = (int)g->blocks.size();
+    // the tile pairs: block X against every block of a higher class
+    std::vector<int64_t> pair0((size_t)nb + 1, 0);
+    for (int x = 0; x < nb; x++) pair0[x + 1] = pair0[x] + (nb - std::min(g->boff[g->blocks[x].c + 1], nb));
+    BlockDesc *d_blk = nullptr;
+    int32_t *d_bo = nullptr;
+    int64_t *d_p0 = nullptr;
+    if (st == KZ_OK) st = graph_alloc(g, &d_blk, (size_t)std::max(nb, 1), s);
+    if (st == KZ_OK) st = graph_alloc(g, &d_bo, (size_t)g->k + 1, s);
+    if (st == KZ_OK) st = graph_alloc(g, &d_p0, (size_t)nb + 1, s);
+    if (st == KZ_OK && nb > 0)
+      st = cuda_status(cudaMemcpyAsync(d_blk, g->blocks.data(), sizeof(BlockDesc) * nb, cudaMemcpyHostToDevice, s));
+    if (st == KZ_OK)
+      st = cuda_status(cudaMemcpyAsync(d_bo, g->boff.data(), sizeof(int32_t) * (g->k + 1), cudaMemcpyHostToDevice, s));
+    if (st == KZ_OK)
+      st = cuda_status(cudaMemcpyAsync(d_p0, pair0.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, s));
+    if (st == KZ_OK) {
+      const int grid = std::max(1, std::min(g->n, (staged ? 1 : 4) * sm_count()));
+      pack_dense_rows_kernel<<<grid, 512, smem, s>>>(a, d_bits, row_words, g->n, g->d_perm, g->d_cpos, staged);
+      const int64_t pairs = pair0[nb];
+      const int sgrid = (int)std::max<int64_t>(1, std::min<int64_t>((pairs + 7) / 8, 32 * sm_count()));
+      if (pairs > 0) symmetrize_kernel<<<sgrid, 256, 0, s>>>(g->A0, d_blk, d_bo, d_p0, nb, g->k, g->ldw);
+      st = cuda_status(cudaGetLastError());
+    }
   }
   kz_status st2 = st == KZ_OK ? pack_finish(g, s, a, tmp) : KZ_OK;
   return st != KZ_OK ? st : st2;

@@ -10,14 +10,17 @@
 // Round structure of a learned kernelization (bitset rows):
 //   1. one full plain Jacobi sweep (the multi-CTA sweep kernel);
 //   2. learned rounds: per-vertex statistics of the live graph (degree,
-//      colour cover, smallest class count; the vertex rule falls out of them);
+//      colour cover, per-class counts; the vertex rule falls out of them);
 //      the frontier = live edges at a vertex whose live degree changed since
 //      the previous round (no other edge can have started to fail); the MLP
-//      scores the frontier and only edges above the threshold are tested
-//      (warp per edge, exact over all planes); failing vertices and edges are
-//      removed in place;
-//   3. when a learned round finds nothing, a full plain sweep certifies; if it
-//      deletes something, learned rounds resume.
+//      scores the frontier on the tensor cores and only edges above the
+//      threshold are tested (warp per edge, exact, stopping once every needed
+//      class is covered); failing vertices and edges are removed in place.
+//      When the listed edges are more than an eighth of the live ones, a full
+//      pass replaces the round (it tests every edge for less);
+//   3. when a learned round finds nothing, the skipped (pending) edges are
+//      tested if they are few, else a full pass certifies; if it deletes
+//      something, learned rounds resume.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -355,6 +358,7 @@ struct Stats {
   int32_t *minc;      // smallest neighbour count over the other classes
   uint8_t *vfail;     // vertex rule fails on this snapshot
   uint8_t *changed;   // live degree changed since the previous round
+  int32_t *ccnt;      // n x k: live neighbours of each class
 };
 
 struct RowView {
@@ -387,6 +391,7 @@ __global__ void stats_kernel(RowView r, Stats s, int first_round, unsigned long 
       if (word) atomicAdd(&cls[wib][w % r.k], __popc(word));
     }
     __syncwarp();
+    for (int c = lane; c < r.k; c += 32) s.ccnt[x * r.k + c] = cls[wib][c];
     if (lane == 0) {
       const int own = r.col[x];
       int deg = 0, cover = 0, minc = 0x7fffffff;
@@ -476,7 +481,19 @@ __device__ __forceinline__ void edge_features(const RowView &r, const Stats &s, 
   f[12] = (du + dvv) / (2.f * n);
   f[13] = log2f(n) / 16.f;
   f[14] = live_frac;
-  f[15] = 1.f;
+  // the chance that some needed class holds no common neighbour if each
+  // endpoint's neighbours in a class were drawn at random from it: with
+  // lambda = sum over needed classes c of exp(-cnt_x[c] cnt_y[c] / |C_c|)
+  // (the expected number of uncovered classes), 1 - exp(-lambda)
+  const int cx = r.col[x], cy = r.col[y];
+  const int32_t *ax = s.ccnt + (int64_t)x * r.k, *ay = s.ccnt + (int64_t)y * r.k;
+  float lam = 0.f;
+  for (int c = 0; c < r.k; c++) {
+    if (c == cx || c == cy) continue;
+    const float size = (float)max(r.coff[c + 1] - r.coff[c], 1);
+    lam += __expf(-(float)ax[c] * (float)ay[c] / size);
+  }
+  f[15] = 1.f - __expf(-lam);
 }
 
 // Pending-set bit of the (unordered) pair {x, y}: kept in the row of the
@@ -763,6 +780,7 @@ kz_status ensure_bufs(kz_graph g, LearnedBufs &b, cudaStream_t s) {
   KZ_TRY(graph_alloc(g, &b.s.minc, n, s));
   KZ_TRY(graph_alloc(g, &b.s.vfail, n, s));
   KZ_TRY(graph_alloc(g, &b.s.changed, n, s));
+  KZ_TRY(graph_alloc(g, &b.s.ccnt, n * (size_t)g->k, s));
   KZ_TRY(graph_alloc(g, &b.fr, m, s));
   KZ_TRY(graph_alloc(g, &b.work, m, s));
   KZ_TRY(graph_alloc(g, &b.dead, m, s));
@@ -807,6 +825,11 @@ int32_t read_cur(kz_graph g, cudaStream_t s) {
 }  // namespace
 
 namespace kz {
+
+// A list of edges to test one by one is worth it while it holds at most this
+// share of the live edges; beyond it a full pass (block-wise on the bitset
+// rows, or all pairs on the tensor cores) is cheaper per edge.
+constexpr unsigned long long kListShareInv = 8;
 
 // Learned schedule (see the file comment).  full_path is the path of the
 // full passes: KZ_PATH_BITSET (the multi-CTA sweep) or KZ_PATH_TENSOR.
@@ -870,6 +893,15 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cu
     frontier_kernel<<<grid, 256, 0, s>>>(r, b.s, b.fr, b.cnt + 0, cap);
     score_kernel<<<2 * sms, 32 * kScoreWarps, 0, s>>>(r, b.s, g->model->w16, b.fr, b.cnt, logit_thr, round, b.work,
                                                       b.cnt + 1, b.pend);
+    KZ_CUDA_TRY(cudaGetLastError());
+    KZ_TRY(read_counts());
+    if (h[1] * kListShareInv > h[4] / 2) {
+      // so many edges listed that testing them one by one costs more than a
+      // full pass, which tests every edge anyway
+      KZ_CUDA_TRY(cudaMemsetAsync(b.pend, 0, (size_t)g->n * g->ldw * 4, s));
+      need_full = true;
+      continue;
+    }
     test_edges_kernel<<<grid, 256, 0, s>>>(r, b.work, b.cnt + 1, b.dead, b.cnt + 2);
     KZ_CUDA_TRY(cudaGetLastError());
     KZ_TRY(read_counts());
@@ -882,7 +914,7 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cu
       flush_pending_kernel<<<grid, 256, 0, s>>>(r, b.pend, b.work, b.cnt + 1, cap);
       KZ_TRY(read_counts());
       const unsigned long long pending = h[1], live_edges = h[4] / 2;
-      if (pending == 0 || pending * 8 > live_edges) {
+      if (pending == 0 || pending * kListShareInv > live_edges) {
         need_full = true;
         continue;
       }
