@@ -53,6 +53,59 @@ void dev_free(void *p, size_t bytes, cudaStream_t s) {
   cudaFreeAsync(p, s);
 }
 
+// The pinned staging arena of the loaders (see LoadStage): one per process,
+// grown when a load needs more, used by one load at a time.
+namespace {
+std::mutex g_stage_mu;
+char *g_stage = nullptr;
+size_t g_stage_cap = 0, g_stage_off = 0;
+thread_local LoadStage *t_stage = nullptr;
+constexpr size_t kStageMinBytes = size_t(4) << 20;
+}  // namespace
+
+LoadStage::LoadStage(cudaStream_t s) : stream(s) {
+  g_stage_mu.lock();
+  g_stage_off = 0;
+  t_stage = this;
+}
+
+LoadStage::~LoadStage() {
+  // every staged copy of this load has landed before the arena is reused
+  cudaStreamSynchronize(stream);
+  cudaGetLastError();
+  t_stage = nullptr;
+  g_stage_mu.unlock();
+}
+
+kz_status h2d(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return KZ_OK;
+  LoadStage *st = t_stage;
+  if (!st || st->stream != s) return cuda_status(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+  const size_t need = (bytes + 255) & ~size_t(255);
+  if (g_stage_off + need > g_stage_cap) {
+    // the arena is full: wait for the copies in flight, then reuse or grow it
+    KZ_CUDA_TRY(cudaStreamSynchronize(s));
+    g_stage_off = 0;
+    if (need > g_stage_cap) {
+      if (g_stage) cudaFreeHost(g_stage);
+      g_stage = nullptr;
+      g_stage_cap = 0;
+      const size_t cap = std::max(need, kStageMinBytes);
+      char *p = nullptr;
+      if (cudaMallocHost(&p, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_status(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+      }
+      g_stage = p;
+      g_stage_cap = cap;
+    }
+  }
+  char *slot = g_stage + g_stage_off;
+  memcpy(slot, src, bytes);
+  g_stage_off += need;
+  return cuda_status(cudaMemcpyAsync(dst, slot, bytes, cudaMemcpyHostToDevice, s));
+}
+
 }  // namespace kz
 
 using namespace kz;
@@ -136,6 +189,7 @@ kz_status load_common(int32_t n, int32_t k, const int32_t *colour, void *stream,
   g->uid = g_next_uid.fetch_add(1);
   g->stream = (cudaStream_t)stream;
   cudaGetDevice(&g->device);
+  LoadStage stage(g->stream);  // small host tables travel through one pinned arena
   relabel(g, colour);
   kz_status st = KZ_OK;
   if (want_csr) st = csr(g);  // host-side duplicate check comes first
@@ -147,11 +201,9 @@ kz_status load_common(int32_t n, int32_t k, const int32_t *colour, void *stream,
     if (st == KZ_OK) st = graph_alloc(g, &g->d_inv, (size_t)std::max(n, 1), g->stream);
     if (st == KZ_OK) st = graph_alloc(g, &g->d_cpos, (size_t)std::max(n, 1), g->stream);
     if (st == KZ_OK && n > 0)
-      st = cuda_status(cudaMemcpyAsync(g->d_perm, g->perm.data(), sizeof(int32_t) * n,
-                                       cudaMemcpyHostToDevice, g->stream));
+      st = h2d(g->d_perm, g->perm.data(), sizeof(int32_t) * n, g->stream);
     if (st == KZ_OK && n > 0)
-      st = cuda_status(cudaMemcpyAsync(g->d_inv, g->inv.data(), sizeof(int32_t) * n,
-                                       cudaMemcpyHostToDevice, g->stream));
+      st = h2d(g->d_inv, g->inv.data(), sizeof(int32_t) * n, g->stream);
     if (st == KZ_OK && n > 0) {
       // position of every caller vertex inside a row of the block-plane layout
       std::vector<int32_t> cpos((size_t)n);
@@ -160,8 +212,7 @@ kz_status load_common(int32_t n, int32_t k, const int32_t *colour, void *stream,
           const int ix = x - g->coff[c];
           cpos[g->perm[x]] = ((((ix >> 5) * k) + c) << 5) | (ix & 31);
         }
-      st = cuda_status(cudaMemcpyAsync(g->d_cpos, cpos.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice,
-                                       g->stream));
+      st = h2d(g->d_cpos, cpos.data(), sizeof(int32_t) * n, g->stream);
     }
     if (st == KZ_OK) st = pack(g);
     if (st == KZ_OK) st = bitset_finish_load(g, g->stream);

@@ -767,17 +767,14 @@ kz_status bitset_finish_load(kz_graph g, cudaStream_t s) {
   KZ_CUDA_TRY(cudaMemsetAsync(g->V0, 0, (size_t)g->ldw * 4, s));
   KZ_TRY(graph_alloc(g, &g->d_blocks, (size_t)std::max(nb, 1), s));
   if (nb) {
-    KZ_CUDA_TRY(cudaMemcpyAsync(g->d_blocks, g->blocks.data(), sizeof(BlockDesc) * nb,
-                                cudaMemcpyHostToDevice, s));
+    KZ_TRY(h2d(g->d_blocks, g->blocks.data(), sizeof(BlockDesc) * nb, s));
     init_vlive_kernel<<<(nb + 255) / 256, 256, 0, s>>>(g->V0, g->d_blocks, nb, g->k);
     KZ_CUDA_TRY(cudaGetLastError());
   }
   KZ_TRY(graph_alloc(g, &g->d_coff, (size_t)g->k + 1, s));
-  KZ_CUDA_TRY(cudaMemcpyAsync(g->d_coff, g->coff.data(), sizeof(int32_t) * (g->k + 1),
-                              cudaMemcpyHostToDevice, s));
+  KZ_TRY(h2d(g->d_coff, g->coff.data(), sizeof(int32_t) * (g->k + 1), s));
   KZ_TRY(graph_alloc(g, &g->d_rounds, (size_t)g->k, s));
-  KZ_CUDA_TRY(cudaMemcpyAsync(g->d_rounds, g->rounds.data(), sizeof(int32_t) * g->k,
-                              cudaMemcpyHostToDevice, s));
+  KZ_TRY(h2d(g->d_rounds, g->rounds.data(), sizeof(int32_t) * g->k, s));
   KZ_TRY(cta_prepare(g, s));  // block-pair offsets and class block offsets (the unit list needs them)
   // the half-word plane-0 test pays off when 16 members of a class almost
   // always hold a common neighbour: dense graphs
@@ -891,15 +888,14 @@ static kz_status ensure_plan(kz_graph g, int form, cudaStream_t s) {
     if (g->n_units > 0) {
       int32_t *d_off = nullptr;
       KZ_TRY(graph_alloc(g, &d_off, (size_t)nb + 1, s));
-      KZ_CUDA_TRY(cudaMemcpyAsync(d_off, unit_off.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice, s));
+      KZ_TRY(h2d(d_off, unit_off.data(), sizeof(int32_t) * (nb + 1), s));
       const int ugrid = (int)std::min<int64_t>((g->n_units + 255) / 256, 8 * sm_count());
       fill_units_kernel<<<std::max(ugrid, 1), 256, 0, s>>>(g->d_units, d_off, g->d_blocks, g->d_boff, nb);
       KZ_CUDA_TRY(cudaGetLastError());
     }
   }
   KZ_TRY(graph_alloc(g, &pl.d_cta_begin, cta_begin.size(), s));
-  KZ_CUDA_TRY(cudaMemcpyAsync(pl.d_cta_begin, cta_begin.data(), sizeof(int32_t) * cta_begin.size(),
-                              cudaMemcpyHostToDevice, s));
+  KZ_TRY(h2d(pl.d_cta_begin, cta_begin.data(), sizeof(int32_t) * cta_begin.size(), s));
   pl.grid = grid;
   return KZ_OK;
 }
@@ -1324,10 +1320,10 @@ static kz_status pack_setup(kz_graph g, cudaStream_t s, PackArgs &a, std::vector
   KZ_TRY(graph_alloc(g, &d_cnt, 2, s));
   tmp.clear();
   if (g->n) {
-    KZ_CUDA_TRY(cudaMemcpyAsync(d_inv, g->inv.data(), (size_t)g->n * 4, cudaMemcpyHostToDevice, s));
-    KZ_CUDA_TRY(cudaMemcpyAsync(d_col, col_new.data(), (size_t)g->n * 4, cudaMemcpyHostToDevice, s));
+    KZ_TRY(h2d(d_inv, g->inv.data(), (size_t)g->n * 4, s));
+    KZ_TRY(h2d(d_col, col_new.data(), (size_t)g->n * 4, s));
   }
-  KZ_CUDA_TRY(cudaMemcpyAsync(d_coff, g->coff.data(), ((size_t)g->k + 1) * 4, cudaMemcpyHostToDevice, s));
+  KZ_TRY(h2d(d_coff, g->coff.data(), ((size_t)g->k + 1) * 4, s));
   KZ_CUDA_TRY(cudaMemsetAsync(d_err, 0, 16, s));
   KZ_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 16, s));
   a.A = g->A0;
@@ -1392,11 +1388,11 @@ kz_status bitset_pack_dense(kz_graph g, const uint64_t *d_bits, int64_t row_word
     if (st == KZ_OK) st = graph_alloc(g, &d_bo, (size_t)g->k + 1, s);
     if (st == KZ_OK) st = graph_alloc(g, &d_p0, (size_t)nb + 1, s);
     if (st == KZ_OK && nb > 0)
-      st = cuda_status(cudaMemcpyAsync(d_blk, g->blocks.data(), sizeof(BlockDesc) * nb, cudaMemcpyHostToDevice, s));
+      st = h2d(d_blk, g->blocks.data(), sizeof(BlockDesc) * nb, s);
     if (st == KZ_OK)
-      st = cuda_status(cudaMemcpyAsync(d_bo, g->boff.data(), sizeof(int32_t) * (g->k + 1), cudaMemcpyHostToDevice, s));
+      st = h2d(d_bo, g->boff.data(), sizeof(int32_t) * (g->k + 1), s);
     if (st == KZ_OK)
-      st = cuda_status(cudaMemcpyAsync(d_p0, pair0.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, s));
+      st = h2d(d_p0, pair0.data(), sizeof(int64_t) * (nb + 1), s);
     if (st == KZ_OK) {
       const int grid = std::max(1, std::min(g->n, (staged ? 1 : 4) * sm_count()));
       pack_dense_rows_kernel<<<grid, 512, smem, s>>>(a, d_bits, row_words, g->n, g->d_perm, g->d_cpos, staged);

@@ -289,11 +289,9 @@ kz_status cta_prepare(kz_graph g, cudaStream_t s) {
   std::vector<int32_t> poff((size_t)nb + 1, 0);
   for (int x = 0; x < nb; x++) poff[x + 1] = poff[x] + (nb - g->boff[g->blocks[x].c + 1]);
   KZ_TRY(graph_alloc(g, &g->d_pair_off, (size_t)nb + 1, s));
-  KZ_CUDA_TRY(cudaMemcpyAsync(g->d_pair_off, poff.data(), sizeof(int32_t) * (nb + 1),
-                              cudaMemcpyHostToDevice, s));
+  KZ_TRY(h2d(g->d_pair_off, poff.data(), sizeof(int32_t) * (nb + 1), s));
   KZ_TRY(graph_alloc(g, &g->d_boff, (size_t)g->k + 1, s));
-  KZ_CUDA_TRY(cudaMemcpyAsync(g->d_boff, g->boff.data(), sizeof(int32_t) * (g->k + 1),
-                              cudaMemcpyHostToDevice, s));
+  KZ_TRY(h2d(g->d_boff, g->boff.data(), sizeof(int32_t) * (g->k + 1), s));
   g->n_pairs = poff[nb];
   return KZ_OK;
 }
@@ -309,8 +307,9 @@ kz_status cta_upload_descriptor(kz_graph g, cudaStream_t s) {
   KZ_TRY(graph_alloc(g, &g->d_zero, 4, s));
   KZ_CUDA_TRY(cudaMemsetAsync(g->d_zero, 0, 16, s));
   CtaGraph h = describe(g, 0);
-  // a copy from pageable memory has left the local by the time the call returns
-  KZ_CUDA_TRY(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+  // staged (or, outside a load, a copy from pageable memory, which has left
+  // the local by the time the call returns)
+  KZ_TRY(h2d(d, &h, sizeof(h), s));
   return KZ_OK;
 }
 

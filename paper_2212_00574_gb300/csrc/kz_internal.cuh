@@ -108,6 +108,22 @@ struct CtaGraph {
 void *dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void *p, size_t bytes, cudaStream_t s);
 
+// Host-to-device copy of a host table.  While a LoadStage is active on this
+// thread the bytes are first copied into one pinned staging arena, so the
+// copy is asynchronous (the host does not wait for the stream's earlier work)
+// and the source may be released at once; otherwise an ordinary copy.
+kz_status h2d(void *dst, const void *src, size_t bytes, cudaStream_t s);
+
+// Scope of one graph load: holds the staging arena for this thread and waits
+// for the stream at its end (so the arena is free for the next load).
+struct LoadStage {
+  explicit LoadStage(cudaStream_t s);
+  ~LoadStage();
+  LoadStage(const LoadStage &) = delete;
+  LoadStage &operator=(const LoadStage &) = delete;
+  cudaStream_t stream;
+};
+
 }  // namespace kz
 
 namespace kz {
