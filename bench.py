@@ -438,7 +438,7 @@ def learned_comparison(kz, torch, graphs, stream, flush, local, args, pg, rank):
     train_s = time.perf_counter() - t0
     out = {"training": {"records": int(len(y)), "positive_share": float(np.mean(y)), "loss_first": losses[0],
                         "loss_last": losses[-1], "seconds": round(train_s, 2),
-                        "graphs": "24 batch-style cascading graphs (n 128..1500, p 0.15..0.45), other seeds"}}
+                        "graphs": "24 cascading k-partite graphs (n log-uniform 256..32768, k 8..32, p = sqrt(mu k / n) with mu 3..9), other seeds"}}
     try:
         for name, g, h in graphs:
             kz.kz_attach_model(h, model, 0.5)

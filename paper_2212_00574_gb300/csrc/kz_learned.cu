@@ -8,19 +8,26 @@
 // result is the unique greatest fixpoint.
 //
 // Round structure of a learned kernelization (bitset rows):
-//   1. one full plain Jacobi sweep (the multi-CTA sweep kernel);
+//   1. full passes (the multi-CTA sweep or the tensor form) while the
+//      cascade is heavy: as long as the last pass deleted so many edges that
+//      the frontier they leave would exceed an eighth of the live edges;
 //   2. learned rounds: per-vertex statistics of the live graph (degree,
 //      colour cover, per-class counts; the vertex rule falls out of them);
-//      the frontier = live edges at a vertex whose live degree changed since
-//      the previous round (no other edge can have started to fail); the MLP
-//      scores the frontier on the tensor cores and only edges above the
-//      threshold are tested (warp per edge, exact, stopping once every needed
-//      class is covered); failing vertices and edges are removed in place.
-//      When the listed edges are more than an eighth of the live ones, a full
-//      pass replaces the round (it tests every edge for less);
-//   3. when a learned round finds nothing, the skipped (pending) edges are
-//      tested if they are few, else a full pass certifies; if it deletes
-//      something, learned rounds resume.
+//      the frontier = the edges that may have started to fail.  After edge
+//      deletions alone that is the dirty set: an edge fails only by losing a
+//      common neighbour, so deleting {a, b} can only make {a, w} and {b, w}
+//      fail, w a common neighbour of a and b; after vertex deletions it is
+//      every live edge at a vertex whose live degree changed.  The MLP scores
+//      the frontier on the tensor cores and only edges above the threshold
+//      are tested (warp per edge, exact, stopping once every needed class is
+//      covered); the others wait in a pending set.  Failing vertices and
+//      edges are removed in place;
+//   3. when a learned round finds nothing, the pending edges are tested if
+//      they are few (the score kernel keeps their count, so a large set
+//      costs no flush), else a full pass certifies; if it deletes something,
+//      learned rounds resume.
+// Every list larger than an eighth of the live edges gives way to a full
+// pass, which tests every edge for less.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -510,8 +517,10 @@ __device__ __forceinline__ void pend_bit(const RowView &r, int x, int y, int64_t
 // shared memory and runs the network on it (kz_mlp.cuh).  Edges above the
 // threshold are listed for an exact test this round (and leave the pending
 // set); the others join the pending set, to be tested later unless they die
-// first.  The live counts for the density features come from the device
-// (cnt[4] = twice the live edges, cnt[5] = live vertices).
+// first; n_pend keeps the size of the pending set (an upper bound on its
+// live part: pending edges that lost an endpoint stay counted).  The live
+// counts for the density features come from the device (cnt[4] = twice the
+// live edges, cnt[5] = live vertices).
 constexpr int kScoreWarps = 8;
 
 __global__ void __launch_bounds__(32 * kScoreWarps) score_kernel(RowView r, Stats s,
@@ -521,7 +530,8 @@ __global__ void __launch_bounds__(32 * kScoreWarps) score_kernel(RowView r, Stat
                                                                   float logit_threshold, int round,
                                                                   int2 *__restrict__ work,
                                                                   unsigned long long *n_work,
-                                                                  uint32_t *__restrict__ pend) {
+                                                                  uint32_t *__restrict__ pend,
+                                                                  unsigned long long *n_pend) {
   __shared__ SmemNet net;
   __shared__ __align__(16) __nv_bfloat16 sx[kScoreWarps][kTileRows * kXLd];
   const bool all = !(logit_threshold > -INFINITY);
@@ -554,13 +564,16 @@ __global__ void __launch_bounds__(32 * kScoreWarps) score_kernel(RowView r, Stat
       take = valid && logit > logit_threshold;
       __syncwarp();
     }
+    int delta = 0;  // change of the pending count by this lane's edge
     if (valid) {
       int64_t pw;
       uint32_t pb;
       pend_bit(r, e.x, e.y, pw, pb);
-      if (take) atomicAnd(&pend[pw], ~pb);
-      else atomicOr(&pend[pw], pb);
+      if (take) delta = (atomicAnd(&pend[pw], ~pb) & pb) ? -1 : 0;
+      else delta = (atomicOr(&pend[pw], pb) & pb) ? 0 : 1;
     }
+    delta = __reduce_add_sync(0xffffffffu, delta);
+    if (lane == 0 && delta) atomicAdd(n_pend, (unsigned long long)(long long)delta);
     const uint32_t m = __ballot_sync(0xffffffffu, take);
     unsigned long long at = 0;
     if (lane == 0 && m) at = atomicAdd(n_work, (unsigned long long)__popc(m));
@@ -591,6 +604,85 @@ __global__ void flush_pending_kernel(RowView r, uint32_t *__restrict__ pend, int
       if ((int64_t)pos < cap) out[pos] = make_int2((int)x, r.coff[c] + 32 * rr + b);
     }
   }
+}
+
+// Edges deleted by the last full pass (set in the old rows, clear in the new
+// ones), each listed once, from its smaller end.
+__global__ void diff_dead_kernel(RowView rold, const uint32_t *__restrict__ Anew, int2 *__restrict__ out,
+                                 unsigned long long *count, int64_t cap) {
+  const int rk = rold.R * rold.k;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = tid; t < (int64_t)rold.n * rk; t += stride) {
+    const int64_t x = t / rk;
+    const int w = (int)(t - x * rk);
+    const int64_t idx = x * rold.ldw + w;
+    uint32_t bits = rold.A[idx] & ~Anew[idx];
+    const int c = w % rold.k, rr = w / rold.k;
+    while (bits) {
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1;
+      const int y = rold.coff[c] + 32 * rr + b;
+      if (y <= (int)x) continue;
+      const unsigned long long pos = atomicAdd(count, 1ull);
+      if ((int64_t)pos < cap) out[pos] = make_int2((int)x, y);
+    }
+  }
+}
+
+// Dirty pairs of a round's edge deletions.  An edge can start failing only
+// by losing a common neighbour, so when {a, b} goes, the edges that can
+// start failing are {a, w} and {b, w} for the w in N(a) and N(b) both (rows
+// as they were before the deletions, so that two deletions at the same w
+// are seen too).  Every such pair joins the dirty set (pending-set layout);
+// n_marks counts the pairs newly set.  One warp per deleted edge, the two
+// rows read four words a lane at a time.
+__global__ void mark_dirty_kernel(RowView rold, const int2 *__restrict__ dead,
+                                  const unsigned long long *__restrict__ n_dead, int64_t cap,
+                                  uint32_t *__restrict__ dirty, unsigned long long *n_marks) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = min((int64_t)*n_dead, cap);
+  const int rk = rold.R * rold.k;
+  for (int64_t q = warp0; q < total; q += warps) {
+    const int2 e = dead[q];
+    const uint32_t *ra = rold.A + (int64_t)e.x * rold.ldw, *rb = rold.A + (int64_t)e.y * rold.ldw;
+    unsigned int added = 0;
+    for (int w = 4 * lane; w < rk; w += 128) {
+      const uint4 a = *reinterpret_cast<const uint4 *>(ra + w);
+      const uint4 b = *reinterpret_cast<const uint4 *>(rb + w);
+      const uint32_t both[4] = {a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w};
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        uint32_t m = both[j];
+        if (!m) continue;  // also every zero padding word past rk
+        const int c = (w + j) % rold.k, rr = (w + j) / rold.k;
+        while (m) {
+          const int bit = __ffs(m) - 1;
+          m &= m - 1;
+          const int y = rold.coff[c] + 32 * rr + bit;
+          int64_t pw;
+          uint32_t pb;
+          pend_bit(rold, e.x, y, pw, pb);
+          added += (atomicOr(&dirty[pw], pb) & pb) ? 0u : 1u;
+          pend_bit(rold, e.y, y, pw, pb);
+          added += (atomicOr(&dirty[pw], pb) & pb) ? 0u : 1u;
+        }
+      }
+    }
+    added = __reduce_add_sync(0xffffffffu, added);
+    if (lane == 0 && added) atomicAdd(n_marks, (unsigned long long)added);
+  }
+}
+
+// Vertex and edge deletions of the last productive full pass, from the
+// device state's per-sweep record (all ones when the record is not kept).
+__global__ void last_pass_kernel(const DevState *st, unsigned long long *out) {
+  const int64_t i = st->sweeps - 1;
+  const bool kept = i >= 0 && i < kTraceCap;
+  out[0] = kept ? (unsigned long long)st->trace_dv[i] : ~0ull;
+  out[1] = kept ? (unsigned long long)st->trace_de[i] : ~0ull;
 }
 
 // Exact edge rule for listed edges, one warp per edge.  The lanes read the
@@ -763,12 +855,17 @@ int sms_now() {
   return std::max(sms, 1);
 }
 
+constexpr int kCounters = 10;
+
 // Per-graph scratch of the learned schedule (allocated on first use).
 struct LearnedBufs {
   Stats s;
   int2 *fr = nullptr, *work = nullptr, *dead = nullptr;
-  uint32_t *pend = nullptr;  // pending edges (bitset rows, pair kept in the smaller id's row)
-  unsigned long long *cnt = nullptr;  // [0] frontier [1] work [2] dead [3] dv [4] edges2 [5] verts
+  uint32_t *pend = nullptr;   // pending edges (bitset rows, pair kept in the smaller id's row)
+  uint32_t *dirty = nullptr;  // dirty edges: may have started failing (same layout)
+  // [0] frontier [1] work [2] dead [3] dv [4] edges2 [5] verts [6] pending
+  // [7] dirty [8] last full pass's dv [9] its de
+  unsigned long long *cnt = nullptr;
   int32_t *col = nullptr;
 };
 
@@ -784,9 +881,11 @@ kz_status ensure_bufs(kz_graph g, LearnedBufs &b, cudaStream_t s) {
   KZ_TRY(graph_alloc(g, &b.fr, m, s));
   KZ_TRY(graph_alloc(g, &b.work, m, s));
   KZ_TRY(graph_alloc(g, &b.dead, m, s));
-  KZ_TRY(graph_alloc(g, &b.cnt, 8, s));
+  KZ_TRY(graph_alloc(g, &b.cnt, kCounters, s));
   KZ_TRY(graph_alloc(g, &b.pend, (size_t)std::max(g->n, 1) * g->ldw, s));
+  KZ_TRY(graph_alloc(g, &b.dirty, (size_t)std::max(g->n, 1) * g->ldw, s));
   KZ_CUDA_TRY(cudaMemsetAsync(b.pend, 0, (size_t)std::max(g->n, 1) * g->ldw * 4, s));
+  KZ_CUDA_TRY(cudaMemsetAsync(b.dirty, 0, (size_t)std::max(g->n, 1) * g->ldw * 4, s));
   std::vector<int32_t> col_new((size_t)g->n);
   for (int c = 0; c < g->k; c++)
     for (int x = g->coff[c]; x < g->coff[c + 1]; x++) col_new[x] = c;
@@ -831,6 +930,17 @@ namespace kz {
 // rows, or all pairs on the tensor cores) is cheaper per edge.
 constexpr unsigned long long kListShareInv = 8;
 
+// Whether the dirty set that de edge deletions leave (about 2 de times the
+// mean common neighbours of a live edge, a random-graph estimate from the
+// live density) fits the list budget.
+static bool dirty_set_fits(kz_graph g, unsigned long long de, double live_edges) {
+  const double n = std::max(g->n, 2), k = std::max(g->k, 3);
+  const double pairs = n * n * (k - 1.0) / (2.0 * k);  // vertex pairs in different classes
+  const double dens = live_edges / pairs;
+  const double common = n * (k - 2.0) / k * dens * dens;
+  return 2.0 * (double)de * common * (double)kListShareInv <= live_edges;
+}
+
 // Learned schedule (see the file comment).  full_path is the path of the
 // full passes: KZ_PATH_BITSET (the multi-CTA sweep) or KZ_PATH_TENSOR.
 kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cudaStream_t s) {
@@ -853,12 +963,13 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cu
   KZ_TRY(bitset_begin_run(g, max_sweeps, s));
   if (g->n == 0) return KZ_OK;
   const int64_t cap = std::max<int64_t>(g->m, 1);
+  const size_t set_bytes = (size_t)g->n * g->ldw * 4;
   auto full_pass = [&](int *cont) -> kz_status {
     if (full_path == KZ_PATH_TENSOR) return tensor_one_pass(g, opt, s, cont);
     return bitset_one_pass(g, s, cont);
   };
   // counters and the run's productive sweeps, read back in one wait
-  unsigned long long h[8];
+  unsigned long long h[kCounters];
   int64_t sweeps = 0;
   auto read_counts = [&]() -> kz_status {
     KZ_CUDA_TRY(cudaMemcpyAsync(h, b.cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -866,39 +977,78 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cu
     KZ_CUDA_TRY(cudaStreamSynchronize(s));
     return KZ_OK;
   };
-  // degrees before the first pass, so that the first learned round's frontier
-  // is what that pass changed
+  // the pending and dirty sets emptied: a full pass tests every edge
+  bool dirty_valid = false;
+  auto clear_sets = [&]() -> kz_status {
+    KZ_CUDA_TRY(cudaMemsetAsync(b.pend, 0, set_bytes, s));
+    KZ_CUDA_TRY(cudaMemsetAsync(b.dirty, 0, set_bytes, s));
+    KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 6, 0, sizeof(unsigned long long) * 2, s));
+    dirty_valid = false;
+    return KZ_OK;
+  };
+  // degrees before the first pass, so that a degree frontier after it is
+  // what that pass changed
   {
     RowView r0 = view_of(g, b, read_cur(g, s));
-    KZ_CUDA_TRY(cudaMemsetAsync(b.cnt, 0, sizeof(unsigned long long) * 8, s));
+    KZ_CUDA_TRY(cudaMemsetAsync(b.cnt, 0, sizeof(unsigned long long) * kCounters, s));
     stats_kernel<<<grid, 256, 0, s>>>(r0, b.s, 1, b.cnt + 3);
     KZ_CUDA_TRY(cudaGetLastError());
   }
-  KZ_CUDA_TRY(cudaMemsetAsync(b.pend, 0, (size_t)g->n * g->ldw * 4, s));
+  KZ_TRY(clear_sets());
   int round = 1;
   bool need_full = true;
   RowView r;
   for (;;) {
     if (need_full) {
-      // a full pass: the first one, and the certifying ones
+      // a full pass: the first one, those of the cascade's heavy sweeps, and
+      // the certifying ones
       int cont = 0;
       KZ_TRY(full_pass(&cont));
       if (!cont) return KZ_OK;  // nothing deleted (or the sweep limit): certified / stopped
       need_full = false;
-      r = view_of(g, b, read_cur(g, s));
+      const int cur = read_cur(g, s);
+      r = view_of(g, b, cur);
+      KZ_CUDA_TRY(cudaMemsetAsync(b.cnt, 0, sizeof(unsigned long long) * 6, s));
+      count_live_kernel<<<grid, 256, 0, s>>>(r, b.cnt + 4, b.cnt + 5);
+      last_pass_kernel<<<1, 1, 0, s>>>(g->st, b.cnt + 8);
+      KZ_CUDA_TRY(cudaGetLastError());
+      KZ_TRY(read_counts());
+      round = (int)std::min<int64_t>(sweeps, 1 << 20);
+      if (h[8] == 0) {
+        if (!dirty_set_fits(g, h[9], (double)(h[4] / 2))) {
+          // still in the cascade's heavy sweeps: the next one is a full pass
+          need_full = true;
+          continue;
+        }
+        // few edge deletions: the next frontier is their dirty set, marked
+        // from the pass's old rows (the other ping-pong buffer)
+        const RowView rold = view_of(g, b, cur ^ 1);
+        diff_dead_kernel<<<grid, 256, 0, s>>>(rold, r.A, b.dead, b.cnt + 2, cap);
+        mark_dirty_kernel<<<grid, 256, 0, s>>>(rold, b.dead, b.cnt + 2, cap, b.dirty, b.cnt + 7);
+        KZ_CUDA_TRY(cudaGetLastError());
+        dirty_valid = true;
+      }
+      // (a pass that deleted vertices leaves the degree frontier)
     }
-    KZ_CUDA_TRY(cudaMemsetAsync(b.cnt, 0, sizeof(unsigned long long) * 8, s));
+    KZ_CUDA_TRY(cudaMemsetAsync(b.cnt, 0, sizeof(unsigned long long) * 6, s));
     count_live_kernel<<<grid, 256, 0, s>>>(r, b.cnt + 4, b.cnt + 5);
     stats_kernel<<<grid, 256, 0, s>>>(r, b.s, 0, b.cnt + 3);
-    frontier_kernel<<<grid, 256, 0, s>>>(r, b.s, b.fr, b.cnt + 0, cap);
+    if (dirty_valid) {
+      // the dirty pairs still live, listed once; the dirty set empties
+      flush_pending_kernel<<<grid, 256, 0, s>>>(r, b.dirty, b.fr, b.cnt + 0, cap);
+      KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 7, 0, sizeof(unsigned long long), s));
+    } else {
+      frontier_kernel<<<grid, 256, 0, s>>>(r, b.s, b.fr, b.cnt + 0, cap);
+    }
     score_kernel<<<2 * sms, 32 * kScoreWarps, 0, s>>>(r, b.s, g->model->w16, b.fr, b.cnt, logit_thr, round, b.work,
-                                                      b.cnt + 1, b.pend);
+                                                      b.cnt + 1, b.pend, b.cnt + 6);
     KZ_CUDA_TRY(cudaGetLastError());
     KZ_TRY(read_counts());
-    if (h[1] * kListShareInv > h[4] / 2) {
+    const unsigned long long live_edges = h[4] / 2;
+    if (h[1] * kListShareInv > live_edges) {
       // so many edges listed that testing them one by one costs more than a
       // full pass, which tests every edge anyway
-      KZ_CUDA_TRY(cudaMemsetAsync(b.pend, 0, (size_t)g->n * g->ldw * 4, s));
+      KZ_TRY(clear_sets());
       need_full = true;
       continue;
     }
@@ -910,11 +1060,19 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cu
       // the scored edges found nothing: the pending ones next, when they are
       // few; otherwise (or when they hold no failure either) a full pass
       learned_finish_kernel<<<1, 1, 0, s>>>(g->st, b.cnt + 3, b.cnt + 2, b.cnt + 1, nullptr);
+      if (h[6] * kListShareInv > live_edges) {
+        // the pending set's count already rules the list out: no flush
+        KZ_TRY(clear_sets());
+        need_full = true;
+        continue;
+      }
       KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 1, 0, sizeof(unsigned long long) * 2, s));
       flush_pending_kernel<<<grid, 256, 0, s>>>(r, b.pend, b.work, b.cnt + 1, cap);
+      KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 6, 0, sizeof(unsigned long long), s));  // flushed
       KZ_TRY(read_counts());
-      const unsigned long long pending = h[1], live_edges = h[4] / 2;
+      const unsigned long long pending = h[1];
       if (pending == 0 || pending * kListShareInv > live_edges) {
+        KZ_TRY(clear_sets());
         need_full = true;
         continue;
       }
@@ -924,6 +1082,7 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cu
       de = h[2];
       if (de == 0) {
         learned_finish_kernel<<<1, 1, 0, s>>>(g->st, b.cnt + 3, b.cnt + 2, b.cnt + 1, nullptr);
+        KZ_TRY(clear_sets());
         need_full = true;
         continue;
       }
@@ -936,10 +1095,29 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cu
       KZ_CUDA_TRY(cudaStreamSynchronize(s));
       return KZ_OK;
     }
+    if (dv == 0) {
+      // the next frontier: the dirty pairs of this round's deletions, marked
+      // while the rows still hold them
+      mark_dirty_kernel<<<grid, 256, 0, s>>>(r, b.dead, b.cnt + 2, cap, b.dirty, b.cnt + 7);
+      dirty_valid = true;
+    } else if (dirty_valid) {
+      // vertex deletions: the degree frontier covers them and the dirty pairs
+      KZ_CUDA_TRY(cudaMemsetAsync(b.dirty, 0, set_bytes, s));
+      KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 7, 0, sizeof(unsigned long long), s));
+      dirty_valid = false;
+    }
     apply_kernel<<<grid, 256, 0, s>>>(r, b.s.vfail, b.dead, b.cnt + 2);
     learned_finish_kernel<<<1, 1, 0, s>>>(g->st, b.cnt + 3, b.cnt + 2, b.cnt + 1, nullptr);
     KZ_CUDA_TRY(cudaGetLastError());
     round++;
+    if (dirty_valid) {
+      KZ_TRY(read_counts());
+      if (h[7] * kListShareInv > h[4] / 2) {
+        // a dirty set beyond the list budget: a full pass next
+        KZ_TRY(clear_sets());
+        need_full = true;
+      }
+    }
   }
 }
 

@@ -23,10 +23,22 @@ def init_weights(seed: int = 0) -> np.ndarray:
     return w
 
 
-def cascade_specs(count: int, seed: int):
-    """Batch-style graphs in the range where the plain method cascades over
-    several sweeps (moderate n, sparse to medium density)."""
-    return synth.batch_specs(count, seed, n_lo=128, n_hi=1500, p_lo=0.15, p_hi=0.45)
+def cascade_specs(count: int, seed: int, n_lo: int = 256, n_hi: int = 32768):
+    """Batch-style graphs (random k-partite, a planted clique on every other
+    one) in the regime where the plain method cascades over many sweeps, at
+    every scale from n_lo to n_hi: n log-uniform, k uniform in 8..32, and p
+    set so that an edge expects mu = U[3, 9] common neighbours per class
+    (p = sqrt(mu k / n)), the range in which a sweep's deletions make further
+    edges fail.  (n, k, p, planted, graph seed) per graph."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for j in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
+        k = int(rng.integers(8, 33))
+        mu = float(rng.uniform(3.0, 9.0))
+        p = float(min(0.6, max(0.02, np.sqrt(mu * k / n))))
+        specs.append((n, k, p, j % 2 == 0, int(seed * 1000003 + j)))
+    return specs
 
 
 def collect(specs, per_sweep_cap: int = 4096, seed: int = 1) -> tuple:

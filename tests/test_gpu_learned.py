@@ -132,7 +132,7 @@ def test_trace_labels_match_plain_sweeps():
 
 @pytest.fixture(scope="module")
 def trained():
-    X, y = learned.collect(learned.cascade_specs(24, 901), per_sweep_cap=3000)
+    X, y = learned.collect(learned.cascade_specs(24, 901, n_hi=8192), per_sweep_cap=3000)
     m, losses = learned.train(X, y, steps=300, batch=4096, lr=3e-3)
     yield m, losses, (X, y)
     kz.kz_model_free(m)
@@ -149,7 +149,7 @@ def test_training_reduces_loss(trained):
 def test_learned_schedule_is_bit_identical(trained, threshold, path):
     # full passes on the bitset sweep (AUTO on these sizes) or the tensor form
     m = trained[0]
-    for i, (n, k, p, planted, seed) in enumerate(learned.cascade_specs(6, 77)):
+    for i, (n, k, p, planted, seed) in enumerate(learned.cascade_specs(6, 77, n_hi=2048)):
         g = synth.kpartite(n, k, p, seed, planted=planted)
         orc = oracle.fixpoint(g.colour, g.get_edges(), g.k)
         with kz.KernelGraph.from_synth(g) as kg:
@@ -166,7 +166,7 @@ def test_learned_gain_over_plain(trained):
     the plain Jacobi sweeps; the numbers are printed for the record."""
     m = trained[0]
     tot = {"plain": 0, "frontier": 0, "learned": 0}
-    for (n, k, p, planted, seed) in learned.cascade_specs(12, 4040):
+    for (n, k, p, planted, seed) in learned.cascade_specs(12, 4040, n_hi=8192):
         g = synth.kpartite(n, k, p, seed, planted=planted)
         for name, kw, thr in (("plain", {}, None), ("frontier", {"schedule": "learned"}, 0.0),
                               ("learned", {"schedule": "learned"}, 0.5)):
