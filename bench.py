@@ -426,6 +426,38 @@ def roofline_of(kz, torch, g, st, step_ms, workload, args, dev, stream):
                     "traffic_source (null when none matches the kernel's current sources)"}
 
 
+# multiply-adds per scored edge of the 16 -> 64 -> 64 -> 1 network, x 2 flops
+MLP_FLOPS_PER_EDGE = 2 * (16 * 64 + 64 * 64 + 64)
+
+
+def mlp_roofline(kz, torch, model, stream, rows=1 << 22, reps=10):
+    """The network's forward kernel (bf16 mma.sync, fp32 accumulation; the
+    scoring kernel runs the same tile code after computing the features) on
+    `rows` feature rows, against the measured dense bf16 peak."""
+    X = torch.randn(rows, 16, device="cuda", dtype=torch.float32)
+    out = torch.empty(rows, device="cuda", dtype=torch.float32)
+    for _ in range(3):
+        kz.kz_mlp_forward(model, X.data_ptr(), rows, out.data_ptr(), stream)
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        kz.kz_mlp_forward(model, X.data_ptr(), rows, out.data_ptr(), stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    s = statistics.median(times)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    peak = peaks["bf16_tflops"] * 1e12
+    flops = MLP_FLOPS_PER_EDGE * rows
+    return {"bound": "tensor", "kernel": "mlp_forward_kernel", "rows": rows, "flops_per_edge": MLP_FLOPS_PER_EDGE,
+            "achieved": flops / s / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": flops / s / peak,
+            "us": 1e6 * s, "bytes_per_edge": 16 * 4 + 4, "hbm_gbs": (16 * 4 + 4) * rows / s / 1e9,
+            "note": "peak = measured dense bf16 burst (cuBLAS), of measured; the kernel runs on the legacy "
+                    "warp-level mma.sync path"}
+
+
 def learned_comparison(kz, torch, graphs, stream, flush, local, args, pg, rank):
     """Train the edge-scoring network (plain-method traces of cascading graphs
     with other seeds; the library's forward/backward/Adam kernels), then time
@@ -436,29 +468,35 @@ def learned_comparison(kz, torch, graphs, stream, flush, local, args, pg, rank):
     X, y = learned.collect(learned.cascade_specs(24, synth.SEED_BASE + 900 + rank), per_sweep_cap=3000)
     model, losses = learned.train(X, y, steps=300, batch=4096, lr=3e-3)
     train_s = time.perf_counter() - t0
-    out = {"training": {"records": int(len(y)), "positive_share": float(np.mean(y)), "loss_first": losses[0],
+    mlp = mlp_roofline(kz, torch, model, stream)
+    out = {"mlp_roofline": mlp,
+           "training": {"records": int(len(y)), "positive_share": float(np.mean(y)), "loss_first": losses[0],
                         "loss_last": losses[-1], "seconds": round(train_s, 2),
                         "graphs": "24 cascading k-partite graphs (n log-uniform 256..32768, k 8..32, p = sqrt(mu k / n) with mu 3..9), other seeds"}}
     try:
+        arms = (("plain", "plain", None), ("learned", "learned", 0.5), ("frontier", "learned", 0.0))
         for name, g, h in graphs:
-            kz.kz_attach_model(h, model, 0.5)
             res = {}
-            for label, sched in (("plain", "plain"), ("learned", "learned")):
+            for label, sched, thr in arms:
+                if thr is not None:
+                    kz.kz_attach_model(h, model, thr)
                 opts = kz.kz_default_options(schedule=sched)
                 t = timed_steps(kz, torch, [h], lambda: kz.kz_kernelize(h, opts, stream), stream, flush,
                                 args.compare_steps, 2, local, pg)
                 st = kz.kz_fetch_stats(h)
                 alive, bits, _ = kz.kz_fetch_kernel_dense(h, g.n)
                 res[label] = dict(ms=t["median_ms"], st=st, alive=alive, bits=bits, clocks=t["clocks"])
-            same = bool(np.array_equal(res["plain"]["alive"], res["learned"]["alive"])
-                        and np.array_equal(res["plain"]["bits"], res["learned"]["bits"]))
+            same = all(np.array_equal(res["plain"]["alive"], res[a]["alive"])
+                       and np.array_equal(res["plain"]["bits"], res[a]["bits"]) for a, _, _ in arms)
             p, lr = res["plain"], res["learned"]
-            out[name] = {"time_to_fixpoint_ms": {"plain": p["ms"], "learned": lr["ms"]},
+            labels = [a for a, _, _ in arms]
+            out[name] = {"time_to_fixpoint_ms": {a: res[a]["ms"] for a in labels},
                          "speedup": p["ms"] / lr["ms"],
+                         "speedup_frontier_only": p["ms"] / res["frontier"]["ms"],
                          "plain_path": {v: k for k, v in kz.PATHS.items()}.get(p["st"]["path"]),
-                         "sweeps": {"plain": p["st"]["sweeps"], "learned": lr["st"]["sweeps"]},
-                         "passes": {"plain": p["st"]["passes"], "learned": lr["st"]["passes"]},
-                         "edge_tests": {"plain": p["st"]["edge_tests"], "learned": lr["st"]["edge_tests"]},
+                         "sweeps": {a: res[a]["st"]["sweeps"] for a in labels},
+                         "passes": {a: res[a]["st"]["passes"] for a in labels},
+                         "edge_tests": {a: res[a]["st"]["edge_tests"] for a in labels},
                          "kernel_edges": p["st"]["m_live"], "bit_identical": same,
                          "sm_mhz": lr["clocks"].get("sm_mhz"), "reasons": lr["clocks"].get("reasons")}
     finally:

@@ -287,13 +287,7 @@ kz_status kz_load_graph_dense(int32_t n, int32_t k, const int32_t *colour,
   return load_common(n, k, colour, stream, out, [&](kz_graph g) -> kz_status {
     const size_t bytes = (size_t)n * row_words * 8;
     if (bytes == 0) return bitset_pack_edges(g, nullptr, 0, true, g->stream);
-    uint64_t *d_bits = (uint64_t *)dev_alloc(bytes, g->stream);
-    kz_status st = d_bits ? KZ_OK : KZ_ERR_OOM;
-    if (st == KZ_OK)
-      st = cuda_status(cudaMemcpyAsync(d_bits, adj_bits, bytes, cudaMemcpyHostToDevice, g->stream));
-    if (st == KZ_OK) st = bitset_pack_dense(g, d_bits, row_words, g->stream);
-    if (d_bits) dev_free(d_bits, bytes, g->stream);
-    return st;
+    return bitset_pack_dense(g, adj_bits, row_words, g->stream);
   }, no_csr, false);
 }
 
@@ -651,18 +645,14 @@ kz_status kz_fetch_kernel_dense(kz_graph g, uint8_t *vertex_alive, uint64_t *adj
   }
   // everything on the stream, one wait at the end: the caller-ordered rows
   // and vertex flags (gathered on the device), the bit count, the run record
-  const size_t bytes = (size_t)g->n * row_words * 8;
   const size_t aux = 16 + (size_t)g->n;
-  uint64_t *d_out = (uint64_t *)dev_alloc(std::max<size_t>(bytes, 16), g->stream);
   uint8_t *d_aux = (uint8_t *)dev_alloc(aux, g->stream);
-  kz_status st = (d_out && d_aux) ? KZ_OK : KZ_ERR_OOM;
+  kz_status st = d_aux ? KZ_OK : KZ_ERR_OOM;
   unsigned long long cnt = 0;
   std::vector<uint8_t> alive((size_t)std::max(g->n, 1));
   DevState hs;
   unsigned long long *d_cnt = reinterpret_cast<unsigned long long *>(d_aux);
-  if (st == KZ_OK) st = bitset_unpack_gather(g, d_out, row_words, d_aux + 16, d_cnt, g->stream);
-  if (st == KZ_OK && bytes)
-    st = cuda_status(cudaMemcpyAsync(adj_bits, d_out, bytes, cudaMemcpyDeviceToHost, g->stream));
+  if (st == KZ_OK) st = bitset_fetch_dense(g, adj_bits, row_words, d_aux + 16, d_cnt, g->stream);
   if (st == KZ_OK && g->n)
     st = cuda_status(cudaMemcpyAsync(alive.data(), d_aux + 16, (size_t)g->n, cudaMemcpyDeviceToHost, g->stream));
   if (st == KZ_OK)
@@ -670,7 +660,6 @@ kz_status kz_fetch_kernel_dense(kz_graph g, uint8_t *vertex_alive, uint64_t *adj
   if (st == KZ_OK)
     st = cuda_status(cudaMemcpyAsync(&hs, g->st, offsetof(DevState, trace_dv), cudaMemcpyDeviceToHost, g->stream));
   if (st == KZ_OK) st = cuda_status(cudaStreamSynchronize(g->stream));
-  if (d_out) dev_free(d_out, bytes, g->stream);
   if (d_aux) dev_free(d_aux, aux, g->stream);
   if (st != KZ_OK) return st;
   int64_t n_live = 0;

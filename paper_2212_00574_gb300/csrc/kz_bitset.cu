@@ -161,128 +161,6 @@ __global__ void fill_units_kernel(int2 *__restrict__ units, const int32_t *__res
   }
 }
 
-// ---------------------------------------------------------------------------
-// packing kernels
-// ---------------------------------------------------------------------------
-
-struct PackArgs {
-  uint32_t *A;
-  int32_t ldw, k;
-  const int32_t *inv;     // caller -> relabelled
-  const int32_t *col;     // relabelled colour
-  const int32_t *coff;    // k + 1
-  unsigned long long *edge_count;
-  int32_t *error;         // first error code seen (0 = none)
-};
-
-__global__ void pack_edges_kernel(PackArgs a, const int32_t *__restrict__ edges, int64_t m,
-                                  int dedup) {
-  unsigned long long mine = 0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int32_t x = a.inv[edges[2 * e]], y = a.inv[edges[2 * e + 1]];
-    if (x > y) {
-      int32_t t = x;
-      x = y;
-      y = t;
-    }
-    const int32_t cx = a.col[x], cy = a.col[y];
-    const int32_t ix = x - a.coff[cx], iy = y - a.coff[cy];
-    const uint32_t bx = 1u << (ix & 31), by = 1u << (iy & 31);
-    const int64_t wxy = (int64_t)x * a.ldw + (iy >> 5) * a.k + cy;
-    const int64_t wyx = (int64_t)y * a.ldw + (ix >> 5) * a.k + cx;
-    const uint32_t old = atomicOr(&a.A[wxy], by);
-    if (old & by) {
-      if (!dedup) atomicCAS(a.error, 0, (int32_t)KZ_ERR_DUPLICATE_EDGE);
-      continue;
-    }
-    atomicOr(&a.A[wyx], bx);
-    mine++;
-  }
-  for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
-  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(a.edge_count, mine);
-}
-
-// Row form of the dense packer, first half: one CTA per relabelled row x at
-// a time.  The lanes walk the caller's row i = perm[x] column by column
-// (consecutive columns on consecutive lanes, so the row word is a broadcast
-// and the position table, staged in shared memory when it fits, is read
-// without bank conflicts); every upper-triangle bit j > i is set at j's
-// position in a shared-memory copy of the output row, which is then written
-// out whole.  Every edge lands in the row of its endpoint with the smaller
-// caller id; symmetrize_kernel adds the other half.  An edge inside one class
-// lands in an own-class word: an illegal colouring.
-__global__ void pack_dense_rows_kernel(PackArgs a, const uint64_t *__restrict__ bits, int64_t row_words, int32_t n,
-                                       const int32_t *__restrict__ perm, const int32_t *__restrict__ cpos_g,
-                                       int32_t cpos_in_smem) {
-  extern __shared__ __align__(16) uint32_t psm[];
-  uint32_t *sout = psm;                                           // ldw words
-  int32_t *scpos = reinterpret_cast<int32_t *>(psm + a.ldw);      // n entries (when staged)
-  const int32_t *cpos = cpos_in_smem ? scpos : cpos_g;
-  if (cpos_in_smem)
-    for (int32_t j = threadIdx.x; j < n; j += blockDim.x) scpos[j] = cpos_g[j];
-  unsigned long long mine = 0;
-  for (int32_t x = blockIdx.x; x < n; x += gridDim.x) {
-    for (int32_t w = threadIdx.x; w < a.ldw; w += blockDim.x) sout[w] = 0u;
-    __syncthreads();
-    const int32_t i = perm[x];
-    const uint64_t *row = bits + (int64_t)i * row_words;
-    for (int32_t j = i + 1 + threadIdx.x; j < n; j += blockDim.x) {
-      if ((row[j >> 6] >> (j & 63)) & 1ull) {
-        const int32_t pp = cpos[j];
-        atomicOr(&sout[pp >> 5], 1u << (pp & 31));
-        mine++;
-      }
-    }
-    __syncthreads();
-    const int32_t own = a.col[x];
-    for (int32_t w = threadIdx.x; w < a.ldw; w += blockDim.x) {
-      uint32_t out = sout[w];
-      if (out && w % a.k == own) {
-        atomicCAS(a.error, 0, (int32_t)KZ_ERR_ILLEGAL_COLOURING);
-        out = 0u;
-      }
-      a.A[(int64_t)x * a.ldw + w] = out;
-    }
-    __syncthreads();
-  }
-  for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
-  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(a.edge_count, mine);
-}
-
-// Second half: every 32 x 32 tile of a block X against a block Y of a higher
-// class becomes the OR of itself and the transpose of the (Y, X) tile, and
-// the (Y, X) tile the transpose of the result.  One warp per tile pair, over
-// all pairs (pair q of block X is partner boff[class(X) + 1] + q - pair0[X]),
-// so that many independent tiles are in flight.
-__global__ void symmetrize_kernel(uint32_t *__restrict__ A, const BlockDesc *__restrict__ blocks,
-                                  const int32_t *__restrict__ boff, const int64_t *__restrict__ pair0, int32_t nb,
-                                  int32_t k, int32_t ldw) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t total = pair0[nb];
-  for (int64_t q = warp0; q < total; q += warps) {
-    int lo = 0, hi = nb;  // the last X with pair0[X] <= q
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (pair0[mid] <= q) lo = mid;
-      else hi = mid;
-    }
-    const BlockDesc X = blocks[lo];
-    const BlockDesc Y = blocks[boff[X.c + 1] + (int32_t)(q - pair0[lo])];
-    const bool vx = lane < X.size, vy = lane < Y.size;
-    uint32_t *px = A + (int64_t)(X.base + lane) * ldw + Y.r * k + Y.c;
-    uint32_t *py = A + (int64_t)(Y.base + lane) * ldw + X.r * k + X.c;
-    const uint32_t xy = vx ? *px : 0u;  // row X.base + lane, bits over Y's members
-    const uint32_t yx = vy ? *py : 0u;  // row Y.base + lane, bits over X's members
-    const uint32_t nxy = xy | transpose32(yx);
-    const uint32_t nyx = transpose32(nxy);
-    if (vx) *px = nxy;
-    if (vy) *py = nyx;
-  }
-}
-
 __global__ void init_vlive_kernel(uint32_t *V, const BlockDesc *blocks, int nb, int k) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
     const BlockDesc d = blocks[b];
@@ -1195,215 +1073,6 @@ kz_status bitset_barrier_timeout_probe(kz_graph g, uint32_t spin_limit, cudaStre
   void *kargs[] = {&args};
   KZ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(threads), kargs, smem, s));
   return KZ_OK;
-}
-
-// ---------------------------------------------------------------------------
-// unpacking to caller ids
-// ---------------------------------------------------------------------------
-
-// Shared memory the row kernels use: the row (ldw words) plus the position
-// table (n entries) when both fit in kStagedSmemBytes.
-constexpr size_t kStagedSmemBytes = 200 * 1024;
-
-static kz_status row_kernel_smem(kz_graph g, const void *fn, size_t *smem, int32_t *staged) {
-  const size_t row = (size_t)g->ldw * 4, table = (size_t)g->n * 4;
-  *staged = row + table <= kStagedSmemBytes ? 1 : 0;
-  *smem = row + (*staged ? table : 0);
-  KZ_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(*smem, 1)));
-  return KZ_OK;
-}
-
-// Row form of the unpacker: one CTA per caller row ox at a time; the
-// relabelled row inv[ox] is staged in shared memory (with the position table
-// when it fits).  Each warp builds 32 caller words (2048 columns) in 64
-// rounds: in a round the lanes take 32 consecutive columns (the position
-// table is read without bank conflicts), look up their bits in the staged
-// row, and a ballot gives half of one word, kept by the lane that writes it.
-// The CTA also writes ox's vertex flag.
-__global__ void unpack_rows_kernel(const uint32_t *__restrict__ A0, const uint32_t *__restrict__ A1,
-                                   const uint32_t *__restrict__ V0, const uint32_t *__restrict__ V1,
-                                   const int32_t *__restrict__ cur, int32_t n, int32_t ldw,
-                                   const int32_t *__restrict__ inv, const int32_t *__restrict__ cpos_g,
-                                   int32_t cpos_in_smem, uint64_t *__restrict__ out, int64_t row_words,
-                                   uint8_t *__restrict__ alive, unsigned long long *__restrict__ edge_count) {
-  extern __shared__ __align__(16) uint32_t usm[];
-  uint32_t *srow = usm;
-  int32_t *scpos = reinterpret_cast<int32_t *>(usm + ldw);
-  const int32_t *cpos = cpos_in_smem ? scpos : cpos_g;
-  if (cpos_in_smem)
-    for (int32_t j = threadIdx.x; j < n; j += blockDim.x) scpos[j] = cpos_g[j];
-  const bool one = (*cur & 1) != 0;
-  const uint32_t *A = one ? A1 : A0;
-  const uint32_t *V = one ? V1 : V0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  unsigned long long mine = 0;
-  for (int32_t ox = blockIdx.x; ox < n; ox += gridDim.x) {
-    __syncthreads();
-    const uint32_t *row = A + (int64_t)inv[ox] * ldw;
-    for (int32_t w = threadIdx.x; w < ldw; w += blockDim.x) srow[w] = row[w];
-    __syncthreads();
-    for (int64_t w0 = (int64_t)warp * 32; w0 < row_words; w0 += (int64_t)nwarps * 32) {
-      uint64_t word = 0;
-      for (int h = 0; h < 64; h++) {
-        const int64_t col = w0 * 64 + 32 * h + lane;
-        bool bit = false;
-        if (col < n) {
-          const int32_t p = cpos[col];
-          bit = (srow[p >> 5] >> (p & 31)) & 1u;
-        }
-        const uint32_t half = __ballot_sync(0xffffffffu, bit);
-        if (lane == (h >> 1)) word |= (uint64_t)half << ((h & 1) * 32);
-      }
-      if (w0 + lane < row_words) {
-        out[(int64_t)ox * row_words + w0 + lane] = word;
-        mine += __popcll(word);
-      }
-    }
-    if (threadIdx.x == 0) {
-      const int32_t p = cpos[ox];
-      alive[ox] = (uint8_t)((V[p >> 5] >> (p & 31)) & 1u);
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
-  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(edge_count, mine);
-}
-
-kz_status bitset_unpack_gather(kz_graph g, uint64_t *d_out, int64_t row_words, uint8_t *d_alive,
-                               unsigned long long *d_edge_count, cudaStream_t s) {
-  KZ_CUDA_TRY(cudaMemsetAsync(d_edge_count, 0, sizeof(unsigned long long), s));
-  if (g->n == 0) return KZ_OK;
-  size_t smem = 0;
-  int32_t staged = 0;
-  KZ_TRY(row_kernel_smem(g, (const void *)unpack_rows_kernel, &smem, &staged));
-  const int grid = std::max(1, std::min(g->n, (staged ? 1 : 4) * sm_count()));
-  unpack_rows_kernel<<<grid, 512, smem, s>>>(g->A[0], g->A[1], g->V[0], g->V[1], &g->st->cur, g->n, g->ldw,
-                                             g->d_inv, g->d_cpos, staged, d_out, row_words, d_alive, d_edge_count);
-  return cuda_status(cudaGetLastError());
-}
-
-kz_status bitset_vertex_alive(kz_graph g, uint8_t *host_alive, int64_t *n_live) {
-  int32_t cur = 0;
-  KZ_CUDA_TRY(cudaMemcpy(&cur, &g->st->cur, sizeof(int32_t), cudaMemcpyDeviceToHost));
-  std::vector<uint32_t> V((size_t)g->ldw);
-  KZ_CUDA_TRY(cudaMemcpy(V.data(), g->V[cur & 1], (size_t)g->ldw * 4, cudaMemcpyDeviceToHost));
-  int64_t live = 0;
-  for (int32_t x = 0; x < g->n; x++) {
-    // class of x: coff is sorted
-    const int c = (int)(std::upper_bound(g->coff.begin(), g->coff.end(), x) - g->coff.begin()) - 1;
-    const int i = x - g->coff[c];
-    const bool a = (V[(size_t)(i >> 5) * g->k + c] >> (i & 31)) & 1u;
-    live += a;
-    if (host_alive) host_alive[g->perm[x]] = a ? 1 : 0;
-  }
-  if (n_live) *n_live = live;
-  return KZ_OK;
-}
-
-// Shared set-up of the two packers: relabelling tables on the device and the
-// zeroed pristine adjacency.  Returns the temporaries to free after the sync.
-static kz_status pack_setup(kz_graph g, cudaStream_t s, PackArgs &a, std::vector<void *> &tmp) {
-  KZ_TRY(graph_alloc(g, &g->A0, (size_t)g->n * g->ldw, s));
-  if (g->n > 0 && g->ldw > 0)
-    KZ_CUDA_TRY(cudaMemsetAsync(g->A0, 0, (size_t)g->n * g->ldw * 4, s));
-  std::vector<int32_t> col_new((size_t)g->n);
-  for (int c = 0; c < g->k; c++)
-    for (int x = g->coff[c]; x < g->coff[c + 1]; x++) col_new[x] = c;
-  // small tables of the packers: carved from the graph's chunks (one
-  // allocator call at most), released with the graph
-  int32_t *d_inv = nullptr, *d_col = nullptr, *d_coff = nullptr, *d_err = nullptr;
-  unsigned long long *d_cnt = nullptr;
-  const size_t nn = (size_t)std::max(g->n, 1);
-  KZ_TRY(graph_alloc(g, &d_inv, nn, s));
-  KZ_TRY(graph_alloc(g, &d_col, nn, s));
-  KZ_TRY(graph_alloc(g, &d_coff, (size_t)g->k + 1, s));
-  KZ_TRY(graph_alloc(g, &d_err, 4, s));
-  KZ_TRY(graph_alloc(g, &d_cnt, 2, s));
-  tmp.clear();
-  if (g->n) {
-    KZ_TRY(h2d(d_inv, g->inv.data(), (size_t)g->n * 4, s));
-    KZ_TRY(h2d(d_col, col_new.data(), (size_t)g->n * 4, s));
-  }
-  KZ_TRY(h2d(d_coff, g->coff.data(), ((size_t)g->k + 1) * 4, s));
-  KZ_CUDA_TRY(cudaMemsetAsync(d_err, 0, 16, s));
-  KZ_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 16, s));
-  a.A = g->A0;
-  a.ldw = g->ldw;
-  a.k = g->k;
-  a.inv = d_inv;
-  a.col = d_col;
-  a.coff = d_coff;
-  a.edge_count = d_cnt;
-  a.error = d_err;
-  return KZ_OK;
-}
-
-static kz_status pack_finish(kz_graph g, cudaStream_t s, PackArgs &a, std::vector<void *> &tmp) {
-  int32_t err = 0;
-  unsigned long long cnt = 0;
-  cudaError_t e1 = cudaMemcpyAsync(&err, a.error, 4, cudaMemcpyDeviceToHost, s);
-  cudaError_t e2 = cudaMemcpyAsync(&cnt, a.edge_count, 8, cudaMemcpyDeviceToHost, s);
-  cudaError_t e3 = cudaStreamSynchronize(s);
-  tmp.clear();
-  if (e1 != cudaSuccess) return cuda_status(e1);
-  if (e2 != cudaSuccess) return cuda_status(e2);
-  if (e3 != cudaSuccess) return cuda_status(e3);
-  if (err) return (kz_status)err;
-  g->m = (int64_t)cnt;
-  return KZ_OK;
-}
-
-kz_status bitset_pack_edges(kz_graph g, const int32_t *d_edges, int64_t m, bool dedup,
-                            cudaStream_t s) {
-  PackArgs a;
-  std::vector<void *> tmp;
-  kz_status st = pack_setup(g, s, a, tmp);
-  if (st == KZ_OK && m > 0) {
-    const int threads = 256;
-    const int grid = (int)std::min<int64_t>((m + threads - 1) / threads, 64 * sm_count());
-    pack_edges_kernel<<<grid, threads, 0, s>>>(a, d_edges, m, dedup ? 1 : 0);
-    st = cuda_status(cudaGetLastError());
-  }
-  kz_status st2 = st == KZ_OK ? pack_finish(g, s, a, tmp) : KZ_OK;
-  return st != KZ_OK ? st : st2;
-}
-
-kz_status bitset_pack_dense(kz_graph g, const uint64_t *d_bits, int64_t row_words, cudaStream_t s) {
-  PackArgs a;
-  std::vector<void *> tmp;
-  kz_status st = pack_setup(g, s, a, tmp);
-  const int64_t words = (int64_t)g->n * g->ldw;
-  if (st == KZ_OK && words > 0) {
-    // the upper triangle row by row, then the transposed half tile by tile
-    size_t smem = 0;
-    int32_t staged = 0;
-    st = row_kernel_smem(g, (const void *)pack_dense_rows_kernel, &smem, &staged);
-    const int nb = (int)g->blocks.size();
-    // the tile pairs: block X against every block of a higher class
-    std::vector<int64_t> pair0((size_t)nb + 1, 0);
-    for (int x = 0; x < nb; x++) pair0[x + 1] = pair0[x] + (nb - std::min(g->boff[g->blocks[x].c + 1], nb));
-    BlockDesc *d_blk = nullptr;
-    int32_t *d_bo = nullptr;
-    int64_t *d_p0 = nullptr;
-    if (st == KZ_OK) st = graph_alloc(g, &d_blk, (size_t)std::max(nb, 1), s);
-    if (st == KZ_OK) st = graph_alloc(g, &d_bo, (size_t)g->k + 1, s);
-    if (st == KZ_OK) st = graph_alloc(g, &d_p0, (size_t)nb + 1, s);
-    if (st == KZ_OK && nb > 0)
-      st = h2d(d_blk, g->blocks.data(), sizeof(BlockDesc) * nb, s);
-    if (st == KZ_OK)
-      st = h2d(d_bo, g->boff.data(), sizeof(int32_t) * (g->k + 1), s);
-    if (st == KZ_OK)
-      st = h2d(d_p0, pair0.data(), sizeof(int64_t) * (nb + 1), s);
-    if (st == KZ_OK) {
-      const int grid = std::max(1, std::min(g->n, (staged ? 1 : 4) * sm_count()));
-      pack_dense_rows_kernel<<<grid, 512, smem, s>>>(a, d_bits, row_words, g->n, g->d_perm, g->d_cpos, staged);
-      const int64_t pairs = pair0[nb];
-      const int sgrid = (int)std::max<int64_t>(1, std::min<int64_t>((pairs + 7) / 8, 32 * sm_count()));
-      if (pairs > 0) symmetrize_kernel<<<sgrid, 256, 0, s>>>(g->A0, d_blk, d_bo, d_p0, nb, g->k, g->ldw);
-      st = cuda_status(cudaGetLastError());
-    }
-  }
-  kz_status st2 = st == KZ_OK ? pack_finish(g, s, a, tmp) : KZ_OK;
-  return st != KZ_OK ? st : st2;
 }
 
 }  // namespace kz

@@ -247,19 +247,23 @@ struct kz_graph_s {
 
 namespace kz {
 
-// Kernels and host helpers of the bitset path (kz_bitset.cu).
+// Kernels and host helpers of the bitset path (kz_bitset.cu; loading and
+// fetching in kz_pack.cu).
 kz_status bitset_build_layout(kz_graph g);
 kz_status bitset_pack_edges(kz_graph g, const int32_t *d_edges, int64_t m, bool dedup,
                             cudaStream_t s);
-kz_status bitset_pack_dense(kz_graph g, const uint64_t *d_bits, int64_t row_words, cudaStream_t s);
+// Packs a host dense bit matrix (row-major, row_words words a row), copied
+// in row chunks that overlap the packing; synchronous.
+kz_status bitset_pack_dense(kz_graph g, const uint64_t *h_bits, int64_t row_words, cudaStream_t s);
 kz_status bitset_finish_load(kz_graph g, cudaStream_t s);
 kz_status bitset_reset(kz_graph g, cudaStream_t s);
 kz_status bitset_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s);
-// Caller-ordered dense rows, vertex flags (bytes) and the count of set bits
-// (twice the edges) of the current state, all on the device; the current
-// buffer index is read on the device, so nothing synchronises.
-kz_status bitset_unpack_gather(kz_graph g, uint64_t *d_out, int64_t row_words, uint8_t *d_alive,
-                               unsigned long long *d_edge_count, cudaStream_t s);
+// Caller-ordered dense rows of the current state into host memory (row
+// chunks, each copied while the next is unpacked), vertex flags (bytes, on
+// the device) and the count of set bits (twice the edges, on the device).
+// Asynchronous on s: the caller's wait on s covers every copy.
+kz_status bitset_fetch_dense(kz_graph g, uint64_t *h_out, int64_t row_words, uint8_t *d_alive,
+                             unsigned long long *d_edge_count, cudaStream_t s);
 kz_status bitset_vertex_alive(kz_graph g, uint8_t *host_alive, int64_t *n_live);
 
 // One plain multi-CTA sweep pass (no loop graph); *cont = 1 when it deleted

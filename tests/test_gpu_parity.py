@@ -151,6 +151,53 @@ def test_dense_input_equals_edge_input():
     assert_parity(g, a)
 
 
+def _pack_bool_rows(mat: np.ndarray, row_words: int) -> np.ndarray:
+    """uint64[n, row_words] with bit j % 64 of word j // 64 = mat[i, j]."""
+    n = mat.shape[0]
+    by = np.packbits(mat, axis=1, bitorder="little")
+    out = np.zeros((n, row_words * 8), np.uint8)
+    out[:, :by.shape[1]] = by
+    return out.view(np.uint64)
+
+
+@pytest.mark.parametrize("n,k,classes", [(12000, 6, "geometric"), (11777, 37, "uniform"), (515, 3, "geometric"),
+                                         (6000, 64, "one large")])
+def test_dense_load_fetch_round_trip(n, k, classes):
+    """A graph dense enough that the rules delete nothing comes back exactly:
+    the upper triangle of the input, mirrored, whatever the lower triangle
+    and the diagonal hold, through a padded row stride.  The larger sizes
+    move in row chunks overlapped with the packing and unpacking; k = 6 and
+    k = 3 put several rounds of a class in one group of the symmetrizer,
+    skewed classes leave blocks missing, and one class of 3000 vertices makes
+    rows too long for the unpacker's tile form (its row form runs).  Every
+    class has enough members that no edge of the 0.9-dense graph fails."""
+    rng = np.random.default_rng(n + k)
+    if classes == "geometric":
+        w = 0.6 ** np.arange(k)
+        colour = rng.choice(k, size=n, p=w / w.sum()).astype(np.int32)
+    elif classes == "one large":
+        colour = np.concatenate([np.zeros(3000, np.int32), rng.integers(1, k, size=n - 3000).astype(np.int32)])
+        colour = colour[rng.permutation(n)]
+    else:
+        colour = rng.integers(0, k, size=n).astype(np.int32)
+    upper = np.triu(rng.integers(0, 10, size=(n, n), dtype=np.uint8) < 9, 1)
+    upper &= colour[:, None] != colour[None, :]
+    garbage = np.tril(rng.integers(0, 2, size=(n, n), dtype=np.uint8) == 1, 0)
+    row_words = (n + 63) // 64 + 1
+    bits_in = _pack_bool_rows(upper | garbage, row_words)
+    del garbage
+    full = upper | upper.T
+    h = kz.kz_load_graph_dense(n, k, colour, bits_in)
+    try:
+        kz.kz_kernelize(h)
+        alive, bits, st = kz.kz_fetch_kernel_dense(h, n, out_bits=np.zeros((n, row_words), np.uint64))
+    finally:
+        kz.kz_free_graph(h)
+    assert st["sweeps"] == 0 and alive.all()
+    assert st["m"] == int(upper.sum()) and st["m_live"] == st["m"]
+    assert np.array_equal(bits, _pack_bool_rows(full, row_words))
+
+
 def test_reset_and_rerun():
     g = synth.tiny_random(8, 250, 6, 0.1, planted=True)
     with kz.KernelGraph.from_synth(g) as kg:
