@@ -676,6 +676,38 @@ __global__ void mark_dirty_kernel(RowView rold, const int2 *__restrict__ dead,
   }
 }
 
+// Up to `cap` live edges {x, y}, x < y, from every `step`-th row (a sample
+// spread over the classes, for timing the exact test).  The count may pass
+// cap; clamp_kernel brings it back.
+__global__ void sample_edges_kernel(RowView r, int2 *__restrict__ out, unsigned long long *count, int64_t cap,
+                                    int32_t step) {
+  const int rk = r.R * r.k;
+  const int64_t rows = ((int64_t)r.n + step - 1) / step;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = tid; t < rows * rk; t += stride) {
+    if (*(volatile unsigned long long *)count >= (unsigned long long)cap) return;
+    const int64_t j = t / rk;
+    const int w = (int)(t - j * rk);
+    const int64_t x = j * step;
+    uint32_t bits = r.A[x * r.ldw + w];
+    const int c = w % r.k, rr = w / r.k;
+    while (bits) {
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1;
+      const int y = r.coff[c] + 32 * rr + b;
+      if (y <= (int)x) continue;
+      const unsigned long long pos = atomicAdd(count, 1ull);
+      if ((int64_t)pos >= cap) return;
+      out[pos] = make_int2((int)x, y);
+    }
+  }
+}
+
+__global__ void clamp_kernel(unsigned long long *count, unsigned long long cap) {
+  if (*count > cap) *count = cap;
+}
+
 // Vertex and edge deletions of the last productive full pass, from the
 // device state's per-sweep record (all ones when the record is not kept).
 __global__ void last_pass_kernel(const DevState *st, unsigned long long *out) {
@@ -925,21 +957,51 @@ int32_t read_cur(kz_graph g, cudaStream_t s) {
 
 namespace kz {
 
-// A list of edges to test one by one is worth it while it holds at most this
-// share of the live edges; beyond it a full pass (block-wise on the bitset
-// rows, or all pairs on the tensor cores) is cheaper per edge.
+// Whether testing a list of edges one by one beats a full pass.  Both costs
+// are measured during the run (CUDA events around the full passes and the
+// list tests): a list is worth it while its estimated time stays under
+// kListGain of the last full pass's (the rest pays for the round's
+// statistics, scoring and marking).  Until a list test of at least
+// kMinTimedList edges has been timed, a list may hold an eighth of the live
+// edges.
 constexpr unsigned long long kListShareInv = 8;
+constexpr double kListGain = 0.7;
+constexpr unsigned long long kMinTimedList = 1 << 16;
+constexpr int64_t kCalibrationEdges = 1 << 20;  // the sample that times the exact test
 
-// Whether the dirty set that de edge deletions leave (about 2 de times the
-// mean common neighbours of a live edge, a random-graph estimate from the
-// live density) fits the list budget.
-static bool dirty_set_fits(kz_graph g, unsigned long long de, double live_edges) {
+struct ListBudget {
+  double full_ms = -1.0;      // last full pass
+  double per_edge_ms = -1.0;  // list test time per listed edge
+  bool fits(double list, double live_edges) const {
+    if (per_edge_ms < 0.0 || full_ms < 0.0) return list * (double)kListShareInv <= live_edges;
+    return list * per_edge_ms <= kListGain * full_ms;
+  }
+};
+
+// The dirty set that de edge deletions leave: about 2 de times the mean
+// common-neighbour count of a live edge (a random-graph estimate from the
+// live density) marks, landing on the live edges at random.
+static double dirty_estimate(kz_graph g, unsigned long long de, double live_edges) {
   const double n = std::max(g->n, 2), k = std::max(g->k, 3);
   const double pairs = n * n * (k - 1.0) / (2.0 * k);  // vertex pairs in different classes
   const double dens = live_edges / pairs;
   const double common = n * (k - 2.0) / k * dens * dens;
-  return 2.0 * (double)de * common * (double)kListShareInv <= live_edges;
+  const double marks = 2.0 * (double)de * common;
+  return live_edges > 0.0 ? live_edges * -std::expm1(-marks / live_edges) : 0.0;
 }
+
+// Timing events of one run (destroyed with it).
+struct RunEvents {
+  cudaEvent_t a = nullptr, b = nullptr;
+  ~RunEvents() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  double ms() const {
+    float v = 0.f;
+    return cudaEventElapsedTime(&v, a, b) == cudaSuccess ? (double)v : -1.0;
+  }
+};
 
 // Learned schedule (see the file comment).  full_path is the path of the
 // full passes: KZ_PATH_BITSET (the multi-CTA sweep) or KZ_PATH_TENSOR.
@@ -964,9 +1026,33 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cu
   if (g->n == 0) return KZ_OK;
   const int64_t cap = std::max<int64_t>(g->m, 1);
   const size_t set_bytes = (size_t)g->n * g->ldw * 4;
+  RunEvents ev;
+  KZ_CUDA_TRY(cudaEventCreate(&ev.a));
+  KZ_CUDA_TRY(cudaEventCreate(&ev.b));
+  ListBudget budget;
+  bool calibrated = false;
   auto full_pass = [&](int *cont) -> kz_status {
-    if (full_path == KZ_PATH_TENSOR) return tensor_one_pass(g, opt, s, cont);
-    return bitset_one_pass(g, s, cont);
+    KZ_CUDA_TRY(cudaEventRecord(ev.a, s));
+    const kz_status st = full_path == KZ_PATH_TENSOR ? tensor_one_pass(g, opt, s, cont) : bitset_one_pass(g, s, cont);
+    KZ_CUDA_TRY(cudaEventRecord(ev.b, s));
+    KZ_CUDA_TRY(cudaEventSynchronize(ev.b));
+    const double ms = ev.ms();
+    if (ms > 0.0) budget.full_ms = ms;
+    return st;
+  };
+  // an exact test of a list, timed for the budget when the list is long
+  auto test_list = [&](const RowView &rv, const int2 *list, unsigned long long *n_list) -> kz_status {
+    KZ_CUDA_TRY(cudaEventRecord(ev.a, s));
+    test_edges_kernel<<<grid, 256, 0, s>>>(rv, list, n_list, b.dead, b.cnt + 2);
+    KZ_CUDA_TRY(cudaGetLastError());
+    KZ_CUDA_TRY(cudaEventRecord(ev.b, s));
+    return KZ_OK;
+  };
+  // after the counts of a timed list test are read back
+  auto time_list = [&](unsigned long long listed) {
+    if (listed < kMinTimedList) return;
+    const double ms = ev.ms();
+    if (ms > 0.0) budget.per_edge_ms = ms / (double)listed;
   };
   // counters and the run's productive sweeps, read back in one wait
   unsigned long long h[kCounters];
@@ -1014,8 +1100,21 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cu
       KZ_CUDA_TRY(cudaGetLastError());
       KZ_TRY(read_counts());
       round = (int)std::min<int64_t>(sweeps, 1 << 20);
+      if (!calibrated) {
+        // time the exact test once, on a sample of live edges (results dropped)
+        calibrated = true;
+        KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 1, 0, sizeof(unsigned long long) * 2, s));
+        sample_edges_kernel<<<grid, 256, 0, s>>>(r, b.work, b.cnt + 1, std::min<int64_t>(kCalibrationEdges, cap),
+                                                 std::max(1, g->n / 1024));
+        clamp_kernel<<<1, 1, 0, s>>>(b.cnt + 1, (unsigned long long)std::min<int64_t>(kCalibrationEdges, cap));
+        KZ_TRY(test_list(r, b.work, b.cnt + 1));
+        KZ_TRY(read_counts());
+        time_list(h[1]);
+        KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 1, 0, sizeof(unsigned long long) * 2, s));
+      }
       if (h[8] == 0) {
-        if (!dirty_set_fits(g, h[9], (double)(h[4] / 2))) {
+        const double live = (double)(h[4] / 2);
+        if (!budget.fits(dirty_estimate(g, h[9], live), live)) {
           // still in the cascade's heavy sweeps: the next one is a full pass
           need_full = true;
           continue;
@@ -1045,22 +1144,22 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cu
     KZ_CUDA_TRY(cudaGetLastError());
     KZ_TRY(read_counts());
     const unsigned long long live_edges = h[4] / 2;
-    if (h[1] * kListShareInv > live_edges) {
+    if (!budget.fits((double)h[1], (double)live_edges)) {
       // so many edges listed that testing them one by one costs more than a
       // full pass, which tests every edge anyway
       KZ_TRY(clear_sets());
       need_full = true;
       continue;
     }
-    test_edges_kernel<<<grid, 256, 0, s>>>(r, b.work, b.cnt + 1, b.dead, b.cnt + 2);
-    KZ_CUDA_TRY(cudaGetLastError());
+    KZ_TRY(test_list(r, b.work, b.cnt + 1));
     KZ_TRY(read_counts());
+    time_list(h[1]);
     unsigned long long dv = h[3], de = h[2];
     if (dv + de == 0) {
       // the scored edges found nothing: the pending ones next, when they are
       // few; otherwise (or when they hold no failure either) a full pass
       learned_finish_kernel<<<1, 1, 0, s>>>(g->st, b.cnt + 3, b.cnt + 2, b.cnt + 1, nullptr);
-      if (h[6] * kListShareInv > live_edges) {
+      if (!budget.fits((double)h[6], (double)live_edges)) {
         // the pending set's count already rules the list out: no flush
         KZ_TRY(clear_sets());
         need_full = true;
@@ -1071,13 +1170,14 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cu
       KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 6, 0, sizeof(unsigned long long), s));  // flushed
       KZ_TRY(read_counts());
       const unsigned long long pending = h[1];
-      if (pending == 0 || pending * kListShareInv > live_edges) {
+      if (pending == 0 || !budget.fits((double)pending, (double)live_edges)) {
         KZ_TRY(clear_sets());
         need_full = true;
         continue;
       }
-      test_edges_kernel<<<grid, 256, 0, s>>>(r, b.work, b.cnt + 1, b.dead, b.cnt + 2);
+      KZ_TRY(test_list(r, b.work, b.cnt + 1));
       KZ_TRY(read_counts());
+      time_list(h[1]);
       dv = 0;
       de = h[2];
       if (de == 0) {
@@ -1112,7 +1212,7 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cu
     round++;
     if (dirty_valid) {
       KZ_TRY(read_counts());
-      if (h[7] * kListShareInv > h[4] / 2) {
+      if (!budget.fits((double)h[7], (double)(h[4] / 2))) {
         // a dirty set beyond the list budget: a full pass next
         KZ_TRY(clear_sets());
         need_full = true;
