@@ -363,7 +363,8 @@ const char *kz_status_string(kz_status s);
  *   vertex_alive  uint8[n] out: 1 if the vertex is in the kernel
  *   adj_out       uint64[n * row_words] out: the kernel's symmetric bit matrix
  *   counts        int64[4] out: sweeps, passes, edge tests, status
- *   stream        stream for every launch; the call waits for it at the end
+ *   stream        stream for every launch; the call waits for it at the end,
+ *                 so no call can be captured into a CUDA graph
  * Returns the status (also in counts[3]).  n > KZ_NOALLOC_MAX_N, or colour
  * classes so uneven that the bitset rows exceed KZ_NOALLOC_MAX_WORDS words,
  * give KZ_ERR_UNSUPPORTED.  Statuses found on the host (KZ_ERR_ARG, and
