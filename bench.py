@@ -329,7 +329,7 @@ def run_reference(args, world, rank, pg):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": wdesc(args), "n": g.n, "k": g.k, "m": g.m, "seed": workload_seed(args.workload),
-                   "l2": "n/a (CPU)", "parallelism": "replicas"},
+                   "l2": "n/a (CPU)", "parallelism": "single (rank 0 only)"},
         "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
                          "sample": per_step[0]["sample"] + " per step"},
         "extrapolated_ms_per_full_pass": 1e3 * g.m / value,
