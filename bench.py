@@ -59,10 +59,10 @@ PROFILES = os.path.join(ROOT, "profiles")
 # the source files each profiled kernel is compiled from: a traffic record in
 # profiles/ counts only while their hash is the one it was captured with
 KERNEL_SOURCES = {
-    "bitset_persistent_kernel": ["kz_bitset.cu", "kz_rules.cuh", "kz_sweep.cuh", "kz_internal.cuh"],
-    "bitset_sweep_kernel": ["kz_bitset.cu", "kz_rules.cuh", "kz_sweep.cuh", "kz_internal.cuh"],
-    "tensor_edge_kernel": ["kz_tensor.cu", "kz_internal.cuh"],
-    "sparse_triangle_kernel": ["kz_sparse.cu", "kz_internal.cuh"],
+    "bitset_persistent_kernel": ["kz_bitset.cu", "kz_rules.cuh", "kz_sweep.cuh", "kz_state.cuh"],
+    "bitset_sweep_kernel": ["kz_bitset.cu", "kz_rules.cuh", "kz_sweep.cuh", "kz_state.cuh"],
+    "tensor_edge_kernel": ["kz_tensor.cu", "kz_state.cuh"],
+    "sparse_triangle_kernel": ["kz_sparse.cu", "kz_state.cuh"],
 }
 
 

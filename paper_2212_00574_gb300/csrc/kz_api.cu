@@ -261,18 +261,28 @@ kz_status kz_load_graph(int32_t n, int32_t k, const int32_t *colour, int64_t m,
   KZ_TRY(check_colours(n, k, colour));
   KZ_TRY(check_edges(n, colour, m, edges));
   const bool dedup = (flags & KZ_DEDUP) != 0;
+  // the caller's edges go to the device once; both builders read them there
+  int32_t *d_edges = nullptr;
+  const size_t ebytes = (size_t)m * 8;
+  auto upload = [&](kz_graph g) -> kz_status {
+    if (d_edges || m == 0) return KZ_OK;
+    d_edges = (int32_t *)dev_alloc(ebytes, g->stream);
+    if (!d_edges) return KZ_ERR_OOM;
+    return cuda_status(cudaMemcpyAsync(d_edges, edges, ebytes, cudaMemcpyHostToDevice, g->stream));
+  };
   auto pack = [&](kz_graph g) -> kz_status {
     if (m == 0) return bitset_pack_edges(g, nullptr, 0, true, g->stream);
-    int32_t *d_edges = (int32_t *)dev_alloc((size_t)m * 8, g->stream);
-    if (!d_edges) return KZ_ERR_OOM;
-    kz_status st = cuda_status(cudaMemcpyAsync(d_edges, edges, (size_t)m * 8,
-                                               cudaMemcpyHostToDevice, g->stream));
-    if (st == KZ_OK) st = bitset_pack_edges(g, d_edges, m, dedup, g->stream);
-    dev_free(d_edges, (size_t)m * 8, g->stream);
-    return st;
+    KZ_TRY(upload(g));
+    return bitset_pack_edges(g, d_edges, m, dedup, g->stream);
   };
-  auto csr = [&](kz_graph g) -> kz_status { return sparse_load(g, colour, m, edges, dedup, g->stream); };
-  return load_common(n, k, colour, stream, out, pack, csr, true);
+  auto csr = [&](kz_graph g) -> kz_status {
+    KZ_TRY(upload(g));
+    return sparse_load(g, colour, m, d_edges, dedup, g->stream);
+  };
+  const kz_status st = load_common(n, k, colour, stream, out, pack, csr, true);
+  // load_common has waited for the stream (or released the graph, which waits)
+  if (d_edges) dev_free(d_edges, ebytes, (cudaStream_t)stream);
+  return st;
 }
 
 kz_status kz_load_graph_dense(int32_t n, int32_t k, const int32_t *colour,

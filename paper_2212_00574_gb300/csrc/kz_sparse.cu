@@ -109,9 +109,9 @@ __global__ void scan_apply(const int32_t *__restrict__ in, int64_t n, const int6
   if (i == n - 1) out[n] = *total;
 }
 
-// out[0..n] = exclusive prefix of in[0..n-1] (out[n] = total).
-static kz_status exclusive_scan(const int32_t *in, int64_t n, int64_t *out, int64_t *sums,
-                                int64_t *total, cudaStream_t s) {
+// out[0..n] = exclusive prefix of in[0..n-1] (out[n] = total); sums holds
+// n / kScanBlock + 1 partial sums.
+kz_status scan_counts(const int32_t *in, int64_t n, int64_t *out, int64_t *sums, int64_t *total, cudaStream_t s) {
   if (n <= 0) return cuda_status(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
   const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
   scan_block_sums<<<(unsigned)nb, kScanBlock, 0, s>>>(in, n, sums);
@@ -328,63 +328,14 @@ static int sms_here() {
   return std::max(sms, 1);
 }
 
-// Build the CSR structures from the caller's edges (host arrays).  Edges are
-// canonicalised (u < v), sorted and checked for duplicates here.
-kz_status sparse_load(kz_graph g, const int32_t *colour, int64_t m_in, const int32_t *edges, bool dedup,
+// The CSR structures of the caller's edges (d_edges: device int32[2 m_in],
+// built on the device by sparse_build_csr, kz_csr.cu), the colours and the
+// pass scratch.
+kz_status sparse_load(kz_graph g, const int32_t *colour, int64_t m_in, const int32_t *d_edges, bool dedup,
                       cudaStream_t s) {
   const int32_t n = g->n;
-  std::vector<uint64_t> key((size_t)m_in);
-  for (int64_t e = 0; e < m_in; e++) {
-    uint32_t u = (uint32_t)edges[2 * e], v = (uint32_t)edges[2 * e + 1];
-    if (u > v) std::swap(u, v);
-    key[e] = ((uint64_t)u << 32) | v;
-  }
-  std::sort(key.begin(), key.end());
-  size_t m = 0;
-  for (size_t i = 0; i < key.size(); i++) {
-    if (i > 0 && key[i] == key[i - 1]) {
-      if (!dedup) return KZ_ERR_DUPLICATE_EDGE;
-      continue;
-    }
-    key[m++] = key[i];
-  }
-  key.resize(m);
-  g->m = (int64_t)m;
-  // CSR with rows sorted by neighbour: row u = lower neighbours (ascending),
-  // then higher neighbours (ascending).
-  std::vector<int64_t> row((size_t)n + 1, 0);
-  for (size_t e = 0; e < m; e++) {
-    row[(key[e] >> 32) + 1]++;
-    row[(key[e] & 0xffffffffu) + 1]++;
-  }
-  for (int32_t v = 0; v < n; v++) row[v + 1] += row[v];
-  std::vector<int64_t> fill(row.begin(), row.end() - 1);
-  std::vector<int32_t> adj(2 * m), eid(2 * m), eu(m), ev(m);
-  for (size_t e = 0; e < m; e++) {  // lower neighbours: scanning edges sorted by (u, v) fills row v in u order
-    const int32_t u = (int32_t)(key[e] >> 32), v = (int32_t)(key[e] & 0xffffffffu);
-    eu[e] = u;
-    ev[e] = v;
-    adj[fill[v]] = u;
-    eid[fill[v]++] = (int32_t)e;
-  }
-  for (size_t e = 0; e < m; e++) {  // higher neighbours, in v order
-    const int32_t u = eu[e], v = ev[e];
-    adj[fill[u]] = v;
-    eid[fill[u]++] = (int32_t)e;
-  }
-  // orientation rank: degree order, ties by id
-  std::vector<int32_t> order((size_t)n), rank((size_t)n);
-  for (int32_t v = 0; v < n; v++) order[v] = v;
-  std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-    const int64_t da = row[a + 1] - row[a], db = row[b + 1] - row[b];
-    return da != db ? da < db : a < b;
-  });
-  for (int32_t i = 0; i < n; i++) rank[order[i]] = i;
-
-  const size_t nn = (size_t)std::max(n, 1), mm = std::max<size_t>(m, 1);
-  KZ_TRY(graph_alloc(g, &g->sp_row0, nn + 1, s));
-  KZ_TRY(graph_alloc(g, &g->sp_adj0, 2 * mm, s));
-  KZ_TRY(graph_alloc(g, &g->sp_eid0, 2 * mm, s));
+  KZ_TRY(sparse_build_csr(g, d_edges, m_in, dedup, s));
+  const size_t nn = (size_t)std::max(n, 1), mm = (size_t)std::max<int64_t>(g->m, 1);
   for (int i = 0; i < 2; i++) {
     KZ_TRY(graph_alloc(g, &g->sp_row[i], nn + 1, s));
     KZ_TRY(graph_alloc(g, &g->sp_adj[i], 2 * mm, s));
@@ -396,10 +347,7 @@ kz_status sparse_load(kz_graph g, const int32_t *colour, int64_t m_in, const int
   KZ_TRY(graph_alloc(g, &g->sp_oadj, mm, s));
   KZ_TRY(graph_alloc(g, &g->sp_oeid, mm, s));
   KZ_TRY(graph_alloc(g, &g->sp_osrc, mm, s));
-  KZ_TRY(graph_alloc(g, &g->sp_eu, mm, s));
-  KZ_TRY(graph_alloc(g, &g->sp_ev, mm, s));
   KZ_TRY(graph_alloc(g, &g->sp_col, nn, s));
-  KZ_TRY(graph_alloc(g, &g->sp_rank, nn, s));
   KZ_TRY(graph_alloc(g, &g->sp_mask, mm, s));
   KZ_TRY(graph_alloc(g, &g->sp_cnt_live, nn, s));
   KZ_TRY(graph_alloc(g, &g->sp_cnt_or, nn, s));
@@ -410,20 +358,8 @@ kz_status sparse_load(kz_graph g, const int32_t *colour, int64_t m_in, const int
     KZ_TRY(graph_alloc(g, &g->st, 1, s));
     KZ_CUDA_TRY(cudaMemsetAsync(g->st, 0, sizeof(DevState), s));
   }
-  KZ_CUDA_TRY(cudaMemcpyAsync(g->sp_row0, row.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
-  if (m) {
-    KZ_CUDA_TRY(cudaMemcpyAsync(g->sp_adj0, adj.data(), sizeof(int32_t) * 2 * m, cudaMemcpyHostToDevice, s));
-    KZ_CUDA_TRY(cudaMemcpyAsync(g->sp_eid0, eid.data(), sizeof(int32_t) * 2 * m, cudaMemcpyHostToDevice, s));
-    KZ_CUDA_TRY(cudaMemcpyAsync(g->sp_eu, eu.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
-    KZ_CUDA_TRY(cudaMemcpyAsync(g->sp_ev, ev.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
-  }
-  if (n) {
-    KZ_CUDA_TRY(cudaMemcpyAsync(g->sp_col, colour, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
-    KZ_CUDA_TRY(cudaMemcpyAsync(g->sp_rank, rank.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
-  }
+  if (n) KZ_TRY(h2d(g->sp_col, colour, sizeof(int32_t) * n, s));
   g->has_csr = true;
-  // the host vectors die here: wait for the copies
-  KZ_CUDA_TRY(cudaStreamSynchronize(s));
   return sparse_reset(g, s);
 }
 
@@ -460,8 +396,8 @@ kz_status sparse_orient_live(kz_graph g, cudaStream_t s) {
   a.m = g->m;
   const int grid = 8 * sms_here(), threads = 256;
   sparse_count_kernel<<<grid, threads, 0, s>>>(a, g->sp_cnt_live, g->sp_cnt_or);
-  KZ_TRY(exclusive_scan(g->sp_cnt_live, g->n, g->sp_row[nx], g->sp_sums, g->sp_totals, s));
-  KZ_TRY(exclusive_scan(g->sp_cnt_or, g->n, g->sp_orow, g->sp_sums, g->sp_totals + 1, s));
+  KZ_TRY(scan_counts(g->sp_cnt_live, g->n, g->sp_row[nx], g->sp_sums, g->sp_totals, s));
+  KZ_TRY(scan_counts(g->sp_cnt_or, g->n, g->sp_orow, g->sp_sums, g->sp_totals + 1, s));
   sparse_fill_kernel<<<grid, threads, 0, s>>>(a, g->sp_row[nx], g->sp_adj[nx], g->sp_eid[nx], g->sp_orow,
                                               g->sp_oadj, g->sp_oeid, g->sp_osrc);
   return cuda_status(cudaGetLastError());
@@ -490,8 +426,8 @@ kz_status sparse_kernelize(kz_graph g, const kz_options &opt, cudaStream_t s) {
     a.m = g->m;
     // 1. compaction of the live rows and the oriented CSR of the live edges
     sparse_count_kernel<<<grid, threads, 0, s>>>(a, g->sp_cnt_live, g->sp_cnt_or);
-    KZ_TRY(exclusive_scan(g->sp_cnt_live, g->n, g->sp_row[nx], g->sp_sums, g->sp_totals, s));
-    KZ_TRY(exclusive_scan(g->sp_cnt_or, g->n, g->sp_orow, g->sp_sums, g->sp_totals + 1, s));
+    KZ_TRY(scan_counts(g->sp_cnt_live, g->n, g->sp_row[nx], g->sp_sums, g->sp_totals, s));
+    KZ_TRY(scan_counts(g->sp_cnt_or, g->n, g->sp_orow, g->sp_sums, g->sp_totals + 1, s));
     sparse_fill_kernel<<<grid, threads, 0, s>>>(a, g->sp_row[nx], g->sp_adj[nx], g->sp_eid[nx], g->sp_orow,
                                                 g->sp_oadj, g->sp_oeid, g->sp_osrc);
     // the compacted rows are this pass's snapshot

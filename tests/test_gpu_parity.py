@@ -238,6 +238,38 @@ def test_duplicates():
     assert np.array_equal(alive, orc["vlive"]) and np.array_equal(edges, g.edges[orc["elive"].astype(bool)])
 
 
+@pytest.mark.parametrize("path", ["sparse", "auto"])
+def test_device_csr_shapes(path):
+    """The CSR is sorted and deduplicated on the device: edge lists given in
+    both orientations and shuffled, with repeats (KZ_DEDUP), many isolated
+    vertices (more vertices than edges: the rank sort is longer than the edge
+    sort) and a hub of high degree, against the oracle on the sparse path."""
+    rng = np.random.default_rng(77)
+    n, k = 5000, 7
+    colour = rng.integers(0, k, size=n).astype(np.int32)
+    hub = 0
+    others = np.nonzero(colour != colour[hub])[0][:1500]
+    e = [np.stack([np.full(len(others), hub), others], 1)]
+    a, b = rng.integers(0, 600, size=4000), rng.integers(0, 600, size=4000)
+    ok = (a != b) & (colour[a] != colour[b])
+    e.append(np.stack([a[ok], b[ok]], 1))
+    edges = np.concatenate(e).astype(np.int32)
+    canon = np.unique(np.sort(edges, axis=1), axis=0)
+    shuffled = edges[rng.permutation(len(edges))]
+    flip = rng.random(len(shuffled)) < 0.5
+    shuffled[flip] = shuffled[flip][:, ::-1]
+    with_repeats = np.concatenate([shuffled, shuffled[:300]])
+    with kz.KernelGraph(n, k, colour, edges=with_repeats, flags=kz.KZ_DEDUP) as kg:
+        kg.kernelize(path=path)
+        alive, kept, st = kg.fetch()
+    assert st["m"] == len(canon)
+    orc = oracle.fixpoint(colour, canon, k)
+    assert np.array_equal(alive, orc["vlive"]) and np.array_equal(kept, canon[orc["elive"].astype(bool)])
+    with pytest.raises(kz.KzError) as ei:
+        kz.kz_load_graph(n, k, colour, with_repeats)
+    assert ei.value.status == kz.KZ_ERR_DUPLICATE_EDGE
+
+
 def test_dense_illegal_colouring_found_on_device():
     colour = np.array([0, 1, 1], np.int32)
     bits = synth.edges_to_bits(3, np.array([[0, 1], [1, 2]]))
