@@ -474,7 +474,8 @@ def learned_comparison(kz, torch, graphs, stream, flush, local, args, pg, rank):
                         "loss_last": losses[-1], "seconds": round(train_s, 2),
                         "graphs": "24 cascading k-partite graphs (n log-uniform 256..32768, k 8..32, p = sqrt(mu k / n) with mu 3..9), other seeds"}}
     try:
-        arms = (("plain", "plain", None), ("learned", "learned", 0.5), ("frontier", "learned", 0.0))
+        arms = (("plain", "plain", None), ("learned", "learned", 0.5), ("frontier", "learned", 0.0),
+                ("support", "support", None))
         for name, g, h in graphs:
             res = {}
             for label, sched, thr in arms:
@@ -493,6 +494,7 @@ def learned_comparison(kz, torch, graphs, stream, flush, local, args, pg, rank):
             out[name] = {"time_to_fixpoint_ms": {a: res[a]["ms"] for a in labels},
                          "speedup": p["ms"] / lr["ms"],
                          "speedup_frontier_only": p["ms"] / res["frontier"]["ms"],
+                         "speedup_support": p["ms"] / res["support"]["ms"],
                          "plain_path": {v: k for k, v in kz.PATHS.items()}.get(p["st"]["path"]),
                          "sweeps": {a: res[a]["st"]["sweeps"] for a in labels},
                          "passes": {a: res[a]["st"]["passes"] for a in labels},

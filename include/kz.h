@@ -85,12 +85,17 @@ typedef enum {
 typedef enum {
     KZ_SCHED_PLAIN = 0,   /* Jacobi sweeps over every live element */
     KZ_SCHED_LEARNED = 1, /* MLP-ranked worklist, then a full certifying sweep */
-    KZ_SCHED_SUPPORT = 2  /* the same Jacobi sweeps on the CSR state (graphs loaded from an edge
-                             list; path AUTO or SPARSE), with per-class common-neighbour counts
-                             kept up to date as triangles break: a sweep re-tests only elements
-                             whose counts fell.  Sweeps and per-sweep deletions equal PLAIN's;
-                             edge_tests counts the tests made.  Needs about 4 m k bytes
-                             (KZ_ERR_UNSUPPORTED above 6 GiB) */
+    KZ_SCHED_SUPPORT = 2  /* the same Jacobi sweeps, re-testing only what the last sweep's
+                             deletions can have broken.  On the CSR state (graphs loaded from an
+                             edge list; path AUTO or SPARSE): per-class common-neighbour counts
+                             kept up to date as triangles break; needs about 4 m k bytes
+                             (KZ_ERR_UNSUPPORTED above 6 GiB).  On the bitset rows (graphs
+                             without a CSR, or path BITSET or TENSOR): a full first sweep on that
+                             path, then each sweep re-checks, for every edge {a, b} the last one
+                             deleted and every common neighbour w, the pairs {a, w} and {b, w} in
+                             the class of the neighbour they lost.  Either way the sweeps and
+                             per-sweep deletions equal PLAIN's; edge_tests counts the tests made
+                             (distinct pairs re-checked per sweep) */
 } kz_schedule;
 
 /* First test of a pair in the BITSET path's sweep kernels (kz_options.plane0).

@@ -412,13 +412,24 @@ kz_status kz_kernelize(kz_graph g, const kz_options *opt, void *stream) {
     return KZ_OK;
   }
   if (o.schedule == KZ_SCHED_SUPPORT) {
-    // incremental support counts on the CSR state
-    if (!g->has_csr) return KZ_ERR_UNSUPPORTED;
-    if (o.path != KZ_PATH_AUTO && o.path != KZ_PATH_SPARSE) return KZ_ERR_UNSUPPORTED;
-    KZ_TRY(state_to_sparse(g, g->stream));
-    KZ_TRY(sparse_kernelize_support(g, o, g->stream));
+    if (g->has_csr && (o.path == KZ_PATH_AUTO || o.path == KZ_PATH_SPARSE)) {
+      // incremental support counts on the CSR state
+      KZ_TRY(state_to_sparse(g, g->stream));
+      KZ_TRY(sparse_kernelize_support(g, o, g->stream));
+      g->kernelized = true;
+      g->path_ran = KZ_PATH_SPARSE;
+      return KZ_OK;
+    }
+    // re-check sweeps on the bitset rows, the first sweep on the path AUTO
+    // would take (the bitset sweep or the tensor form)
+    if (!g->has_bitset) return KZ_ERR_UNSUPPORTED;
+    if (o.path != KZ_PATH_AUTO && o.path != KZ_PATH_BITSET && o.path != KZ_PATH_TENSOR) return KZ_ERR_UNSUPPORTED;
+    const int full = o.path == KZ_PATH_AUTO ? (tensor_preferred(g) ? KZ_PATH_TENSOR : KZ_PATH_BITSET) : o.path;
+    KZ_TRY(state_to_bitset(g, g->stream));
+    g->ab_synced = false;
+    KZ_TRY(recheck_kernelize(g, o, full, g->stream));
     g->kernelized = true;
-    g->path_ran = KZ_PATH_SPARSE;
+    g->path_ran = full;
     return KZ_OK;
   }
   const int path = o.path == KZ_PATH_AUTO ? auto_path(g) : o.path;

@@ -220,6 +220,9 @@ void dominance_release(kz_graph g);
 
 // Learned schedule (kz_learned.cu).
 kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cudaStream_t s);
+// Schedule SUPPORT on the bitset rows: a full first sweep, then sweeps that
+// re-check only the (pair, class) combinations the last one touched.
+kz_status recheck_kernelize(kz_graph g, const kz_options &opt, int full_path, cudaStream_t s);
 void learned_release(kz_graph g);
 
 // Whole-fixpoint-in-one-CTA kernel (kz_cta.cu).

@@ -756,9 +756,10 @@ __global__ void test_edges_kernel(RowView r, const int2 *__restrict__ work, cons
 }
 
 // Removes the failing edges and the failing vertices (with all their edges)
-// in place.
+// in place, recording each failing vertex's sweep.
 __global__ void apply_kernel(RowView r, const uint8_t *__restrict__ vfail, const int2 *__restrict__ dead,
-                             const unsigned long long *__restrict__ n_dead) {
+                             const unsigned long long *__restrict__ n_dead, int32_t *__restrict__ v_sweep,
+                             const DevState *st) {
   const int lane = threadIdx.x & 31;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -786,7 +787,112 @@ __global__ void apply_kernel(RowView r, const uint8_t *__restrict__ vfail, const
       }
       row[w] = 0u;
     }
-    if (lane == 0) atomicAnd(&r.V[(ix >> 5) * r.k + cx], ~(1u << (ix & 31)));
+    if (lane == 0) {
+      atomicAnd(&r.V[(ix >> 5) * r.k + cx], ~(1u << (ix & 31)));
+      if (v_sweep) v_sweep[x] = (int32_t)(st->sweeps + 1);  // the productive sweep this round becomes
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// dense support rounds (schedule SUPPORT on the bitset rows)
+// ---------------------------------------------------------------------------
+
+// Re-check of one pair {x, y} in class c on the current rows: is it still
+// live, and does it keep a common neighbour in c (class c's words of both
+// rows, eight planes at a time, stopping at the first step with one)?  A pair with none fails
+// and is listed once (failed bitset, pending-set layout).  Returns 1 when the
+// pair is re-checked for the first time this round (checked bitset).
+__device__ __forceinline__ unsigned int recheck_pair(const RowView &r, int x, int y, int c,
+                                                     uint32_t *__restrict__ failed, int2 *__restrict__ out,
+                                                     unsigned long long *n_out, int64_t cap,
+                                                     uint32_t *__restrict__ checked) {
+  const int cy = r.col[y], iy = y - r.coff[cy];
+  const uint32_t *rx = r.A + (int64_t)x * r.ldw;
+  if (!((rx[(iy >> 5) * r.k + cy] >> (iy & 31)) & 1u)) return 0u;  // no longer an edge
+  int64_t pw;
+  uint32_t pb;
+  pend_bit(r, x, y, pw, pb);
+  const unsigned int first = (atomicOr(&checked[pw], pb) & pb) ? 0u : 1u;
+  const uint32_t *ry = r.A + (int64_t)y * r.ldw;
+  // eight planes a step, their loads independent of each other
+  for (int rr = 0; rr < r.R; rr += 8) {
+    uint32_t any = 0u;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      const int w = (rr + j) * r.k + c;
+      if (rr + j < r.R) any |= rx[w] & ry[w];
+    }
+    if (any) return first;
+  }
+  if (!(atomicOr(&failed[pw], pb) & pb)) {
+    const unsigned long long pos = atomicAdd(n_out, 1ull);
+    if ((int64_t)pos < cap) out[pos] = make_int2(min(x, y), max(x, y));
+  }
+  return first;
+}
+
+// One sweep of the dense support schedule (over the deleted edges q0 .. q1 -
+// 1 of the list).  The edges the previous sweep deleted are the only cause
+// of new failures: deleting {a, b} takes the
+// common neighbour b (class col b) from every pair {a, w} and a (class col a)
+// from every {b, w}, w in N(a) and N(b) in the rows before that sweep
+// (rold).  One warp per deleted edge walks those w (four row words a lane)
+// and re-checks each (pair, class) on the current rows (rnew); every edge
+// that fails the edge rule on the current graph is found this way, since it
+// passed before the previous sweep.  A failing vertex's edges all fail the
+// edge rule too (no common neighbour can have the colour it lost), so the
+// listed edges are the sweep's whole edge deletion.
+__global__ void recheck_kernel(RowView rold, RowView rnew, const int2 *__restrict__ dead,
+                               const unsigned long long *__restrict__ n_dead, int64_t q0, int64_t q1, int64_t cap,
+                               uint32_t *__restrict__ failed, int2 *__restrict__ out, unsigned long long *n_out,
+                               uint32_t *__restrict__ checked, unsigned long long *n_checked) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = min(min((int64_t)*n_dead, cap), q1);
+  const int rk = rold.R * rold.k;
+  unsigned int first = 0;
+  for (int64_t q = q0 + warp0; q < total; q += warps) {
+    const int2 e = dead[q];
+    const int ca = rold.col[e.x], cb = rold.col[e.y];
+    const uint32_t *ra = rold.A + (int64_t)e.x * rold.ldw, *rb = rold.A + (int64_t)e.y * rold.ldw;
+    for (int w = 4 * lane; w < rk; w += 128) {
+      const uint4 a = *reinterpret_cast<const uint4 *>(ra + w);
+      const uint4 b = *reinterpret_cast<const uint4 *>(rb + w);
+      const uint32_t both[4] = {a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w};
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        uint32_t m = both[j];
+        if (!m) continue;  // also every zero padding word past rk
+        const int c = (w + j) % rold.k, rr = (w + j) / rold.k;
+        while (m) {
+          const int bit = __ffs(m) - 1;
+          m &= m - 1;
+          const int y = rold.coff[c] + 32 * rr + bit;
+          first += recheck_pair(rnew, e.x, y, cb, failed, out, n_out, cap, checked);
+          first += recheck_pair(rnew, e.y, y, ca, failed, out, n_out, cap, checked);
+        }
+      }
+    }
+  }
+  first = __reduce_add_sync(0xffffffffu, first);
+  if (lane == 0 && first) atomicAdd(n_checked, (unsigned long long)first);
+}
+
+// Closes a dense support sweep: the counts, the trace, and the flip to the
+// buffer that now holds the state.  Nothing deleted: one unproductive pass.
+__global__ void recheck_finish_kernel(DevState *st, const unsigned long long *dv, const unsigned long long *de,
+                                      const unsigned long long *tests) {
+  st->passes += 1;
+  st->tests += (int64_t)*tests;
+  if (*dv + *de > 0) {
+    if (st->sweeps < kTraceCap) {
+      st->trace_dv[st->sweeps] = (int64_t)*dv;
+      st->trace_de[st->sweeps] = (int64_t)*de;
+    }
+    st->sweeps += 1;
+    st->cur ^= 1;
   }
 }
 
@@ -1206,7 +1312,7 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cu
       KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 7, 0, sizeof(unsigned long long), s));
       dirty_valid = false;
     }
-    apply_kernel<<<grid, 256, 0, s>>>(r, b.s.vfail, b.dead, b.cnt + 2);
+    apply_kernel<<<grid, 256, 0, s>>>(r, b.s.vfail, b.dead, b.cnt + 2, g->v_sweep, g->st);
     learned_finish_kernel<<<1, 1, 0, s>>>(g->st, b.cnt + 3, b.cnt + 2, b.cnt + 1, nullptr);
     KZ_CUDA_TRY(cudaGetLastError());
     round++;
@@ -1218,6 +1324,134 @@ kz_status learned_kernelize(kz_graph g, const kz_options &opt, int full_path, cu
         need_full = true;
       }
     }
+  }
+}
+
+// Dense support schedule: the first sweep is a full pass (the bitset sweep
+// or the tensor form); every later sweep either re-checks only the (pair,
+// class) combinations the previous sweep's deletions touched
+// (recheck_kernel, with the vertex rule on the current rows) or, when that
+// would cost more, is a full pass.  Both compute the same Jacobi sweep, so
+// the sweeps and their deletions are the plain method's; a re-check sweep
+// that finds nothing proves the fixpoint.  The choice compares the measured
+// time of a full pass with the measured re-check time per deleted edge
+// (timed first on a sample of kRecheckSample deleted edges, whose work is
+// kept when the rest follows).  The two ping-pong buffers hold the rows
+// before and after a sweep.
+constexpr int64_t kRecheckSample = 1 << 15;
+constexpr double kRecheckGain = 0.8;
+
+kz_status recheck_kernelize(kz_graph g, const kz_options &opt, int full_path, cudaStream_t s) {
+  if (!g->learned_bufs) {
+    LearnedBufs *b = new LearnedBufs();
+    kz_status st = ensure_bufs(g, *b, s);
+    if (st != KZ_OK) {
+      delete b;
+      return st;
+    }
+    g->learned_bufs = b;
+  }
+  LearnedBufs &b = *static_cast<LearnedBufs *>(g->learned_bufs);
+  const int64_t max_sweeps = opt.max_sweeps > 0 ? opt.max_sweeps : (int64_t)g->n + g->m + 1;
+  const int grid = 8 * sms_now();
+  KZ_TRY(bitset_begin_run(g, max_sweeps, s));
+  if (g->n == 0) return KZ_OK;
+  const int64_t cap = std::max<int64_t>(g->m, 1);
+  const size_t set_bytes = (size_t)g->n * g->ldw * 4;
+  const size_t row_bytes = (size_t)g->n * g->ldw * 4, v_bytes = (size_t)g->ldw * 4;
+  unsigned long long h[kCounters];
+  int64_t sweeps = 0;
+  auto read_counts = [&]() -> kz_status {
+    KZ_CUDA_TRY(cudaMemcpyAsync(h, b.cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
+    KZ_CUDA_TRY(cudaMemcpyAsync(&sweeps, &g->st->sweeps, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    KZ_CUDA_TRY(cudaStreamSynchronize(s));
+    return KZ_OK;
+  };
+  RunEvents ev;
+  KZ_CUDA_TRY(cudaEventCreate(&ev.a));
+  KZ_CUDA_TRY(cudaEventCreate(&ev.b));
+  double full_ms = -1.0, per_dead_ms = -1.0;
+  int cur = 0;
+  int2 *dead = b.dead, *fresh = b.work;
+  // a full pass, timed; then its deletions listed from the two buffers
+  auto full_sweep = [&](int *cont) -> kz_status {
+    KZ_CUDA_TRY(cudaEventRecord(ev.a, s));
+    KZ_TRY(full_path == KZ_PATH_TENSOR ? tensor_one_pass(g, opt, s, cont) : bitset_one_pass(g, s, cont));
+    KZ_CUDA_TRY(cudaEventRecord(ev.b, s));
+    KZ_CUDA_TRY(cudaEventSynchronize(ev.b));
+    const double ms = ev.ms();
+    if (ms > 0.0) full_ms = ms;
+    if (!*cont) return KZ_OK;
+    cur = read_cur(g, s);
+    KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 2, 0, sizeof(unsigned long long), s));
+    diff_dead_kernel<<<grid, 256, 0, s>>>(view_of(g, b, cur ^ 1), g->A[cur & 1], dead, b.cnt + 2, cap);
+    KZ_CUDA_TRY(cudaGetLastError());
+    return KZ_OK;
+  };
+  int cont = 0;
+  KZ_TRY(full_sweep(&cont));
+  if (!cont) return KZ_OK;  // nothing deleted (or the sweep limit)
+  for (;;) {
+    // [0] failures found [1] pairs re-checked [2] deleted by the last sweep [3] failing vertices
+    KZ_TRY(read_counts());
+    const int64_t n_dead = (int64_t)std::min<unsigned long long>(h[2], (unsigned long long)cap);
+    const RowView rnew = view_of(g, b, cur), rold = view_of(g, b, cur ^ 1);
+    auto recheck = [&](int64_t q0, int64_t q1) -> kz_status {
+      KZ_CUDA_TRY(cudaEventRecord(ev.a, s));
+      recheck_kernel<<<grid, 256, 0, s>>>(rold, rnew, dead, b.cnt + 2, q0, q1, cap, b.pend, fresh, b.cnt + 0,
+                                          b.dirty, b.cnt + 1);
+      KZ_CUDA_TRY(cudaGetLastError());
+      KZ_CUDA_TRY(cudaEventRecord(ev.b, s));
+      KZ_CUDA_TRY(cudaEventSynchronize(ev.b));
+      const double ms = ev.ms();
+      if (ms > 0.0 && q1 - q0 >= 4096) per_dead_ms = ms / (double)(q1 - q0);
+      return KZ_OK;
+    };
+    KZ_CUDA_TRY(cudaMemsetAsync(b.pend, 0, set_bytes, s));
+    KZ_CUDA_TRY(cudaMemsetAsync(b.dirty, 0, set_bytes, s));
+    KZ_CUDA_TRY(cudaMemsetAsync(b.cnt, 0, sizeof(unsigned long long) * 2, s));
+    KZ_CUDA_TRY(cudaMemsetAsync(b.cnt + 3, 0, sizeof(unsigned long long), s));
+    bool by_recheck = true;
+    int64_t done = 0;
+    if (full_ms > 0.0) {
+      if (per_dead_ms < 0.0 && n_dead > kRecheckSample) {
+        KZ_TRY(recheck(0, kRecheckSample));
+        done = kRecheckSample;
+      }
+      if (per_dead_ms > 0.0 && (double)(n_dead - done) * per_dead_ms > kRecheckGain * full_ms) by_recheck = false;
+    }
+    if (!by_recheck) {
+      // this sweep as a full pass (what a sample re-checked is dropped); the
+      // pass applies the sweep limit itself
+      KZ_TRY(full_sweep(&cont));
+      if (!cont) return KZ_OK;
+      continue;
+    }
+    if (done < n_dead) KZ_TRY(recheck(done, n_dead));
+    stats_kernel<<<grid, 256, 0, s>>>(rnew, b.s, 0, b.cnt + 3);
+    KZ_CUDA_TRY(cudaGetLastError());
+    KZ_TRY(read_counts());
+    const unsigned long long de = std::min<unsigned long long>(h[0], (unsigned long long)cap), dv = h[3];
+    if (de + dv > 0 && sweeps >= max_sweeps) {
+      int32_t lim = KZ_ERR_LIMIT;
+      KZ_CUDA_TRY(cudaMemcpyAsync(&g->st->status, &lim, 4, cudaMemcpyHostToDevice, s));
+      KZ_CUDA_TRY(cudaStreamSynchronize(s));
+      return KZ_OK;
+    }
+    if (de + dv > 0) {
+      // the next state in the other buffer: a copy of the current rows with
+      // this sweep's deletions applied
+      KZ_CUDA_TRY(cudaMemcpyAsync(g->A[(cur & 1) ^ 1], g->A[cur & 1], row_bytes, cudaMemcpyDeviceToDevice, s));
+      KZ_CUDA_TRY(cudaMemcpyAsync(g->V[(cur & 1) ^ 1], g->V[cur & 1], v_bytes, cudaMemcpyDeviceToDevice, s));
+      apply_kernel<<<grid, 256, 0, s>>>(view_of(g, b, cur ^ 1), b.s.vfail, fresh, b.cnt + 0, g->v_sweep, g->st);
+      KZ_CUDA_TRY(cudaGetLastError());
+    }
+    recheck_finish_kernel<<<1, 1, 0, s>>>(g->st, b.cnt + 3, b.cnt + 0, b.cnt + 1);
+    KZ_CUDA_TRY(cudaGetLastError());
+    if (de + dv == 0) return KZ_OK;  // the fixpoint: the last sweep broke nothing
+    cur ^= 1;
+    std::swap(dead, fresh);
+    KZ_CUDA_TRY(cudaMemcpyAsync(b.cnt + 2, b.cnt + 0, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
   }
 }
 

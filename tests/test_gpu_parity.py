@@ -710,6 +710,54 @@ def test_support_schedule_limit_rerun_and_switch():
         kg.kernelize(schedule="support")
         alive, got, st = kg.fetch()
         assert np.array_equal(alive, orc["vlive"]) and np.array_equal(got, edges[orc["elive"].astype(bool)])
-    with kz.KernelGraph.from_synth(g, dense=True) as kg:   # no CSR state: refused
+    with kz.KernelGraph.from_synth(g, dense=True) as kg:   # no CSR state: the bitset rows' re-check sweeps
+        kg.kernelize(schedule="support")
+        alive, got, st = kg.fetch()
+        assert np.array_equal(alive, orc["vlive"]) and np.array_equal(got, edges[orc["elive"].astype(bool)])
+        assert st["sweeps"] == orc["sweeps"] and st["passes"] == orc["passes"]
+    with kz.KernelGraph.from_synth(g) as kg:
         with pytest.raises(kz.KzError):
-            kg.kernelize(schedule="support")
+            kg.kernelize(schedule="support", path="small")
+
+
+# ---------------------------------------------------------------------------
+# schedule SUPPORT on the bitset rows (re-check sweeps)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("path", ["bitset", "tensor", "dense-auto"])
+def test_dense_support_matches_jacobi(path):
+    """The re-check sweeps are the oracle's Jacobi sweeps: same survivors,
+    sweeps, per-sweep deletions and vertex deletion sweeps, no more tests."""
+    seen = 0
+    cases = [synth.tiny_random(900 + s, 400, 6, 0.06 + 0.01 * (s % 5), planted=bool(s % 2)) for s in range(6)]
+    cases += [synth.kpartite(1500, 12, 0.3, seed=3), synth.kpartite(2100, 20, 0.45, seed=4),
+              _two_density_graph(7, 1200, 12, 10, 0.95, 0.05)]
+    for g in cases:
+        if path == "dense-auto":
+            res = gpu_run(g, dense=True, schedule="support")
+        else:
+            res = gpu_run(g, schedule="support", path=path)
+        orc = assert_support_parity(g, res)
+        seen = max(seen, orc["sweeps"])
+    assert seen >= 3
+
+
+def test_dense_support_limits_and_continuation():
+    g = synth.kpartite(1800, 12, 0.2, seed=11)
+    edges = g.get_edges()
+    orc = oracle.fixpoint(g.colour, edges, g.k)
+    assert orc["sweeps"] >= 3
+    with kz.KernelGraph.from_synth(g, dense=True) as kg:
+        for s in range(1, orc["sweeps"] + 2):   # one sweep per call, continued on the handle
+            kg.kernelize(schedule="support", max_sweeps=1)
+            alive, got, st = kg.fetch(allow=(kz.KZ_OK, kz.KZ_ERR_LIMIT))
+            want = oracle.fixpoint(g.colour, edges, g.k, max_sweeps=s, raise_on_limit=False)
+            assert np.array_equal(alive, want["vlive"]) and np.array_equal(got, edges[want["elive"].astype(bool)])
+        kg.reset()
+        kg.kernelize(schedule="support", max_sweeps=2)
+        alive, got, st = kg.fetch(allow=(kz.KZ_ERR_LIMIT,))
+        want = oracle.fixpoint(g.colour, edges, g.k, max_sweeps=2, raise_on_limit=False)
+        assert st["sweeps"] == 2 and np.array_equal(got, edges[want["elive"].astype(bool)])
+        kg.kernelize()                            # plain sweeps finish from there
+        alive, got, st = kg.fetch()
+        assert np.array_equal(alive, orc["vlive"]) and np.array_equal(got, edges[orc["elive"].astype(bool)])
