@@ -798,30 +798,44 @@ __global__ void apply_kernel(RowView r, const uint8_t *__restrict__ vfail, const
 // dense support rounds (schedule SUPPORT on the bitset rows)
 // ---------------------------------------------------------------------------
 
-// Re-check of one pair {x, y} in class c on the current rows: is it still
-// live, and does it keep a common neighbour in c (class c's words of both
-// rows, eight planes at a time, stopping at the first step with one)?  A pair with none fails
-// and is listed once (failed bitset, pending-set layout).  Returns 1 when the
-// pair is re-checked for the first time this round (checked bitset).
-__device__ __forceinline__ unsigned int recheck_pair(const RowView &r, int x, int y, int c,
-                                                     uint32_t *__restrict__ failed, int2 *__restrict__ out,
-                                                     unsigned long long *n_out, int64_t cap,
+// Class-major copy of the rows: row x's words of class c (planes 0 .. R - 1,
+// zero-padded to Rp, a multiple of four) at x * k * Rp + c * Rp, so that a
+// class's words are contiguous for the re-checks.
+__global__ void class_major_kernel(const uint32_t *__restrict__ A, int32_t n, int32_t k, int32_t R, int32_t ldw,
+                                   int32_t Rp, uint32_t *__restrict__ cm) {
+  const int64_t row = (int64_t)k * Rp;
+  const int64_t total = (int64_t)n * row;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = t / row;
+    const int q = (int)(t - x * row), c = q / Rp, rr = q - c * Rp;
+    cm[t] = rr < R ? A[x * ldw + (int64_t)rr * k + c] : 0u;
+  }
+}
+
+// Re-check of one live pair {x, y} in class c on the current rows: does it
+// keep a common neighbour in c (class c's words of both rows from the
+// class-major copy, eight at a time in 16-byte loads, stopping at the first
+// step with one)?  A pair with none fails and is listed once
+// (failed bitset, pending-set layout).  Returns 1 when the pair is
+// re-checked for the first time this round (checked bitset).
+__device__ __forceinline__ unsigned int recheck_pair(const RowView &r, const uint32_t *__restrict__ cm, int Rp,
+                                                     int x, int y, int c, uint32_t *__restrict__ failed,
+                                                     int2 *__restrict__ out, unsigned long long *n_out, int64_t cap,
                                                      uint32_t *__restrict__ checked) {
-  const int cy = r.col[y], iy = y - r.coff[cy];
-  const uint32_t *rx = r.A + (int64_t)x * r.ldw;
-  if (!((rx[(iy >> 5) * r.k + cy] >> (iy & 31)) & 1u)) return 0u;  // no longer an edge
   int64_t pw;
   uint32_t pb;
   pend_bit(r, x, y, pw, pb);
   const unsigned int first = (atomicOr(&checked[pw], pb) & pb) ? 0u : 1u;
-  const uint32_t *ry = r.A + (int64_t)y * r.ldw;
-  // eight planes a step, their loads independent of each other
-  for (int rr = 0; rr < r.R; rr += 8) {
-    uint32_t any = 0u;
-#pragma unroll
-    for (int j = 0; j < 8; j++) {
-      const int w = (rr + j) * r.k + c;
-      if (rr + j < r.R) any |= rx[w] & ry[w];
+  const int64_t cmw = (int64_t)r.k * Rp;
+  const uint4 *px = reinterpret_cast<const uint4 *>(cm + x * cmw + (int64_t)c * Rp);
+  const uint4 *py = reinterpret_cast<const uint4 *>(cm + y * cmw + (int64_t)c * Rp);
+  const int quads = Rp >> 2;
+  for (int q = 0; q < quads; q += 2) {
+    const uint4 a0 = px[q], b0 = py[q];
+    uint32_t any = (a0.x & b0.x) | (a0.y & b0.y) | (a0.z & b0.z) | (a0.w & b0.w);
+    if (q + 1 < quads) {
+      const uint4 a1 = px[q + 1], b1 = py[q + 1];
+      any |= (a1.x & b1.x) | (a1.y & b1.y) | (a1.z & b1.z) | (a1.w & b1.w);
     }
     if (any) return first;
   }
@@ -838,12 +852,14 @@ __device__ __forceinline__ unsigned int recheck_pair(const RowView &r, int x, in
 // common neighbour b (class col b) from every pair {a, w} and a (class col a)
 // from every {b, w}, w in N(a) and N(b) in the rows before that sweep
 // (rold).  One warp per deleted edge walks those w (four row words a lane)
-// and re-checks each (pair, class) on the current rows (rnew); every edge
+// and re-checks each (pair, class) on the current rows (rnew, and their
+// class-major copy cm); every edge
 // that fails the edge rule on the current graph is found this way, since it
 // passed before the previous sweep.  A failing vertex's edges all fail the
 // edge rule too (no common neighbour can have the colour it lost), so the
 // listed edges are the sweep's whole edge deletion.
-__global__ void recheck_kernel(RowView rold, RowView rnew, const int2 *__restrict__ dead,
+__global__ void recheck_kernel(RowView rold, RowView rnew, const uint32_t *__restrict__ cm, int32_t Rp,
+                               const int2 *__restrict__ dead,
                                const unsigned long long *__restrict__ n_dead, int64_t q0, int64_t q1, int64_t cap,
                                uint32_t *__restrict__ failed, int2 *__restrict__ out, unsigned long long *n_out,
                                uint32_t *__restrict__ checked, unsigned long long *n_checked) {
@@ -857,10 +873,16 @@ __global__ void recheck_kernel(RowView rold, RowView rnew, const int2 *__restric
     const int2 e = dead[q];
     const int ca = rold.col[e.x], cb = rold.col[e.y];
     const uint32_t *ra = rold.A + (int64_t)e.x * rold.ldw, *rb = rold.A + (int64_t)e.y * rold.ldw;
+    const uint32_t *na = rnew.A + (int64_t)e.x * rnew.ldw, *nb = rnew.A + (int64_t)e.y * rnew.ldw;
     for (int w = 4 * lane; w < rk; w += 128) {
       const uint4 a = *reinterpret_cast<const uint4 *>(ra + w);
       const uint4 b = *reinterpret_cast<const uint4 *>(rb + w);
       const uint32_t both[4] = {a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w};
+      if (!(both[0] | both[1] | both[2] | both[3])) continue;
+      // the same words of the current rows: which pairs {a, w}, {b, w} are live
+      const uint4 a2 = *reinterpret_cast<const uint4 *>(na + w);
+      const uint4 b2 = *reinterpret_cast<const uint4 *>(nb + w);
+      const uint32_t live_a[4] = {a2.x, a2.y, a2.z, a2.w}, live_b[4] = {b2.x, b2.y, b2.z, b2.w};
 #pragma unroll
       for (int j = 0; j < 4; j++) {
         uint32_t m = both[j];
@@ -870,8 +892,8 @@ __global__ void recheck_kernel(RowView rold, RowView rnew, const int2 *__restric
           const int bit = __ffs(m) - 1;
           m &= m - 1;
           const int y = rold.coff[c] + 32 * rr + bit;
-          first += recheck_pair(rnew, e.x, y, cb, failed, out, n_out, cap, checked);
-          first += recheck_pair(rnew, e.y, y, ca, failed, out, n_out, cap, checked);
+          if ((live_a[j] >> bit) & 1u) first += recheck_pair(rnew, cm, Rp, e.x, y, cb, failed, out, n_out, cap, checked);
+          if ((live_b[j] >> bit) & 1u) first += recheck_pair(rnew, cm, Rp, e.y, y, ca, failed, out, n_out, cap, checked);
         }
       }
     }
@@ -1001,6 +1023,7 @@ struct LearnedBufs {
   int2 *fr = nullptr, *work = nullptr, *dead = nullptr;
   uint32_t *pend = nullptr;   // pending edges (bitset rows, pair kept in the smaller id's row)
   uint32_t *dirty = nullptr;  // dirty edges: may have started failing (same layout)
+  uint32_t *cm = nullptr;     // class-major copy of the current rows (support re-checks), on first use
   // [0] frontier [1] work [2] dead [3] dv [4] edges2 [5] verts [6] pending
   // [7] dirty [8] last full pass's dv [9] its de
   unsigned long long *cnt = nullptr;
@@ -1367,6 +1390,8 @@ kz_status recheck_kernelize(kz_graph g, const kz_options &opt, int full_path, cu
     KZ_CUDA_TRY(cudaStreamSynchronize(s));
     return KZ_OK;
   };
+  const int32_t Rp = (g->R + 3) / 4 * 4;
+  if (!b.cm) KZ_TRY(graph_alloc(g, &b.cm, (size_t)std::max(g->n, 1) * g->k * Rp, s));
   RunEvents ev;
   KZ_CUDA_TRY(cudaEventCreate(&ev.a));
   KZ_CUDA_TRY(cudaEventCreate(&ev.b));
@@ -1396,10 +1421,15 @@ kz_status recheck_kernelize(kz_graph g, const kz_options &opt, int full_path, cu
     KZ_TRY(read_counts());
     const int64_t n_dead = (int64_t)std::min<unsigned long long>(h[2], (unsigned long long)cap);
     const RowView rnew = view_of(g, b, cur), rold = view_of(g, b, cur ^ 1);
+    bool cm_built = false;
     auto recheck = [&](int64_t q0, int64_t q1) -> kz_status {
       KZ_CUDA_TRY(cudaEventRecord(ev.a, s));
-      recheck_kernel<<<grid, 256, 0, s>>>(rold, rnew, dead, b.cnt + 2, q0, q1, cap, b.pend, fresh, b.cnt + 0,
-                                          b.dirty, b.cnt + 1);
+      if (!cm_built) {
+        class_major_kernel<<<grid, 256, 0, s>>>(rnew.A, g->n, g->k, g->R, g->ldw, Rp, b.cm);
+        cm_built = true;
+      }
+      recheck_kernel<<<grid, 256, 0, s>>>(rold, rnew, b.cm, Rp, dead, b.cnt + 2, q0, q1, cap, b.pend, fresh,
+                                          b.cnt + 0, b.dirty, b.cnt + 1);
       KZ_CUDA_TRY(cudaGetLastError());
       KZ_CUDA_TRY(cudaEventRecord(ev.b, s));
       KZ_CUDA_TRY(cudaEventSynchronize(ev.b));
