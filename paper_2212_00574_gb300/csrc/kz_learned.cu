@@ -1,6 +1,8 @@
 // kz_learned.cu -- the learned schedule (include/kz_learned.h): an edge-
 // scoring MLP with hand-written forward / backward / Adam kernels, a trace
-// collector for its training data, and the worklist schedule that uses it.
+// collector for its training data, and the worklist schedule that uses it;
+// and, sharing its row views and buffers, the support schedule's re-check
+// sweeps on the bitset rows (recheck_kernelize).
 //
 // The schedule never changes the kernel (thesis Section 4.2 rules): every
 // deletion it makes is of an element that fails its rule on the current
