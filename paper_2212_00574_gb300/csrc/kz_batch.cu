@@ -124,7 +124,7 @@ __device__ __noinline__ void batch_item(const GraphView &G, const WorkItem wi, i
 }
 
 template <int KMAX>
-__global__ void __launch_bounds__(kBatchWarps * 32, 3) batch_group_kernel(BatchArgs p) {
+__global__ void __launch_bounds__(kBatchWarps * 32, 4) batch_group_kernel(BatchArgs p) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ int s_entry;
   __shared__ int s_go;
