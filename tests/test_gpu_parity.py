@@ -198,6 +198,29 @@ def test_dense_load_fetch_round_trip(n, k, classes):
     assert np.array_equal(bits, _pack_bool_rows(full, row_words))
 
 
+def test_dense_load_beyond_the_tile_packer():
+    """A dense input of more than 49,152 vertices takes the packer's row form
+    (its column words no longer fit in shared memory); sparse enough that the
+    oracle runs in seconds."""
+    rng = np.random.default_rng(50)
+    n, k = 50200, 8
+    colour = rng.integers(0, k, size=n).astype(np.int32)
+    a, b = rng.integers(0, n, size=300000), rng.integers(0, n, size=300000)
+    ok = (a != b) & (colour[a] != colour[b])
+    edges = np.unique(np.sort(np.stack([a[ok], b[ok]], 1), axis=1), axis=0).astype(np.int32)
+    bits = synth.edges_to_bits(n, edges)
+    orc = oracle.fixpoint(colour, edges, k)
+    h = kz.kz_load_graph_dense(n, k, colour, bits)
+    try:
+        kz.kz_kernelize(h)
+        alive, kept, st = kz.kz_fetch_kernel(h, n)
+        assert st["m"] == len(edges)
+    finally:
+        kz.kz_free_graph(h)
+    assert np.array_equal(alive, orc["vlive"]) and np.array_equal(kept, edges[orc["elive"].astype(bool)])
+    assert st["sweeps"] == orc["sweeps"]
+
+
 def test_reset_and_rerun():
     g = synth.tiny_random(8, 250, 6, 0.1, planted=True)
     with kz.KernelGraph.from_synth(g) as kg:
