@@ -12,7 +12,7 @@
 // Round structure of a learned kernelization (bitset rows):
 //   1. full passes (the multi-CTA sweep or the tensor form) while the
 //      cascade is heavy: as long as the last pass deleted so many edges that
-//      the frontier they leave would exceed an eighth of the live edges;
+//      the frontier they leave would cost more to test than a full pass;
 //   2. learned rounds: per-vertex statistics of the live graph (degree,
 //      colour cover, per-class counts; the vertex rule falls out of them);
 //      the frontier = the edges that may have started to fail.  After edge
@@ -28,8 +28,8 @@
 //      they are few (the score kernel keeps their count, so a large set
 //      costs no flush), else a full pass certifies; if it deletes something,
 //      learned rounds resume.
-// Every list larger than an eighth of the live edges gives way to a full
-// pass, which tests every edge for less.
+// A list that would cost more to test than a full pass (both timed during
+// the run) gives way to the full pass.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
