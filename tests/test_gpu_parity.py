@@ -765,6 +765,14 @@ def test_dense_support_matches_jacobi(path):
     assert seen >= 3
 
 
+def test_dense_support_tiny_cases():
+    """Every tiny case (n from 1, k from 1 to 64, all densities) on the bitset
+    rows' re-check sweeps, against the oracle's Jacobi sweeps."""
+    for (i, n, k, p, planted) in _tiny_cases():
+        g = synth.tiny_random(i, n, k, p, planted=planted)
+        assert_support_parity(g, gpu_run(g, dense=True, schedule="support"))
+
+
 def test_dense_support_limits_and_continuation():
     g = synth.kpartite(1800, 12, 0.2, seed=11)
     edges = g.get_edges()
