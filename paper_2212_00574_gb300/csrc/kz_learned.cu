@@ -848,6 +848,13 @@ __device__ __forceinline__ unsigned int recheck_pair(const RowView &r, const uin
   return first;
 }
 
+// Resident CTAs of the re-check kernel per SM: it waits on scattered loads,
+// so it is capped at 40 registers for six CTAs (48 warps) an SM, and its
+// grid-strided launch is exactly that many CTAs.  (Measured on the C5-size
+// cascade: 71 ms to the fixpoint at three CTAs an SM, 60 ms at six, 70 ms at
+// eight, where 32 registers spill.)
+constexpr int kRecheckCtasPerSm = 6;
+
 // One sweep of the dense support schedule (over the deleted edges q0 .. q1 -
 // 1 of the list).  The edges the previous sweep deleted are the only cause
 // of new failures: deleting {a, b} takes the
@@ -860,7 +867,7 @@ __device__ __forceinline__ unsigned int recheck_pair(const RowView &r, const uin
 // passed before the previous sweep.  A failing vertex's edges all fail the
 // edge rule too (no common neighbour can have the colour it lost), so the
 // listed edges are the sweep's whole edge deletion.
-__global__ void recheck_kernel(RowView rold, RowView rnew, const uint32_t *__restrict__ cm, int32_t Rp,
+__global__ void __launch_bounds__(256, kRecheckCtasPerSm) recheck_kernel(RowView rold, RowView rnew, const uint32_t *__restrict__ cm, int32_t Rp,
                                const int2 *__restrict__ dead,
                                const unsigned long long *__restrict__ n_dead, int64_t q0, int64_t q1, int64_t cap,
                                uint32_t *__restrict__ failed, int2 *__restrict__ out, unsigned long long *n_out,
@@ -1430,8 +1437,9 @@ kz_status recheck_kernelize(kz_graph g, const kz_options &opt, int full_path, cu
         class_major_kernel<<<grid, 256, 0, s>>>(rnew.A, g->n, g->k, g->R, g->ldw, Rp, b.cm);
         cm_built = true;
       }
-      recheck_kernel<<<grid, 256, 0, s>>>(rold, rnew, b.cm, Rp, dead, b.cnt + 2, q0, q1, cap, b.pend, fresh,
-                                          b.cnt + 0, b.dirty, b.cnt + 1);
+      recheck_kernel<<<kRecheckCtasPerSm * sms_now(), 256, 0, s>>>(rold, rnew, b.cm, Rp, dead, b.cnt + 2, q0, q1,
+                                                                    cap, b.pend, fresh, b.cnt + 0, b.dirty,
+                                                                    b.cnt + 1);
       KZ_CUDA_TRY(cudaGetLastError());
       KZ_CUDA_TRY(cudaEventRecord(ev.b, s));
       KZ_CUDA_TRY(cudaEventSynchronize(ev.b));
