@@ -765,6 +765,23 @@ def test_dense_support_matches_jacobi(path):
     assert seen >= 3
 
 
+def test_dense_support_refusals():
+    """The re-check sweeps follow the thesis's thresholds only and run on their
+    own: a clique size below the colour count, dominance rounds and the in-CTA
+    path are refused, and the handle stays usable."""
+    g = synth.kpartite(600, 8, 0.4, seed=21)
+    edges = g.get_edges()
+    orc = oracle.fixpoint(g.colour, edges, g.k)
+    with kz.KernelGraph.from_synth(g, dense=True) as kg:
+        for opts in ({"clique_k": g.k - 1}, {"dominance": 1}, {"path": "small"}, {"path": "sparse"}):
+            with pytest.raises(kz.KzError) as ei:
+                kg.kernelize(schedule="support", **opts)
+            assert ei.value.status in (kz.KZ_ERR_UNSUPPORTED, kz.KZ_ERR_ARG), (opts, ei.value.status)
+        kg.kernelize(schedule="support")
+        alive, kept, st = kg.fetch()
+    assert np.array_equal(alive, orc["vlive"]) and np.array_equal(kept, edges[orc["elive"].astype(bool)])
+
+
 def test_dense_support_tiny_cases():
     """Every tiny case (n from 1, k from 1 to 64, all densities) on the bitset
     rows' re-check sweeps, against the oracle's Jacobi sweeps."""
